@@ -1,0 +1,187 @@
+/*
+ * panel.h -- C ABI of the batched 2D panel solver for NVIDIA GB300 (sm_103a).
+ *
+ * The library evaluates a batch of airfoils with the constant-strength vortex,
+ * stream-function panel method of Section 2 of Einkemmer, "Evaluation of the
+ * Intel Xeon Phi 7120 and NVIDIA K80 as Accelerators for Two-Dimensional Panel
+ * Codes" (arXiv 1511.02166):
+ *
+ *   panel_assemble  dense influence matrix (panel integral F_i of Section 2,
+ *                   collocation at x_{j+1/2}), the C column, the Kutta row
+ *                   gamma_0 + gamma_{n-1} = 0 and the right-hand side
+ *                   phi_v(x_{j+1/2}) = v_inf (y cos a - x sin a);
+ *   panel_solve     LU with partial pivoting and triangular solves (Section 3
+ *                   names LU as the solver), with iterative refinement in the
+ *                   mixed-precision mode;
+ *   panel_forces    Cp at the control points and the lift coefficient
+ *                   (Section 2, Figure 2 report C_L);
+ *   panel_adjoint   dCl/d(node coordinates) by a transposed solve with the
+ *                   stored LU and a contraction with dM/dx (the method has no
+ *                   gradient in the paper; the formulas are the chain rule of
+ *                   the same panel integral).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Batch layout.  Airfoil b has n_b = node_offsets[b+1] - node_offsets[b] >= 3
+ *   distinct nodes x_0..x_{n_b-1} (counter-clockwise, x_0 at the trailing edge;
+ *   the closing node x_{n_b} = x_0 is implied, Section 2 / Figure 1), stored as
+ *   nodes[2*(node_offsets[b] + k) + {0,1}] (float64 x, y).  The bordered system
+ *   has m_b = n_b + 1 unknowns u = (gamma_0..gamma_{n_b-1}, C).
+ *   Vectors of length m_b are packed at vec offset node_offsets[b] + b.
+ *   Matrices are m_b x m_b row-major at element offset mat_offsets[b], where
+ *   mat_offsets is the exclusive prefix sum of m_b^2 (panel_plan fills it).
+ * Memory.  Every pointer argument of the compute entry points is DEVICE memory
+ *   owned by the caller (e.g. allocated by torch); the library allocates
+ *   nothing, never synchronises the stream and launches only on `stream`
+ *   (a cudaStream_t; NULL means the legacy default stream).
+ * Errors.  The return value is a call-level status (panel_status): argument
+ *   errors are detected on the host before anything is launched; a launch
+ *   failure returns PANEL_ECUDA.  Per-airfoil problems are written to info[b]
+ *   on the device: 0 ok; k > 0 the k-th pivot of the LU was exactly zero;
+ *   -1 fewer than 3 nodes; -2 clockwise or zero signed area; -3 a zero-length
+ *   panel; -4 a non-finite coordinate; -5 refinement did not converge within
+ *   max_iter (mixed mode; the last iterate is still written); -6 n_b larger
+ *   than the n_max passed to the call (nothing is written for that airfoil).
+ * Precision modes (flags).
+ *   PANEL_FP64   plain path: FP64 assembly (native log/atan2), FP64 LU with
+ *                partial pivoting, FP64 triangular solves, no refinement.
+ *   PANEL_MIXED  GB300 path: the matrix is assembled in double-float (pairs of
+ *                FP32, about 48 significant bits) into two FP32 planes
+ *                A = A_hi + A_lo; the LU factor is FP32 (of A_hi, with the C
+ *                column and Kutta row rescaled); the solution is refined with
+ *                double-float residuals b - (A_hi + A_lo) u until
+ *                |du|_inf <= tol |u|_inf.  u and all reported outputs are FP64.
+ */
+#ifndef PANEL_H
+#define PANEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PANEL_OK = 0,
+  PANEL_EINVAL = 1,   /* bad argument: size, NULL pointer, flag combination  */
+  PANEL_ENOTSUP = 2,  /* size beyond what the library supports (n_b > PANEL_N_MAX) */
+  PANEL_ECUDA = 3     /* a CUDA launch or device query failed                 */
+} panel_status;
+
+#define PANEL_FP64 0x1
+#define PANEL_MIXED 0x2
+/* panel_solve: also solve the transposed system M^T lambda = dCl/du for unit
+ * upstream gradient (used later by panel_adjoint), sharing the residual passes. */
+#define PANEL_WITH_ADJOINT 0x10
+
+/* Largest panel count per airfoil the library accepts. */
+#define PANEL_N_MAX 2048
+
+/* Per-airfoil status codes written to info[b]. */
+#define PANEL_INFO_FEW_NODES (-1)
+#define PANEL_INFO_ORIENTATION (-2)
+#define PANEL_INFO_ZERO_PANEL (-3)
+#define PANEL_INFO_NONFINITE (-4)
+#define PANEL_INFO_NOCONV (-5)
+#define PANEL_INFO_TOO_LARGE (-6) /* n_b exceeds the n_max given to the call */
+
+/*
+ * panel_plan (HOST memory only, no GPU work).
+ * From host node_offsets[B+1] compute mat_offsets[B+1] (exclusive prefix sum
+ * of (n_b+1)^2), order[B] (airfoil indices by decreasing n_b, ties by index:
+ * the launch order of the persistent kernels) and *n_max.  Returns PANEL_EINVAL
+ * for B < 0, decreasing offsets or NULL pointers, PANEL_ENOTSUP if some
+ * n_b > PANEL_N_MAX.  Airfoils with n_b < 3 are accepted here and flagged in
+ * info[b] by panel_assemble.
+ */
+int panel_plan(int B, const int64_t* node_offsets, int64_t* mat_offsets, int32_t* order,
+               int32_t* n_max);
+
+/*
+ * panel_assemble -- Section 2: influence matrix, C column, Kutta row, rhs.
+ *   nodes [sum n_b][2] f64, node_offsets [B+1] i64, mat_offsets [B+1] i64,
+ *   order [B] i32 (from panel_plan), alpha [B] f64 (radians),
+ *   vinf [B] f64 or NULL (1.0).
+ *   PANEL_FP64:  A64 [sum m_b^2] f64 receives M; A_hi/A_lo must be NULL.
+ *   PANEL_MIXED: A_hi, A_lo [sum m_b^2] f32 receive M = A_hi + A_lo;
+ *                A64 may be NULL.
+ *   rhs [sum m_b] f64 receives b (b_n = 0 for the Kutta row);
+ *   info [B] i32 receives 0 or a geometry code (the matrix of a rejected
+ *   airfoil is left unwritten).
+ */
+int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                   const int64_t* mat_offsets, const int32_t* order, const double* alpha,
+                   const double* vinf, double* A64, float* A_hi, float* A_lo, double* rhs,
+                   int32_t* info, void* stream);
+
+/*
+ * panel_solve -- LU with partial pivoting and solve (Section 3), refined in
+ * PANEL_MIXED mode.
+ *   PANEL_FP64:  reads A64; LU [sum m_b^2] f64 receives the factors (L unit
+ *                lower, U upper, row-major, in one array); no refinement.
+ *   PANEL_MIXED: reads A_hi, A_lo; LU [sum m_b^2] f32 receives the FP32
+ *                factors of the rescaled matrix (may be NULL when
+ *                PANEL_WITH_ADJOINT is set and no later panel_adjoint call
+ *                needs them).
+ *   piv [sum m_b] i32 receives the pivot rows (LAPACK style, 0-based).
+ *   rhs [sum m_b] f64; u [sum m_b] f64 receives (gamma, C).
+ *   lambda [sum m_b] f64 or NULL: with PANEL_WITH_ADJOINT receives the
+ *   solution of M^T lambda = g, g_i = 2 |h_i| / (v_inf c) (i < n_b), g_n = 0,
+ *   i.e. dCl/du for unit upstream gradient; needs nodes, vinf and chord.
+ *   max_iter >= 0 refinement steps at most, tol > 0 stopping threshold on
+ *   |du|_inf / |u|_inf (ignored by PANEL_FP64).
+ *   info [B] i32: airfoils with info[b] != 0 on entry are skipped; on exit
+ *   k > 0 for a zero pivot, PANEL_INFO_NOCONV if not converged.
+ *   iters [B] i32 or NULL receives the refinement steps taken.
+ */
+int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                const int64_t* mat_offsets, const int32_t* order, const double* A64,
+                const float* A_hi, const float* A_lo, void* LU, int32_t* piv,
+                const double* rhs, const double* vinf, const double* chord, double* u,
+                double* lambda, int max_iter, double tol, int32_t* info, int32_t* iters,
+                void* stream);
+
+/*
+ * panel_forces -- Cp_j = 1 - (gamma_j / v_inf)^2 at the control points,
+ * Cl = 2 sum_i gamma_i |h_i| / (v_inf c) (Kutta-Joukowski), and the
+ * pressure-integrated Cl_p, Cd_p with outward normals (h_y, -h_x)/|h|.
+ *   u [sum m_b] f64 from panel_solve; alpha [B] f64; vinf, chord [B] f64 or
+ *   NULL (1.0); cp [sum n_b] f64; cl [B] f64; cl_p, cd_p [B] f64 or NULL.
+ *   Airfoils with info[b] != 0 get NaN outputs (info may be NULL).
+ *   FP64 throughout (warp-shuffle reductions).
+ */
+int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const double* u,
+                 const double* alpha, const double* vinf, const double* chord,
+                 const int32_t* info, double* cp, double* cl, double* cl_p, double* cd_p,
+                 void* stream);
+
+/*
+ * panel_adjoint -- grad_nodes = grad_cl[b] * dCl/d(nodes of airfoil b).
+ *   dCl/dx_k = dCl/dx_k|_u + lambda^T (db/dx_k - (dM/dx_k) u),  M^T lambda = dCl/du.
+ *   If lambda_in is non-NULL it holds lambda from panel_solve(PANEL_WITH_ADJOINT);
+ *   otherwise lambda is solved here from LU/piv (and refined against the
+ *   matrix in PANEL_MIXED mode) into lambda_out (required then, [sum m_b] f64).
+ *   The contraction re-evaluates the panel-integral derivatives per pair
+ *   (two per pair: with respect to the control point and to the panel end).
+ *   grad_cl [B] f64 upstream gradient; grad_nodes [sum n_b][2] f64 output.
+ *   Skips airfoils with info[b] != 0 (their gradient is set to NaN).
+ */
+int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                  const int64_t* mat_offsets, const int32_t* order, const double* A64,
+                  const float* A_hi, const float* A_lo, const void* LU, const int32_t* piv,
+                  const double* u, const double* lambda_in, double* lambda_out,
+                  const double* alpha, const double* vinf, const double* chord,
+                  const double* grad_cl, double* grad_nodes, int max_iter, double tol,
+                  const int32_t* info, void* stream);
+
+/* Human-readable name of a panel_status value (static string). */
+const char* panel_strerror(int status);
+
+/* Library version string. */
+const char* panel_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PANEL_H */

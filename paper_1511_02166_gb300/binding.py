@@ -1,0 +1,154 @@
+"""Thin ctypes binding of the C ABI in include/panel.h.
+
+Argument marshalling only: torch CUDA tensors become device pointers, the
+current torch stream becomes the cudaStream_t, numpy arrays become host
+pointers for ``panel_plan``.  Every step of the computation runs in the CUDA
+library; if the library cannot be loaded, the call raises (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PANEL_OK, PANEL_EINVAL, PANEL_ENOTSUP, PANEL_ECUDA = 0, 1, 2, 3
+PANEL_FP64 = 0x1
+PANEL_MIXED = 0x2
+PANEL_WITH_ADJOINT = 0x10
+PANEL_N_MAX = 2048
+
+INFO_FEW_NODES = -1
+INFO_ORIENTATION = -2
+INFO_ZERO_PANEL = -3
+INFO_NONFINITE = -4
+INFO_NOCONV = -5
+INFO_TOO_LARGE = -6
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+#: symbol -> (restype, argtypes); mirrors include/panel.h
+SIGNATURES = {
+    "panel_plan": (_I, [_I, _P, _P, _P, _P]),
+    "panel_assemble": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "panel_solve": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                         _I, _D, _P, _P, _P]),
+    "panel_forces": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "panel_adjoint": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                           _P, _P, _P, _I, _D, _P, _P]),
+    "panel_strerror": (ctypes.c_char_p, [_I]),
+    "panel_version": (ctypes.c_char_p, []),
+}
+
+
+class PanelError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpanel.so (building it first if needed); raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise PanelError("libpanel.so is missing: run paper_1511_02166_gb300.build")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(status: int, what: str):
+    if status != PANEL_OK:
+        msg = load().panel_strerror(status).decode()
+        raise PanelError("%s failed: %s (%d)" % (what, msg, status))
+
+
+def panel_plan(node_offsets: np.ndarray):
+    """Host plan: (mat_offsets[B+1] i64, order[B] i32, n_max)."""
+    node_offsets = np.ascontiguousarray(node_offsets, dtype=np.int64)
+    B = len(node_offsets) - 1
+    mat = np.zeros(B + 1, dtype=np.int64)
+    order = np.zeros(max(B, 1), dtype=np.int32)
+    nmax = np.zeros(1, dtype=np.int32)
+    _check(load().panel_plan(B, _ptr(node_offsets), _ptr(mat), _ptr(order), _ptr(nmax)),
+           "panel_plan")
+    return mat, order[:B], int(nmax[0])
+
+
+def panel_assemble(B, n_max, flags, nodes, node_offsets, mat_offsets, order, alpha, vinf,
+                   A64, A_hi, A_lo, rhs, info, stream=None):
+    _check(load().panel_assemble(B, n_max, flags, _ptr(nodes), _ptr(node_offsets),
+                                 _ptr(mat_offsets), _ptr(order), _ptr(alpha), _ptr(vinf),
+                                 _ptr(A64), _ptr(A_hi), _ptr(A_lo), _ptr(rhs), _ptr(info),
+                                 _stream(stream)), "panel_assemble")
+
+
+def panel_solve(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64, A_hi, A_lo,
+                LU, piv, rhs, vinf, chord, u, lam, max_iter, tol, info, iters, stream=None):
+    _check(load().panel_solve(B, n_max, flags, _ptr(nodes), _ptr(node_offsets),
+                              _ptr(mat_offsets), _ptr(order), _ptr(A64), _ptr(A_hi), _ptr(A_lo),
+                              _ptr(LU), _ptr(piv), _ptr(rhs), _ptr(vinf), _ptr(chord), _ptr(u),
+                              _ptr(lam), int(max_iter), float(tol), _ptr(info), _ptr(iters),
+                              _stream(stream)), "panel_solve")
+
+
+def panel_forces(B, nodes, node_offsets, u, alpha, vinf, chord, info, cp, cl, cl_p, cd_p,
+                 stream=None):
+    _check(load().panel_forces(B, _ptr(nodes), _ptr(node_offsets), _ptr(u), _ptr(alpha),
+                               _ptr(vinf), _ptr(chord), _ptr(info), _ptr(cp), _ptr(cl),
+                               _ptr(cl_p), _ptr(cd_p), _stream(stream)), "panel_forces")
+
+
+def panel_adjoint(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64, A_hi, A_lo,
+                  LU, piv, u, lambda_in, lambda_out, alpha, vinf, chord, grad_cl, grad_nodes,
+                  max_iter, tol, info, stream=None):
+    _check(load().panel_adjoint(B, n_max, flags, _ptr(nodes), _ptr(node_offsets),
+                                _ptr(mat_offsets), _ptr(order), _ptr(A64), _ptr(A_hi),
+                                _ptr(A_lo), _ptr(LU), _ptr(piv), _ptr(u), _ptr(lambda_in),
+                                _ptr(lambda_out), _ptr(alpha), _ptr(vinf), _ptr(chord),
+                                _ptr(grad_cl), _ptr(grad_nodes), int(max_iter), float(tol),
+                                _ptr(info), _stream(stream)), "panel_adjoint")
+
+
+def panel_strerror(status: int) -> str:
+    return load().panel_strerror(int(status)).decode()
+
+
+def panel_version() -> str:
+    return load().panel_version().decode()

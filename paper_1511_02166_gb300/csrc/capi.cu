@@ -1,0 +1,166 @@
+// capi.cu -- the extern "C" entry points declared in include/panel.h.
+//
+// Host-side argument validation, then stream-ordered kernel launches.  No
+// allocation, no synchronisation.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "panel_common.cuh"
+
+namespace panel {
+cudaError_t launch_assemble_f64(const Batch&, const double*, const double*, double*, double*,
+                                int32_t*, cudaStream_t);
+cudaError_t launch_solve_f64(const Batch&, const double*, double*, int32_t*, const double*,
+                             const double*, const double*, double*, double*, int32_t*, int32_t*,
+                             cudaStream_t);
+cudaError_t launch_adjoint_f64(const Batch&, const double*, const int32_t*, const double*,
+                               const double*, double*, const double*, const double*,
+                               const double*, const double*, double*, const int32_t*,
+                               cudaStream_t);
+cudaError_t launch_forces(const Batch&, const double*, const double*, const double*,
+                          const double*, const int32_t*, double*, double*, double*, double*,
+                          cudaStream_t);
+}  // namespace panel
+
+using panel::Batch;
+
+namespace {
+
+int mode_of(int flags) {
+  const int m = flags & (PANEL_FP64 | PANEL_MIXED);
+  if (m == PANEL_FP64 || m == PANEL_MIXED) return m;
+  return 0;
+}
+
+bool flags_ok(int flags) {
+  return mode_of(flags) != 0 && (flags & ~(PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT)) == 0;
+}
+
+Batch make_batch(int B, int n_max, const double* nodes, const int64_t* node_offsets,
+                 const int64_t* mat_offsets, const int32_t* order) {
+  Batch b;
+  b.B = B;
+  b.n_max = n_max;
+  b.nodes = nodes;
+  b.node_off = node_offsets;
+  b.mat_off = mat_offsets;
+  b.order = order;
+  return b;
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? PANEL_OK : PANEL_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+const char* panel_strerror(int status) {
+  switch (status) {
+    case PANEL_OK: return "ok";
+    case PANEL_EINVAL: return "invalid argument";
+    case PANEL_ENOTSUP: return "size or mode not supported";
+    case PANEL_ECUDA: return "CUDA launch failed";
+    default: return "unknown panel status";
+  }
+}
+
+const char* panel_version(void) { return "panel-gb300 0.1 (sm_103a)"; }
+
+int panel_plan(int B, const int64_t* node_offsets, int64_t* mat_offsets, int32_t* order,
+               int32_t* n_max) {
+  if (B < 0 || !node_offsets || !mat_offsets || !order || !n_max) return PANEL_EINVAL;
+  int64_t nm = 0;
+  mat_offsets[0] = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t n = node_offsets[b + 1] - node_offsets[b];
+    if (n < 0) return PANEL_EINVAL;
+    if (n > PANEL_N_MAX) return PANEL_ENOTSUP;
+    nm = std::max(nm, n);
+    mat_offsets[b + 1] = mat_offsets[b] + (n + 1) * (n + 1);
+  }
+  std::vector<int32_t> idx(B);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t c) {
+    return (node_offsets[a + 1] - node_offsets[a]) > (node_offsets[c + 1] - node_offsets[c]);
+  });
+  std::copy(idx.begin(), idx.end(), order);
+  *n_max = (int32_t)std::max<int64_t>(nm, 3);
+  return PANEL_OK;
+}
+
+int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                   const int64_t* mat_offsets, const int32_t* order, const double* alpha,
+                   const double* vinf, double* A64, float* A_hi, float* A_lo, double* rhs,
+                   int32_t* info, void* stream) {
+  if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || !flags_ok(flags)) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !mat_offsets || !order || !alpha || !rhs || !info)
+    return PANEL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch bt = make_batch(B, n_max, nodes, node_offsets, mat_offsets, order);
+  if (mode_of(flags) == PANEL_FP64) {
+    if (!A64 || A_hi || A_lo) return PANEL_EINVAL;
+    return status_of(panel::launch_assemble_f64(bt, alpha, vinf, A64, rhs, info, s));
+  }
+  return PANEL_ENOTSUP;
+}
+
+int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                const int64_t* mat_offsets, const int32_t* order, const double* A64,
+                const float* A_hi, const float* A_lo, void* LU, int32_t* piv,
+                const double* rhs, const double* vinf, const double* chord, double* u,
+                double* lambda, int max_iter, double tol, int32_t* info, int32_t* iters,
+                void* stream) {
+  if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || !flags_ok(flags)) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!node_offsets || !mat_offsets || !order || !piv || !rhs || !u || !info) return PANEL_EINVAL;
+  const bool adj = (flags & PANEL_WITH_ADJOINT) != 0;
+  if (adj && (!lambda || !nodes)) return PANEL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch bt = make_batch(B, n_max, nodes, node_offsets, mat_offsets, order);
+  if (mode_of(flags) == PANEL_FP64) {
+    if (!A64 || !LU) return PANEL_EINVAL;
+    return status_of(panel::launch_solve_f64(bt, A64, (double*)LU, piv, rhs, vinf, chord, u,
+                                             adj ? lambda : nullptr, info, iters, s));
+  }
+  (void)A_hi; (void)A_lo; (void)max_iter; (void)tol;
+  return PANEL_ENOTSUP;
+}
+
+int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const double* u,
+                 const double* alpha, const double* vinf, const double* chord,
+                 const int32_t* info, double* cp, double* cl, double* cl_p, double* cd_p,
+                 void* stream) {
+  if (B < 0) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !u || !alpha || !cp || !cl) return PANEL_EINVAL;
+  Batch bt = make_batch(B, 0, nodes, node_offsets, nullptr, nullptr);
+  return status_of(panel::launch_forces(bt, u, alpha, vinf, chord, info, cp, cl, cl_p, cd_p,
+                                        (cudaStream_t)stream));
+}
+
+int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                  const int64_t* mat_offsets, const int32_t* order, const double* A64,
+                  const float* A_hi, const float* A_lo, const void* LU, const int32_t* piv,
+                  const double* u, const double* lambda_in, double* lambda_out,
+                  const double* alpha, const double* vinf, const double* chord,
+                  const double* grad_cl, double* grad_nodes, int max_iter, double tol,
+                  const int32_t* info, void* stream) {
+  if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || !flags_ok(flags)) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !mat_offsets || !order || !u || !alpha || !grad_nodes)
+    return PANEL_EINVAL;
+  if (!lambda_in && (!lambda_out || !LU || !piv)) return PANEL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch bt = make_batch(B, n_max, nodes, node_offsets, mat_offsets, order);
+  if (mode_of(flags) == PANEL_FP64) {
+    return status_of(panel::launch_adjoint_f64(bt, (const double*)LU, piv, u, lambda_in,
+                                               lambda_out, alpha, vinf, chord, grad_cl,
+                                               grad_nodes, info, s));
+  }
+  (void)A64; (void)A_hi; (void)A_lo; (void)max_iter; (void)tol;
+  return PANEL_ENOTSUP;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// panel_common.cuh -- device helpers shared by the panel-method kernels.
+//
+// Geometry conventions follow Section 2 of the paper: airfoil b has n nodes
+// x_0..x_{n-1} (x_0 at the trailing edge, counter-clockwise), the closing node
+// x_n = x_0 is implied, panel i runs from x_i to x_{i+1}, and the control
+// point of panel j is x_{j+1/2} = (x_j + x_{j+1}) / 2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/panel.h"
+
+namespace panel {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
+
+// Launch-side view of a batch.  All pointers are device memory.
+struct Batch {
+  int B;
+  int n_max;
+  const double* nodes;         // [sum n][2]
+  const int64_t* node_off;     // [B+1]
+  const int64_t* mat_off;      // [B+1]
+  const int32_t* order;        // [B]
+};
+
+__device__ __forceinline__ int airfoil_n(const Batch& bt, int b) {
+  return (int)(bt.node_off[b + 1] - bt.node_off[b]);
+}
+__device__ __forceinline__ int64_t vec_off(const Batch& bt, int b) { return bt.node_off[b] + b; }
+
+// Warp-wide sums.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of one double; `scratch` holds >= 32 doubles.  All threads
+// of the block must call it; every thread gets the result.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide max of a non-negative double (same contract as block_sum).
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? scratch[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_max(t);
+  if (threadIdx.x == 0) scratch[0] = t;
+  __syncthreads();
+  double r = scratch[0];
+  __syncthreads();
+  return r;
+}
+
+// Geometry validation of one airfoil (Section 2 node conventions), by one
+// block.  Loads the nodes into xs/ys (shared, >= n entries each) and returns
+// 0 or a PANEL_INFO_* code, identical in every thread.
+__device__ __forceinline__ int load_and_check_geometry(const double* nodes, int n, double* xs,
+                                                       double* ys, double* scratch) {
+  if (n < 3) return PANEL_INFO_FEW_NODES;
+  double bad = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double x = nodes[2 * k], y = nodes[2 * k + 1];
+    xs[k] = x;
+    ys[k] = y;
+    if (!isfinite(x) || !isfinite(y)) bad = 1.0;
+  }
+  if (block_max(bad, scratch) > 0.0) return PANEL_INFO_NONFINITE;  // (syncs)
+  double zero = 0.0, area = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    int k1 = (k + 1 == n) ? 0 : k + 1;
+    double hx = xs[k1] - xs[k], hy = ys[k1] - ys[k];
+    if (hx == 0.0 && hy == 0.0) zero = 1.0;
+    area += xs[k] * ys[k1] - xs[k1] * ys[k];
+  }
+  if (block_max(zero, scratch) > 0.0) return PANEL_INFO_ZERO_PANEL;
+  area = block_sum(area, scratch);
+  if (!(area > 0.0)) return PANEL_INFO_ORIENTATION;
+  return 0;
+}
+
+}  // namespace panel

@@ -1,0 +1,160 @@
+"""Device-resident batches and the torch autograd wrapper over the C ABI.
+
+``PanelBatch`` owns the torch tensors of one ragged population (inputs,
+matrices, factors, solutions, forces and gradients) and runs the four library
+calls on the current torch stream.  ``PanelCl`` is a ``torch.autograd.Function``
+mapping node coordinates to Cl whose backward is ``panel_adjoint``.
+Everything numerical happens in the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as bd
+
+MODES = {"fp64": bd.PANEL_FP64, "mixed": bd.PANEL_MIXED}
+
+
+def _require_cuda(device):
+    dev = torch.device(device)
+    if dev.type != "cuda" or not torch.cuda.is_available():
+        raise RuntimeError("the panel library runs on a CUDA device only (no CPU fallback)")
+    return dev
+
+
+class PanelBatch:
+    """A population resident in device memory, with its workspace.
+
+    nodes [sum n_b][2] float64, offsets [B+1] int64 (host or device), alpha [B]
+    float64 radians.  mode 'mixed' (double-float assembly, FP32 LU, refined) or
+    'fp64' (plain FP64 path).
+    """
+
+    def __init__(self, nodes, offsets, alpha, mode: str = "mixed", vinf=None, chord=None,
+                 device="cuda", max_iter: int = 10, tol: float = 1e-12):
+        self.device = _require_cuda(device)
+        if mode not in MODES:
+            raise ValueError("mode must be one of %s" % sorted(MODES))
+        self.mode = mode
+        self.flags = MODES[mode]
+        self.max_iter = int(max_iter)
+        self.tol = float(tol)
+        offsets_h = np.ascontiguousarray(
+            offsets.cpu().numpy() if torch.is_tensor(offsets) else offsets, dtype=np.int64)
+        self.mat_offsets_h, order_h, self.n_max = bd.panel_plan(offsets_h)
+        self.offsets_h = offsets_h
+        self.B = len(offsets_h) - 1
+        total = int(offsets_h[-1])
+        self.total_nodes = total
+        self.total_vec = total + self.B
+        self.total_mat = int(self.mat_offsets_h[-1])
+        dev = self.device
+        f64 = dict(dtype=torch.float64, device=dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.nodes = torch.as_tensor(nodes, dtype=torch.float64).to(dev).contiguous()
+        if self.nodes.shape != (total, 2):
+            raise ValueError("nodes must be [%d][2]" % total)
+        self.node_offsets = torch.as_tensor(offsets_h).to(dev)
+        self.mat_offsets = torch.as_tensor(self.mat_offsets_h).to(dev)
+        self.order = torch.as_tensor(order_h).to(dev)
+        self.alpha = torch.as_tensor(alpha, dtype=torch.float64).to(dev).contiguous()
+        self.vinf = None if vinf is None else torch.as_tensor(vinf, **f64).contiguous()
+        self.chord = None if chord is None else torch.as_tensor(chord, **f64).contiguous()
+        if self.flags == bd.PANEL_FP64:
+            self.A64 = torch.empty(self.total_mat, **f64)
+            self.A_hi = self.A_lo = None
+            self.LU = torch.empty(self.total_mat, **f64)
+        else:
+            self.A64 = None
+            self.A_hi = torch.empty(self.total_mat, dtype=torch.float32, device=dev)
+            self.A_lo = torch.empty(self.total_mat, dtype=torch.float32, device=dev)
+            self.LU = torch.empty(self.total_mat, dtype=torch.float32, device=dev)
+        self.piv = torch.empty(self.total_vec, **i32)
+        self.rhs = torch.empty(self.total_vec, **f64)
+        self.u = torch.empty(self.total_vec, **f64)
+        self.lam = torch.empty(self.total_vec, **f64)
+        self.info = torch.zeros(self.B, **i32)
+        self.iters = torch.zeros(self.B, **i32)
+        self.cp = torch.empty(total, **f64)
+        self.cl = torch.empty(self.B, **f64)
+        self.cl_p = torch.empty(self.B, **f64)
+        self.cd_p = torch.empty(self.B, **f64)
+        self.grad = torch.empty(total, 2, **f64)
+        self.have_lambda = False
+
+    # -- the four library calls -------------------------------------------------
+    def assemble(self):
+        bd.panel_assemble(self.B, self.n_max, self.flags, self.nodes, self.node_offsets,
+                          self.mat_offsets, self.order, self.alpha, self.vinf, self.A64,
+                          self.A_hi, self.A_lo, self.rhs, self.info)
+
+    def solve(self, with_adjoint: bool = False):
+        flags = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
+        bd.panel_solve(self.B, self.n_max, flags, self.nodes, self.node_offsets,
+                       self.mat_offsets, self.order, self.A64, self.A_hi, self.A_lo, self.LU,
+                       self.piv, self.rhs, self.vinf, self.chord, self.u,
+                       self.lam if with_adjoint else None, self.max_iter, self.tol, self.info,
+                       self.iters)
+        self.have_lambda = with_adjoint
+
+    def forces(self):
+        bd.panel_forces(self.B, self.nodes, self.node_offsets, self.u, self.alpha, self.vinf,
+                        self.chord, self.info, self.cp, self.cl, self.cl_p, self.cd_p)
+
+    def adjoint(self, grad_cl=None):
+        gc = None if grad_cl is None else torch.as_tensor(
+            grad_cl, dtype=torch.float64, device=self.device).contiguous()
+        bd.panel_adjoint(self.B, self.n_max, self.flags, self.nodes, self.node_offsets,
+                         self.mat_offsets, self.order, self.A64, self.A_hi, self.A_lo, self.LU,
+                         self.piv, self.u, self.lam if self.have_lambda else None,
+                         None if self.have_lambda else self.lam, self.alpha, self.vinf,
+                         self.chord, gc, self.grad, self.max_iter, self.tol, self.info)
+        self.have_lambda = True
+
+    def run(self, with_grad: bool = False):
+        """Assemble, solve, forces (and the adjoint for unit upstream gradient)."""
+        self.assemble()
+        self.solve(with_adjoint=with_grad)
+        self.forces()
+        if with_grad:
+            self.adjoint()
+        return self
+
+    # -- views -----------------------------------------------------------------
+    def vec(self, t, b):
+        o = int(self.offsets_h[b]) + b
+        return t[o:o + int(self.offsets_h[b + 1] - self.offsets_h[b]) + 1]
+
+    def matrix(self, b):
+        """Airfoil b's assembled matrix as float64 (A64, or A_hi + A_lo)."""
+        o = int(self.mat_offsets_h[b])
+        m = int(self.offsets_h[b + 1] - self.offsets_h[b]) + 1
+        if self.A64 is not None:
+            return self.A64[o:o + m * m].view(m, m)
+        return (self.A_hi[o:o + m * m].double() + self.A_lo[o:o + m * m].double()).view(m, m)
+
+    def gamma(self, b):
+        return self.vec(self.u, b)[:-1]
+
+
+class PanelCl(torch.autograd.Function):
+    """Cl of every airfoil of a batch as a differentiable function of the nodes.
+
+    forward(nodes [sum n][2] f64 cuda, offsets (host int64 [B+1]), alpha [B], mode)
+    -> cl [B].  backward maps dL/dCl to dL/dnodes with panel_adjoint (a
+    transposed solve with the stored LU and the dM/dx contraction).
+    """
+
+    @staticmethod
+    def forward(ctx, nodes, offsets, alpha, mode="mixed"):
+        pb = PanelBatch(nodes.detach(), offsets, alpha.detach(), mode=mode, device=nodes.device)
+        pb.run(with_grad=False)
+        ctx.pb = pb
+        return pb.cl.clone()
+
+    @staticmethod
+    def backward(ctx, grad_cl):
+        pb = ctx.pb
+        pb.adjoint(grad_cl.contiguous())
+        return pb.grad.clone(), None, None, None

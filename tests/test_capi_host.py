@@ -1,0 +1,82 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+symbol include/panel.h declares; the host planner and argument validation work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1511_02166_gb300 import binding as bd
+from paper_1511_02166_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "panel.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(panel_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(build.build())
+    syms = declared_symbols()
+    assert "panel_assemble" in syms and "panel_adjoint" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) <= set(bd.SIGNATURES)
+
+
+def test_constants_match_header():
+    txt = open(os.path.join(ROOT, "include", "panel.h")).read()
+    for name, val in [("PANEL_FP64", bd.PANEL_FP64), ("PANEL_MIXED", bd.PANEL_MIXED),
+                      ("PANEL_WITH_ADJOINT", bd.PANEL_WITH_ADJOINT),
+                      ("PANEL_N_MAX", bd.PANEL_N_MAX)]:
+        m = re.search(r"#define %s\s+(0x[0-9a-fA-F]+|\d+)" % name, txt)
+        assert m and int(m.group(1), 0) == val, name
+    for name, val in [("PANEL_INFO_FEW_NODES", bd.INFO_FEW_NODES),
+                      ("PANEL_INFO_ORIENTATION", bd.INFO_ORIENTATION),
+                      ("PANEL_INFO_ZERO_PANEL", bd.INFO_ZERO_PANEL),
+                      ("PANEL_INFO_NONFINITE", bd.INFO_NONFINITE),
+                      ("PANEL_INFO_NOCONV", bd.INFO_NOCONV),
+                      ("PANEL_INFO_TOO_LARGE", bd.INFO_TOO_LARGE)]:
+        m = re.search(r"#define %s \((-\d+)\)" % name, txt)
+        assert m and int(m.group(1)) == val, name
+
+
+def test_plan_offsets_and_order():
+    sizes = np.array([5, 200, 3, 200, 17, 0])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    mat, order, nmax = bd.panel_plan(off)
+    assert nmax == 200
+    assert list(mat) == list(np.concatenate([[0], np.cumsum((sizes + 1) ** 2)]))
+    assert list(order) == [1, 3, 4, 0, 2, 5]  # decreasing size, stable
+    empty, order0, _ = bd.panel_plan(np.zeros(1, np.int64))
+    assert list(empty) == [0] and len(order0) == 0
+
+
+def test_plan_rejects_bad_offsets():
+    with pytest.raises(bd.PanelError):
+        bd.panel_plan(np.array([0, 5, 3], np.int64))
+    with pytest.raises(bd.PanelError):
+        bd.panel_plan(np.array([0, bd.PANEL_N_MAX + 1], np.int64))
+
+
+def test_argument_validation_before_any_launch():
+    lib = bd.load()
+    # negative batch, bad flags and missing pointers are rejected on the host
+    assert lib.panel_assemble(-1, 10, bd.PANEL_FP64, *([None] * 11), None) == bd.PANEL_EINVAL
+    assert lib.panel_assemble(1, 10, 0x3, *([None] * 11), None) == bd.PANEL_EINVAL
+    assert lib.panel_assemble(1, 10, bd.PANEL_FP64, *([None] * 11), None) == bd.PANEL_EINVAL
+    assert lib.panel_assemble(1, bd.PANEL_N_MAX + 1, bd.PANEL_FP64, *([None] * 11),
+                              None) == bd.PANEL_EINVAL
+    assert lib.panel_solve(1, 10, 0x40 | bd.PANEL_FP64, *([None] * 14), 3, 1e-12, None, None,
+                           None) == bd.PANEL_EINVAL
+    assert lib.panel_forces(1, *([None] * 11), None) == bd.PANEL_EINVAL
+    assert lib.panel_adjoint(1, 10, bd.PANEL_MIXED, *([None] * 17), 3, 1e-12, None,
+                             None) == bd.PANEL_EINVAL
+    # an empty batch is a no-op
+    assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
+    assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"
+    assert "sm_103a" in bd.panel_version()
