@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark: airfoil solves/s and dCl/dx gradients/s on one GB300.
+
+One step = the whole hot path over one batch resident in device memory:
+panel_assemble (geometry + influence matrix + Kutta row), panel_solve (LU +
+refinement, with the transposed system for the adjoint), panel_forces
+(Cp, Cl) and panel_adjoint (dCl/d(nodes)).  Every airfoil of the batch gets
+Cl and its node gradient, so `value` counts airfoils (solve + gradient) per
+second over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
+                  [--mode mixed|fp64] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain C restatement of the
+method) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "airfoil solves/sec and dCl/dx gradients/sec on 1 GB300 at <=1e-10 Cl error"
+DEFAULT_CONFIG = "naca_b4096_n200"
+L2_BYTES = 135528448
+
+# Algorithmic work per unit (derivations in the design doc).
+#  * assembly: one (control point, panel) pair of the far-field double-float
+#    evaluation = ASSEMBLY_FLOP_PER_PAIR FP32 flops (FMA = 2);
+#  * LU: 2/3 m^3 flops per airfoil;
+#  * adjoint contraction: one pair = ADJOINT_FLOP_PER_PAIR flops.
+ASSEMBLY_FLOP_PER_PAIR = 300
+ADJOINT_FLOP_PER_PAIR = 300
+# FP32 peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.lines = []
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_baseline(config, seconds=15.0, max_airfoils=None):
+    import oracle
+    from paper_1511_02166_gb300 import inputs
+
+    spec = inputs.SPECS[config]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = oracle.max_threads()
+    # grow the sample until it takes about `seconds`
+    k = 4 * threads
+    done, elapsed = 0, 0.0
+    pop_all = inputs.make_population(spec, batch=min(spec.batch, max_airfoils or spec.batch))
+    while True:
+        sub = pop_all.subset(np.arange(min(k, pop_all.batch)))
+        t0 = time.perf_counter()
+        oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
+        oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
+        dt = time.perf_counter() - t0
+        done, elapsed = sub.batch, dt
+        if dt > seconds / 4 or sub.batch >= pop_all.batch:
+            break
+        k = min(pop_all.batch, int(k * max(2.0, seconds / 4 / max(dt, 1e-3))))
+    return {"value": done / elapsed, "unit": "airfoils/s", "cores": int(threads),
+            "host_cores": int(cores), "kind": "oracle",
+            "sample": "%d of %d airfoils of %s (solve + forward-tangent gradient), %.1f s"
+                      % (done, spec.batch, config, elapsed)}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.config, seconds=max(5.0, 20.0 / max(args.steps, 1)))
+    out = {"metric": METRIC, "value": cb["value"], "unit": "airfoils/s", "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.config}, "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "airfoils/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1511_02166_gb300 import binding as bd
+    from paper_1511_02166_gb300 import inputs
+    from paper_1511_02166_gb300.solver import PanelBatch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    spec = inputs.SPECS[args.config]
+    # weak scaling: each rank evaluates its own batch of the configured size
+    spec_r = inputs.PopulationSpec(spec.name, spec.batch, spec.n_min, spec.n_max, spec.perturbed,
+                                   spec.seed_index + 1000 * rank)
+    pop = inputs.make_population(spec_r)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=args.mode, device=dev,
+                    max_iter=args.max_iter, tol=args.tol)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    names = ["assemble", "solve", "forces", "adjoint"]
+    fns = [pb.assemble, lambda: pb.solve(with_adjoint=True), pb.forces, pb.adjoint]
+
+    def step(evs=None):
+        for k, fn in enumerate(fns):
+            if evs is not None:
+                evs[k][0].record(stream)
+            fn()
+            if evs is not None:
+                evs[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = pb.info.cpu().numpy()
+    iters = pb.iters.cpu().numpy()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clk = ClockSampler(local)
+    clk.start()
+    kern = {nm: [] for nm in names}
+    totals = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in names]
+        e0.record(stream)
+        step(evs)
+        e1.record(stream)
+        e1.synchronize()
+        totals.append(e0.elapsed_time(e1))
+        for k, nm in enumerate(names):
+            kern[nm].append(evs[k][0].elapsed_time(evs[k][1]))
+    barrier()
+    clocks = clk.stop()
+    ms = float(np.mean(totals))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    B = pop.batch
+    value = world * B / (ms * 1e-3)
+
+    # ---- e2e through the public API with host buffers ----
+    nodes_h = torch.from_numpy(pop.nodes).pin_memory()
+    alpha_h = torch.from_numpy(pop.alpha).pin_memory()
+    cl_h = torch.empty(B, dtype=torch.float64).pin_memory()
+    grad_h = torch.empty(pop.nodes.shape, dtype=torch.float64).pin_memory()
+    h2d = nodes_h.numel() * 8 + alpha_h.numel() * 8
+    d2h = cl_h.numel() * 8 + grad_h.numel() * 8
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pb.nodes.copy_(nodes_h, non_blocking=True)
+        pb.alpha.copy_(alpha_h, non_blocking=True)
+        step()
+        cl_h.copy_(pb.cl, non_blocking=True)
+        grad_h.copy_(pb.grad, non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = float(np.mean(e2e_ms))
+
+    # ---- roofline of the dominant kernel ----
+    kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
+    sizes = pop.sizes.astype(np.float64)
+    pairs = float((sizes ** 2).sum())
+    m3 = float(((sizes + 1) ** 3).sum())
+    peaks = _peaks()
+    fp_peak = FP32_PEAK_TFLOPS if args.mode == "mixed" else FP64_PEAK_TFLOPS
+    work = {
+        "assemble": pairs * ASSEMBLY_FLOP_PER_PAIR if args.mode == "mixed" else None,
+        "solve": 2.0 / 3.0 * m3,
+        "forces": None,
+        "adjoint": pairs * ADJOINT_FLOP_PER_PAIR,
+    }
+    kernels = {}
+    for nm in names:
+        w = work[nm]
+        ach = (w / (kms[nm] * 1e-3) / 1e12) if w else None
+        kernels[nm] = {"ms": kms[nm], "tflops": ach,
+                       "frac": (ach / fp_peak) if ach else None}
+    dom = max(kms, key=kms.get)
+    dk = kernels[dom]
+    roofline = {"kernel": dom, "bound": "alu", "achieved": dk["tflops"], "peak": fp_peak,
+                "unit": "TFLOP/s", "frac": dk["frac"], "traffic": None,
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+                if args.mode == "mixed" else "FP64 nominal 1.25 TFLOP/s"}
+
+    launches_per_step = 4 if args.mode == "fp64" else 4
+    if args.mode == "mixed" and pb.n_max + 1 > 230:
+        launches_per_step += 2
+    out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+df32" if args.mode == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": args.config, "batch_per_gpu": B, "mode": args.mode,
+                      "n_min": int(sizes.min()), "n_max": int(sizes.max()),
+                      "l2": "flushed before every timed step (%d MB write)"
+                            % (flush.numel() * 4 // 2**20),
+                      "max_iter": args.max_iter, "tol": args.tol,
+                      "parallelism": "dp%d (independent airfoils)" % world},
+           "gradients_per_s": value,
+           "kernels_ms": kms,
+           "kernels": kernels,
+           "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
+           "info_nonzero": int((info != 0).sum()),
+           "e2e": {"value": world * B / (e2e * 1e-3), "unit": "airfoils/s",
+                   "ms_per_step": e2e, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)},
+           "roofline": roofline,
+           "gpu_launches": launches_per_step * args.steps,
+           "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.config, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--max-iter", type=int, default=10)
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -39,7 +39,7 @@
  *   failure returns PANEL_ECUDA.  Per-airfoil problems are written to info[b]
  *   on the device: 0 ok; k > 0 the k-th pivot of the LU was exactly zero;
  *   -1 fewer than 3 nodes; -2 clockwise or zero signed area; -3 a zero-length
- *   panel; -4 a non-finite coordinate; -5 refinement did not converge within
+ *   panel; -4 a non-finite coordinate or one with magnitude >= 1024; -5 refinement did not converge within
  *   max_iter (mixed mode; the last iterate is still written); -6 n_b larger
  *   than the n_max passed to the call (nothing is written for that airfoil).
  * Precision modes (flags).
@@ -164,8 +164,9 @@ int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const 
  *   matrix in PANEL_MIXED mode) into lambda_out (required then, [sum m_b] f64).
  *   The contraction re-evaluates the panel-integral derivatives per pair
  *   (two per pair: with respect to the control point and to the panel end).
- *   grad_cl [B] f64 upstream gradient; grad_nodes [sum n_b][2] f64 output.
- *   Skips airfoils with info[b] != 0 (their gradient is set to NaN).
+ *   grad_cl [B] f64 upstream gradient (NULL means 1); grad_nodes [sum n_b][2]
+ *   f64 output.  info [B] i32 (in/out): airfoils with info[b] != 0 are skipped
+ *   (gradient set to NaN); the refinement of lambda may set PANEL_INFO_NOCONV.
  */
 int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
                   const int64_t* mat_offsets, const int32_t* order, const double* A64,
@@ -173,7 +174,20 @@ int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_
                   const double* u, const double* lambda_in, double* lambda_out,
                   const double* alpha, const double* vinf, const double* chord,
                   const double* grad_cl, double* grad_nodes, int max_iter, double tol,
-                  const int32_t* info, void* stream);
+                  int32_t* info, void* stream);
+
+/*
+ * panel_df_eval -- diagnostic: evaluate the double-float primitives of the
+ * PANEL_MIXED assembly on `count` device inputs (results rounded to f64):
+ *   op 0: out[k] = log(a[k])                      (a[k] > 0)
+ *   op 1: out[k] = atan2(a[k], b[k])
+ *   op 2: out[k] = A coefficient -G of Section 2 for the control point
+ *         (a[2k], a[2k+1]) and the panel (b[4k], b[4k+1]) -> (b[4k+2], b[4k+3]).
+ * Inputs are rounded to double-float first.  Used by the tests to compare the
+ * emulated arithmetic with FP64.
+ */
+int panel_df_eval(int op, int count, const double* a, const double* b, double* out,
+                  void* stream);
 
 /* Human-readable name of a panel_status value (static string). */
 const char* panel_strerror(int status);

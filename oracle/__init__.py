@@ -21,9 +21,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "panel_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_LIBS = {"double": os.path.join(_BUILD, "liboracle.so"),
+         "long": os.path.join(_BUILD, "liboracle_ld.so")}
 _lock = threading.Lock()
-_lib = None
+_loaded = {}
+_current = threading.local()
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
@@ -32,57 +34,84 @@ _INT = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile panel_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    """Compile panel_oracle.c twice (gcc -O2, OpenMP): working type double
+    (liboracle.so) and long double (liboracle_ld.so)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    for kind, path in _LIBS.items():
+        if (not force and os.path.exists(path)
+                and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+            continue
+        tmp = path + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if kind == "long":
+            cmd.insert(1, "-DORACLE_LONG_DOUBLE")
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, path)
+    return _LIBS["double"]
 
 
-def _load():
-    global _lib
+def _bind(lib):
+    lib.oracle_is_extended.restype = ctypes.c_int
+    lib.oracle_is_extended.argtypes = []
+    lib.oracle_signed_area.restype = ctypes.c_double
+    lib.oracle_signed_area.argtypes = [ctypes.c_int, _D]
+    lib.oracle_panel_integral.restype = ctypes.c_double
+    lib.oracle_panel_integral.argtypes = [ctypes.c_double] * 6
+    lib.oracle_panel_integral_dual.restype = None
+    lib.oracle_panel_integral_dual.argtypes = [_D, _D, _D]
+    lib.oracle_assemble.restype = None
+    lib.oracle_assemble.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]
+    lib.oracle_lu_factor.restype = ctypes.c_int
+    lib.oracle_lu_factor.argtypes = [ctypes.c_int, _D, _INT]
+    lib.oracle_lu_solve.restype = None
+    lib.oracle_lu_solve.argtypes = [ctypes.c_int, _D, _INT, _D]
+    lib.oracle_lu_solve_transposed.restype = None
+    lib.oracle_lu_solve_transposed.argtypes = [ctypes.c_int, _D, _INT, _D]
+    lib.oracle_forces.restype = None
+    lib.oracle_forces.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, _D, _D]
+    lib.oracle_evaluate.restype = ctypes.c_int
+    lib.oracle_evaluate.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _D, _D, _D]
+    lib.oracle_cl_gradient.restype = ctypes.c_int
+    lib.oracle_cl_gradient.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, _D]
+    lib.oracle_evaluate_batch.restype = None
+    lib.oracle_evaluate_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _D, _D,
+                                          _D, _D, _I32, ctypes.c_int]
+    lib.oracle_cl_gradient_batch.restype = None
+    lib.oracle_cl_gradient_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _I32,
+                                             ctypes.c_int]
+    lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_max_threads.argtypes = []
+    return lib
+
+
+def _load(kind=None):
+    kind = kind or getattr(_current, "kind", "double")
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        lib.oracle_signed_area.restype = ctypes.c_double
-        lib.oracle_signed_area.argtypes = [ctypes.c_int, _D]
-        lib.oracle_panel_integral.restype = ctypes.c_double
-        lib.oracle_panel_integral.argtypes = [ctypes.c_double] * 6
-        lib.oracle_panel_integral_dual.restype = None
-        lib.oracle_panel_integral_dual.argtypes = [_D, _D, _D]
-        lib.oracle_assemble.restype = None
-        lib.oracle_assemble.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, _D, _D]
-        lib.oracle_lu_factor.restype = ctypes.c_int
-        lib.oracle_lu_factor.argtypes = [ctypes.c_int, _D, _INT]
-        lib.oracle_lu_solve.restype = None
-        lib.oracle_lu_solve.argtypes = [ctypes.c_int, _D, _INT, _D]
-        lib.oracle_lu_solve_transposed.restype = None
-        lib.oracle_lu_solve_transposed.argtypes = [ctypes.c_int, _D, _INT, _D]
-        lib.oracle_forces.restype = None
-        lib.oracle_forces.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_double, _D, _D]
-        lib.oracle_evaluate.restype = ctypes.c_int
-        lib.oracle_evaluate.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
-                                        ctypes.c_double, _D, _D, _D]
-        lib.oracle_cl_gradient.restype = ctypes.c_int
-        lib.oracle_cl_gradient.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_double, _D]
-        lib.oracle_evaluate_batch.restype = None
-        lib.oracle_evaluate_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _D, _D,
-                                              _D, _D, _I32, ctypes.c_int]
-        lib.oracle_cl_gradient_batch.restype = None
-        lib.oracle_cl_gradient_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _I32,
-                                                 ctypes.c_int]
-        lib.oracle_max_threads.restype = ctypes.c_int
-        lib.oracle_max_threads.argtypes = []
-        _lib = lib
-        return lib
+        if kind not in _loaded:
+            build()
+            _loaded[kind] = _bind(ctypes.CDLL(_LIBS[kind]))
+        return _loaded[kind]
+
+
+class extended:
+    """Context manager: inside ``with oracle.extended():`` every oracle call of
+    this thread uses the long double build of the same source."""
+
+    def __enter__(self):
+        self._prev = getattr(_current, "kind", "double")
+        _current.kind = "long"
+        return self
+
+    def __exit__(self, *exc):
+        _current.kind = self._prev
+        return False
+
+
+def is_extended() -> bool:
+    return bool(_load().oracle_is_extended())
 
 
 def _dp(a):

@@ -19,7 +19,12 @@
  *              condition gamma_0 = -gamma_{n-1} written as an extra row, giving
  *              an (n+1) x (n+1) system in u = (gamma_0..gamma_{n-1}, C) (Section 2);
  *   solve      LU with partial pivoting (ties go to the lowest row), then forward
- *              and back substitution (Section 3 names LU as the solver);
+ *              and back substitution (Section 3 names LU as the solver), then two
+ *              steps of iterative refinement whose residual b - M x is accumulated
+ *              in long double: the result is the solution of the FP64-assembled
+ *              system to about 1e-15, so the FP64 LU's own rounding error
+ *              (condition number x 1e-16, which reaches 1e-10 for some 500-panel
+ *              airfoils) does not enter comparisons;
  *   forces     surface speed |gamma_j|, Cp_j = 1 - (gamma_j / v_inf)^2,
  *              Cl = 2 sum_i gamma_i |h_i| / (v_inf c) (Kutta-Joukowski), and the
  *              pressure-integrated Cl_p, Cd_p.  The paper reports C_L without a
@@ -28,7 +33,13 @@
  *              through the same influence formula and a re-solve with the LU,
  *              one tangent per coordinate (O(n^3) per airfoil by design).
  *
- * Everything is IEEE double, no fast-math, no blocking or reordering beyond the
+ * Arithmetic is in `real`: IEEE double by default.  The same source compiled
+ * with -DORACLE_LONG_DOUBLE computes in long double (80-bit on x86-64, 128-bit
+ * on aarch64) and serves as the reference where the system is so ill
+ * conditioned that the FP64 evaluation itself is off by more than the
+ * comparison tolerance (some perturbed 500-panel airfoils: the FP64 entries are
+ * right to 1e-16, their solution only to ~1e-9).  Inputs and outputs are double
+ * in both builds.  No fast-math, no blocking or reordering beyond the
  * definitions.  Batch entry points run airfoils in parallel with OpenMP; each
  * airfoil is computed serially.
  */
@@ -40,14 +51,35 @@
 #include <omp.h>
 #endif
 
-static const double TWO_PI = 6.283185307179586476925286766559;
+#ifdef ORACLE_LONG_DOUBLE
+typedef long double real;
+#define R_LOG logl
+#define R_ATAN2 atan2l
+#define R_SQRT sqrtl
+#define R_FABS fabsl
+#define R_COS cosl
+#define R_SIN sinl
+#else
+typedef double real;
+#define R_LOG log
+#define R_ATAN2 atan2
+#define R_SQRT sqrt
+#define R_FABS fabs
+#define R_COS cos
+#define R_SIN sin
+#endif
+
+static const real TWO_PI = 6.283185307179586476925286766559L;
+
+/* 1 for the long double build, 0 for the double build. */
+int oracle_is_extended(void) { return sizeof(real) > sizeof(double); }
 
 /* ------------------------------------------------------------------------ */
 /* Geometry (Section 2, Figure 1)                                           */
 /* ------------------------------------------------------------------------ */
 
 /* Node i of an n-node airfoil with the closing convention x_n = x_0. */
-static void node(const double *nodes, int n, int i, double *x, double *y) {
+static void node(const double *nodes, int n, int i, real *x, real *y) {
   int k = i % n;
   *x = nodes[2 * k];
   *y = nodes[2 * k + 1];
@@ -55,14 +87,14 @@ static void node(const double *nodes, int n, int i, double *x, double *y) {
 
 /* Signed polygon area (shoelace); positive for counter-clockwise nodes. */
 double oracle_signed_area(int n, const double *nodes) {
-  double a = 0.0;
+  real a = 0.0;
   for (int i = 0; i < n; ++i) {
-    double x0, y0, x1, y1;
+    real x0, y0, x1, y1;
     node(nodes, n, i, &x0, &y0);
     node(nodes, n, i + 1, &x1, &y1);
     a += x0 * y1 - x1 * y0;
   }
-  return 0.5 * a;
+  return (double)(0.5 * a);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -70,7 +102,7 @@ double oracle_signed_area(int n, const double *nodes) {
 /* ------------------------------------------------------------------------ */
 
 /*
- * Returns F_i(p) / gamma_i for the panel from a = x_i to b = x_{i+1}:
+ * F_i(p) / gamma_i for the panel from a = x_i to b = x_{i+1}:
  *
  *   (1/2pi)(1/|h|) [ 1/2 <p-a,h> log|p-a|^2 - 1/2 <p-b,h> log|p-b|^2
  *                    - I atan2(I, <p-a,h>) + I atan2(I, <p-b,h>) - |h|^2 ]
@@ -78,31 +110,35 @@ double oracle_signed_area(int n, const double *nodes) {
  * with h = b - a, I = <h_perp, p-a>, h_perp = (h_y, -h_x) (outward for
  * counter-clockwise nodes, |h_perp| = |h|).
  */
-double oracle_panel_integral(double px, double py, double ax, double ay, double bx,
-                             double by) {
-  double hx = bx - ax, hy = by - ay;
-  double hn = sqrt(hx * hx + hy * hy);
-  double dax = px - ax, day = py - ay; /* p - x_i     */
-  double dbx = px - bx, dby = py - by; /* p - x_{i+1} */
-  double dot_a = dax * hx + day * hy;  /* <p - x_i, h>     */
-  double dot_b = dbx * hx + dby * hy;  /* <p - x_{i+1}, h> */
-  double I = hy * dax - hx * day;      /* <h_perp, p - x_i> */
-  double ra2 = dax * dax + day * day;
-  double rb2 = dbx * dbx + dby * dby;
-  double bracket = 0.5 * dot_a * log(ra2) - 0.5 * dot_b * log(rb2) - I * atan2(I, dot_a) +
-                   I * atan2(I, dot_b) - hn * hn;
+static real panel_integral(real px, real py, real ax, real ay, real bx, real by) {
+  real hx = bx - ax, hy = by - ay;
+  real hn = R_SQRT(hx * hx + hy * hy);
+  real dax = px - ax, day = py - ay; /* p - x_i     */
+  real dbx = px - bx, dby = py - by; /* p - x_{i+1} */
+  real dot_a = dax * hx + day * hy;  /* <p - x_i, h>     */
+  real dot_b = dbx * hx + dby * hy;  /* <p - x_{i+1}, h> */
+  real I = hy * dax - hx * day;      /* <h_perp, p - x_i> */
+  real ra2 = dax * dax + day * day;
+  real rb2 = dbx * dbx + dby * dby;
+  real bracket = 0.5 * dot_a * R_LOG(ra2) - 0.5 * dot_b * R_LOG(rb2) -
+                 I * R_ATAN2(I, dot_a) + I * R_ATAN2(I, dot_b) - hn * hn;
   return bracket / (hn * TWO_PI);
 }
 
+double oracle_panel_integral(double px, double py, double ax, double ay, double bx,
+                             double by) {
+  return (double)panel_integral(px, py, ax, ay, bx, by);
+}
+
 /* A_ji = -F_i(x_{j+1/2}) / gamma_i: the coefficient of gamma_i in row j. */
-static double influence(const double *nodes, int n, int j, int i) {
-  double xj, yj, xj1, yj1, xa, ya, xb, yb;
+static real influence(const double *nodes, int n, int j, int i) {
+  real xj, yj, xj1, yj1, xa, ya, xb, yb;
   node(nodes, n, j, &xj, &yj);
   node(nodes, n, j + 1, &xj1, &yj1);
   node(nodes, n, i, &xa, &ya);
   node(nodes, n, i + 1, &xb, &yb);
-  double px = 0.5 * (xj + xj1), py = 0.5 * (yj + yj1);
-  return -oracle_panel_integral(px, py, xa, ya, xb, yb);
+  real px = 0.5 * (xj + xj1), py = 0.5 * (yj + yj1);
+  return -panel_integral(px, py, xa, ya, xb, yb);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -114,22 +150,33 @@ static double influence(const double *nodes, int n, int j, int i) {
  *   M[j][i] = A_ji, M[j][n] = 1, b_j = phi_v(x_{j+1/2})           (j < n)
  *   M[n][0] = M[n][n-1] = 1, all other M[n][*] = 0, b_n = 0         (Kutta)
  */
-void oracle_assemble(int n, const double *nodes, double alpha, double vinf, double *M,
-                     double *b) {
+static void assemble(int n, const double *nodes, real alpha, real vinf, real *M, real *b) {
   int m = n + 1;
   for (int j = 0; j < n; ++j) {
     for (int i = 0; i < n; ++i) M[j * m + i] = influence(nodes, n, j, i);
     M[j * m + n] = 1.0;
-    double xj, yj, xj1, yj1;
+    real xj, yj, xj1, yj1;
     node(nodes, n, j, &xj, &yj);
     node(nodes, n, j + 1, &xj1, &yj1);
-    double px = 0.5 * (xj + xj1), py = 0.5 * (yj + yj1);
-    b[j] = vinf * (py * cos(alpha) - px * sin(alpha));
+    real px = 0.5 * (xj + xj1), py = 0.5 * (yj + yj1);
+    b[j] = vinf * (py * R_COS(alpha) - px * R_SIN(alpha));
   }
   for (int i = 0; i < m; ++i) M[n * m + i] = 0.0;
   M[n * m + 0] = 1.0;
   M[n * m + (n - 1)] = 1.0;
   b[n] = 0.0;
+}
+
+void oracle_assemble(int n, const double *nodes, double alpha, double vinf, double *M,
+                     double *b) {
+  int m = n + 1;
+  real *Mr = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *br = (real *)malloc(sizeof(real) * (size_t)m);
+  assemble(n, nodes, alpha, vinf, Mr, br);
+  for (size_t k = 0; k < (size_t)m * m; ++k) M[k] = (double)Mr[k];
+  for (int k = 0; k < m; ++k) b[k] = (double)br[k];
+  free(Mr);
+  free(br);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -138,25 +185,25 @@ void oracle_assemble(int n, const double *nodes, double alpha, double vinf, doub
 
 /* piv[k] = row exchanged with row k at step k.  Returns 0, or k+1 if the
  * k-th pivot is exactly zero (LAPACK convention; factorisation stops). */
-int oracle_lu_factor(int m, double *A, int *piv) {
+static int lu_factor(int m, real *A, int *piv) {
   for (int k = 0; k < m; ++k) {
     int p = k;
-    double best = fabs(A[k * m + k]);
+    real best = R_FABS(A[k * m + k]);
     for (int r = k + 1; r < m; ++r) {
-      double v = fabs(A[r * m + k]);
+      real v = R_FABS(A[r * m + k]);
       if (v > best) { best = v; p = r; }
     }
     piv[k] = p;
     if (best == 0.0) return k + 1;
     if (p != k) {
       for (int c = 0; c < m; ++c) {
-        double t = A[k * m + c];
+        real t = A[k * m + c];
         A[k * m + c] = A[p * m + c];
         A[p * m + c] = t;
       }
     }
     for (int r = k + 1; r < m; ++r) {
-      double l = A[r * m + k] / A[k * m + k];
+      real l = A[r * m + k] / A[k * m + k];
       A[r * m + k] = l;
       for (int c = k + 1; c < m; ++c) A[r * m + c] -= l * A[k * m + c];
     }
@@ -164,11 +211,11 @@ int oracle_lu_factor(int m, double *A, int *piv) {
   return 0;
 }
 
-/* Solve (LU) x = P b in place given the factors of oracle_lu_factor. */
-void oracle_lu_solve(int m, const double *LU, const int *piv, double *x) {
+/* Solve (LU) x = P b in place given the factors of lu_factor. */
+static void lu_solve(int m, const real *LU, const int *piv, real *x) {
   for (int k = 0; k < m; ++k) {
     int p = piv[k];
-    if (p != k) { double t = x[k]; x[k] = x[p]; x[p] = t; }
+    if (p != k) { real t = x[k]; x[k] = x[p]; x[p] = t; }
   }
   for (int r = 1; r < m; ++r)
     for (int c = 0; c < r; ++c) x[r] -= LU[r * m + c] * x[c];
@@ -178,8 +225,8 @@ void oracle_lu_solve(int m, const double *LU, const int *piv, double *x) {
   }
 }
 
-/* Solve (LU)^T y = g, i.e. M^T y = g, given the factors of oracle_lu_factor. */
-void oracle_lu_solve_transposed(int m, const double *LU, const int *piv, double *y) {
+/* Solve M^T y = g in place given the factors of lu_factor. */
+static void lu_solve_transposed(int m, const real *LU, const int *piv, real *y) {
   /* M = P^T L U  =>  M^T = U^T L^T P.  Solve U^T z = g, L^T w = z, y = P^T w. */
   for (int r = 0; r < m; ++r) {
     for (int c = 0; c < r; ++c) y[r] -= LU[c * m + r] * y[c];
@@ -189,8 +236,52 @@ void oracle_lu_solve_transposed(int m, const double *LU, const int *piv, double 
     for (int c = r + 1; c < m; ++c) y[r] -= LU[c * m + r] * y[c];
   for (int k = m - 1; k >= 0; --k) {
     int p = piv[k];
-    if (p != k) { double t = y[k]; y[k] = y[p]; y[p] = t; }
+    if (p != k) { real t = y[k]; y[k] = y[p]; y[p] = t; }
   }
+}
+
+/* x += M^{-1} (b - M x), the residual accumulated in long double, `steps` times. */
+static void refine(int m, const real *M, const real *LU, const int *piv, const real *b, real *x,
+                   int steps) {
+  real *r = (real *)malloc(sizeof(real) * (size_t)m);
+  for (int s = 0; s < steps; ++s) {
+    for (int i = 0; i < m; ++i) {
+      long double acc = b[i];
+      for (int j = 0; j < m; ++j) acc -= (long double)M[i * m + j] * (long double)x[j];
+      r[i] = (real)acc;
+    }
+    lu_solve(m, LU, piv, r);
+    for (int i = 0; i < m; ++i) x[i] += r[i];
+  }
+  free(r);
+}
+
+/* double-array wrappers of the LU routines (for the library-comparison pins) */
+int oracle_lu_factor(int m, double *A, int *piv) {
+  real *Ar = (real *)malloc(sizeof(real) * (size_t)m * m);
+  for (size_t k = 0; k < (size_t)m * m; ++k) Ar[k] = A[k];
+  int info = lu_factor(m, Ar, piv);
+  for (size_t k = 0; k < (size_t)m * m; ++k) A[k] = (double)Ar[k];
+  free(Ar);
+  return info;
+}
+
+static void solve_wrapper(int m, const double *LU, const int *piv, double *x, int transposed) {
+  real *Lr = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *xr = (real *)malloc(sizeof(real) * (size_t)m);
+  for (size_t k = 0; k < (size_t)m * m; ++k) Lr[k] = LU[k];
+  for (int k = 0; k < m; ++k) xr[k] = x[k];
+  if (transposed) lu_solve_transposed(m, Lr, piv, xr);
+  else lu_solve(m, Lr, piv, xr);
+  for (int k = 0; k < m; ++k) x[k] = (double)xr[k];
+  free(Lr);
+  free(xr);
+}
+void oracle_lu_solve(int m, const double *LU, const int *piv, double *x) {
+  solve_wrapper(m, LU, piv, x, 0);
+}
+void oracle_lu_solve_transposed(int m, const double *LU, const int *piv, double *y) {
+  solve_wrapper(m, LU, piv, y, 1);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -204,25 +295,33 @@ void oracle_lu_solve_transposed(int m, const double *LU, const int *piv, double 
  *   F     = -sum_j Cp_j n_j |h_j|,  n_j = (h_y, -h_x)/|h_j| (outward)
  *   Cl_p  = (-F_x sin a + F_y cos a)/c,  Cd_p = (F_x cos a + F_y sin a)/c
  */
-void oracle_forces(int n, const double *nodes, const double *u, double alpha, double vinf,
-                   double chord, double *cp, double *out3) {
-  double circ = 0.0, fx = 0.0, fy = 0.0;
+static void forces(int n, const double *nodes, const real *u, real alpha, real vinf, real chord,
+                   double *cp, double *out3) {
+  real circ = 0.0, fx = 0.0, fy = 0.0;
   for (int j = 0; j < n; ++j) {
-    double xa, ya, xb, yb;
+    real xa, ya, xb, yb;
     node(nodes, n, j, &xa, &ya);
     node(nodes, n, j + 1, &xb, &yb);
-    double hx = xb - xa, hy = yb - ya;
-    double len = sqrt(hx * hx + hy * hy);
-    double g = u[j];
-    double c = 1.0 - (g / vinf) * (g / vinf);
-    if (cp) cp[j] = c;
+    real hx = xb - xa, hy = yb - ya;
+    real len = R_SQRT(hx * hx + hy * hy);
+    real g = u[j];
+    real c = 1.0 - (g / vinf) * (g / vinf);
+    if (cp) cp[j] = (double)c;
     circ += g * len;
-    fx -= c * hy;   /* -Cp * n_x * |h| with n_x |h| = h_y  */
+    fx -= c * hy;    /* -Cp * n_x * |h| with n_x |h| = h_y  */
     fy -= c * (-hx); /* -Cp * n_y * |h| with n_y |h| = -h_x */
   }
-  out3[0] = 2.0 * circ / (vinf * chord);
-  out3[1] = (-fx * sin(alpha) + fy * cos(alpha)) / chord;
-  out3[2] = (fx * cos(alpha) + fy * sin(alpha)) / chord;
+  out3[0] = (double)(2.0 * circ / (vinf * chord));
+  out3[1] = (double)((-fx * R_SIN(alpha) + fy * R_COS(alpha)) / chord);
+  out3[2] = (double)((fx * R_COS(alpha) + fy * R_SIN(alpha)) / chord);
+}
+
+void oracle_forces(int n, const double *nodes, const double *u, double alpha, double vinf,
+                   double chord, double *cp, double *out3) {
+  real *ur = (real *)malloc(sizeof(real) * (size_t)(n + 1));
+  for (int k = 0; k <= n; ++k) ur[k] = u[k];
+  forces(n, nodes, ur, alpha, vinf, chord, cp, out3);
+  free(ur);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -230,8 +329,8 @@ void oracle_forces(int n, const double *nodes, const double *u, double alpha, do
 /* ------------------------------------------------------------------------ */
 
 /*
- * Assemble, factor, solve and reduce one airfoil.  u[n+1] = (gamma, C),
- * cp[n] (may be NULL), out3 = (Cl, Cl_p, Cd_p) (may be NULL).
+ * Assemble, factor, solve (refined) and reduce one airfoil.  u[n+1] = (gamma,
+ * C), cp[n] (may be NULL), out3 = (Cl, Cl_p, Cd_p) (may be NULL).
  * Returns 0, a negative geometry code (-1: n < 3, -2: clockwise or zero area),
  * or k+1 for a zero pivot at step k.
  */
@@ -240,18 +339,28 @@ int oracle_evaluate(int n, const double *nodes, double alpha, double vinf, doubl
   if (n < 3) return -1;
   if (!(oracle_signed_area(n, nodes) > 0.0)) return -2;
   int m = n + 1;
-  double *M = (double *)malloc(sizeof(double) * (size_t)m * m);
+  real *M = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *LU = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *b = (real *)malloc(sizeof(real) * (size_t)m);
+  real *x = (real *)malloc(sizeof(real) * (size_t)m);
   int *piv = (int *)malloc(sizeof(int) * (size_t)m);
-  oracle_assemble(n, nodes, alpha, vinf, M, u);
-  int info = oracle_lu_factor(m, M, piv);
+  assemble(n, nodes, alpha, vinf, M, b);
+  memcpy(LU, M, sizeof(real) * (size_t)m * m);
+  int info = lu_factor(m, LU, piv);
   if (info == 0) {
-    oracle_lu_solve(m, M, piv, u);
+    memcpy(x, b, sizeof(real) * (size_t)m);
+    lu_solve(m, LU, piv, x);
+    refine(m, M, LU, piv, b, x, 2);
+    for (int k = 0; k < m; ++k) u[k] = (double)x[k];
     if (cp || out3) {
       double tmp[3];
-      oracle_forces(n, nodes, u, alpha, vinf, chord, cp, out3 ? out3 : tmp);
+      forces(n, nodes, x, alpha, vinf, chord, cp, out3 ? out3 : tmp);
     }
   }
   free(M);
+  free(LU);
+  free(b);
+  free(x);
   free(piv);
   return info;
 }
@@ -260,29 +369,28 @@ int oracle_evaluate(int n, const double *nodes, double alpha, double vinf, doubl
 /* Forward-mode dual numbers for the gradient oracle                        */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { double v, d; } dual;
+typedef struct { real v, d; } dual;
 
-static dual dc(double v) { dual r = {v, 0.0}; return r; }
 static dual dadd(dual a, dual b) { dual r = {a.v + b.v, a.d + b.d}; return r; }
 static dual dsub(dual a, dual b) { dual r = {a.v - b.v, a.d - b.d}; return r; }
 static dual dmul(dual a, dual b) { dual r = {a.v * b.v, a.d * b.v + a.v * b.d}; return r; }
-static dual dscale(double s, dual a) { dual r = {s * a.v, s * a.d}; return r; }
+static dual dscale(real s, dual a) { dual r = {s * a.v, s * a.d}; return r; }
 static dual ddiv(dual a, dual b) {
   dual r = {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)};
   return r;
 }
-static dual dlog(dual a) { dual r = {log(a.v), a.d / a.v}; return r; }
+static dual dlog(dual a) { dual r = {R_LOG(a.v), a.d / a.v}; return r; }
 static dual dsqrt(dual a) {
-  double s = sqrt(a.v);
+  real s = R_SQRT(a.v);
   dual r = {s, a.d / (2.0 * s)};
   return r;
 }
 static dual datan2(dual y, dual x) {
-  dual r = {atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v)};
+  dual r = {R_ATAN2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v)};
   return r;
 }
 
-/* The same printed panel integral as oracle_panel_integral, in dual numbers. */
+/* The same printed panel integral as panel_integral, in dual numbers. */
 static dual panel_integral_dual(dual px, dual py, dual ax, dual ay, dual bx, dual by) {
   dual hx = dsub(bx, ax), hy = dsub(by, ay);
   dual hn = dsqrt(dadd(dmul(hx, hx), dmul(hy, hy)));
@@ -307,8 +415,8 @@ void oracle_panel_integral_dual(const double *in6, const double *seed6, double *
   dual v[6];
   for (int k = 0; k < 6; ++k) { v[k].v = in6[k]; v[k].d = seed6[k]; }
   dual r = panel_integral_dual(v[0], v[1], v[2], v[3], v[4], v[5]);
-  out2[0] = r.v;
-  out2[1] = r.d;
+  out2[0] = (double)r.v;
+  out2[1] = (double)r.d;
 }
 
 /* Node i (closing convention) as a dual number, tangent 1 on coordinate
@@ -335,14 +443,20 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
   if (n < 3) return -1;
   if (!(oracle_signed_area(n, nodes) > 0.0)) return -2;
   int m = n + 1;
-  double *M = (double *)malloc(sizeof(double) * (size_t)m * m);
-  double *u = (double *)malloc(sizeof(double) * (size_t)m);
-  double *r = (double *)malloc(sizeof(double) * (size_t)m);
+  real *M = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *LU = (real *)malloc(sizeof(real) * (size_t)m * m);
+  real *b = (real *)malloc(sizeof(real) * (size_t)m);
+  real *u = (real *)malloc(sizeof(real) * (size_t)m);
+  real *r = (real *)malloc(sizeof(real) * (size_t)m);
   int *piv = (int *)malloc(sizeof(int) * (size_t)m);
-  oracle_assemble(n, nodes, alpha, vinf, M, u);
-  int info = oracle_lu_factor(m, M, piv);
+  const real ra = alpha, rv = vinf, rc = chord;
+  assemble(n, nodes, ra, rv, M, b);
+  memcpy(LU, M, sizeof(real) * (size_t)m * m);
+  int info = lu_factor(m, LU, piv);
   if (info == 0) {
-    oracle_lu_solve(m, M, piv, u);
+    memcpy(u, b, sizeof(real) * (size_t)m);
+    lu_solve(m, LU, piv, u);
+    refine(m, M, LU, piv, b, u, 2);
     for (int k = 0; k < n; ++k) {
       for (int coord = 0; coord < 2; ++coord) {
         for (int j = 0; j < m; ++j) r[j] = 0.0;
@@ -353,8 +467,8 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
           node_dual(nodes, n, j + 1, k, coord, &xj1, &yj1);
           dual px = dscale(0.5, dadd(xj, xj1)), py = dscale(0.5, dadd(yj, yj1));
           /* right-hand side phi_v(x_{j+1/2}) */
-          double dbj = vinf * (py.d * cos(alpha) - px.d * sin(alpha));
-          double dMu = 0.0;
+          real dbj = rv * (py.d * R_COS(ra) - px.d * R_SIN(ra));
+          real dMu = 0.0;
           for (int i = 0; i < n; ++i) {
             int col_touches = (i % n == k) || ((i + 1) % n == k);
             if (!row_touches && !col_touches) continue;
@@ -367,8 +481,8 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
           r[j] = dbj - dMu;
         }
         r[n] = 0.0; /* the Kutta row is constant */
-        oracle_lu_solve(m, M, piv, r);
-        double dcl = 0.0;
+        lu_solve(m, LU, piv, r);
+        real dcl = 0.0;
         for (int i = 0; i < n; ++i) {
           dual xa, ya, xb, yb;
           node_dual(nodes, n, i, k, coord, &xa, &ya);
@@ -377,11 +491,13 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
           dual len = dsqrt(dadd(dmul(hx, hx), dmul(hy, hy)));
           dcl += r[i] * len.v + u[i] * len.d;
         }
-        grad[2 * k + coord] = 2.0 * dcl / (vinf * chord);
+        grad[2 * k + coord] = (double)(2.0 * dcl / (rv * rc));
       }
     }
   }
   free(M);
+  free(LU);
+  free(b);
   free(u);
   free(r);
   free(piv);

@@ -45,6 +45,7 @@ SIGNATURES = {
     "panel_forces": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_adjoint": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                            _P, _P, _P, _I, _D, _P, _P]),
+    "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
 }
@@ -144,6 +145,11 @@ def panel_adjoint(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64,
                                 _ptr(lambda_out), _ptr(alpha), _ptr(vinf), _ptr(chord),
                                 _ptr(grad_cl), _ptr(grad_nodes), int(max_iter), float(tol),
                                 _ptr(info), _stream(stream)), "panel_adjoint")
+
+
+def panel_df_eval(op, count, a, b, out, stream=None):
+    _check(load().panel_df_eval(int(op), int(count), _ptr(a), _ptr(b), _ptr(out),
+                                _stream(stream)), "panel_df_eval")
 
 
 def panel_strerror(status: int) -> str:

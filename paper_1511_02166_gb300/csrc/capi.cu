@@ -21,6 +21,17 @@ cudaError_t launch_adjoint_f64(const Batch&, const double*, const int32_t*, cons
 cudaError_t launch_forces(const Batch&, const double*, const double*, const double*,
                           const double*, const int32_t*, double*, double*, double*, double*,
                           cudaStream_t);
+cudaError_t launch_assemble_df(const Batch&, const double*, const double*, float*, float*,
+                               double*, int32_t*, cudaStream_t);
+cudaError_t launch_solve_mixed(const Batch&, const float*, const float*, float*, int32_t*,
+                               const double*, const double*, const double*, double*, int, double,
+                               int32_t*, int32_t*, int, cudaStream_t);
+cudaError_t launch_df_eval(int, int, const double*, const double*, double*, cudaStream_t);
+size_t adjoint_df_smem(int n_max);
+constexpr size_t kMaxDynSmem = 232448;
+cudaError_t launch_adjoint_df(const Batch&, const double*, const double*, const double*,
+                              const double*, const double*, const double*, double*,
+                              const int32_t*, cudaStream_t);
 }  // namespace panel
 
 using panel::Batch;
@@ -103,7 +114,8 @@ int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64
     if (!A64 || A_hi || A_lo) return PANEL_EINVAL;
     return status_of(panel::launch_assemble_f64(bt, alpha, vinf, A64, rhs, info, s));
   }
-  return PANEL_ENOTSUP;
+  if (!A_hi || !A_lo) return PANEL_EINVAL;
+  return status_of(panel::launch_assemble_df(bt, alpha, vinf, A_hi, A_lo, rhs, info, s));
 }
 
 int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
@@ -124,8 +136,14 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
     return status_of(panel::launch_solve_f64(bt, A64, (double*)LU, piv, rhs, vinf, chord, u,
                                              adj ? lambda : nullptr, info, iters, s));
   }
-  (void)A_hi; (void)A_lo; (void)max_iter; (void)tol;
-  return PANEL_ENOTSUP;
+  if (!A_hi || !A_lo || max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
+  if (!LU) return PANEL_EINVAL;
+  cudaError_t e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, piv, rhs, vinf, chord, u,
+                                            max_iter, tol, info, iters, 0, s);
+  if (e == cudaSuccess && adj)
+    e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, piv, rhs, vinf, chord, lambda,
+                                  max_iter, tol, info, nullptr, 1, s);
+  return status_of(e);
 }
 
 int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const double* u,
@@ -146,7 +164,7 @@ int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_
                   const double* u, const double* lambda_in, double* lambda_out,
                   const double* alpha, const double* vinf, const double* chord,
                   const double* grad_cl, double* grad_nodes, int max_iter, double tol,
-                  const int32_t* info, void* stream) {
+                  int32_t* info, void* stream) {
   if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || !flags_ok(flags)) return PANEL_EINVAL;
   if (B == 0) return PANEL_OK;
   if (!nodes || !node_offsets || !mat_offsets || !order || !u || !alpha || !grad_nodes)
@@ -159,8 +177,32 @@ int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_
                                                lambda_out, alpha, vinf, chord, grad_cl,
                                                grad_nodes, info, s));
   }
-  (void)A64; (void)A_hi; (void)A_lo; (void)max_iter; (void)tol;
-  return PANEL_ENOTSUP;
+  (void)A64;
+  if (!A_hi || !A_lo || !info) return PANEL_EINVAL;
+  const double* lam = lambda_in;
+  if (!lam) {
+    if (max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
+    cudaError_t e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, (int32_t*)piv, nullptr,
+                                              vinf, chord, lambda_out, max_iter, tol, info,
+                                              nullptr, 1, s);
+    if (e != cudaSuccess) return PANEL_ECUDA;
+    lam = lambda_out;
+  }
+  // the double-float contraction keeps ~160 B per panel in shared memory; for
+  // larger airfoils the FP64 contraction is used
+  if (panel::adjoint_df_smem(n_max) <= panel::kMaxDynSmem)
+    return status_of(panel::launch_adjoint_df(bt, u, lam, alpha, vinf, chord, grad_cl,
+                                              grad_nodes, info, s));
+  return status_of(panel::launch_adjoint_f64(bt, nullptr, nullptr, u, lam, nullptr, alpha, vinf,
+                                             chord, grad_cl, grad_nodes, info, s));
+}
+
+int panel_df_eval(int op, int count, const double* a, const double* b, double* out,
+                  void* stream) {
+  if (op < 0 || op > 2 || count < 0) return PANEL_EINVAL;
+  if (count == 0) return PANEL_OK;
+  if (!a || !out || (op >= 1 && !b)) return PANEL_EINVAL;
+  return status_of(panel::launch_df_eval(op, count, a, b, out, (cudaStream_t)stream));
 }
 
 }  // extern "C"

@@ -1,0 +1,259 @@
+// k_adjoint_df.cu -- the dM/dx contraction of the adjoint in double-float
+// (mixed-precision path).
+//
+// dCl/dx_k = dCl/dx_k|_u + lambda^T (db/dx_k - (dM/dx_k) u) with M_ji = -G_ji,
+// G(p; a, b) = (1/2pi) int_a^b log|p - s| ds (Section 2's panel integral), so
+//   dCl/dx_k = (2/(v c)) (gamma_{k-1} t_{k-1} - gamma_k t_k)
+//            + v/2 (-sin a, cos a) (lambda_{k-1} + lambda_k)
+//            + 1/2 (lambda_{k-1} P_{k-1} + lambda_k P_k) + u_k A_k + u_{k-1} B_{k-1},
+//   P_j = sum_i u_i dG_ji/dp,  A_i = sum_j lambda_j dG_ji/da,  B_i = sum_j lambda_j dG_ji/db.
+// Per pair two gradients are evaluated (dG/da = -dG/dp - dG/db):
+//
+//  far field (|P| >= 4L, P = p - c, complex notation, Delta = b - a = L t,
+//  u = Delta^2 / (4 P^2), |u| <= 1/64), from 2pi G = L Re H,
+//  H = log P - sum_n u^n / (2n (2n+1)):
+//     2pi dG/dp     = L conj(F1(u) / P),    F1(u) = 1 + u/3 + u^2/5 + ... = atanh(w)/w,
+//     2pi dG/dDelta = t (log|P| + Re(log(1 - u))/2 + i Im F1(u)),
+//     dG/db = -dG/dp / 2 + dG/dDelta.
+//  near field (panel frame: xi = (p-a).t, eta = (p-a).n, l1 = log|p-a|^2,
+//  l2 = log|p-b|^2, theta the subtended angle):
+//     2pi dG/dp = (l1 - l2)/2 t + theta n,
+//     2pi dG/db = l2/2 t + ((l1 - l2)/2 eta - theta xi)/L n.
+//  On the own panel theta (+-pi) cancels between the terms and is set to 0.
+//
+// Layout: one block per airfoil; each warp owns 32 consecutive columns (panels
+// i, one per lane) and sweeps all rows j: A_i, B_i accumulate in the lane's
+// registers (double-float), the row sums P_j are warp-reduced and added into
+// shared FP64 accumulators.
+#include "panel_common.cuh"
+#include "panel_df.cuh"
+
+namespace panel {
+
+struct cdf {
+  df2 re, im;
+};
+__device__ __forceinline__ cdf cmul(const cdf& a, const cdf& b) {
+  cdf r;
+  r.re = df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im));
+  r.im = df_add(df_mul(a.re, b.im), df_mul(a.im, b.re));
+  return r;
+}
+
+// 2pi dG/dp and 2pi dG/db for the pair (p; panel i).
+__device__ __forceinline__ void panel_dG_df(const point3& p, const float* __restrict__ s, int ld,
+                                            int i, bool self, const float4* __restrict__ tlog,
+                                            const float2* __restrict__ tatan, df2& gpx, df2& gpy,
+                                            df2& gbx, df2& gby) {
+  const df2 px = split_diff(p.xh, p.xm, p.xl, s[kCx * ld + i], s[(kCx + 1) * ld + i],
+                            s[(kCx + 2) * ld + i]);
+  const df2 py = split_diff(p.yh, p.ym, p.yl, s[kCy * ld + i], s[(kCy + 1) * ld + i],
+                            s[(kCy + 2) * ld + i]);
+  const df2 px2 = df_sqr(px), py2 = df_sqr(py);
+  const df2 rho2 = df_add(px2, py2);
+  const float Lh = s[kL * ld + i];
+  const df2 tx = pf(s, ld, kTx, i), ty = pf(s, ld, kTy, i);
+  const df2 L = pf(s, ld, kL, i);
+  if (rho2.hi >= 16.0f * Lh * Lh) {
+    const df2 X = df_sub(px2, py2);
+    df2 Y = df_mul(px, py);
+    Y.hi *= 2.0f;
+    Y.lo *= 2.0f;
+    const df2 c2 = pf(s, ld, kC2, i), s2 = pf(s, ld, kS2, i);
+    const df2 inv = df_rcp(rho2);
+    const df2 q = df_mul(df_mul_f(pf(s, ld, kQ6, i), 6.0f), inv);  // L^2 / (4 |P|^2)
+    // u = q (cos 2phi + i sin(2beta - 2phi)...) = q (Z + i W) / |P|^2
+    cdf u;
+    u.re = df_mul(q, df_mul(df_add(df_mul(c2, X), df_mul(s2, Y)), inv));
+    u.im = df_mul(q, df_mul(df_sub(df_mul(s2, X), df_mul(c2, Y)), inv));
+    const cdf u2 = cmul(u, u);
+    // F1 - 1 = u/3 + u^2/5 + [u^3/7 + u^4/9 + u^5/11 + u^6/13 + u^7/15 in float32]
+    // Re log(1 - u) = -Re(u) - Re(u^2)/2 - [Re(u^3)/3 + ... in float32]
+    const float ur = u.re.hi, ui = u.im.hi, u2r = u2.re.hi, u2i = u2.im.hi;
+    const float u3r = u2r * ur - u2i * ui, u3i = u2r * ui + u2i * ur;
+    const float u4r = u2r * u2r - u2i * u2i, u4i = 2.0f * u2r * u2i;
+    const float u5r = u4r * ur - u4i * ui, u5i = u4r * ui + u4i * ur;
+    const float u6r = u4r * u2r - u4i * u2i, u6i = u4r * u2i + u4i * u2r;
+    const float u7r = u6r * ur - u6i * ui, u7i = u6r * ui + u6i * ur;
+    const float tFr = u3r * (1.0f / 7.0f) + u4r * (1.0f / 9.0f) + u5r * (1.0f / 11.0f) +
+                      u6r * (1.0f / 13.0f) + u7r * (1.0f / 15.0f);
+    const float tFi = u3i * (1.0f / 7.0f) + u4i * (1.0f / 9.0f) + u5i * (1.0f / 11.0f) +
+                      u6i * (1.0f / 13.0f) + u7i * (1.0f / 15.0f);
+    const float tLr = u3r * (1.0f / 3.0f) + u4r * 0.25f + u5r * 0.2f + u6r * (1.0f / 6.0f) +
+                      u7r * (1.0f / 7.0f);
+    const df2 third = df_const(kThird);
+    cdf F;  // F1 - 1
+    F.re = df_add(df_mul(u.re, third), df_mul_f(u2.re, 0.2f));
+    F.re = fast_two_sum(F.re.hi, __fadd_rn(F.re.lo, tFr));
+    F.im = df_add(df_mul(u.im, third), df_mul_f(u2.im, 0.2f));
+    F.im = fast_two_sum(F.im.hi, __fadd_rn(F.im.lo, tFi));
+    // 2pi dG/dp = L inv conj(F1) P,  conj(F1) P = P + conj(F - 0) P
+    const df2 fr = df_add_f(F.re, 1.0f);
+    const df2 Li = df_mul(L, inv);
+    gpx = df_mul(Li, df_add(df_mul(fr, px), df_mul(F.im, py)));
+    gpy = df_mul(Li, df_sub(df_mul(fr, py), df_mul(F.im, px)));
+    // K = log|P| + Re log(1 - u)/2 + i Im F1
+    df2 lg = df_log(rho2, tlog);
+    lg.hi *= 0.5f;
+    lg.lo *= 0.5f;
+    df2 rl = df_add(u.re, mkdf(0.5f * u2.re.hi, 0.5f * u2.re.lo));
+    rl = fast_two_sum(rl.hi, __fadd_rn(rl.lo, tLr));  // -Re log(1 - u)
+    const df2 Kr = df_sub(lg, mkdf(0.5f * rl.hi, 0.5f * rl.lo));
+    const df2 Ki = F.im;
+    // dG/db = -gp/2 + t K
+    gbx = df_sub(df_sub(df_mul(tx, Kr), df_mul(ty, Ki)), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo));
+    gby = df_sub(df_add(df_mul(ty, Kr), df_mul(tx, Ki)), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo));
+    return;
+  }
+  // near field, panel frame (n = t rotated by +90 degrees)
+  const df2 zeta = df_add(df_mul(px, tx), df_mul(py, ty));
+  const df2 eta = df_sub(df_mul(py, tx), df_mul(px, ty));
+  const df2 half = mkdf(0.5f * L.hi, 0.5f * L.lo);
+  const df2 xi = df_add(zeta, half);
+  const df2 a2 = df_sub(zeta, half);
+  const df2 eta2 = df_sqr(eta);
+  const df2 l1 = df_log(df_add(df_sqr(xi), eta2), tlog);
+  const df2 l2 = df_log(df_add(df_sqr(a2), eta2), tlog);
+  df2 th = mkdf(0.0f);
+  if (!self) {
+    const df2 quarterL2 = df_mul_f(pf(s, ld, kQ6, i), 6.0f);
+    th = df_atan2(df_mul(L, eta), df_sub(rho2, quarterL2), tatan);
+  }
+  df2 hd = df_sub(l1, l2);
+  hd.hi *= 0.5f;
+  hd.lo *= 0.5f;
+  gpx = df_sub(df_mul(hd, tx), df_mul(th, ty));
+  gpy = df_add(df_mul(hd, ty), df_mul(th, tx));
+  const df2 cn = df_div(df_sub(df_mul(hd, eta), df_mul(th, xi)), L);
+  const df2 hl2 = mkdf(0.5f * l2.hi, 0.5f * l2.lo);
+  gbx = df_sub(df_mul(hl2, tx), df_mul(cn, ty));
+  gby = df_add(df_mul(hl2, ty), df_mul(cn, tx));
+}
+
+__device__ __forceinline__ df2 warp_sum_df2(df2 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    a = df_add(a, mkdf(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)));
+  return a;
+}
+
+__global__ void __launch_bounds__(256) k_adjoint_df(
+    Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
+    const double* __restrict__ alpha, const double* __restrict__ vinf,
+    const double* __restrict__ chord, const double* __restrict__ grad_cl,
+    double* __restrict__ grad, const int32_t* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = bt.n_max;
+  float4* tlog = reinterpret_cast<float4*>(smraw);        // 257
+  float2* tatan = reinterpret_cast<float2*>(tlog + 257);  // 34
+  double* xs = reinterpret_cast<double*>(tatan + 34);     // n_max
+  double* ys = xs + ld;
+  double* P = ys + ld;                                    // 2 n_max (FP64 row sums)
+  double* Ac = P + 2 * ld;                                // 2 n_max
+  double* Bc = Ac + 2 * ld;                               // 2 n_max
+  float* lamh = reinterpret_cast<float*>(Bc + 2 * ld);    // n_max (lambda as float pairs)
+  float* laml = lamh + ld;
+  float* pc = laml + ld;                                  // kPanelFields * n_max
+
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  double* gout = grad + 2 * bt.node_off[b];
+  if ((info && info[b] != 0) || n > ld || n < 3) {
+    for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) gout[k] = nan("");
+    return;
+  }
+  const double* nodes = bt.nodes + 2 * bt.node_off[b];
+  const double* ub = u + vec_off(bt, b);
+  const double* lb = lambda + vec_off(bt, b);
+  df_stage_tables(tlog, tatan);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    xs[k] = nodes[2 * k];
+    ys[k] = nodes[2 * k + 1];
+    P[2 * k] = P[2 * k + 1] = 0.0;
+    const df2 l = df_from_double(lb[k]);
+    lamh[k] = l.hi;
+    laml[k] = l.lo;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int k1 = (k + 1 == n) ? 0 : k + 1;
+    panel_constants(pc, ld, k, xs[k], ys[k], xs[k1], ys[k1]);
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ncb = (n + 31) >> 5;
+  for (int cb = warp; cb < ncb; cb += nw) {
+    const int i = cb * 32 + lane;
+    const bool ok = i < n;
+    const int ii = ok ? i : n - 1;
+    const df2 ui = ok ? df_from_double(ub[ii]) : mkdf(0.0f);
+    df2 sAx = mkdf(0.0f), sAy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+    for (int j = 0; j < n; ++j) {
+      const point3 pj = load_point(pc, ld, j);
+      df2 gpx, gpy, gbx, gby;
+      panel_dG_df(pj, pc, ld, ii, ii == j, tlog, tatan, gpx, gpy, gbx, gby);
+      const df2 lj = mkdf(lamh[j], laml[j]);
+      // A_i += lambda_j (-gp - gb), B_i += lambda_j gb
+      sBx = df_add(sBx, df_mul(lj, gbx));
+      sBy = df_add(sBy, df_mul(lj, gby));
+      sAx = df_sub(sAx, df_mul(lj, df_add(gpx, gbx)));
+      sAy = df_sub(sAy, df_mul(lj, df_add(gpy, gby)));
+      df2 rx = ok ? df_mul(ui, gpx) : mkdf(0.0f);
+      df2 ry = ok ? df_mul(ui, gpy) : mkdf(0.0f);
+      rx = warp_sum_df2(rx);
+      ry = warp_sum_df2(ry);
+      if (lane == 0) {
+        atomicAdd(&P[2 * j], (double)rx.hi + (double)rx.lo);
+        atomicAdd(&P[2 * j + 1], (double)ry.hi + (double)ry.lo);
+      }
+    }
+    if (ok) {
+      Ac[2 * i] = df_to_double(sAx);
+      Ac[2 * i + 1] = df_to_double(sAy);
+      Bc[2 * i] = df_to_double(sBx);
+      Bc[2 * i + 1] = df_to_double(sBy);
+    }
+  }
+  __syncthreads();
+  const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
+  const double ca = cos(alpha[b]), sa = sin(alpha[b]);
+  const double gscale = grad_cl ? grad_cl[b] : 1.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int km = (k == 0) ? n - 1 : k - 1;
+    const int k1 = (k + 1 == n) ? 0 : k + 1;
+    // unit tangents of panels k-1 and k from the FP64 nodes
+    const double hkx = xs[k1] - xs[k], hky = ys[k1] - ys[k];
+    const double hmx = xs[k] - xs[km], hmy = ys[k] - ys[km];
+    const double Lk = sqrt(hkx * hkx + hky * hky), Lm = sqrt(hmx * hmx + hmy * hmy);
+    double gx = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
+    double gy = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
+    gx += 0.5 * v * (-sa) * (lb[km] + lb[k]);
+    gy += 0.5 * v * ca * (lb[km] + lb[k]);
+    gx += kInvTwoPi * (0.5 * (lb[km] * P[2 * km] + lb[k] * P[2 * k]) + ub[k] * Ac[2 * k] +
+                       ub[km] * Bc[2 * km]);
+    gy += kInvTwoPi * (0.5 * (lb[km] * P[2 * km + 1] + lb[k] * P[2 * k + 1]) +
+                       ub[k] * Ac[2 * k + 1] + ub[km] * Bc[2 * km + 1]);
+    gout[2 * k] = gscale * gx;
+    gout[2 * k + 1] = gscale * gy;
+  }
+}
+
+size_t adjoint_df_smem(int n_max) {
+  return 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
+         (size_t)kPanelFields * n_max * 4;
+}
+
+cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* lambda,
+                              const double* alpha, const double* vinf, const double* chord,
+                              const double* grad_cl, double* grad, const int32_t* info,
+                              cudaStream_t s) {
+  const size_t smem = adjoint_df_smem(bt.n_max);
+  cudaError_t e = cudaFuncSetAttribute(k_adjoint_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_adjoint_df<<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad, info);
+  return cudaGetLastError();
+}
+
+}  // namespace panel

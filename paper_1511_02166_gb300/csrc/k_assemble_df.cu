@@ -1,0 +1,138 @@
+// k_assemble_df.cu -- mixed-precision assembly: the bordered system of Section 2
+// in double-float, stored as two float32 planes A = A_hi + A_lo.
+//
+// One block per airfoil (launched in size order).  Prologue: validate the
+// geometry (FP64), build the per-panel constants in shared memory and stage the
+// log/atan tables.  Main loop: pairs (j, i) in row-major order, consecutive
+// threads on consecutive columns, so each warp writes contiguous runs of both
+// planes.  The right-hand side phi_v(x_{j+1/2}) is FP64.
+#include "panel_common.cuh"
+#include "panel_df.cuh"
+
+namespace panel {
+
+__global__ void __launch_bounds__(256) k_assemble_df(Batch bt, const double* __restrict__ alpha,
+                                                     const double* __restrict__ vinf,
+                                                     float* __restrict__ A_hi,
+                                                     float* __restrict__ A_lo,
+                                                     double* __restrict__ rhs,
+                                                     int32_t* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = bt.n_max;
+  float4* tlog = reinterpret_cast<float4*>(smraw);                   // 257
+  float2* tatan = reinterpret_cast<float2*>(tlog + 257);             // 33 (+1 pad)
+  double* xs = reinterpret_cast<double*>(tatan + 34);                // n_max
+  double* ys = xs + ld;                                              // n_max
+  double* scratch = ys + ld;                                         // 32
+  float* pc = reinterpret_cast<float*>(scratch + 32);                // 20 * n_max
+
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const int m = n + 1;
+  if (n > ld) {
+    if (threadIdx.x == 0) info[b] = PANEL_INFO_TOO_LARGE;
+    return;
+  }
+  const double* nodes = bt.nodes + 2 * bt.node_off[b];
+  const int st = load_and_check_geometry(nodes, n, xs, ys, scratch);
+  if (threadIdx.x == 0) info[b] = st;
+  if (st != 0) return;
+  df_stage_tables(tlog, tatan);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int k1 = (k + 1 == n) ? 0 : k + 1;
+    panel_constants(pc, ld, k, xs[k], ys[k], xs[k1], ys[k1]);
+  }
+  const double v = vinf ? vinf[b] : 1.0;
+  const double ca = cos(alpha[b]), sa = sin(alpha[b]);
+  double* rb = rhs + vec_off(bt, b);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    if (j < n) {
+      const int j1 = (j + 1 == n) ? 0 : j + 1;
+      rb[j] = v * (0.5 * (ys[j] + ys[j1]) * ca - 0.5 * (xs[j] + xs[j1]) * sa);
+    } else {
+      rb[j] = 0.0;
+    }
+  }
+  __syncthreads();
+
+  const int64_t base = bt.mat_off[b];
+  float* Ah = A_hi + base;
+  float* Al = A_lo + base;
+  // border: C column of ones and the Kutta row (gamma_0 + gamma_{n-1} = 0)
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    if (j < n) {
+      Ah[(int64_t)j * m + n] = 1.0f;
+      Al[(int64_t)j * m + n] = 0.0f;
+    }
+    Ah[(int64_t)n * m + j] = (j == 0 || j == n - 1) ? 1.0f : 0.0f;
+    Al[(int64_t)n * m + j] = 0.0f;
+  }
+  // pairs (j, i), j, i < n, row-major over the threads of the block
+  const int stride = blockDim.x;
+  const int dj = stride / n, di = stride % n;
+  int j = threadIdx.x / n, i = threadIdx.x % n;
+  point3 pj = load_point(pc, ld, j < n ? j : 0);
+  while (j < n) {
+    const df2 g = panel_G_df(pj, pc, ld, i, tlog, tatan);
+    const int64_t e = (int64_t)j * m + i;
+    Ah[e] = -g.hi;
+    Al[e] = -g.lo;
+    const int jo = j;
+    i += di;
+    j += dj;
+    if (i >= n) {
+      i -= n;
+      ++j;
+    }
+    if (j != jo && j < n) pj = load_point(pc, ld, j);
+  }
+}
+
+size_t assemble_df_smem(int n_max) {
+  return 257 * 16 + 34 * 8 + (size_t)(2 * n_max + 32) * 8 + (size_t)kPanelFields * n_max * 4;
+}
+
+cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const double* vinf,
+                               float* A_hi, float* A_lo, double* rhs, int32_t* info,
+                               cudaStream_t s) {
+  const size_t smem = assemble_df_smem(bt.n_max);
+  cudaError_t e = cudaFuncSetAttribute(k_assemble_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic evaluation of the double-float primitives on arrays (panel_df_eval)
+// ---------------------------------------------------------------------------
+__global__ void k_df_eval(int op, int count, const double* __restrict__ a,
+                          const double* __restrict__ b, double* __restrict__ out) {
+  __shared__ float4 tlog[257];
+  __shared__ float2 tatan[34];
+  __shared__ float pc[kPanelFields * 256];  // 22.5 KB
+  df_stage_tables(tlog, tatan);
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  if (op == 0) {
+    out[k] = df_to_double(df_log(df_from_double(a[k]), tlog));
+  } else if (op == 1) {
+    out[k] = df_to_double(df_atan2(df_from_double(a[k]), df_from_double(b[k]), tatan));
+  } else {
+    // op 2: A coefficient -G for control point a[2k..] and panel b[4k..4k+3]
+    const int t = threadIdx.x;
+    panel_constants(pc, 256, t, b[4 * k], b[4 * k + 1], b[4 * k + 2], b[4 * k + 3]);
+    const df2 g = panel_G_df(make_point(a[2 * k], a[2 * k + 1]), pc, 256, t, tlog, tatan);
+    out[k] = -df_to_double(g);
+  }
+}
+
+cudaError_t launch_df_eval(int op, int count, const double* a, const double* b, double* out,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_df_eval<<<(count + 255) / 256, 256, 0, s>>>(op, count, a, b, out);
+  return cudaGetLastError();
+}
+
+}  // namespace panel

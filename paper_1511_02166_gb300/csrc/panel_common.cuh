@@ -14,6 +14,9 @@ namespace panel {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
+// Node coordinates must be finite and below this magnitude (the split of
+// coordinates into float32 triples in the mixed path relies on it).
+constexpr double kCoordLimit = 1024.0;
 
 // Launch-side view of a batch.  All pointers are device memory.
 struct Batch {
@@ -93,7 +96,7 @@ __device__ __forceinline__ int load_and_check_geometry(const double* nodes, int 
     double x = nodes[2 * k], y = nodes[2 * k + 1];
     xs[k] = x;
     ys[k] = y;
-    if (!isfinite(x) || !isfinite(y)) bad = 1.0;
+    if (!(fabs(x) < kCoordLimit) || !(fabs(y) < kCoordLimit)) bad = 1.0;  // also NaN/inf
   }
   if (block_max(bad, scratch) > 0.0) return PANEL_INFO_NONFINITE;  // (syncs)
   double zero = 0.0, area = 0.0;

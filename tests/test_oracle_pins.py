@@ -538,3 +538,17 @@ def test_batch_matches_single_and_flags_bad_geometry():
     g, info = oracle.cl_gradient_batch(p2.nodes, p2.offsets[:3], p2.alpha[:2], nthreads=2)
     g0, _ = oracle.cl_gradient(good[0], pop.alpha[0])
     assert np.array_equal(g[:len(good[0])], g0)
+
+
+def test_refined_solution_has_tiny_extended_residual():
+    # The oracle refines its FP64 LU solution with long-double residuals, so u
+    # solves the FP64-assembled system to ~1e-15 even where cond(M) ~ 1e6.
+    pop = inputs.make_population("uneven_b10000_n64_512", batch=12)
+    b = int(np.argmax(pop.sizes))
+    nodes = pop.airfoil(b)
+    r = oracle.evaluate(nodes, pop.alpha[b])
+    M, rhs = oracle.assemble(nodes, pop.alpha[b])
+    Ml = M.astype(np.longdouble)
+    res = rhs.astype(np.longdouble) - Ml @ r["u"].astype(np.longdouble)
+    scale = np.abs(Ml).sum(1).max() * np.abs(r["u"]).max()
+    assert float(np.abs(res).max() / scale) < 4e-17
