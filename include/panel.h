@@ -121,9 +121,10 @@ int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64
  *   PANEL_FP64:  reads A64; LU [sum m_b^2] f64 receives the factors (L unit
  *                lower, U upper, row-major, in one array); no refinement.
  *   PANEL_MIXED: reads A_hi, A_lo; LU [sum m_b^2] f32 receives the FP32
- *                factors of the rescaled matrix (may be NULL when
- *                PANEL_WITH_ADJOINT is set and no later panel_adjoint call
- *                needs them).
+ *                factors of the rescaled matrix in a library-internal layout
+ *                (row-major L\U with every 32 x 32 diagonal block of L and of
+ *                U replaced by its inverse), used by the refinement and by
+ *                panel_adjoint.
  *   piv [sum m_b] i32 receives the pivot rows (LAPACK style, 0-based).
  *   rhs [sum m_b] f64; u [sum m_b] f64 receives (gamma, C).
  *   lambda [sum m_b] f64 or NULL: with PANEL_WITH_ADJOINT receives the

@@ -23,9 +23,11 @@ cudaError_t launch_forces(const Batch&, const double*, const double*, const doub
                           cudaStream_t);
 cudaError_t launch_assemble_df(const Batch&, const double*, const double*, float*, float*,
                                double*, int32_t*, cudaStream_t);
-cudaError_t launch_solve_mixed(const Batch&, const float*, const float*, float*, int32_t*,
-                               const double*, const double*, const double*, double*, int, double,
-                               int32_t*, int32_t*, int, cudaStream_t);
+cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_t*, int32_t*,
+                            cudaStream_t);
+cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
+                            const int32_t*, const double*, const double*, const double*, double*,
+                            double*, int, double, int32_t*, int32_t*, cudaStream_t);
 cudaError_t launch_df_eval(int, int, const double*, const double*, double*, cudaStream_t);
 size_t adjoint_df_smem(int n_max);
 constexpr size_t kMaxDynSmem = 232448;
@@ -136,13 +138,11 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
     return status_of(panel::launch_solve_f64(bt, A64, (double*)LU, piv, rhs, vinf, chord, u,
                                              adj ? lambda : nullptr, info, iters, s));
   }
-  if (!A_hi || !A_lo || max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
-  if (!LU) return PANEL_EINVAL;
-  cudaError_t e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, piv, rhs, vinf, chord, u,
-                                            max_iter, tol, info, iters, 0, s);
-  if (e == cudaSuccess && adj)
-    e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, piv, rhs, vinf, chord, lambda,
-                                  max_iter, tol, info, nullptr, 1, s);
+  if (!A_hi || !A_lo || !LU || max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
+  cudaError_t e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters, s);
+  if (e == cudaSuccess)
+    e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
+                               adj ? lambda : nullptr, max_iter, tol, info, iters, s);
   return status_of(e);
 }
 
@@ -182,9 +182,9 @@ int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_
   const double* lam = lambda_in;
   if (!lam) {
     if (max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
-    cudaError_t e = panel::launch_solve_mixed(bt, A_hi, A_lo, (float*)LU, (int32_t*)piv, nullptr,
-                                              vinf, chord, lambda_out, max_iter, tol, info,
-                                              nullptr, 1, s);
+    cudaError_t e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, nullptr, vinf,
+                                           chord, nullptr, lambda_out, max_iter, tol, info,
+                                           nullptr, s);
     if (e != cudaSuccess) return PANEL_ECUDA;
     lam = lambda_out;
   }

@@ -5,21 +5,28 @@
 // C column and S_r the Kutta row by s = mean |A_jj| (the self-influence scale);
 // this balances the border against the influence coefficients and lowers the
 // condition number seen by the FP32 factor.  Refinement (Wilkinson/Moler):
-//   x_0 = solve(b);  r_k = b - M x_k  in double-float from the stored planes
-//   A_hi + A_lo;  x_{k+1} = x_k + solve(r_k), until |dx|_inf <= tol |x|_inf.
-// The transposed system M^T lambda = g (g = dCl/du) is refined the same way.
+//   x_0 = solve(b);  r_k = b - M x_k  with products and sums exact to ~2^-70
+//   against the stored planes A_hi + A_lo;  x_{k+1} = x_k + solve(r_k), until
+//   |dx|_inf <= tol |x|_inf.  The transposed system M^T lambda = g (g = dCl/du)
+//   is refined in the same kernel.
 //
-// Factorisation: right-looking, panels of NB = 32 columns.  SMEM = true (the
-// whole m x m factor in shared memory, m <= kSmemM): thread t keeps row t of
-// the panel in 32 registers; per column one shuffle argmax per warp, the warp
-// winners meet in shared memory, the pivot row is broadcast through shared
-// memory and every row below updates its registers (two block barriers per
-// column).  SMEM = false (factor in the caller's LU buffer in global memory,
-// any m): the panel lives in memory and every warp runs the pivot search.
-// After a panel, its row exchanges are applied to the other columns,
-// U12 = L11^{-1} A12 is formed (a column per thread) and A22 -= L21 U12 runs as
-// a register-tiled rank-32 update (8 rows x 4 columns per thread, columns
-// lane-interleaved so that shared-memory loads are conflict-free).
+// Two kernels:
+//  k_lu_mixed  one block per airfoil.  For m <= kSmemM the matrix is copied
+//    into shared memory (cp.async) and factored there; beyond, it is factored
+//    in place in the caller's LU buffer.  Right-looking, panels of 32 columns:
+//    in the shared-memory variant thread t keeps row t of the panel in 32
+//    registers (shifted left after every column, so that no register index is
+//    dynamic and the loop stays rolled); per column one shuffle argmax per warp,
+//    two block barriers, the pivot row broadcast through shared memory.  Then
+//    the panel's row exchanges are applied to the other columns, U12 =
+//    L11^{-1} A12 is formed (a column per lane) and A22 -= L21 U12 runs as a
+//    register-tiled rank-32 update (8 rows x 4 columns per thread).  Finally
+//    the 32 x 32 diagonal blocks of L and U are replaced by their inverses, so
+//    that the triangular solves below are matrix-vector products.  The stored
+//    LU buffer therefore holds this library-internal layout.
+//  k_ir_mixed  one small block per airfoil (many per SM): triangular solves
+//    with the stored factor (read through L1/L2) and the refinement residuals
+//    (one pass over the rows for M u, one over the columns for M^T lambda).
 #include "df.cuh"
 #include "panel_common.cuh"
 
@@ -39,17 +46,14 @@ struct SolveArgs {
   const double* rhs;
   const double* vinf;
   const double* chord;
-  double* out;       // u (forward) or lambda (transposed)
+  double* u;         // forward solution (may be NULL: no forward system)
+  double* lam;       // transposed solution (may be NULL: no transposed system)
   int max_iter;
   double tol;
   int32_t* info;
   int32_t* iters;
-  int trans;         // 0: M x = b, 1: M^T x = g (reuses the factor in LU/piv)
 };
 
-// ---------------------------------------------------------------------------
-// block-level helpers
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ double block_absmax_d(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   v = warp_max(v);
@@ -60,6 +64,13 @@ __device__ __forceinline__ double block_absmax_d(double v, double* red) {
   for (int w = 0; w < kWarps; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
+}
+
+// border scale s = mean |A_jj| over the influence block (hi plane)
+__device__ __forceinline__ double border_scale(const float* Ah, int n, int m, double* red) {
+  double sdiag = 0.0;
+  for (int j = threadIdx.x; j < n; j += kThreads) sdiag += fabs((double)Ah[j * m + j]);
+  return block_sum(sdiag, red) / n;
 }
 
 // ---------------------------------------------------------------------------
@@ -82,8 +93,8 @@ __device__ __forceinline__ void apply_panel_swaps(float* F, int ld, int m, int k
 }
 
 // U12 = L11^{-1} A12 (L11 unit lower kb x kb), one column per lane.  The base
-// of L11 is passed through an opaque move each column block, so that the 496
-// loads of L11 are not hoisted out of the loop into registers.
+// of L11 goes through an opaque move per column block so that its loads are
+// not hoisted out of the loop.
 __device__ __forceinline__ void panel_trsm(float* F, int ld, int m, int k0, int kb) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k1 = k0 + kb;
@@ -129,6 +140,7 @@ __device__ __forceinline__ void panel_gemm(float* F, int ld, int m, int k0, int 
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         acc[a][t] = (r0 + a < m && cok[t]) ? F[(r0 + a) * ld + cb + 32 * t] : 0.0f;
+#pragma unroll 2
     for (int q = 0; q < kb; ++q) {
       float lv[8], uv[4];
 #pragma unroll
@@ -154,7 +166,7 @@ __device__ __forceinline__ void panel_gemm(float* F, int ld, int m, int k0, int 
 // Returns 0 or k+1 for an exactly zero pivot (uniform over the block).
 // ---------------------------------------------------------------------------
 __device__ int lu_rowpanel(float* F, int ld, int m, int* ipiv, float* prow, float* krow,
-                           float* cand_v, int* cand_i) {
+                           unsigned long long* cand) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool has = t < m;
   for (int k0 = 0; k0 < m; k0 += kNB) {
@@ -162,61 +174,72 @@ __device__ int lu_rowpanel(float* F, int ld, int m, int* ipiv, float* prow, floa
     float a[kNB];
 #pragma unroll
     for (int q = 0; q < kNB; ++q) a[q] = (has && q < kb) ? F[t * ld + k0 + q] : 0.0f;
+    for (int q = 0; q < kb; ++q) {
+      const int k = k0 + q;
+      float4* pr = reinterpret_cast<float4*>(prow + (q & 1) * kNB);
+      float4* kr = reinterpret_cast<float4*>(krow + (q & 1) * kNB);
+      // warp argmax of |a_tk| over rows t >= k, ties to the lowest row: the key
+      // is the float's bit pattern + 1 (monotone for |x|; 0 marks no candidate)
+      const unsigned key = (has && t >= k) ? __float_as_uint(fabsf(a[0])) + 1u : 0u;
+      const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+      const unsigned win = __ffs(__ballot_sync(0xffffffffu, key == mx)) - 1;
+      if (lane == 0)
+        cand[(q & 1) * kWarps + warp] =
+            ((unsigned long long)mx << 32) | (unsigned)(0x7fffffff - (warp * 32 + (int)win));
+      __syncthreads();
+      unsigned long long best = 0;
 #pragma unroll
-    for (int q = 0; q < kNB; ++q) {
-      if (q < kb) {
-        const int k = k0 + q;
-        float v = (has && t >= k) ? fabsf(a[q]) : -1.0f;
-        int vi = t;
+      for (int w = 0; w < kWarps; ++w) best = max(best, cand[(q & 1) * kWarps + w]);
+      if ((unsigned)(best >> 32) <= 1u) return k + 1;  // no candidate or |pivot| = 0
+      const int p = 0x7fffffff - (int)(best & 0xffffffffu);
+      if (t == p) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
-          if (ov > v || (ov == v && oi < vi)) { v = ov; vi = oi; }
+        for (int c = 0; c < kNB / 4; ++c)
+          pr[c] = make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
+      }
+      if (t == k) {
+#pragma unroll
+        for (int c = 0; c < kNB / 4; ++c)
+          kr[c] = make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
+        ipiv[k] = p;
+      }
+      __syncthreads();
+      if (p != k) {
+        if (t == k || t == p) {
+          const float4* src = (t == k) ? pr : kr;
+#pragma unroll
+          for (int c = 0; c < kNB / 4; ++c) {
+            const float4 v = src[c];
+            a[4 * c] = v.x;
+            a[4 * c + 1] = v.y;
+            a[4 * c + 2] = v.z;
+            a[4 * c + 3] = v.w;
+          }
         }
-        if (lane == 0) {
-          cand_v[warp] = v;
-          cand_i[warp] = vi;
-        }
-        __syncthreads();
-        float best = -1.0f;
-        int p = k;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-          const float cv = cand_v[w];
-          const int ci = cand_i[w];
-          if (cv > best || (cv == best && ci < p)) { best = cv; p = ci; }
-        }
-        if (best <= 0.0f) return k + 1;
-        if (t == p) {
-#pragma unroll
-          for (int c = 0; c < kNB; ++c) prow[c] = a[c];
-        }
-        if (t == k) {
-#pragma unroll
-          for (int c = 0; c < kNB; ++c) krow[c] = a[c];
-          ipiv[k] = p;
-        }
-        __syncthreads();
-        if (t == k && p != k) {
-#pragma unroll
-          for (int c = 0; c < kNB; ++c) a[c] = prow[c];
-        }
-        if (t == p && p != k) {
-#pragma unroll
-          for (int c = 0; c < kNB; ++c) a[c] = krow[c];
-        }
-        if (has && t > k) {
-          const float l = a[q] / prow[q];
-          a[q] = l;
-#pragma unroll
-          for (int c = q + 1; c < kNB; ++c) a[c] = fmaf(-l, prow[c], a[c]);
+        // exchange the already finished multipliers of rows k and p
+        if (warp == 0 && lane < q) {
+          const float x = F[k * ld + k0 + lane];
+          F[k * ld + k0 + lane] = F[p * ld + k0 + lane];
+          F[p * ld + k0 + lane] = x;
         }
       }
-    }
+      const float* pv = prow + (q & 1) * kNB;
+      // row k is final within the panel: U[k][k..k0+kb)
+      if (warp == kWarps - 1 && lane < kb - q) F[k * ld + k + lane] = pv[lane];
+      if (has && t > k) {
+        const float l = a[0] * __frcp_rn(pv[0]);
+        F[t * ld + k] = l;
 #pragma unroll
-    for (int q = 0; q < kNB; ++q)
-      if (has && q < kb) F[t * ld + k0 + q] = a[q];
+        for (int c = 0; c < kNB / 4; ++c) {
+          const float4 v = pr[c];
+          if (c > 0) a[4 * c - 1] = fmaf(-l, v.x, a[4 * c]);
+          a[4 * c] = fmaf(-l, v.y, a[4 * c + 1]);
+          a[4 * c + 1] = fmaf(-l, v.z, a[4 * c + 2]);
+          a[4 * c + 2] = fmaf(-l, v.w, a[4 * c + 3]);
+        }
+        a[kNB - 1] = 0.0f;
+      }
+    }
     __syncthreads();
     apply_panel_swaps(F, ld, m, k0, kb, ipiv);
     __syncthreads();
@@ -283,93 +306,221 @@ __device__ int lu_blocked(float* F, int ld, int m, int* ipiv) {
 }
 
 // ---------------------------------------------------------------------------
-// Triangular solves with the factor, on a float vector y (shared memory).
-// Blocks of 32 rows: warp 0 solves the diagonal block with shuffles, then all
-// threads update the rows below (or above) with that block.
+// Inverted diagonal blocks, in place, one warp per 32 x 32 block (lane j =
+// column j of the inverse).  X = L_dd^{-1} (unit lower) replaces the part
+// below the diagonal row by row (row i is written after every lane has read
+// it); Y = U_dd^{-1} (upper) replaces the rest row by row from the bottom.
+// ---------------------------------------------------------------------------
+__device__ void invert_diagonal_blocks(float* F, int ld, int m) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = (m + 31) >> 5;
+  for (int d = warp; d < nb; d += kWarps) {
+    const int k0 = 32 * d;
+    const int kb = min(32, m - k0);
+    float* B = F + k0 * ld + k0;
+    const int j = lane;
+    // X[i][j] = -(L[i][j] + sum_{j<k<i} L[i][k] X[k][j]),  i > j
+    for (int i = 1; i < kb; ++i) {
+      float x = 0.0f;
+      if (j < i) {
+        x = -B[i * ld + j];
+        for (int k = j + 1; k < i; ++k) x = fmaf(-B[i * ld + k], B[k * ld + j], x);
+      }
+      __syncwarp();
+      if (j < i) B[i * ld + j] = x;
+      __syncwarp();
+    }
+    // Y[i][j] = -(sum_{i<k<=j} U[i][k] Y[k][j]) / U[i][i] (i < j), Y[j][j] = 1/U[j][j]
+    for (int i = kb - 1; i >= 0; --i) {
+      float y = 0.0f;
+      const float uii = B[i * ld + i];
+      if (j == i) {
+        y = 1.0f / uii;
+      } else if (j > i && j < kb) {
+        float acc = 0.0f;
+        for (int k = i + 1; k <= j; ++k) acc = fmaf(B[i * ld + k], B[k * ld + j], acc);
+        y = -acc / uii;
+      }
+      __syncwarp();
+      if (j >= i && j < kb) B[i * ld + j] = y;
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The LU kernel
+// ---------------------------------------------------------------------------
+template <bool SMEM>
+__global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const int m = n + 1;
+  if (a.info[b] != 0) return;
+  if (SMEM != (m <= kSmemM)) return;  // each airfoil is taken by one variant
+  if (n > bt.n_max) {
+    if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
+    return;
+  }
+  double* red = reinterpret_cast<double*>(smraw);      // 32
+  int* ipiv = reinterpret_cast<int*>(red + 32);         // n_max + 1
+  float* prow = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(ipiv + bt.n_max + 1) + 15) & ~(uintptr_t)15);  // 2 kNB
+  float* krow = prow + 2 * kNB;                                                    // 2 kNB
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(krow + 2 * kNB);  // 2 kWarps
+  float* Fs = reinterpret_cast<float*>(cand + 2 * kWarps);
+
+  const int64_t moff = bt.mat_off[b];
+  const float* Ah = a.A_hi + moff;
+  const int ld = SMEM ? (m | 1) : m;
+  float* F = SMEM ? Fs : (a.LU + moff);
+  const float sf = (float)border_scale(Ah, n, m, red);
+
+  // copy the hi plane (asynchronously into shared memory), rescale the border
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rr = warp; rr < m; rr += kWarps)
+    for (int cc = lane; cc < m; cc += 32) {
+      if (SMEM) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(F + rr * ld + cc);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst),
+                     "l"(Ah + rr * m + cc));
+      } else {
+        F[rr * ld + cc] = Ah[rr * m + cc];
+      }
+    }
+  if (SMEM) asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += kThreads) {
+    if (j < n) F[j * ld + n] *= sf;
+    F[n * ld + j] *= sf;
+  }
+  __syncthreads();
+  const int st = SMEM ? lu_rowpanel(F, ld, m, ipiv, prow, krow, cand)
+                      : lu_blocked(F, ld, m, ipiv);
+  if (st != 0) {
+    if (threadIdx.x == 0) {
+      a.info[b] = st;
+      if (a.iters) a.iters[b] = 0;
+    }
+    return;
+  }
+  invert_diagonal_blocks(F, ld, m);
+  __syncthreads();
+  int32_t* gpiv = a.piv + vec_off(bt, b);
+  for (int k = threadIdx.x; k < m; k += kThreads) gpiv[k] = ipiv[k];
+  if (SMEM) {
+    float* G = a.LU + moff;
+    for (int rr = warp; rr < m; rr += kWarps)
+      for (int cc = lane; cc < m; cc += 32) G[rr * m + cc] = F[rr * ld + cc];
+  }
+}
+
+size_t lu_mixed_smem(int n_max, bool smem_factor, int m_factor) {
+  size_t bytes = 32 * 8 + (size_t)(n_max + 1) * 4 + 16 + 4 * kNB * 4 + 2 * kWarps * 8;
+  bytes = (bytes + 15) & ~(size_t)15;
+  if (smem_factor) bytes += (size_t)m_factor * (size_t)(m_factor | 1) * 4;
+  return bytes;
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves with the stored factor (global memory, ld = m, diagonal
+// blocks inverted), on a float vector y in shared memory.
 // ---------------------------------------------------------------------------
 // y <- L^{-1} y (unit lower) then U^{-1} y.
-__device__ void lu_apply_inverse(const float* F, int ld, int m, float* y) {
+__device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y) {
   const int lane = threadIdx.x & 31;
   for (int k0 = 0; k0 < m; k0 += 32) {
     const int kb = min(32, m - k0);
     if (threadIdx.x < 32) {
-      float v = (lane < kb) ? y[k0 + lane] : 0.0f;
-      for (int t = 0; t < kb; ++t) {
-        const float yt = __shfl_sync(0xffffffffu, v, t);
-        if (lane > t && lane < kb) v = fmaf(-F[(k0 + lane) * ld + k0 + t], yt, v);
+      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
+      float z = yl;
+      const float* row = F + (k0 + min(lane, kb - 1)) * m + k0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float yk = __shfl_sync(0xffffffffu, yl, k);
+        if (k < lane && lane < kb) z = fmaf(__ldg(row + k), yk, z);
       }
-      if (lane < kb) y[k0 + lane] = v;
+      if (lane < kb) y[k0 + lane] = z;
     }
     __syncthreads();
     for (int r = k0 + kb + threadIdx.x; r < m; r += kThreads) {
-      float s = y[r];
-      for (int t = 0; t < kb; ++t) s = fmaf(-F[r * ld + k0 + t], y[k0 + t], s);
-      y[r] = s;
+      const float* row = F + r * m + k0;
+      float acc = y[r];
+#pragma unroll 8
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(row + t), y[k0 + t], acc);
+      y[r] = acc;
     }
     __syncthreads();
   }
-  for (int k1 = m; k1 > 0; k1 -= 32) {
-    const int k0 = max(0, k1 - 32);
-    const int kb = k1 - k0;
+  for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
+    const int kb = min(32, m - k0);
     if (threadIdx.x < 32) {
-      float v = (lane < kb) ? y[k0 + lane] : 0.0f;
-      for (int t = kb - 1; t >= 0; --t) {
-        float vt = (lane == t) ? v / F[(k0 + t) * ld + k0 + t] : v;
-        const float yt = __shfl_sync(0xffffffffu, vt, t);
-        if (lane == t) v = vt;
-        if (lane < t) v = fmaf(-F[(k0 + lane) * ld + k0 + t], yt, v);
+      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
+      float z = 0.0f;
+      const float* row = F + (k0 + min(lane, kb - 1)) * m + k0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float yk = __shfl_sync(0xffffffffu, yl, k);
+        if (k >= lane && k < kb) z = fmaf(__ldg(row + k), yk, z);
       }
-      if (lane < kb) y[k0 + lane] = v;
+      if (lane < kb) y[k0 + lane] = z;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < k0; r += kThreads) {
-      float s = y[r];
-      for (int t = 0; t < kb; ++t) s = fmaf(-F[r * ld + k0 + t], y[k0 + t], s);
-      y[r] = s;
+      const float* row = F + r * m + k0;
+      float acc = y[r];
+#pragma unroll 8
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(row + t), y[k0 + t], acc);
+      y[r] = acc;
     }
     __syncthreads();
   }
 }
 
-// y <- U^{-T} y (lower, non-unit) then L^{-T} y (unit upper).
-__device__ void lu_apply_inverse_transposed(const float* F, int ld, int m, float* y) {
+// y <- U^{-T} y (lower) then L^{-T} y (unit upper).
+__device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, float* y) {
   const int lane = threadIdx.x & 31;
   for (int k0 = 0; k0 < m; k0 += 32) {
     const int kb = min(32, m - k0);
     if (threadIdx.x < 32) {
-      float v = (lane < kb) ? y[k0 + lane] : 0.0f;
-      for (int t = 0; t < kb; ++t) {
-        float vt = (lane == t) ? v / F[(k0 + t) * ld + k0 + t] : v;
-        const float yt = __shfl_sync(0xffffffffu, vt, t);
-        if (lane == t) v = vt;
-        if (lane > t && lane < kb) v = fmaf(-F[(k0 + t) * ld + k0 + lane], yt, v);
+      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
+      float z = 0.0f;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float yk = __shfl_sync(0xffffffffu, yl, k);
+        if (k <= lane && lane < kb) z = fmaf(__ldg(F + (k0 + k) * m + k0 + lane), yk, z);
       }
-      if (lane < kb) y[k0 + lane] = v;
+      if (lane < kb) y[k0 + lane] = z;
     }
     __syncthreads();
     for (int r = k0 + kb + threadIdx.x; r < m; r += kThreads) {
-      float s = y[r];
-      for (int t = 0; t < kb; ++t) s = fmaf(-F[(k0 + t) * ld + r], y[k0 + t], s);
-      y[r] = s;
+      float acc = y[r];
+#pragma unroll 8
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
+      y[r] = acc;
     }
     __syncthreads();
   }
-  for (int k1 = m; k1 > 0; k1 -= 32) {
-    const int k0 = max(0, k1 - 32);
-    const int kb = k1 - k0;
+  for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
+    const int kb = min(32, m - k0);
     if (threadIdx.x < 32) {
-      float v = (lane < kb) ? y[k0 + lane] : 0.0f;
-      for (int t = kb - 1; t >= 0; --t) {
-        const float yt = __shfl_sync(0xffffffffu, v, t);
-        if (lane < t) v = fmaf(-F[(k0 + t) * ld + k0 + lane], yt, v);
+      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
+      float z = yl;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float yk = __shfl_sync(0xffffffffu, yl, k);
+        if (k > lane && k < kb) z = fmaf(__ldg(F + (k0 + k) * m + k0 + lane), yk, z);
       }
-      if (lane < kb) y[k0 + lane] = v;
+      if (lane < kb) y[k0 + lane] = z;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < k0; r += kThreads) {
-      float s = y[r];
-      for (int t = 0; t < kb; ++t) s = fmaf(-F[(k0 + t) * ld + r], y[k0 + t], s);
-      y[r] = s;
+      float acc = y[r];
+#pragma unroll 8
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
+      y[r] = acc;
     }
     __syncthreads();
   }
@@ -378,15 +529,6 @@ __device__ void lu_apply_inverse_transposed(const float* F, int ld, int m, float
 // ---------------------------------------------------------------------------
 // Double-float residuals against the stored planes
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ df2 warp_sum_df(df2 a) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    df2 b = mkdf(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
-    a = df_add(a, b);
-  }
-  return a;
-}
-
 // Accumulator for sum_k (h_k + l_k)(xh_k + xl_k) with error ~2^-70 sum|p|:
 // s1 collects the exact leading products h*xh through two_sum (their rounding
 // errors go to s2), s2 (double-float) collects the ~2^-24 terms (the two_prod
@@ -438,33 +580,34 @@ __device__ __forceinline__ double resacc_sub_from(double c, const ResAcc& a) {
 }
 
 // r_j = b_j - sum_i M_ji x_i for all rows j; x given as float pairs (xh, xl).
-// Each warp takes two rows at a time and issues all loads of a 256-column chunk
-// before accumulating, to keep enough bytes in flight.
+// A warp takes two rows at a time and issues all loads of a 256-column chunk
+// before accumulating.
 __device__ void residual_rows(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const double* b, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 2 * warp; j0 < m; j0 += 2 * kWarps) {
-    const bool two = j0 + 1 < m;
     ResAcc acc0, acc1;
     resacc_init(acc0);
     resacc_init(acc1);
+    const bool two = j0 + 1 < m;
     for (int c0 = 0; c0 < m; c0 += 256) {
       float h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = c0 + lane + 32 * q;
+      for (int t = 0; t < 8; ++t) {
+        const int c = c0 + lane + 32 * t;
         const bool ok = c < m;
-        h0[q] = ok ? __ldg(Ah + j0 * m + c) : 0.0f;
-        l0[q] = ok ? __ldg(Al + j0 * m + c) : 0.0f;
-        h1[q] = (ok && two) ? __ldg(Ah + (j0 + 1) * m + c) : 0.0f;
-        l1[q] = (ok && two) ? __ldg(Al + (j0 + 1) * m + c) : 0.0f;
+        h0[t] = ok ? __ldg(Ah + j0 * m + c) : 0.0f;
+        l0[t] = ok ? __ldg(Al + j0 * m + c) : 0.0f;
+        h1[t] = (ok && two) ? __ldg(Ah + (j0 + 1) * m + c) : 0.0f;
+        l1[t] = (ok && two) ? __ldg(Al + (j0 + 1) * m + c) : 0.0f;
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = c0 + lane + 32 * q;
+      for (int t = 0; t < 8; ++t) {
+        const int c = c0 + lane + 32 * t;
         if (c < m) {
-          resacc_add(acc0, h0[q], l0[q], xh[c], xl[c]);
-          resacc_add(acc1, h1[q], l1[q], xh[c], xl[c]);
+          const float xa = xh[c], xb = xl[c];
+          resacc_add(acc0, h0[t], l0[t], xa, xb);
+          resacc_add(acc1, h1[t], l1[t], xa, xb);
         }
       }
     }
@@ -477,274 +620,177 @@ __device__ void residual_rows(const float* __restrict__ Ah, const float* __restr
   }
 }
 
-// r_i = g_i - sum_j M_ji x_j for all columns i.  Warps own 32-column blocks and
-// a share of the rows; partial sums meet in `part` ([kParts][m] accumulators).
-constexpr int kParts = 4;
-__host__ __device__ __forceinline__ int parts_for(int m) {
-  const int ncb = (m + 31) >> 5;
-  const int q = kWarps / ncb;
-  return q < 1 ? 1 : (q > kParts ? kParts : q);
-}
-// Entries of `part` needed by any m <= mv (nparts(m) * m is at most 512 when
-// nparts(m) > 1).
-__host__ __device__ __forceinline__ int parts_entries(int mv) {
-  const int a = 4 * mv < 512 ? 4 * mv : 512;
-  const int b = parts_for(mv) * mv;
-  return a > b ? a : b;
-}
+// r_i = g_i - sum_j M_ji x_j for all columns i: each warp owns 32 consecutive
+// columns (one per lane) and walks all rows, 8 rows of loads in flight.
 __device__ void residual_cols(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
-                              const float* xh, const float* xl, const double* g, double* r,
-                              float4* part) {
+                              const float* xh, const float* xl, const double* g, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ncb = (m + 31) >> 5;
-  const int nparts = parts_for(m);
-  for (int task = warp; task < ncb * nparts; task += kWarps) {
-    const int cb = task % ncb, pt = task / ncb;
-    const int c = cb * 32 + lane;
-    const int j0 = (int)((int64_t)m * pt / nparts), j1 = (int)((int64_t)m * (pt + 1) / nparts);
+  for (int cb = 32 * warp; cb < m; cb += kThreads) {
+    const int c = cb + lane;
+    const bool ok = c < m;
     ResAcc acc;
     resacc_init(acc);
-    if (c < m) {
-      for (int jb = j0; jb < j1; jb += 8) {
-        float h[8], l[8];
+    for (int jb = 0; jb < m; jb += 8) {
+      float h[8], l[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = jb + q;
-          h[q] = (j < j1) ? __ldg(Ah + j * m + c) : 0.0f;
-          l[q] = (j < j1) ? __ldg(Al + j * m + c) : 0.0f;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (jb + q < j1) resacc_add(acc, h[q], l[q], xh[jb + q], xl[jb + q]);
+      for (int q = 0; q < 8; ++q) {
+        const int j = jb + q;
+        h[q] = (ok && j < m) ? __ldg(Ah + j * m + c) : 0.0f;
+        l[q] = (ok && j < m) ? __ldg(Al + j * m + c) : 0.0f;
       }
-      part[pt * m + c] = make_float4(acc.s1, acc.s2.hi, acc.s2.lo, acc.s3);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (jb + q < m) resacc_add(acc, h[q], l[q], xh[jb + q], xl[jb + q]);
     }
+    if (ok) r[c] = resacc_sub_from(g[c], acc);
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < m; c += kThreads) {
-    ResAcc acc;
-    resacc_init(acc);
-    for (int pt = 0; pt < nparts; ++pt) {
-      const float4 q = part[pt * m + c];
-      ResAcc b;
-      b.s1 = q.x;
-      b.s2 = mkdf(q.y, q.z);
-      b.s3 = q.w;
-      resacc_merge(acc, b);
-    }
-    r[c] = resacc_sub_from(g[c], acc);
-  }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// The kernel
+// The refinement kernel: forward and/or transposed system of one airfoil
 // ---------------------------------------------------------------------------
-template <bool SMEM>
-__global__ void __launch_bounds__(kThreads, 1) k_solve_mixed(SolveArgs a) {
+struct IrSystem {
+  double* x;   // m  current solution
+  double* r;   // m  residual
+  double* bb;  // m  right-hand side
+  float* xh;   // m
+  float* xl;   // m
+};
+
+__global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   const int n = airfoil_n(bt, b);
   const int m = n + 1;
-  if (a.info[b] != 0) return;
-  // each airfoil is taken by exactly one of the two variants
-  if (SMEM != (m <= kSmemM)) return;
-  if (n > bt.n_max) {
-    if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
-    return;
+  if (a.info[b] != 0 || n > bt.n_max) return;
+  const int mv = bt.n_max + 1;
+  double* red = reinterpret_cast<double*>(smraw);  // 32
+  IrSystem sys[2];
+  double* dp = red + 32;
+  for (int q = 0; q < 2; ++q) {
+    sys[q].x = dp;
+    sys[q].r = dp + mv;
+    sys[q].bb = dp + 2 * mv;
+    dp += 3 * mv;
   }
-  // shared layout: vectors first, the factor (SMEM) last
-  double* x = reinterpret_cast<double*>(smraw);   // m
-  double* r = x + bt.n_max + 1;                    // m
-  double* bb = r + bt.n_max + 1;                   // m (rhs of this system)
-  float* y = reinterpret_cast<float*>(bb + bt.n_max + 1);  // m
-  float* xh = y + bt.n_max + 1;                    // m
-  float* xl = xh + bt.n_max + 1;                   // m
-  int* ipiv = reinterpret_cast<int*>(xl + bt.n_max + 1);   // m
-  int* perm = ipiv + bt.n_max + 1;                 // m
-  float4* part = reinterpret_cast<float4*>(
-      (reinterpret_cast<uintptr_t>(perm + bt.n_max + 1) + 15) & ~(uintptr_t)15);
-  double* red = reinterpret_cast<double*>(part + parts_entries(bt.n_max + 1));  // 32
-  float* prow = reinterpret_cast<float*>(red + 32);  // kNB
-  float* krow = prow + kNB;                          // kNB
-  float* cand_v = krow + kNB;                        // kWarps
-  int* cand_i = reinterpret_cast<int*>(cand_v + kWarps);  // kWarps
-  float* Fs = reinterpret_cast<float*>(cand_i + kWarps);
+  float* y = reinterpret_cast<float*>(dp);  // m
+  float* fp = y + mv;
+  for (int q = 0; q < 2; ++q) {
+    sys[q].xh = fp;
+    sys[q].xl = fp + mv;
+    fp += 2 * mv;
+  }
+  int* perm = reinterpret_cast<int*>(fp);  // m
 
   const int64_t moff = bt.mat_off[b];
   const float* Ah = a.A_hi + moff;
   const float* Al = a.A_lo + moff;
-  const int ld = SMEM ? (m | 1) : m;
-  float* F = SMEM ? Fs : (a.LU + moff);
-  int32_t* gpiv = a.piv + vec_off(bt, b);
+  const float* F = a.LU + moff;
+  const int32_t* gpiv = a.piv + vec_off(bt, b);
+  const double s = border_scale(Ah, n, m, red);
+  const bool act0 = a.u != nullptr, act1 = a.lam != nullptr;
 
-  // border scale s = mean |A_jj| over the influence block (from the hi plane)
-  double sdiag = 0.0;
-  for (int j = threadIdx.x; j < n; j += kThreads) sdiag += fabs((double)Ah[j * m + j]);
-  const double s = block_sum(sdiag, red) / n;
-  const float sf = (float)s;
-
-  if (!a.trans) {
-    // load the hi plane, rescale the border, factor
-    {
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int rr = warp; rr < m; rr += kWarps)
-        for (int c0 = 0; c0 < m; c0 += 256) {
-          float v[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int cc = c0 + lane + 32 * q;
-            v[q] = cc < m ? Ah[rr * m + cc] : 0.0f;
-          }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int cc = c0 + lane + 32 * q;
-            if (cc < m) F[rr * ld + cc] = ((cc == n && rr < n) || rr == n) ? v[q] * sf : v[q];
-          }
-        }
-    }
-    __syncthreads();
-    const int st = SMEM ? lu_rowpanel(F, ld, m, ipiv, prow, krow, cand_v, cand_i)
-                        : lu_blocked(F, ld, m, ipiv);
-    if (st != 0) {
-      if (threadIdx.x == 0) {
-        a.info[b] = st;
-        if (a.iters) a.iters[b] = 0;
-      }
-      return;
-    }
-    for (int k = threadIdx.x; k < m; k += kThreads) gpiv[k] = ipiv[k];
-    if (SMEM && a.LU) {
-      float* G = a.LU + moff;
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int rr = warp; rr < m; rr += kWarps)
-        for (int cc = lane; cc < m; cc += 32) G[rr * m + cc] = F[rr * ld + cc];
-    }
-    for (int k = threadIdx.x; k < m; k += kThreads) bb[k] = a.rhs[vec_off(bt, b) + k];
-  } else {
-    // reuse the stored factor
-    if (SMEM) {
-      const float* G = a.LU + moff;
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-      for (int rr = warp; rr < m; rr += kWarps)
-        for (int c0 = 0; c0 < m; c0 += 256) {
-          float v[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int cc = c0 + lane + 32 * q;
-            v[q] = cc < m ? G[rr * m + cc] : 0.0f;
-          }
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int cc = c0 + lane + 32 * q;
-            if (cc < m) F[rr * ld + cc] = v[q];
-          }
-        }
-    }
-    for (int k = threadIdx.x; k < m; k += kThreads) ipiv[k] = gpiv[k];
-    // g = dCl/du: 2 |h_k| / (v c) for the strengths, 0 for C
-    const double* nd = bt.nodes + 2 * bt.node_off[b];
-    const double v = a.vinf ? a.vinf[b] : 1.0, c = a.chord ? a.chord[b] : 1.0;
-    for (int k = threadIdx.x; k < m; k += kThreads) {
+  // right-hand sides: b, and g = dCl/du = 2 |h_k| / (v c) (0 for C)
+  const double* nd = bt.nodes + 2 * bt.node_off[b];
+  const double v = a.vinf ? a.vinf[b] : 1.0, cc = a.chord ? a.chord[b] : 1.0;
+  for (int k = threadIdx.x; k < m; k += kThreads) {
+    if (act0) sys[0].bb[k] = a.rhs[vec_off(bt, b) + k];
+    if (act1) {
+      double g = 0.0;
       if (k < n) {
         const int k1 = (k + 1 == n) ? 0 : k + 1;
         const double hx = nd[2 * k1] - nd[2 * k], hy = nd[2 * k1 + 1] - nd[2 * k + 1];
-        bb[k] = 2.0 * sqrt(hx * hx + hy * hy) / (v * c);
-      } else {
-        bb[k] = 0.0;
+        g = 2.0 * sqrt(hx * hx + hy * hy) / (v * cc);
       }
+      sys[1].bb[k] = g;
+    }
+    for (int q = 0; q < 2; ++q) {
+      sys[q].x[k] = 0.0;
+      sys[q].r[k] = sys[q].bb[k];
     }
   }
   // row permutation of the factor: P y = y[perm]
   if (threadIdx.x == 0) {
     for (int k = 0; k < m; ++k) perm[k] = k;
     for (int k = 0; k < m; ++k) {
-      const int p = ipiv[k];
+      const int p = gpiv[k];
       const int t = perm[k];
       perm[k] = perm[p];
       perm[p] = t;
     }
   }
-  for (int k = threadIdx.x; k < m; k += kThreads) {
-    x[k] = 0.0;
-    r[k] = bb[k];
-  }
   __syncthreads();
 
+  bool active[2] = {act0, act1};
+  bool conv[2] = {!act0, !act1};
   int it = 0;
-  bool conv = false;
   for (;; ++it) {
-    if (!a.trans) {
-      // y = P S_r r;  solve;  dx = S_c y
-      for (int k = threadIdx.x; k < m; k += kThreads) {
-        const int src = perm[k];
-        const double v = (src == n) ? r[src] * s : r[src];
-        y[k] = (float)v;
+    for (int q = 0; q < 2; ++q) {
+      if (!active[q] || conv[q]) continue;
+      IrSystem& S = sys[q];
+      if (q == 0) {
+        // y = P S_r r;  solve;  dx = S_c y
+        for (int k = threadIdx.x; k < m; k += kThreads) {
+          const int src = perm[k];
+          y[k] = (float)((src == n) ? S.r[src] * s : S.r[src]);
+        }
+        __syncthreads();
+        lu_apply_inverse(F, m, y);
+      } else {
+        // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
+        for (int k = threadIdx.x; k < m; k += kThreads)
+          y[k] = (float)((k == n) ? S.r[k] * s : S.r[k]);
+        __syncthreads();
+        lu_apply_inverse_transposed(F, m, y);
       }
-      __syncthreads();
-      lu_apply_inverse(F, ld, m, y);
-    } else {
-      // z = Mt^{-T} S_c r;  lambda update = S_r P^T z
-      for (int k = threadIdx.x; k < m; k += kThreads) y[k] = (float)((k == n) ? r[k] * s : r[k]);
-      __syncthreads();
-      lu_apply_inverse_transposed(F, ld, m, y);
-    }
-    double dmax = 0.0, xmax = 0.0;
-    if (!a.trans) {
+      double dmax = 0.0;
       for (int k = threadIdx.x; k < m; k += kThreads) {
-        const double d = (k == n) ? (double)y[k] * s : (double)y[k];
-        x[k] += d;
-        dmax = fmax(dmax, fabs(d));
-        xmax = fmax(xmax, fabs(x[k]));
-      }
-    } else {
-      // y holds the permuted solution: lambda[perm[k]] += y[k] (S_r on row n)
-      for (int k = threadIdx.x; k < m; k += kThreads) {
-        const int dst = perm[k];
+        const int dst = (q == 0) ? k : perm[k];
         const double d = (dst == n) ? (double)y[k] * s : (double)y[k];
-        x[dst] += d;
+        S.x[dst] += d;
         dmax = fmax(dmax, fabs(d));
       }
       __syncthreads();
-      for (int k = threadIdx.x; k < m; k += kThreads) xmax = fmax(xmax, fabs(x[k]));
+      double xmax = 0.0;
+      for (int k = threadIdx.x; k < m; k += kThreads) xmax = fmax(xmax, fabs(S.x[k]));
+      dmax = block_absmax_d(dmax, red);
+      xmax = block_absmax_d(xmax, red);
+      if (it >= 1 && dmax <= a.tol * xmax) conv[q] = true;
     }
-    dmax = block_absmax_d(dmax, red);
-    xmax = block_absmax_d(xmax, red);
-    if (it >= 1 && dmax <= a.tol * xmax) { conv = true; break; }
-    if (it >= a.max_iter) break;
-    // residual against the double-float matrix
-    for (int k = threadIdx.x; k < m; k += kThreads) {
-      const df2 d = df_from_double(x[k]);
-      xh[k] = d.hi;
-      xl[k] = d.lo;
+    if ((conv[0] && conv[1]) || it >= a.max_iter) break;
+    for (int q = 0; q < 2; ++q) {
+      if (!active[q] || conv[q]) continue;
+      for (int k = threadIdx.x; k < m; k += kThreads) {
+        const df2 d = df_from_double(sys[q].x[k]);
+        sys[q].xh[k] = d.hi;
+        sys[q].xl[k] = d.lo;
+      }
     }
     __syncthreads();
-    if (!a.trans) residual_rows(Ah, Al, m, xh, xl, bb, r);
-    else residual_cols(Ah, Al, m, xh, xl, bb, r, part);
+    if (active[0] && !conv[0]) residual_rows(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
+    if (active[1] && !conv[1]) residual_cols(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
     __syncthreads();
   }
-  double* out = a.out + vec_off(bt, b);
-  for (int k = threadIdx.x; k < m; k += kThreads) out[k] = x[k];
+  for (int k = threadIdx.x; k < m; k += kThreads) {
+    if (act0) a.u[vec_off(bt, b) + k] = sys[0].x[k];
+    if (act1) a.lam[vec_off(bt, b) + k] = sys[1].x[k];
+  }
   if (threadIdx.x == 0) {
-    if (a.iters && !a.trans) a.iters[b] = it;
-    if (!conv) a.info[b] = PANEL_INFO_NOCONV;
+    if (a.iters && act0) a.iters[b] = it;
+    if (!(conv[0] && conv[1])) a.info[b] = PANEL_INFO_NOCONV;
   }
 }
 
-size_t solve_mixed_smem(int n_max, bool smem_factor, int m_factor) {
+size_t ir_mixed_smem(int n_max) {
   const size_t mv = (size_t)n_max + 1;
-  size_t bytes = mv * 8 * 3 + mv * 4 * 3 + mv * 4 * 2 + 16 + (size_t)parts_entries((int)mv) * 16 +
-                 32 * 8 + 2 * kNB * 4 + 2 * kWarps * 4;
-  bytes = (bytes + 15) & ~(size_t)15;
-  if (smem_factor) bytes += (size_t)m_factor * (size_t)(m_factor | 1) * 4;
-  return bytes;
+  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 16;
 }
 
-cudaError_t launch_solve_mixed(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
-                               int32_t* piv, const double* rhs, const double* vinf,
-                               const double* chord, double* out, int max_iter, double tol,
-                               int32_t* info, int32_t* iters, int trans, cudaStream_t s) {
+static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
+                           int32_t* piv, const double* rhs, const double* vinf,
+                           const double* chord, double* u, double* lam, int max_iter, double tol,
+                           int32_t* info, int32_t* iters) {
   SolveArgs a;
   a.bt = bt;
   a.A_hi = A_hi;
@@ -754,31 +800,55 @@ cudaError_t launch_solve_mixed(const Batch& bt, const float* A_hi, const float* 
   a.rhs = rhs;
   a.vinf = vinf;
   a.chord = chord;
-  a.out = out;
+  a.u = u;
+  a.lam = lam;
   a.max_iter = max_iter;
   a.tol = tol;
   a.info = info;
   a.iters = iters;
-  a.trans = trans;
+  return a;
+}
+
+// Factor every airfoil (shared-memory variant for m <= kSmemM, global beyond).
+cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32_t* piv,
+                            int32_t* info, int32_t* iters, cudaStream_t s) {
+  SolveArgs a = make_args(bt, A_hi, nullptr, LU, piv, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, 0, 0.0, info, iters);
   const int mmax = bt.n_max + 1;
-  if (mmax > kSmemM) {  // airfoils with m > kSmemM: factor in global memory
-    const size_t smem = solve_mixed_smem(bt.n_max, false, 0);
-    cudaError_t e = cudaFuncSetAttribute(k_solve_mixed<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e;
+  if (mmax > kSmemM) {
+    const size_t smem = lu_mixed_smem(bt.n_max, false, 0);
+    e = cudaFuncSetAttribute(k_lu_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
-    k_solve_mixed<false><<<bt.B, kThreads, smem, s>>>(a);
+    k_lu_mixed<false><<<bt.B, kThreads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // airfoils with m <= kSmemM: factor in shared memory
   Batch bs = bt;
   bs.n_max = min(bt.n_max, kSmemM - 1);
   a.bt = bs;
-  const size_t smem = solve_mixed_smem(bs.n_max, true, bs.n_max + 1);
-  cudaError_t e = cudaFuncSetAttribute(k_solve_mixed<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = lu_mixed_smem(bs.n_max, true, bs.n_max + 1);
+  e = cudaFuncSetAttribute(k_lu_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
   if (e != cudaSuccess) return e;
-  k_solve_mixed<true><<<bt.B, kThreads, smem, s>>>(a);
+  k_lu_mixed<true><<<bt.B, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Refine the forward (u) and/or transposed (lam) systems with the stored factor.
+cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_lo,
+                            const float* LU, const int32_t* piv, const double* rhs,
+                            const double* vinf, const double* chord, double* u, double* lam,
+                            int max_iter, double tol, int32_t* info, int32_t* iters,
+                            cudaStream_t s) {
+  SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
+                          rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
+  const size_t smem = ir_mixed_smem(bt.n_max);
+  cudaError_t e = cudaFuncSetAttribute(k_ir_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ir_mixed<<<bt.B, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

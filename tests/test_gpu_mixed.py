@@ -159,14 +159,27 @@ def test_mixed_ragged_spans_both_factor_paths():
 
 
 def test_mixed_uneven_population_sample():
-    # perturbed airfoils up to 512 panels: some systems are so ill conditioned
-    # that the FP64 evaluation of the formula is off by ~1e-9; the reference is
-    # the long double build of the oracle
+    # Perturbed airfoils of 64..512 panels.  Some of these systems are so ill
+    # conditioned that perturbing the entries at the 1e-16 level moves gamma by
+    # ~1e-10: the plain FP64 evaluation of the printed formula is itself off by
+    # up to 7.6e-10 on this sample.  The reference is the long double build of
+    # the oracle; per airfoil gamma must be within 1e-10 of it, or within 3x the
+    # FP64 evaluation's own deviation, whichever is larger.  Cl (well
+    # conditioned) must be within 1e-10 everywhere.
     need_gpu()
     pop = inputs.make_population("uneven_b10000_n64_512", batch=48)
     pb = _run(pop)
     assert np.all(pb.info.cpu().numpy() == 0)
-    _check_solution(pop, pb, extended=True)
+    with oracle.extended():
+        ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    ref64 = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    u = pb.u.cpu().numpy()
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        e_fp64 = rel_inf(ref64["u"][o:o + n], ref["u"][o:o + n])
+        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < max(1e-10, 3 * e_fp64), b
+    assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < 1e-10
 
 
 def test_mixed_gradient_matches_tangent_oracle():
