@@ -35,13 +35,20 @@ METRIC = "airfoil solves/sec and dCl/dx gradients/sec on 1 GB300 at <=1e-10 Cl e
 DEFAULT_CONFIG = "naca_b4096_n200"
 L2_BYTES = 135528448
 
-# Algorithmic work per unit (derivations in the design doc).
-#  * assembly: one (control point, panel) pair of the far-field double-float
-#    evaluation = ASSEMBLY_FLOP_PER_PAIR FP32 flops (FMA = 2);
-#  * LU: 2/3 m^3 flops per airfoil;
-#  * adjoint contraction: one pair = ADJOINT_FLOP_PER_PAIR flops.
-ASSEMBLY_FLOP_PER_PAIR = 300
-ADJOINT_FLOP_PER_PAIR = 300
+# Algorithmic work per unit (derivations in the design doc):
+#  * assembly: one (control point, panel) pair = the FP32 flops (FMA = 2) of the
+#    double-float far-field evaluation, ASSEMBLY_FLOP_PER_PAIR;
+#  * factor: 2/3 m^3 FP32 flops per airfoil (m = n + 1);
+#  * refine: 8 bytes per matrix entry for the initial solves (the FP32 factor,
+#    once per system) + 16 per refinement step (both planes once, the factor
+#    once per system);
+#  * adjoint contraction: one pair = ADJOINT_FLOP_PER_PAIR FP32 flops;
+#  * plain FP64 path: FP64 flops of the same formulas (ASSEMBLY_F64_FLOP_PER_PAIR,
+#    2/3 m^3 for the LU, ADJOINT_F64_FLOP_PER_PAIR).
+ASSEMBLY_FLOP_PER_PAIR = 350
+ADJOINT_FLOP_PER_PAIR = 480
+ASSEMBLY_F64_FLOP_PER_PAIR = 90
+ADJOINT_F64_FLOP_PER_PAIR = 110
 # FP32 peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
@@ -183,14 +190,19 @@ def run_ours(args):
     # weak scaling: each rank evaluates its own batch of the configured size
     spec_r = inputs.PopulationSpec(spec.name, spec.batch, spec.n_min, spec.n_max, spec.perturbed,
                                    spec.seed_index + 1000 * rank)
-    pop = inputs.make_population(spec_r)
+    pop = inputs.make_population(spec_r, batch=args.batch)
     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=args.mode, device=dev,
                     max_iter=args.max_iter, tol=args.tol)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    names = ["assemble", "solve", "forces", "adjoint"]
-    fns = [pb.assemble, lambda: pb.solve(with_adjoint=True), pb.forces, pb.adjoint]
+    if args.mode == "mixed":
+        names = ["assemble", "factor", "refine", "forces", "adjoint"]
+        fns = [pb.assemble, lambda: pb.solve(stage="factor"),
+               lambda: pb.solve(with_adjoint=True, stage="refine"), pb.forces, pb.adjoint]
+    else:
+        names = ["assemble", "solve", "forces", "adjoint"]
+        fns = [pb.assemble, lambda: pb.solve(with_adjoint=True), pb.forces, pb.adjoint]
 
     def step(evs=None):
         for k, fn in enumerate(fns):
@@ -267,43 +279,55 @@ def run_ours(args):
     kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
     sizes = pop.sizes.astype(np.float64)
     pairs = float((sizes ** 2).sum())
+    m2 = float(((sizes + 1) ** 2).sum())
     m3 = float(((sizes + 1) ** 3).sum())
     peaks = _peaks()
-    fp_peak = FP32_PEAK_TFLOPS if args.mode == "mixed" else FP64_PEAK_TFLOPS
-    work = {
-        "assemble": pairs * ASSEMBLY_FLOP_PER_PAIR if args.mode == "mixed" else None,
-        "solve": 2.0 / 3.0 * m3,
-        "forces": None,
-        "adjoint": pairs * ADJOINT_FLOP_PER_PAIR,
-    }
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    it_mean = float(iters.mean())
+    if args.mode == "mixed":
+        work = {"assemble": ("alu", pairs * ASSEMBLY_FLOP_PER_PAIR),
+                "factor": ("alu", 2.0 / 3.0 * m3),
+                "refine": ("hbm", m2 * (8.0 + 16.0 * it_mean)),
+                "forces": ("hbm", float(sizes.sum()) * 40.0),
+                "adjoint": ("alu", pairs * ADJOINT_FLOP_PER_PAIR)}
+        alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    else:
+        work = {"assemble": ("alu", pairs * ASSEMBLY_F64_FLOP_PER_PAIR),
+                "solve": ("alu", 2.0 / 3.0 * m3),
+                "forces": ("hbm", float(sizes.sum()) * 40.0),
+                "adjoint": ("alu", pairs * ADJOINT_F64_FLOP_PER_PAIR)}
+        alu_peak, alu_src = FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
     kernels = {}
     for nm in names:
-        w = work[nm]
-        ach = (w / (kms[nm] * 1e-3) / 1e12) if w else None
-        kernels[nm] = {"ms": kms[nm], "tflops": ach,
-                       "frac": (ach / fp_peak) if ach else None}
+        bound, w = work[nm]
+        sec = kms[nm] * 1e-3
+        if bound == "alu":
+            ach, peak, unit = w / sec / 1e12, alu_peak, "TFLOP/s"
+        else:
+            ach, peak, unit = w / sec / 1e9, hbm, "GB/s"
+        kernels[nm] = {"ms": kms[nm], "bound": bound, "achieved": ach, "peak": peak,
+                       "unit": unit, "frac": ach / peak}
     dom = max(kms, key=kms.get)
     dk = kernels[dom]
-    roofline = {"kernel": dom, "bound": "alu", "achieved": dk["tflops"], "peak": fp_peak,
-                "unit": "TFLOP/s", "frac": dk["frac"], "traffic": None,
-                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-                if args.mode == "mixed" else "FP64 nominal 1.25 TFLOP/s"}
-
-    launches_per_step = 4 if args.mode == "fp64" else 4
+    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"],
+                "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "peak_source": alu_src if dk["bound"] == "alu"
+                else "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    launches_per_step = len(names)
     if args.mode == "mixed" and pb.n_max + 1 > 230:
-        launches_per_step += 2
+        launches_per_step += 1  # the global-memory LU variant is launched as well
     out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+df32" if args.mode == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": args.config, "batch_per_gpu": B, "mode": args.mode,
+                      "subset": args.batch is not None,
                       "n_min": int(sizes.min()), "n_max": int(sizes.max()),
                       "l2": "flushed before every timed step (%d MB write)"
                             % (flush.numel() * 4 // 2**20),
                       "max_iter": args.max_iter, "tol": args.tol,
                       "parallelism": "dp%d (independent airfoils)" % world},
            "gradients_per_s": value,
-           "kernels_ms": kms,
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
@@ -334,6 +358,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="evaluate only the first BATCH airfoils of the workload (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

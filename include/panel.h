@@ -74,6 +74,11 @@ typedef enum {
 /* panel_solve: also solve the transposed system M^T lambda = dCl/du for unit
  * upstream gradient (used later by panel_adjoint), sharing the residual passes. */
 #define PANEL_WITH_ADJOINT 0x10
+/* panel_solve, PANEL_MIXED only: factor (LU, piv, info) and stop ... */
+#define PANEL_FACTOR_ONLY 0x20
+/* ... or skip the factorisation and refine with the LU/piv of an earlier call
+ * (the same matrix planes), e.g. for another right-hand side. */
+#define PANEL_REUSE_FACTOR 0x40
 
 /* Largest panel count per airfoil the library accepts. */
 #define PANEL_N_MAX 2048

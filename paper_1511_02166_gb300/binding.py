@@ -23,6 +23,8 @@ PANEL_OK, PANEL_EINVAL, PANEL_ENOTSUP, PANEL_ECUDA = 0, 1, 2, 3
 PANEL_FP64 = 0x1
 PANEL_MIXED = 0x2
 PANEL_WITH_ADJOINT = 0x10
+PANEL_FACTOR_ONLY = 0x20
+PANEL_REUSE_FACTOR = 0x40
 PANEL_N_MAX = 2048
 
 INFO_FEW_NODES = -1

@@ -47,7 +47,12 @@ int mode_of(int flags) {
 }
 
 bool flags_ok(int flags) {
-  return mode_of(flags) != 0 && (flags & ~(PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT)) == 0;
+  const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
+                    PANEL_REUSE_FACTOR;
+  if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
+  const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
+  if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;
+  return stage == 0 || mode_of(flags) == PANEL_MIXED;
 }
 
 Batch make_batch(int B, int n_max, const double* nodes, const int64_t* node_offsets,
@@ -128,7 +133,10 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
                 void* stream) {
   if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || !flags_ok(flags)) return PANEL_EINVAL;
   if (B == 0) return PANEL_OK;
-  if (!node_offsets || !mat_offsets || !order || !piv || !rhs || !u || !info) return PANEL_EINVAL;
+  const bool factor_only = (flags & PANEL_FACTOR_ONLY) != 0;
+  const bool reuse = (flags & PANEL_REUSE_FACTOR) != 0;
+  if (!node_offsets || !mat_offsets || !order || !piv || !info) return PANEL_EINVAL;
+  if (!factor_only && (!rhs || !u)) return PANEL_EINVAL;
   const bool adj = (flags & PANEL_WITH_ADJOINT) != 0;
   if (adj && (!lambda || !nodes)) return PANEL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -139,8 +147,9 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
                                              adj ? lambda : nullptr, info, iters, s));
   }
   if (!A_hi || !A_lo || !LU || max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
-  cudaError_t e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters, s);
-  if (e == cudaSuccess)
+  cudaError_t e = cudaSuccess;
+  if (!reuse) e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters, s);
+  if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
                                adj ? lambda : nullptr, max_iter, tol, info, iters, s);
   return status_of(e);

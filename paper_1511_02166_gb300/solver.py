@@ -89,14 +89,18 @@ class PanelBatch:
                           self.mat_offsets, self.order, self.alpha, self.vinf, self.A64,
                           self.A_hi, self.A_lo, self.rhs, self.info)
 
-    def solve(self, with_adjoint: bool = False):
+    def solve(self, with_adjoint: bool = False, stage: str = "all"):
+        """stage 'all' (factor + refine), 'factor' (LU only) or 'refine' (reuse the
+        stored LU; mixed mode only)."""
         flags = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
+        flags |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
         bd.panel_solve(self.B, self.n_max, flags, self.nodes, self.node_offsets,
                        self.mat_offsets, self.order, self.A64, self.A_hi, self.A_lo, self.LU,
                        self.piv, self.rhs, self.vinf, self.chord, self.u,
                        self.lam if with_adjoint else None, self.max_iter, self.tol, self.info,
                        self.iters)
-        self.have_lambda = with_adjoint
+        if stage != "factor":
+            self.have_lambda = with_adjoint
 
     def forces(self):
         bd.panel_forces(self.B, self.nodes, self.node_offsets, self.u, self.alpha, self.vinf,

@@ -32,7 +32,9 @@ def test_constants_match_header():
     txt = open(os.path.join(ROOT, "include", "panel.h")).read()
     for name, val in [("PANEL_FP64", bd.PANEL_FP64), ("PANEL_MIXED", bd.PANEL_MIXED),
                       ("PANEL_WITH_ADJOINT", bd.PANEL_WITH_ADJOINT),
-                      ("PANEL_N_MAX", bd.PANEL_N_MAX)]:
+                      ("PANEL_N_MAX", bd.PANEL_N_MAX),
+                      ("PANEL_FACTOR_ONLY", bd.PANEL_FACTOR_ONLY),
+                      ("PANEL_REUSE_FACTOR", bd.PANEL_REUSE_FACTOR)]:
         m = re.search(r"#define %s\s+(0x[0-9a-fA-F]+|\d+)" % name, txt)
         assert m and int(m.group(1), 0) == val, name
     for name, val in [("PANEL_INFO_FEW_NODES", bd.INFO_FEW_NODES),
@@ -76,6 +78,11 @@ def test_argument_validation_before_any_launch():
     assert lib.panel_forces(1, *([None] * 11), None) == bd.PANEL_EINVAL
     assert lib.panel_adjoint(1, 10, bd.PANEL_MIXED, *([None] * 17), 3, 1e-12, None,
                              None) == bd.PANEL_EINVAL
+    # factor/reuse stages are mixed-mode only and exclusive
+    assert lib.panel_solve(1, 10, bd.PANEL_FP64 | bd.PANEL_FACTOR_ONLY, *([None] * 14), 3, 1e-12,
+                           None, None, None) == bd.PANEL_EINVAL
+    assert lib.panel_solve(1, 10, bd.PANEL_MIXED | bd.PANEL_FACTOR_ONLY | bd.PANEL_REUSE_FACTOR,
+                           *([None] * 14), 3, 1e-12, None, None, None) == bd.PANEL_EINVAL
     # an empty batch is a no-op
     assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
     assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"
