@@ -23,8 +23,11 @@
 //
 // Layout: one block per airfoil; each warp owns 32 consecutive columns (panels
 // i, one per lane) and sweeps all rows j: A_i, B_i accumulate in the lane's
-// registers (double-float), the row sums P_j are warp-reduced and added into
-// shared FP64 accumulators.
+// registers (double-float), the row sums P_j are warp-reduced and kept as one
+// double-float partial per warp in shared memory (PARTIALS, n <= kPartialsN),
+// summed at the end; beyond that size they go into shared FP64 accumulators by
+// atomics (FP64 instructions run at 1/64 of the FP32 rate on GB300, so the
+// partials are the fast path).
 #include "panel_common.cuh"
 #include "panel_df.cuh"
 
@@ -137,6 +140,9 @@ __device__ __forceinline__ df2 warp_sum_df2(df2 a) {
   return a;
 }
 
+constexpr int kPartialsN = 512;
+
+template <bool PARTIALS>
 __global__ void __launch_bounds__(256) k_adjoint_df(
     Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
     const double* __restrict__ alpha, const double* __restrict__ vinf,
@@ -154,6 +160,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
   float* lamh = reinterpret_cast<float*>(Bc + 2 * ld);    // n_max (lambda as float pairs)
   float* laml = lamh + ld;
   float* pc = laml + ld;                                  // kPanelFields * n_max
+  float4* Pw = reinterpret_cast<float4*>(pc + kPanelFields * ld);  // 8 * n_max (PARTIALS)
 
   const int b = bt.order[blockIdx.x];
   const int n = airfoil_n(bt, b);
@@ -170,6 +177,8 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     xs[k] = nodes[2 * k];
     ys[k] = nodes[2 * k + 1];
     P[2 * k] = P[2 * k + 1] = 0.0;
+    if (PARTIALS)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Pw[w * ld + k] = make_float4(0, 0, 0, 0);
     const df2 l = df_from_double(lb[k]);
     lamh[k] = l.hi;
     laml[k] = l.lo;
@@ -204,8 +213,14 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
       rx = warp_sum_df2(rx);
       ry = warp_sum_df2(ry);
       if (lane == 0) {
-        atomicAdd(&P[2 * j], (double)rx.hi + (double)rx.lo);
-        atomicAdd(&P[2 * j + 1], (double)ry.hi + (double)ry.lo);
+        if (PARTIALS) {
+          const float4 q = Pw[warp * ld + j];
+          const df2 sx = df_add(mkdf(q.x, q.y), rx), sy = df_add(mkdf(q.z, q.w), ry);
+          Pw[warp * ld + j] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+        } else {
+          atomicAdd(&P[2 * j], (double)rx.hi + (double)rx.lo);
+          atomicAdd(&P[2 * j + 1], (double)ry.hi + (double)ry.lo);
+        }
       }
     }
     if (ok) {
@@ -216,6 +231,19 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     }
   }
   __syncthreads();
+  if (PARTIALS) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      df2 sx = mkdf(0.0f), sy = mkdf(0.0f);
+      for (int w = 0; w < nw; ++w) {
+        const float4 q = Pw[w * ld + k];
+        sx = df_add(sx, mkdf(q.x, q.y));
+        sy = df_add(sy, mkdf(q.z, q.w));
+      }
+      P[2 * k] = df_to_double(sx);
+      P[2 * k + 1] = df_to_double(sy);
+    }
+    __syncthreads();
+  }
   const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
   const double ca = cos(alpha[b]), sa = sin(alpha[b]);
   const double gscale = grad_cl ? grad_cl[b] : 1.0;
@@ -240,8 +268,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
 }
 
 size_t adjoint_df_smem(int n_max) {
-  return 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
-         (size_t)kPanelFields * n_max * 4;
+  size_t b = 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
+             (size_t)kPanelFields * n_max * 4;
+  if (n_max <= kPartialsN) b += (size_t)8 * n_max * 16;
+  return b;
 }
 
 cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* lambda,
@@ -249,10 +279,20 @@ cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* la
                               const double* grad_cl, double* grad, const int32_t* info,
                               cudaStream_t s) {
   const size_t smem = adjoint_df_smem(bt.n_max);
-  cudaError_t e = cudaFuncSetAttribute(k_adjoint_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_adjoint_df<<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad, info);
+  cudaError_t e;
+  if (bt.n_max <= kPartialsN) {
+    e = cudaFuncSetAttribute(k_adjoint_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adjoint_df<true><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad,
+                                               info);
+  } else {
+    e = cudaFuncSetAttribute(k_adjoint_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_adjoint_df<false><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl,
+                                                grad, info);
+  }
   return cudaGetLastError();
 }
 

@@ -426,73 +426,77 @@ size_t lu_mixed_smem(int n_max, bool smem_factor, int m_factor) {
 
 // ---------------------------------------------------------------------------
 // Triangular solves with the stored factor (global memory, ld = m, diagonal
-// blocks inverted), on a float vector y in shared memory.
+// blocks inverted), on a float vector y in shared memory; `t32` is a 32-float
+// shared scratch.  Every 32-row block takes two block barriers and all eight
+// warps: a warp owns 4 rows of the block and reduces across its lanes.
 // ---------------------------------------------------------------------------
-// y <- L^{-1} y (unit lower) then U^{-1} y.
-__device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y <- L^{-1} y then U^{-1} y, left-looking: the rows of block d read their
+// own contiguous segments L[i][0..k0) (coalesced across the lanes).
+__device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, float* t32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < m; k0 += 32) {
     const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) {
-      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
-      float z = yl;
-      const float* row = F + (k0 + min(lane, kb - 1)) * m + k0;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, yl, k);
-        if (k < lane && lane < kb) z = fmaf(__ldg(row + k), yk, z);
-      }
-      if (lane < kb) y[k0 + lane] = z;
+    for (int q = warp; q < kb; q += kWarps) {
+      const int i = k0 + q;
+      const float* row = F + i * m;
+      float acc = 0.0f;
+      for (int k = lane; k < k0; k += 32) acc = fmaf(__ldg(row + k), y[k], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
-    for (int r = k0 + kb + threadIdx.x; r < m; r += kThreads) {
-      const float* row = F + r * m + k0;
-      float acc = y[r];
-#pragma unroll 8
-      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(row + t), y[k0 + t], acc);
-      y[r] = acc;
+    for (int q = warp; q < kb; q += kWarps) {
+      const int i = k0 + q;
+      // z_i = t_i + sum_{k<i} X[i][k] t_k  (X unit lower, stored below the diagonal)
+      float v = (lane < q) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = t32[q] + v;
     }
     __syncthreads();
   }
   for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
     const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) {
-      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
-      float z = 0.0f;
-      const float* row = F + (k0 + min(lane, kb - 1)) * m + k0;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, yl, k);
-        if (k >= lane && k < kb) z = fmaf(__ldg(row + k), yk, z);
-      }
-      if (lane < kb) y[k0 + lane] = z;
+    for (int q = warp; q < kb; q += kWarps) {
+      const int i = k0 + q;
+      const float* row = F + i * m;
+      float acc = 0.0f;
+      for (int k = k0 + kb + lane; k < m; k += 32) acc = fmaf(__ldg(row + k), y[k], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < k0; r += kThreads) {
-      const float* row = F + r * m + k0;
-      float acc = y[r];
-#pragma unroll 8
-      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(row + t), y[k0 + t], acc);
-      y[r] = acc;
+    for (int q = warp; q < kb; q += kWarps) {
+      const int i = k0 + q;
+      // x_i = sum_{k>=i} Y[i][k] t_k  (Y upper with diagonal)
+      float v = (lane >= q && lane < kb) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = v;
     }
     __syncthreads();
   }
 }
 
-// y <- U^{-T} y (lower) then L^{-T} y (unit upper).
-__device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, float* y) {
-  const int lane = threadIdx.x & 31;
+// y <- U^{-T} y then L^{-T} y.  Right-looking updates (a thread per row r reads
+// U[k][r], coalesced across r); the diagonal products are split over the warps.
+__device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, float* y,
+                                            float* t32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < m; k0 += 32) {
     const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) {
-      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
-      float z = 0.0f;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, yl, k);
-        if (k <= lane && lane < kb) z = fmaf(__ldg(F + (k0 + k) * m + k0 + lane), yk, z);
-      }
-      if (lane < kb) y[k0 + lane] = z;
+    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
+    __syncthreads();
+    for (int q = warp; q < kb; q += kWarps) {
+      // z_i = sum_{k<=i} Y[k][i] t_k
+      const int i = k0 + q;
+      float v = (lane <= q) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = v;
     }
     __syncthreads();
     for (int r = k0 + kb + threadIdx.x; r < m; r += kThreads) {
@@ -505,15 +509,14 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
   }
   for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
     const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) {
-      const float yl = (lane < kb) ? y[k0 + lane] : 0.0f;
-      float z = yl;
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
-        const float yk = __shfl_sync(0xffffffffu, yl, k);
-        if (k > lane && k < kb) z = fmaf(__ldg(F + (k0 + k) * m + k0 + lane), yk, z);
-      }
-      if (lane < kb) y[k0 + lane] = z;
+    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
+    __syncthreads();
+    for (int q = warp; q < kb; q += kWarps) {
+      // z_i = t_i + sum_{k>i} X[k][i] t_k
+      const int i = k0 + q;
+      float v = (lane > q && lane < kb) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = t32[q] + v;
     }
     __syncthreads();
     for (int r = threadIdx.x; r < k0; r += kThreads) {
@@ -682,6 +685,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
     fp += 2 * mv;
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
+  float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
 
   const int64_t moff = bt.mat_off[b];
   const float* Ah = a.A_hi + moff;
@@ -736,13 +740,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
           y[k] = (float)((src == n) ? S.r[src] * s : S.r[src]);
         }
         __syncthreads();
-        lu_apply_inverse(F, m, y);
+        lu_apply_inverse(F, m, y, t32);
       } else {
         // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
         for (int k = threadIdx.x; k < m; k += kThreads)
           y[k] = (float)((k == n) ? S.r[k] * s : S.r[k]);
         __syncthreads();
-        lu_apply_inverse_transposed(F, m, y);
+        lu_apply_inverse_transposed(F, m, y, t32);
       }
       double dmax = 0.0;
       for (int k = threadIdx.x; k < m; k += kThreads) {
@@ -784,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
 
 size_t ir_mixed_smem(int n_max) {
   const size_t mv = (size_t)n_max + 1;
-  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 16;
+  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 16;
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,

@@ -130,9 +130,10 @@ def test_mixed_small_config_matches_oracle():
     _check_solution(pop, pb)
 
 
-def test_mixed_unrefined_within_2e4():
-    # FP32 LU with partial pivoting alone: the measured worst case over these
-    # airfoils is ~1.1e-4 (cond ~3e4 after the border rescaling)
+def test_mixed_unrefined_within_5e4():
+    # FP32 LU with partial pivoting and FP32 triangular solves alone (no
+    # refinement): the measured worst case over these airfoils is ~2.4e-4
+    # (cond ~3e4 after the border rescaling, times the FP32 rounding)
     need_gpu()
     pop = inputs.make_population("naca_b4096_n200", batch=32)
     pb = _run(pop, max_iter=0)
@@ -143,7 +144,7 @@ def test_mixed_unrefined_within_2e4():
     for b in range(pop.batch):
         o = pop.offsets[b] + b
         n = pop.offsets[b + 1] - pop.offsets[b]
-        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 2e-4
+        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 5e-4
 
 
 def test_mixed_ragged_spans_both_factor_paths():
