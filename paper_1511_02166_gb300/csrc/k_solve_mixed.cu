@@ -253,59 +253,6 @@ __device__ int lu_rowpanel(float* F, int ld, int m, int* ipiv, float* prow, floa
 }
 
 // ---------------------------------------------------------------------------
-// LU with partial pivoting, factor in global memory (any m).
-// ---------------------------------------------------------------------------
-__device__ int lu_blocked(float* F, int ld, int m, int* ipiv) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < m; k0 += kNB) {
-    const int kb = min(kNB, m - k0);
-    for (int k = k0; k < k0 + kb; ++k) {
-      float best = -1.0f;
-      int bi = k;
-      for (int r = k + lane; r < m; r += 32) {
-        const float v = fabsf(F[r * ld + k]);
-        if (v > best) { best = v; bi = r; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      const int p = bi;
-      if (best <= 0.0f) return k + 1;
-      __syncthreads();  // everyone has read column k before rows move
-      if (p != k && threadIdx.x < kb) {
-        const int c = k0 + threadIdx.x;
-        const float tt = F[k * ld + c];
-        F[k * ld + c] = F[p * ld + c];
-        F[p * ld + c] = tt;
-      }
-      if (threadIdx.x == 0) ipiv[k] = p;
-      __syncthreads();
-      const float inv = 1.0f / F[k * ld + k];
-      const int c = k0 + lane;
-      const float fkc = (lane < kb && c > k) ? F[k * ld + c] : 0.0f;
-      for (int r = k + 1 + warp; r < m; r += kWarps) {
-        const float l = F[r * ld + k] * inv;
-        __syncwarp();
-        if (lane < kb && c > k) F[r * ld + c] = fmaf(-l, fkc, F[r * ld + c]);
-        if (c == k) F[r * ld + k] = l;
-      }
-      __syncthreads();
-    }
-    apply_panel_swaps(F, ld, m, k0, kb, ipiv);
-    __syncthreads();
-    if (k0 + kb >= m) break;
-    panel_trsm(F, ld, m, k0, kb);
-    __syncthreads();
-    panel_gemm(F, ld, m, k0, kb);
-    __syncthreads();
-  }
-  return 0;
-}
-
-// ---------------------------------------------------------------------------
 // Inverted diagonal blocks, in place, one warp per 32 x 32 block (lane j =
 // column j of the inverse).  X = L_dd^{-1} (unit lower) replaces the part
 // below the diagonal row by row (row i is written after every lane has read
@@ -349,9 +296,8 @@ __device__ void invert_diagonal_blocks(float* F, int ld, int m) {
 }
 
 // ---------------------------------------------------------------------------
-// The LU kernel
+// The LU kernel, factor in shared memory (m <= kSmemM)
 // ---------------------------------------------------------------------------
-template <bool SMEM>
 __global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
@@ -359,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
   const int n = airfoil_n(bt, b);
   const int m = n + 1;
   if (a.info[b] != 0) return;
-  if (SMEM != (m <= kSmemM)) return;  // each airfoil is taken by one variant
+  if (m > kSmemM) return;  // taken by k_lu_global
   if (n > bt.n_max) {
     if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
     return;
@@ -370,35 +316,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
       (reinterpret_cast<uintptr_t>(ipiv + bt.n_max + 1) + 15) & ~(uintptr_t)15);  // 2 kNB
   float* krow = prow + 2 * kNB;                                                    // 2 kNB
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(krow + 2 * kNB);  // 2 kWarps
-  float* Fs = reinterpret_cast<float*>(cand + 2 * kWarps);
+  float* F = reinterpret_cast<float*>(cand + 2 * kWarps);
 
   const int64_t moff = bt.mat_off[b];
   const float* Ah = a.A_hi + moff;
-  const int ld = SMEM ? (m | 1) : m;
-  float* F = SMEM ? Fs : (a.LU + moff);
+  const int ld = m | 1;
   const float sf = (float)border_scale(Ah, n, m, red);
 
-  // copy the hi plane (asynchronously into shared memory), rescale the border
+  // copy the hi plane asynchronously into shared memory, rescale the border
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int rr = warp; rr < m; rr += kWarps)
     for (int cc = lane; cc < m; cc += 32) {
-      if (SMEM) {
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(F + rr * ld + cc);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst),
-                     "l"(Ah + rr * m + cc));
-      } else {
-        F[rr * ld + cc] = Ah[rr * m + cc];
-      }
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(F + rr * ld + cc);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(Ah + rr * m + cc));
     }
-  if (SMEM) asm volatile("cp.async.wait_all;\n" ::);
+  asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
   for (int j = threadIdx.x; j < m; j += kThreads) {
     if (j < n) F[j * ld + n] *= sf;
     F[n * ld + j] *= sf;
   }
   __syncthreads();
-  const int st = SMEM ? lu_rowpanel(F, ld, m, ipiv, prow, krow, cand)
-                      : lu_blocked(F, ld, m, ipiv);
+  const int st = lu_rowpanel(F, ld, m, ipiv, prow, krow, cand);
   if (st != 0) {
     if (threadIdx.x == 0) {
       a.info[b] = st;
@@ -410,18 +349,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
   __syncthreads();
   int32_t* gpiv = a.piv + vec_off(bt, b);
   for (int k = threadIdx.x; k < m; k += kThreads) gpiv[k] = ipiv[k];
-  if (SMEM) {
-    float* G = a.LU + moff;
-    for (int rr = warp; rr < m; rr += kWarps)
-      for (int cc = lane; cc < m; cc += 32) G[rr * m + cc] = F[rr * ld + cc];
-  }
+  float* G = a.LU + moff;
+  for (int rr = warp; rr < m; rr += kWarps)
+    for (int cc = lane; cc < m; cc += 32) G[rr * m + cc] = F[rr * ld + cc];
 }
 
-size_t lu_mixed_smem(int n_max, bool smem_factor, int m_factor) {
+size_t lu_mixed_smem(int n_max) {
+  const int mf = n_max + 1;
   size_t bytes = 32 * 8 + (size_t)(n_max + 1) * 4 + 16 + 4 * kNB * 4 + 2 * kWarps * 8;
   bytes = (bytes + 15) & ~(size_t)15;
-  if (smem_factor) bytes += (size_t)m_factor * (size_t)(m_factor | 1) * 4;
-  return bytes;
+  return bytes + (size_t)mf * (size_t)(mf | 1) * 4;
+}
+
+// ---------------------------------------------------------------------------
+// The LU kernel, factor in global memory (m > kSmemM): blocked right-looking
+// with the current panel of NB columns staged in shared memory (rows spread
+// over the threads), the row exchanges, U12 and the rank-NB update applied to
+// the factor in the caller's LU buffer through L2.  Shared memory stays small
+// (the panel plus a 128-column slab of U12), so several airfoils share an SM
+// and hide each other's latencies.
+// ---------------------------------------------------------------------------
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int LDP = NB + 1;
+  constexpr int CW = 128;  // GEMM column slab
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const int m = n + 1;
+  if (a.info[b] != 0) return;
+  if (m <= kSmemM) return;  // taken by k_lu_mixed
+  if (n > bt.n_max) {
+    if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
+    return;
+  }
+  const int mv = bt.n_max + 1;
+  float* P = reinterpret_cast<float*>(smraw);           // mv x LDP panel
+  float* U = P + mv * LDP;                              // NB x CW slab of U12
+  double* red = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(U + NB * CW) + 15) & ~(uintptr_t)15);  // 32
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(red + 32);  // kWarps
+  int* ipiv = reinterpret_cast<int*>(cand + kWarps);    // mv
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t moff = bt.mat_off[b];
+  const float* Ah = a.A_hi + moff;
+  float* F = a.LU + moff;
+  const float sf = (float)border_scale(Ah, n, m, red);
+  for (int rr = warp; rr < m; rr += kWarps)
+    for (int cc = lane; cc < m; cc += 32) {
+      const float v = Ah[rr * m + cc];
+      F[rr * m + cc] = ((cc == n && rr < n) || rr == n) ? v * sf : v;
+    }
+  __syncthreads();
+
+  for (int k0 = 0; k0 < m; k0 += NB) {
+    const int kb = min(NB, m - k0);
+    const int rows = m - k0;
+    // ---- stage the panel ----
+    for (int r = warp; r < rows; r += kWarps)
+      if (lane < kb) P[r * LDP + lane] = F[(k0 + r) * m + k0 + lane];
+    __syncthreads();
+    // ---- factor the panel (rows over the threads) ----
+    for (int q = 0; q < kb; ++q) {
+      unsigned bk = 0;
+      int br = 0x7fffffff;
+      for (int r = q + tid; r < rows; r += kThreads) {
+        const unsigned key = __float_as_uint(fabsf(P[r * LDP + q])) + 1u;
+        if (key > bk) { bk = key; br = r; }
+      }
+      const unsigned mx = __reduce_max_sync(0xffffffffu, bk);
+      const unsigned rmin = __reduce_min_sync(0xffffffffu, bk == mx ? (unsigned)br : 0xffffffffu);
+      if (lane == 0) cand[warp] = ((unsigned long long)mx << 32) | (0x7fffffffu - rmin);
+      __syncthreads();
+      unsigned long long best = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) best = max(best, cand[w]);
+      if ((unsigned)(best >> 32) <= 1u) {
+        if (tid == 0) {
+          a.info[b] = k0 + q + 1;
+          if (a.iters) a.iters[b] = 0;
+        }
+        return;
+      }
+      const int p = (int)(0x7fffffffu - (unsigned)(best & 0xffffffffu));
+      if (p != q && tid < kb) {
+        const float t = P[q * LDP + tid];
+        P[q * LDP + tid] = P[p * LDP + tid];
+        P[p * LDP + tid] = t;
+      }
+      if (tid == 0) ipiv[k0 + q] = k0 + p;
+      __syncthreads();
+      const float inv = 1.0f / P[q * LDP + q];
+      for (int r = q + 1 + tid; r < rows; r += kThreads) {
+        const float l = P[r * LDP + q] * inv;
+        P[r * LDP + q] = l;
+        for (int c = q + 1; c < kb; ++c) P[r * LDP + c] = fmaf(-l, P[q * LDP + c], P[r * LDP + c]);
+      }
+      __syncthreads();
+    }
+    // ---- write the panel back, exchange rows outside it ----
+    for (int r = warp; r < rows; r += kWarps)
+      if (lane < kb) F[(k0 + r) * m + k0 + lane] = P[r * LDP + lane];
+    for (int c = tid; c < m; c += kThreads) {
+      if (c >= k0 && c < k0 + kb) continue;
+      for (int k = k0; k < k0 + kb; ++k) {
+        const int pk = ipiv[k];
+        if (pk != k) {
+          const float t = F[k * m + c];
+          F[k * m + c] = F[pk * m + c];
+          F[pk * m + c] = t;
+        }
+      }
+    }
+    __syncthreads();
+    const int k1 = k0 + kb;
+    if (k1 >= m) break;
+    // ---- U12 = L11^{-1} A12, a column per lane, shifted registers ----
+    for (int cb = k1 + 32 * warp; cb < m; cb += kThreads) {
+      const int c = cb + lane;
+      const bool ok = c < m;
+      float col[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) col[t] = (ok && t < kb) ? F[(k0 + t) * m + c] : 0.0f;
+      for (int q = 0; q < kb; ++q) {
+        const float x = col[0];
+        if (ok) F[(k0 + q) * m + c] = x;
+#pragma unroll
+        for (int t = 1; t < NB; ++t) {
+          const float l = (q + t < kb) ? P[(q + t) * LDP + q] : 0.0f;
+          col[t - 1] = fmaf(-l, x, col[t]);
+        }
+        col[NB - 1] = 0.0f;
+      }
+    }
+    __syncthreads();
+    // ---- A22 -= L21 U12, 128-column slabs of U12 staged in shared memory ----
+    const int nrt = (m - k1 + 7) >> 3;
+    for (int cc = k1; cc < m; cc += CW) {
+      for (int t = warp; t < kb; t += kWarps)
+#pragma unroll
+        for (int j = 0; j < CW / 32; ++j) {
+          const int c = cc + lane + 32 * j;
+          U[t * CW + lane + 32 * j] = (c < m) ? F[(k0 + t) * m + c] : 0.0f;
+        }
+      __syncthreads();
+      for (int rt = warp; rt < nrt; rt += kWarps) {
+        const int r0 = k1 + 8 * rt;
+        float acc[8][4];
+#pragma unroll
+        for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = r0 + aa, c = cc + lane + 32 * j;
+            acc[aa][j] = (r < m && c < m) ? F[r * m + c] : 0.0f;
+          }
+#pragma unroll 4
+        for (int q = 0; q < kb; ++q) {
+          float lv[8], uv[4];
+#pragma unroll
+          for (int aa = 0; aa < 8; ++aa) lv[aa] = (r0 + aa < m) ? P[(r0 + aa - k0) * LDP + q] : 0.0f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) uv[j] = U[q * CW + lane + 32 * j];
+#pragma unroll
+          for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[aa][j] = fmaf(-lv[aa], uv[j], acc[aa][j]);
+        }
+#pragma unroll
+        for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = r0 + aa, c = cc + lane + 32 * j;
+            if (r < m && c < m) F[r * m + c] = acc[aa][j];
+          }
+      }
+      __syncthreads();
+    }
+  }
+  invert_diagonal_blocks(F, m, m);
+  __syncthreads();
+  int32_t* gpiv = a.piv + vec_off(bt, b);
+  for (int k = tid; k < m; k += kThreads) gpiv[k] = ipiv[k];
+}
+
+template <int NB>
+size_t lu_global_smem(int n_max) {
+  const size_t mv = (size_t)n_max + 1;
+  size_t bytes = mv * (NB + 1) * 4 + (size_t)NB * 128 * 4;
+  bytes = (bytes + 15) & ~(size_t)15;
+  return bytes + 32 * 8 + kWarps * 8 + mv * 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -813,30 +931,37 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   return a;
 }
 
-// Factor every airfoil (shared-memory variant for m <= kSmemM, global beyond).
+// Factor every airfoil (shared-memory kernel for m <= kSmemM, global beyond).
+constexpr size_t kMaxSmem = 232448;
 cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32_t* piv,
                             int32_t* info, int32_t* iters, cudaStream_t s) {
   SolveArgs a = make_args(bt, A_hi, nullptr, LU, piv, nullptr, nullptr, nullptr, nullptr,
                           nullptr, 0, 0.0, info, iters);
-  const int mmax = bt.n_max + 1;
   cudaError_t e;
-  if (mmax > kSmemM) {
-    const size_t smem = lu_mixed_smem(bt.n_max, false, 0);
-    e = cudaFuncSetAttribute(k_lu_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_lu_mixed<false><<<bt.B, kThreads, smem, s>>>(a);
+  if (bt.n_max + 1 > kSmemM) {
+    if (lu_global_smem<32>(bt.n_max) <= kMaxSmem) {
+      const size_t smem = lu_global_smem<32>(bt.n_max);
+      e = cudaFuncSetAttribute(k_lu_global<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      k_lu_global<32><<<bt.B, kThreads, smem, s>>>(a);
+    } else {
+      const size_t smem = lu_global_smem<16>(bt.n_max);
+      e = cudaFuncSetAttribute(k_lu_global<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      k_lu_global<16><<<bt.B, kThreads, smem, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   Batch bs = bt;
   bs.n_max = min(bt.n_max, kSmemM - 1);
   a.bt = bs;
-  const size_t smem = lu_mixed_smem(bs.n_max, true, bs.n_max + 1);
-  e = cudaFuncSetAttribute(k_lu_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+  const size_t smem = lu_mixed_smem(bs.n_max);
+  e = cudaFuncSetAttribute(k_lu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_lu_mixed<true><<<bt.B, kThreads, smem, s>>>(a);
+  k_lu_mixed<<<bt.B, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
