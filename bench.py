@@ -193,6 +193,7 @@ def run_ours(args):
     pop = inputs.make_population(spec_r, batch=args.batch)
     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=args.mode, device=dev,
                     max_iter=args.max_iter, tol=args.tol)
+    tuned = pb.autotune() if (args.autotune and args.mode == "mixed") else {}
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -224,24 +225,39 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # per-call breakdown (CUDA events around every library call), untimed for `value`
+    kern = {nm: [] for nm in names}
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in names]
+        step(evs)
+        torch.cuda.synchronize()
+        for k, nm in enumerate(names):
+            kern[nm].append(evs[k][0].elapsed_time(evs[k][1]))
+
+    if args.graph:
+        pb.capture(with_grad=True)
+        run_step = pb.step
+    else:
+        run_step = step
+    for _ in range(args.warmup):
+        run_step()
+    torch.cuda.synchronize()
+
     clk = ClockSampler(local)
     clk.start()
-    kern = {nm: [] for nm in names}
     totals = []
     barrier()
     for _ in range(args.steps):
         flush.zero_()  # L2 flush outside the timed events
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in names]
         e0.record(stream)
-        step(evs)
+        run_step()
         e1.record(stream)
         e1.synchronize()
         totals.append(e0.elapsed_time(e1))
-        for k, nm in enumerate(names):
-            kern[nm].append(evs[k][0].elapsed_time(evs[k][1]))
     barrier()
     clocks = clk.stop()
     ms = float(np.mean(totals))
@@ -267,7 +283,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         pb.nodes.copy_(nodes_h, non_blocking=True)
         pb.alpha.copy_(alpha_h, non_blocking=True)
-        step()
+        run_step()
         cl_h.copy_(pb.cl, non_blocking=True)
         grad_h.copy_(pb.grad, non_blocking=True)
         torch.cuda.synchronize()
@@ -313,9 +329,7 @@ def run_ours(args):
                 "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
                 "peak_source": alu_src if dk["bound"] == "alu"
                 else "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    launches_per_step = len(names)
-    if args.mode == "mixed" and pb.n_max + 1 > 230:
-        launches_per_step += 1  # the global-memory LU variant is launched as well
+    launches_per_step = pb.launches_per_step(with_grad=True)
     out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -326,6 +340,8 @@ def run_ours(args):
                       "l2": "flushed before every timed step (%d MB write)"
                             % (flush.numel() * 4 // 2**20),
                       "max_iter": args.max_iter, "tol": args.tol,
+                      "graph": bool(args.graph), "size_buckets": len(pb.buckets),
+                      "lu_global_buckets": int(sum(pb.lu_global)),
                       "parallelism": "dp%d (independent airfoils)" % world},
            "gradients_per_s": value,
            "kernels": kernels,
@@ -358,6 +374,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the calls one by one instead of replaying a CUDA graph")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--batch", type=int, default=None,
                     help="evaluate only the first BATCH airfoils of the workload (profiling)")
     args = ap.parse_args()

@@ -24,7 +24,7 @@ cudaError_t launch_forces(const Batch&, const double*, const double*, const doub
 cudaError_t launch_assemble_df(const Batch&, const double*, const double*, float*, float*,
                                double*, int32_t*, cudaStream_t);
 cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_t*, int32_t*,
-                            cudaStream_t);
+                            bool, cudaStream_t);
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t);
@@ -48,10 +48,11 @@ int mode_of(int flags) {
 
 bool flags_ok(int flags) {
   const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
-                    PANEL_REUSE_FACTOR;
+                    PANEL_REUSE_FACTOR | PANEL_LU_GLOBAL;
   if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
   const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
   if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;
+  if ((flags & PANEL_LU_GLOBAL) && mode_of(flags) != PANEL_MIXED) return false;
   return stage == 0 || mode_of(flags) == PANEL_MIXED;
 }
 
@@ -148,7 +149,9 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
   }
   if (!A_hi || !A_lo || !LU || max_iter < 0 || !(tol > 0.0)) return PANEL_EINVAL;
   cudaError_t e = cudaSuccess;
-  if (!reuse) e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters, s);
+  if (!reuse)
+    e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters,
+                               (flags & PANEL_LU_GLOBAL) != 0, s);
   if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
                                adj ? lambda : nullptr, max_iter, tol, info, iters, s);

@@ -281,14 +281,12 @@ cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* la
   const size_t smem = adjoint_df_smem(bt.n_max);
   cudaError_t e;
   if (bt.n_max <= kPartialsN) {
-    e = cudaFuncSetAttribute(k_adjoint_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = ensure_smem(k_adjoint_df<true>, smem);
     if (e != cudaSuccess) return e;
     k_adjoint_df<true><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad,
                                                info);
   } else {
-    e = cudaFuncSetAttribute(k_adjoint_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = ensure_smem(k_adjoint_df<false>, smem);
     if (e != cudaSuccess) return e;
     k_adjoint_df<false><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl,
                                                 grad, info);

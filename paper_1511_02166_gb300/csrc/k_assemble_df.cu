@@ -96,8 +96,7 @@ cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const doubl
                                float* A_hi, float* A_lo, double* rhs, int32_t* info,
                                cudaStream_t s) {
   const size_t smem = assemble_df_smem(bt.n_max);
-  cudaError_t e = cudaFuncSetAttribute(k_assemble_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem(k_assemble_df, smem);
   if (e != cudaSuccess) return e;
   k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info);
   return cudaGetLastError();

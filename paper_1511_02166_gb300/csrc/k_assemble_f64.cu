@@ -90,8 +90,7 @@ size_t assemble_f64_smem(int n_max) { return (size_t)(7 * n_max + 32) * sizeof(d
 cudaError_t launch_assemble_f64(const Batch& bt, const double* alpha, const double* vinf,
                                 double* A, double* rhs, int32_t* info, cudaStream_t s) {
   size_t smem = assemble_f64_smem(bt.n_max);
-  cudaError_t e = cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem(k_assemble_f64, smem);
   if (e != cudaSuccess) return e;
   k_assemble_f64<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A, rhs, info);
   return cudaGetLastError();

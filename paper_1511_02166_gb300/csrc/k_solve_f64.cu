@@ -312,8 +312,7 @@ cudaError_t launch_adjoint_f64(const Batch& bt, const double* LU, const int32_t*
                                const double* grad_cl, double* grad, const int32_t* info,
                                cudaStream_t s) {
   size_t smem = adjoint_f64_smem(bt.n_max);
-  cudaError_t e = cudaFuncSetAttribute(k_adjoint_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem(k_adjoint_f64, smem);
   if (e != cudaSuccess) return e;
   k_adjoint_f64<<<bt.B, 256, smem, s>>>(bt, LU, piv, u, lambda_in, lambda_out, alpha, vinf, chord,
                                         grad_cl, grad, info);

@@ -52,6 +52,7 @@ struct SolveArgs {
   double tol;
   int32_t* info;
   int32_t* iters;
+  int force_global;  // k_lu_global takes every airfoil, not only m > kSmemM
 };
 
 __device__ __forceinline__ double block_absmax_d(double v, double* red) {
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
   const int n = airfoil_n(bt, b);
   const int m = n + 1;
   if (a.info[b] != 0) return;
-  if (m <= kSmemM) return;  // taken by k_lu_mixed
+  if (m <= kSmemM && !a.force_global) return;  // taken by k_lu_mixed
   if (n > bt.n_max) {
     if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
     return;
@@ -928,38 +929,38 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.tol = tol;
   a.info = info;
   a.iters = iters;
+  a.force_global = 0;
   return a;
 }
 
 // Factor every airfoil (shared-memory kernel for m <= kSmemM, global beyond).
 constexpr size_t kMaxSmem = 232448;
 cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32_t* piv,
-                            int32_t* info, int32_t* iters, cudaStream_t s) {
+                            int32_t* info, int32_t* iters, bool force_global, cudaStream_t s) {
   SolveArgs a = make_args(bt, A_hi, nullptr, LU, piv, nullptr, nullptr, nullptr, nullptr,
                           nullptr, 0, 0.0, info, iters);
+  a.force_global = force_global ? 1 : 0;
   cudaError_t e;
-  if (bt.n_max + 1 > kSmemM) {
+  if (bt.n_max + 1 > kSmemM || force_global) {
     if (lu_global_smem<32>(bt.n_max) <= kMaxSmem) {
       const size_t smem = lu_global_smem<32>(bt.n_max);
-      e = cudaFuncSetAttribute(k_lu_global<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = ensure_smem(k_lu_global<32>, smem);
       if (e != cudaSuccess) return e;
       k_lu_global<32><<<bt.B, kThreads, smem, s>>>(a);
     } else {
       const size_t smem = lu_global_smem<16>(bt.n_max);
-      e = cudaFuncSetAttribute(k_lu_global<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+      e = ensure_smem(k_lu_global<16>, smem);
       if (e != cudaSuccess) return e;
       k_lu_global<16><<<bt.B, kThreads, smem, s>>>(a);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || force_global) return e;
   }
   Batch bs = bt;
   bs.n_max = min(bt.n_max, kSmemM - 1);
   a.bt = bs;
   const size_t smem = lu_mixed_smem(bs.n_max);
-  e = cudaFuncSetAttribute(k_lu_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = ensure_smem(k_lu_mixed, smem);
   if (e != cudaSuccess) return e;
   k_lu_mixed<<<bt.B, kThreads, smem, s>>>(a);
   return cudaGetLastError();
@@ -974,8 +975,7 @@ cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_l
   SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
                           rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
   const size_t smem = ir_mixed_smem(bt.n_max);
-  cudaError_t e = cudaFuncSetAttribute(k_ir_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_smem(k_ir_mixed, smem);
   if (e != cudaSuccess) return e;
   k_ir_mixed<<<bt.B, kThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -8,6 +8,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "../../include/panel.h"
 
 namespace panel {
@@ -110,6 +114,27 @@ __device__ __forceinline__ int load_and_check_geometry(const double* nodes, int 
   area = block_sum(area, scratch);
   if (!(area > 0.0)) return PANEL_INFO_ORIENTATION;
   return 0;
+}
+
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than any earlier one on the current device: after a warm-up call no
+// attribute is set any more, so later calls can be captured into CUDA graphs.
+inline cudaError_t ensure_smem_impl(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& g = granted[std::make_pair(dev, kernel)];
+  if (bytes <= g || bytes <= 48 * 1024) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g = bytes;
+  return e;
+}
+template <typename K>
+inline cudaError_t ensure_smem(K kernel, size_t bytes) {
+  return ensure_smem_impl(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 }  // namespace panel

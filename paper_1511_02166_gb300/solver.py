@@ -2,16 +2,68 @@
 
 ``PanelBatch`` owns the torch tensors of one ragged population (inputs,
 matrices, factors, solutions, forces and gradients) and runs the four library
-calls on the current torch stream.  ``PanelCl`` is a ``torch.autograd.Function``
-mapping node coordinates to Cl whose backward is ``panel_adjoint``.
-Everything numerical happens in the CUDA library.
+calls on the current torch stream.  A ragged population is cut into size
+buckets (contiguous runs of the size-sorted launch order), each launched with
+its own size bound so that small airfoils get small shared-memory footprints;
+``autotune()`` times the two LU variants per bucket and remembers the faster
+one, and ``capture()`` records a whole step into a CUDA graph.  ``PanelCl`` is
+a ``torch.autograd.Function`` mapping node coordinates to Cl whose backward is
+``panel_adjoint``.  Everything numerical happens in the CUDA library.
 """
 from __future__ import annotations
+
+import json
+import os
+import threading
 
 import numpy as np
 import torch
 
 from . import binding as bd
+
+_tune_lock = threading.Lock()
+
+
+def _tune_cache_path():
+    return os.environ.get("PANEL_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "panel_gb300",
+                                       "autotune.json"))
+
+
+def _load_tune_cache():
+    try:
+        with open(_tune_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_tune_cache(cache):
+    path = _tune_cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def size_buckets(sorted_sizes, width):
+    """Contiguous runs of the (descending) sizes with equal ceil(n / width):
+    a list of (start, count, n_max)."""
+    out = []
+    start = 0
+    B = len(sorted_sizes)
+    while start < B:
+        key = -(-int(sorted_sizes[start]) // width)
+        end = start + 1
+        while end < B and -(-int(sorted_sizes[end]) // width) == key:
+            end += 1
+        out.append((start, end - start, max(int(sorted_sizes[start]), 3)))
+        start = end
+    return out
 
 MODES = {"fp64": bd.PANEL_FP64, "mixed": bd.PANEL_MIXED}
 
@@ -32,7 +84,8 @@ class PanelBatch:
     """
 
     def __init__(self, nodes, offsets, alpha, mode: str = "mixed", vinf=None, chord=None,
-                 device="cuda", max_iter: int = 10, tol: float = 1e-12):
+                 device="cuda", max_iter: int = 10, tol: float = 1e-12,
+                 bucket_width: int | None = 64):
         self.device = _require_cuda(device)
         if mode not in MODES:
             raise ValueError("mode must be one of %s" % sorted(MODES))
@@ -82,23 +135,36 @@ class PanelBatch:
         self.cd_p = torch.empty(self.B, **f64)
         self.grad = torch.empty(total, 2, **f64)
         self.have_lambda = False
+        sizes = np.diff(offsets_h)
+        sorted_sizes = sizes[order_h] if self.B else sizes
+        if bucket_width is None or self.B == 0:
+            self.buckets = [(0, self.B, self.n_max)] if self.B else []
+        else:
+            self.buckets = size_buckets(sorted_sizes, int(bucket_width))
+        self.lu_global = [False] * len(self.buckets)
+        self.graph = None
 
-    # -- the four library calls -------------------------------------------------
+    # -- the four library calls (per size bucket) --------------------------------
     def assemble(self):
-        bd.panel_assemble(self.B, self.n_max, self.flags, self.nodes, self.node_offsets,
-                          self.mat_offsets, self.order, self.alpha, self.vinf, self.A64,
-                          self.A_hi, self.A_lo, self.rhs, self.info)
+        for start, cnt, nmax in self.buckets:
+            bd.panel_assemble(cnt, nmax, self.flags, self.nodes, self.node_offsets,
+                              self.mat_offsets, self.order[start:], self.alpha, self.vinf,
+                              self.A64, self.A_hi, self.A_lo, self.rhs, self.info)
 
     def solve(self, with_adjoint: bool = False, stage: str = "all"):
         """stage 'all' (factor + refine), 'factor' (LU only) or 'refine' (reuse the
         stored LU; mixed mode only)."""
         flags = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
         flags |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
-        bd.panel_solve(self.B, self.n_max, flags, self.nodes, self.node_offsets,
-                       self.mat_offsets, self.order, self.A64, self.A_hi, self.A_lo, self.LU,
-                       self.piv, self.rhs, self.vinf, self.chord, self.u,
-                       self.lam if with_adjoint else None, self.max_iter, self.tol, self.info,
-                       self.iters)
+        for k, (start, cnt, nmax) in enumerate(self.buckets):
+            f = flags
+            if self.lu_global[k] and stage != "refine":
+                f |= bd.PANEL_LU_GLOBAL
+            bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
+                           self.order[start:], self.A64, self.A_hi, self.A_lo, self.LU,
+                           self.piv, self.rhs, self.vinf, self.chord, self.u,
+                           self.lam if with_adjoint else None, self.max_iter, self.tol,
+                           self.info, self.iters)
         if stage != "factor":
             self.have_lambda = with_adjoint
 
@@ -109,11 +175,13 @@ class PanelBatch:
     def adjoint(self, grad_cl=None):
         gc = None if grad_cl is None else torch.as_tensor(
             grad_cl, dtype=torch.float64, device=self.device).contiguous()
-        bd.panel_adjoint(self.B, self.n_max, self.flags, self.nodes, self.node_offsets,
-                         self.mat_offsets, self.order, self.A64, self.A_hi, self.A_lo, self.LU,
-                         self.piv, self.u, self.lam if self.have_lambda else None,
-                         None if self.have_lambda else self.lam, self.alpha, self.vinf,
-                         self.chord, gc, self.grad, self.max_iter, self.tol, self.info)
+        for start, cnt, nmax in self.buckets:
+            bd.panel_adjoint(cnt, nmax, self.flags, self.nodes, self.node_offsets,
+                             self.mat_offsets, self.order[start:], self.A64, self.A_hi,
+                             self.A_lo, self.LU, self.piv, self.u,
+                             self.lam if self.have_lambda else None,
+                             None if self.have_lambda else self.lam, self.alpha, self.vinf,
+                             self.chord, gc, self.grad, self.max_iter, self.tol, self.info)
         self.have_lambda = True
 
     def run(self, with_grad: bool = False):
@@ -124,6 +192,91 @@ class PanelBatch:
         if with_grad:
             self.adjoint()
         return self
+
+    def step(self, with_grad: bool = True):
+        """One pass of the whole hot path; replays the captured graph if there is one."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.run(with_grad=with_grad)
+
+    def launches_per_step(self, with_grad: bool = True) -> int:
+        """Kernel launches of one step (mixed mode: per bucket assemble, factor
+        (the global variant is launched as well when the bucket holds m > 230),
+        refine, adjoint; one forces launch)."""
+        n = 1  # forces
+        for k, (start, cnt, nmax) in enumerate(self.buckets):
+            n += 1  # assemble
+            if self.flags == bd.PANEL_MIXED:
+                n += 1 if self.lu_global[k] else (2 if nmax + 1 > 230 else 1)
+                n += 1  # refine
+            else:
+                n += 1
+            n += 1 if with_grad else 0
+        return n
+
+    # -- autotuning and graph capture -------------------------------------------
+    def autotune(self, reps: int = 3, use_cache: bool = True):
+        """Pick, per size bucket, the faster of the two LU variants (mixed mode):
+        the shared-memory-resident factor (one airfoil per SM) or the blocked
+        global-memory factor (several airfoils per SM).  Results are cached by
+        device and bucket size bound."""
+        if self.flags != bd.PANEL_MIXED or not self.buckets:
+            return dict()
+        dev = torch.cuda.get_device_name(self.device)
+        with _tune_lock:
+            cache = _load_tune_cache() if use_cache else {}
+        self.assemble()
+        torch.cuda.synchronize(self.device)
+        chosen = {}
+        for k, (start, cnt, nmax) in enumerate(self.buckets):
+            if nmax + 1 > 230:
+                self.lu_global[k] = True  # the only variant that holds it
+                continue
+            key = "%s|n%d|b%d" % (dev, nmax, min(cnt, 1024) // 152 * 152)
+            if key in cache:
+                self.lu_global[k] = bool(cache[key])
+                chosen[key] = cache[key]
+                continue
+            times = []
+            for variant in (False, True):
+                f = bd.PANEL_MIXED | bd.PANEL_FACTOR_ONLY | (bd.PANEL_LU_GLOBAL if variant else 0)
+
+                def call(f=f, start=start, cnt=cnt, nmax=nmax):
+                    bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets,
+                                   self.mat_offsets, self.order[start:], None, self.A_hi,
+                                   self.A_lo, self.LU, self.piv, self.rhs, None, None, self.u,
+                                   None, self.max_iter, self.tol, self.info, self.iters)
+                call()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    call()
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            self.lu_global[k] = times[1] < times[0]
+            chosen[key] = self.lu_global[k]
+            cache[key] = self.lu_global[k]
+        if use_cache:
+            with _tune_lock:
+                merged = _load_tune_cache()
+                merged.update(cache)
+                _store_tune_cache(merged)
+        self.info.zero_()
+        return chosen
+
+    def capture(self, with_grad: bool = True):
+        """Record one step into a CUDA graph (after a warm-up step outside it)."""
+        self.graph = None
+        self.run(with_grad=with_grad)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(with_grad=with_grad)
+        self.graph = g
+        return g
 
     # -- views -----------------------------------------------------------------
     def vec(self, t, b):

@@ -1,0 +1,98 @@
+"""GPU tests of the batching layer: size buckets, the two LU variants chosen by
+autotuning, and CUDA-graph replay with new inputs written into the captured
+buffers.  Every result is checked against the oracle (long double build, as in
+the ragged tests: gamma within 1e-10, Cl within 1e-10)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_02166_gb300 import inputs
+from tests.gpu_util import cl_err, need_gpu, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(seed, sizes):
+    rng = np.random.default_rng(seed)
+    air = [inputs.naca4(rng.uniform(0, .06), rng.uniform(.2, .6), rng.uniform(.08, .18), n)
+           for n in sizes]
+    return inputs.pack(air, rng.uniform(-0.07, 0.17, len(air)))
+
+
+def _check(pop, u, cl, tol=1e-10):
+    with oracle.extended():
+        ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < tol, b
+    assert cl_err(cl, ref["cl"]) < tol
+
+
+SIZES = [512, 500, 449, 300, 257, 231, 229, 200, 130, 129, 128, 64, 63, 33, 3]
+
+
+def test_buckets_match_single_launch():
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = _ragged(5, SIZES)
+    one = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=None)
+    many = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64)
+    assert len(one.buckets) == 1 and len(many.buckets) == 6
+    one.run(with_grad=True)
+    many.run(with_grad=True)
+    torch.cuda.synchronize()
+    assert np.all(many.info.cpu().numpy() == 0)
+    u1, u2 = one.u.cpu().numpy(), many.u.cpu().numpy()
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        assert rel_inf(u2[o:o + n + 1], u1[o:o + n + 1]) < 1e-12, b
+    g1, g2 = one.grad.cpu().numpy(), many.grad.cpu().numpy()
+    for b in range(pop.batch):
+        s = slice(pop.offsets[b], pop.offsets[b + 1])
+        assert rel_inf(g2[s], g1[s]) < 1e-11, b
+    _check(pop, u2, many.cl.cpu().numpy())
+
+
+def test_forced_global_lu_in_every_bucket():
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = _ragged(6, SIZES)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64)
+    pb.lu_global = [True] * len(pb.buckets)
+    pb.run(with_grad=False)
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop, pb.u.cpu().numpy(), pb.cl.cpu().numpy())
+
+
+def test_autotune_then_graph_replay_with_new_inputs(tmp_path, monkeypatch):
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    monkeypatch.setenv("PANEL_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    sizes = [64 + (37 * k) % 449 for k in range(40)]
+    pop = _ragged(7, sizes)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    chosen = pb.autotune(reps=1)
+    assert (tmp_path / "tune.json").exists() and len(chosen) >= 1
+    pb.capture(with_grad=True)
+    # same sizes, new shapes and angles written into the captured input buffers
+    pop2 = _ragged(8, sizes)
+    pb.nodes.copy_(torch.from_numpy(pop2.nodes))
+    pb.alpha.copy_(torch.from_numpy(pop2.alpha))
+    pb.step()
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop2, pb.u.cpu().numpy(), pb.cl.cpu().numpy())
+    ref, info = oracle.cl_gradient_batch(pop2.nodes, pop2.offsets, pop2.alpha)
+    g = pb.grad.cpu().numpy()
+    for b in range(0, pop2.batch, 7):
+        s = slice(pop2.offsets[b], pop2.offsets[b + 1])
+        assert rel_inf(g[s], ref[s]) < 1e-9, b
+    # a second instance reads the cached choice instead of timing again
+    pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    assert pb2.autotune(reps=1) == chosen and pb2.lu_global == pb.lu_global
