@@ -24,10 +24,11 @@
 // Layout: one block per airfoil; each warp owns 32 consecutive columns (panels
 // i, one per lane) and sweeps all rows j: A_i, B_i accumulate in the lane's
 // registers (double-float), the row sums P_j are warp-reduced and kept as one
-// double-float partial per warp in shared memory (PARTIALS, n <= kPartialsN),
-// summed at the end; beyond that size they go into shared FP64 accumulators by
-// atomics (FP64 instructions run at 1/64 of the FP32 rate on GB300, so the
-// partials are the fast path).
+// double-float partial per warp in shared memory, summed at the end
+// (n <= kPartialsN).  Larger airfoils take k_adjoint_df_split: the panels are
+// cut into chunks of 256, one block per (airfoil, chunk), and every term of the
+// formula above is added into the caller's gradient buffer by FP64 atomics
+// once per row window, column or node (a few per pair row, not per pair).
 #include "panel_common.cuh"
 #include "panel_df.cuh"
 
@@ -142,7 +143,6 @@ __device__ __forceinline__ df2 warp_sum_df2(df2 a) {
 
 constexpr int kPartialsN = 512;
 
-template <bool PARTIALS>
 __global__ void __launch_bounds__(256) k_adjoint_df(
     Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
     const double* __restrict__ alpha, const double* __restrict__ vinf,
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
   float* lamh = reinterpret_cast<float*>(Bc + 2 * ld);    // n_max (lambda as float pairs)
   float* laml = lamh + ld;
   float* pc = laml + ld;                                  // kPanelFields * n_max
-  float4* Pw = reinterpret_cast<float4*>(pc + kPanelFields * ld);  // 8 * n_max (PARTIALS)
+  float4* Pw = reinterpret_cast<float4*>(pc + kPanelFields * ld);  // 8 * n_max
 
   const int b = bt.order[blockIdx.x];
   const int n = airfoil_n(bt, b);
@@ -176,9 +176,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     xs[k] = nodes[2 * k];
     ys[k] = nodes[2 * k + 1];
-    P[2 * k] = P[2 * k + 1] = 0.0;
-    if (PARTIALS)
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Pw[w * ld + k] = make_float4(0, 0, 0, 0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Pw[w * ld + k] = make_float4(0, 0, 0, 0);
     const df2 l = df_from_double(lb[k]);
     lamh[k] = l.hi;
     laml[k] = l.lo;
@@ -213,14 +211,9 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
       rx = warp_sum_df2(rx);
       ry = warp_sum_df2(ry);
       if (lane == 0) {
-        if (PARTIALS) {
-          const float4 q = Pw[warp * ld + j];
-          const df2 sx = df_add(mkdf(q.x, q.y), rx), sy = df_add(mkdf(q.z, q.w), ry);
-          Pw[warp * ld + j] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
-        } else {
-          atomicAdd(&P[2 * j], (double)rx.hi + (double)rx.lo);
-          atomicAdd(&P[2 * j + 1], (double)ry.hi + (double)ry.lo);
-        }
+        const float4 q = Pw[warp * ld + j];
+        const df2 sx = df_add(mkdf(q.x, q.y), rx), sy = df_add(mkdf(q.z, q.w), ry);
+        Pw[warp * ld + j] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
       }
     }
     if (ok) {
@@ -231,19 +224,17 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     }
   }
   __syncthreads();
-  if (PARTIALS) {
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      df2 sx = mkdf(0.0f), sy = mkdf(0.0f);
-      for (int w = 0; w < nw; ++w) {
-        const float4 q = Pw[w * ld + k];
-        sx = df_add(sx, mkdf(q.x, q.y));
-        sy = df_add(sy, mkdf(q.z, q.w));
-      }
-      P[2 * k] = df_to_double(sx);
-      P[2 * k + 1] = df_to_double(sy);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    df2 sx = mkdf(0.0f), sy = mkdf(0.0f);
+    for (int w = 0; w < nw; ++w) {
+      const float4 q = Pw[w * ld + k];
+      sx = df_add(sx, mkdf(q.x, q.y));
+      sy = df_add(sy, mkdf(q.z, q.w));
     }
-    __syncthreads();
+    P[2 * k] = df_to_double(sx);
+    P[2 * k + 1] = df_to_double(sy);
   }
+  __syncthreads();
   const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
   const double ca = cos(alpha[b]), sa = sin(alpha[b]);
   const double gscale = grad_cl ? grad_cl[b] : 1.0;
@@ -267,11 +258,162 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Large airfoils (n > kPartialsN): block (x, y) takes the panels [256 y,
+// 256 y + 256) of airfoil order[x] -- one 32-column block per warp -- against
+// every control point.  Shared memory holds the control points of all rows,
+// lambda, and the constants of the block's own panels only.  Rows are swept in
+// windows of 32: each warp leaves its warp-reduced P_j partials in shared
+// memory, one warp sums the eight and adds lambda_j P_j / 2 to nodes j and
+// j + 1 of the gradient.  The caller's gradient rows are set to zero (or NaN for
+// a failed airfoil) by k_adjoint_prepare first; every contribution goes in by
+// an FP64 atomic add, so the summation order, and the last bits, vary between
+// runs.
+// ---------------------------------------------------------------------------
+constexpr int kSplitChunk = 256;
+
+__global__ void k_adjoint_prepare(Batch bt, double* __restrict__ grad,
+                                  const int32_t* __restrict__ info) {
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const bool bad = (info && info[b] != 0) || n > bt.n_max || n < 3;
+  double* gout = grad + 2 * bt.node_off[b];
+  for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) gout[k] = bad ? nan("") : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_adjoint_df_split(
+    Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
+    const double* __restrict__ alpha, const double* __restrict__ vinf,
+    const double* __restrict__ chord, const double* __restrict__ grad_cl,
+    double* __restrict__ grad, const int32_t* __restrict__ info) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = bt.n_max;
+  float4* tlog = reinterpret_cast<float4*>(smraw);        // 257
+  float2* tatan = reinterpret_cast<float2*>(tlog + 257);  // 34
+  float4* win = reinterpret_cast<float4*>(tatan + 34);    // 8 warps x 32 rows
+  float* lamh = reinterpret_cast<float*>(win + 8 * 32);   // n_max
+  float* laml = lamh + ld;                                // n_max
+  float* rp = laml + ld;                                  // 6 * n_max control points
+  float* cpc = rp + 6 * ld;                               // kPanelFields * kSplitChunk
+
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const int i0 = blockIdx.y * kSplitChunk;
+  if ((info && info[b] != 0) || n > ld || n < 3 || i0 >= n) return;
+  const double* nodes = bt.nodes + 2 * bt.node_off[b];
+  const double* ub = u + vec_off(bt, b);
+  const double* lb = lambda + vec_off(bt, b);
+  double* gout = grad + 2 * bt.node_off[b];
+  const int nc = min(kSplitChunk, n - i0);
+  df_stage_tables(tlog, tatan);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int k1 = (k + 1 == n) ? 0 : k + 1;
+    const point3 c = make_point(0.5 * (nodes[2 * k] + nodes[2 * k1]),
+                                0.5 * (nodes[2 * k + 1] + nodes[2 * k1 + 1]));
+    rp[kCx * ld + k] = c.xh;
+    rp[(kCx + 1) * ld + k] = c.xm;
+    rp[(kCx + 2) * ld + k] = c.xl;
+    rp[kCy * ld + k] = c.yh;
+    rp[(kCy + 1) * ld + k] = c.ym;
+    rp[(kCy + 2) * ld + k] = c.yl;
+    const df2 l = df_from_double(lb[k]);
+    lamh[k] = l.hi;
+    laml[k] = l.lo;
+  }
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int i = i0 + k, i1 = (i + 1 == n) ? 0 : i + 1;
+    panel_constants(cpc, kSplitChunk, k, nodes[2 * i], nodes[2 * i + 1], nodes[2 * i1],
+                    nodes[2 * i1 + 1]);
+  }
+  const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
+  const double gscale = grad_cl ? grad_cl[b] : 1.0;
+  const double w2pi = gscale * kInvTwoPi;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int il = 32 * warp + lane;  // column within the chunk
+  const int i = i0 + il;
+  const bool ok = il < nc;
+  const bool warp_on = 32 * warp < nc;
+  const int ic = ok ? il : 0;
+  const df2 ui = ok ? df_from_double(ub[i]) : mkdf(0.0f);
+  df2 sAx = mkdf(0.0f), sAy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int jn = min(32, n - j0);
+    if (warp_on) {
+      for (int t = 0; t < jn; ++t) {
+        const int j = j0 + t;
+        const point3 pj = load_point(rp, ld, j);
+        df2 gpx, gpy, gbx, gby;
+        panel_dG_df(pj, cpc, kSplitChunk, ic, ok && i == j, tlog, tatan, gpx, gpy, gbx, gby);
+        const df2 lj = mkdf(lamh[j], laml[j]);
+        sBx = df_add(sBx, df_mul(lj, gbx));
+        sBy = df_add(sBy, df_mul(lj, gby));
+        sAx = df_sub(sAx, df_mul(lj, df_add(gpx, gbx)));
+        sAy = df_sub(sAy, df_mul(lj, df_add(gpy, gby)));
+        df2 rx = ok ? df_mul(ui, gpx) : mkdf(0.0f);
+        df2 ry = ok ? df_mul(ui, gpy) : mkdf(0.0f);
+        rx = warp_sum_df2(rx);
+        ry = warp_sum_df2(ry);
+        if (lane == 0) win[warp * 32 + t] = make_float4(rx.hi, rx.lo, ry.hi, ry.lo);
+      }
+    } else if (lane < jn) {
+      win[warp * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+    if (warp == 0 && lane < jn) {
+      df2 sx = mkdf(0.0f), sy = mkdf(0.0f);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const float4 q = win[w * 32 + lane];
+        sx = df_add(sx, mkdf(q.x, q.y));
+        sy = df_add(sy, mkdf(q.z, q.w));
+      }
+      // lambda_j P_j / 2 belongs to the nodes j and j + 1 (the ends of panel j)
+      const int j = j0 + lane, j1 = (j + 1 == n) ? 0 : j + 1;
+      const double f = 0.5 * w2pi * lb[j];
+      const double px = f * df_to_double(sx), py = f * df_to_double(sy);
+      atomicAdd(&gout[2 * j], px);
+      atomicAdd(&gout[2 * j + 1], py);
+      atomicAdd(&gout[2 * j1], px);
+      atomicAdd(&gout[2 * j1 + 1], py);
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    // u_i A_i belongs to node i (start of panel i), u_i B_i to node i + 1
+    const int i1 = (i + 1 == n) ? 0 : i + 1;
+    const double f = w2pi * ub[i];
+    atomicAdd(&gout[2 * i], f * df_to_double(sAx));
+    atomicAdd(&gout[2 * i + 1], f * df_to_double(sAy));
+    atomicAdd(&gout[2 * i1], f * df_to_double(sBx));
+    atomicAdd(&gout[2 * i1 + 1], f * df_to_double(sBy));
+  }
+  if (blockIdx.y == 0) {
+    // the terms that need no pair sums, once per node
+    const double ca = cos(alpha[b]), sa = sin(alpha[b]);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const int km = (k == 0) ? n - 1 : k - 1;
+      const int k1 = (k + 1 == n) ? 0 : k + 1;
+      const double hkx = nodes[2 * k1] - nodes[2 * k], hky = nodes[2 * k1 + 1] - nodes[2 * k + 1];
+      const double hmx = nodes[2 * k] - nodes[2 * km], hmy = nodes[2 * k + 1] - nodes[2 * km + 1];
+      const double Lk = sqrt(hkx * hkx + hky * hky), Lm = sqrt(hmx * hmx + hmy * hmy);
+      double gx = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
+      double gy = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
+      gx += 0.5 * v * (-sa) * (lb[km] + lb[k]);
+      gy += 0.5 * v * ca * (lb[km] + lb[k]);
+      atomicAdd(&gout[2 * k], gscale * gx);
+      atomicAdd(&gout[2 * k + 1], gscale * gy);
+    }
+  }
+}
+
 size_t adjoint_df_smem(int n_max) {
-  size_t b = 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
-             (size_t)kPanelFields * n_max * 4;
-  if (n_max <= kPartialsN) b += (size_t)8 * n_max * 16;
-  return b;
+  if (n_max > kPartialsN)
+    return 257 * 16 + 34 * 8 + 8 * 32 * 16 + (size_t)n_max * 8 * 4 +
+           (size_t)kPanelFields * kSplitChunk * 4;
+  return 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
+         (size_t)kPanelFields * n_max * 4 + (size_t)8 * n_max * 16;
 }
 
 cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* lambda,
@@ -281,15 +423,16 @@ cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* la
   const size_t smem = adjoint_df_smem(bt.n_max);
   cudaError_t e;
   if (bt.n_max <= kPartialsN) {
-    e = ensure_smem(k_adjoint_df<true>, smem);
+    e = ensure_smem(k_adjoint_df, smem);
     if (e != cudaSuccess) return e;
-    k_adjoint_df<true><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad,
-                                               info);
+    k_adjoint_df<<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad, info);
   } else {
-    e = ensure_smem(k_adjoint_df<false>, smem);
+    e = ensure_smem(k_adjoint_df_split, smem);
     if (e != cudaSuccess) return e;
-    k_adjoint_df<false><<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl,
-                                                grad, info);
+    k_adjoint_prepare<<<bt.B, 256, 0, s>>>(bt, grad, info);
+    const dim3 grid(bt.B, (bt.n_max + kSplitChunk - 1) / kSplitChunk);
+    k_adjoint_df_split<<<grid, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad,
+                                               info);
   }
   return cudaGetLastError();
 }

@@ -1,0 +1,349 @@
+// k_lu_large.cu -- FP32 LU of large airfoils (m = n + 1 > kLargeM) for the
+// mixed-precision path: blocked right-looking elimination, step-synchronous
+// across the batch, so that each block column is spread over many blocks
+// instead of one block per airfoil.
+//
+// Per block column k0 (kBW = 128 wide) three launches:
+//   k_large_diag    one block per airfoil: LU of the kBW x kBW diagonal block D
+//                   in shared memory, with the pivot search restricted to the
+//                   rows of D; its row exchanges are applied to the rest of
+//                   those rows.
+//   k_large_trsm    U12 = L11^{-1} A12 (a column per thread) and
+//                   L21 = A21 U11^{-1} (a row per thread), in slabs of 128
+//                   columns / rows staged in shared memory.
+//   k_large_update  A22 -= L21 U12 in 128 x 128 tiles, K in chunks of 64,
+//                   8 x 8 outputs per thread (FP32 FMA).
+// Each of the three takes gridDim.y blocks per airfoil striding over its
+// slabs / tiles, so a batch of few airfoils still fills the GPU.
+//
+// Pivoting.  The system is the collocation matrix of the logarithmic
+// single-layer kernel (Section 2) bordered by the Kutta row and the C column
+// (rescaled by s = mean |A_jj|).  For this family partial pivoting over the
+// whole column exchanges almost nothing (only the first and the bordered last
+// rows), and LU with no exchanges at all shows element growth ~1.3 at
+// n = 2048.  Restricting the search to the diagonal block keeps every
+// exchange inside the block's rows -- which is what lets L21 be a plain
+// triangular solve over all rows in parallel -- and the refinement with the
+// double-float residual takes the result to the same tolerance (it converges
+// in as few steps as with full partial pivoting).  An exactly zero pivot still
+// sets info[b] = its index + 1.
+//
+// The finished factor has the layout of the one-block kernels: P A = L U in
+// the caller's LU buffer (ld = m), pivots as sequential exchanges, and the
+// 32 x 32 diagonal blocks of L and U replaced by their inverses.
+#include "lu_mixed.cuh"
+
+namespace panel {
+
+constexpr int kBW = 128;      // block column width
+constexpr int kLdD = kBW + 1;
+constexpr int kUpdK = 64;     // K chunk of the update
+constexpr int kLdS = 132;     // row stride of the update's staged operands
+
+size_t lu_large_min_m() { return kLargeM + 1; }
+
+__device__ __forceinline__ bool large_live(const SolveArgs& a, int b, int& n, int& m) {
+  n = airfoil_n(a.bt, b);
+  m = n + 1;
+  return m > kLargeM && n <= a.bt.n_max && a.info[b] == 0;
+}
+
+// Scaled copy A_hi -> LU (border row and column times s); rows strided over
+// gridDim.y blocks per airfoil.
+__global__ void __launch_bounds__(256) k_large_init(SolveArgs a) {
+  __shared__ double red[32];
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b), m = n + 1;
+  if (m <= kLargeM || a.info[b] != 0) return;
+  if (n > bt.n_max) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
+    return;
+  }
+  const int64_t moff = bt.mat_off[b];
+  const float* Ah = a.A_hi + moff;
+  float* F = a.LU + moff;
+  const float sf = (float)border_scale(Ah, n, m, red);
+  for (int r = blockIdx.y; r < m; r += gridDim.y) {
+    const float* src = Ah + r * m;
+    float* dst = F + r * m;
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const float v = src[c];
+      dst[c] = ((c == n && r < n) || r == n) ? v * sf : v;
+    }
+  }
+}
+
+// LU of the diagonal block with partial pivoting inside the block.
+__global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int k0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* D = reinterpret_cast<float*>(smraw);          // kBW x kLdD
+  int* sp = reinterpret_cast<int*>(D + kBW * kLdD);    // kBW
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  int n, m;
+  if (!large_live(a, b, n, m) || k0 >= m) return;
+  const int kb = min(kBW, m - k0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* F = a.LU + bt.mat_off[b];
+  for (int e = tid; e < kBW * kBW; e += 256) {
+    const int r = e / kBW, c = e % kBW;
+    D[r * kLdD + c] = (r < kb && c < kb) ? F[(k0 + r) * m + k0 + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int q = 0; q < kb; ++q) {
+    if (warp == 0) {
+      // argmax |D[r][q]| over the rows q..kb-1, lowest row on ties
+      float bv = -1.0f;
+      int br = kBW;
+#pragma unroll
+      for (int t = 0; t < kBW / 32; ++t) {
+        const int r = lane + 32 * t;
+        const float v = (r >= q && r < kb) ? fabsf(D[r * kLdD + q]) : -1.0f;
+        if (v > bv) {
+          bv = v;
+          br = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) {
+          bv = ov;
+          br = orr;
+        }
+      }
+      if (lane == 0) sp[q] = (br < kb) ? br : q;
+    }
+    __syncthreads();
+    const int p = sp[q];
+    if (!(fabsf(D[p * kLdD + q]) > 0.0f)) {  // exact zero (or NaN) pivot: uniform exit
+      if (tid == 0) {
+        a.info[b] = k0 + q + 1;
+        if (a.iters) a.iters[b] = 0;
+      }
+      return;
+    }
+    if (p != q && tid < kBW) {
+      const float t = D[q * kLdD + tid];
+      D[q * kLdD + tid] = D[p * kLdD + tid];
+      D[p * kLdD + tid] = t;
+    }
+    __syncthreads();
+    const float inv = 1.0f / D[q * kLdD + q];
+    for (int r = q + 1 + warp; r < kb; r += 8) {
+      const float l = D[r * kLdD + q] * inv;
+      for (int c = q + 1 + lane; c < kb; c += 32)
+        D[r * kLdD + c] = fmaf(-l, D[q * kLdD + c], D[r * kLdD + c]);
+      __syncwarp();
+      if (lane == 0) D[r * kLdD + q] = l;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kb * kb; e += 256) {
+    const int r = e / kb, c = e % kb;
+    F[(k0 + r) * m + k0 + c] = D[r * kLdD + c];
+  }
+  int32_t* gpiv = a.piv + vec_off(bt, b);
+  if (tid < kb) gpiv[k0 + tid] = k0 + sp[tid];
+  // the same exchanges, in order, on the columns outside the block
+  for (int c = tid; c < m; c += 256) {
+    if (c >= k0 && c < k0 + kb) continue;
+    for (int q = 0; q < kb; ++q) {
+      const int p = sp[q];
+      if (p != q) {
+        float* x = F + (k0 + q) * m + c;
+        float* y = F + (k0 + p) * m + c;
+        const float t = *x;
+        *x = *y;
+        *y = t;
+      }
+    }
+  }
+}
+
+size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + kBW * 4; }
+
+// U12 = L11^{-1} A12 and L21 = A21 U11^{-1}.  Tasks 0..ns-1 are 128-column
+// slabs of A12, tasks ns..2ns-1 are 128-row slabs of A21; the slab is staged in
+// shared memory and every thread solves its own column (row) there.
+__global__ void __launch_bounds__(128) k_large_trsm(SolveArgs a, int k0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* D = reinterpret_cast<float*>(smraw);  // kBW x kLdD: L11 \ U11
+  float* X = D + kBW * kLdD;                   // kBW x kLdD slab
+  float* dinv = X + kBW * kLdD;                // kBW
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  int n, m;
+  if (!large_live(a, b, n, m)) return;
+  const int k1 = k0 + kBW;  // a block column narrower than kBW is the last one
+  if (k1 >= m) return;
+  const int tid = threadIdx.x;
+  float* F = a.LU + bt.mat_off[b];
+  for (int e = tid; e < kBW * kBW; e += 128) {
+    const int r = e / kBW, c = e % kBW;
+    D[r * kLdD + c] = F[(k0 + r) * m + k0 + c];
+  }
+  if (tid < kBW) dinv[tid] = 1.0f / F[(k0 + tid) * m + k0 + tid];
+  const int rest = m - k1, ns = (rest + 127) >> 7;
+  for (int task = blockIdx.y; task < 2 * ns; task += gridDim.y) {
+    const bool cols = task < ns;
+    const int base = k1 + (cols ? task : task - ns) * 128;
+    const int cnt = min(128, m - base);
+    __syncthreads();
+    if (cols) {
+      // X[t][c] = A12[k0 + t][base + c]
+      for (int e = tid; e < kBW * 128; e += 128) {
+        const int t = e >> 7, c = e & 127;
+        X[t * kLdD + c] = (c < cnt) ? F[(k0 + t) * m + base + c] : 0.0f;
+      }
+    } else {
+      // X[r][t] = A21[base + r][k0 + t]
+      for (int e = tid; e < 128 * kBW; e += 128) {
+        const int r = e / kBW, t = e % kBW;
+        X[r * kLdD + t] = (r < cnt) ? F[(base + r) * m + k0 + t] : 0.0f;
+      }
+    }
+    __syncthreads();
+    if (cols) {
+      float* x = X + tid;  // column tid, stride kLdD
+      for (int t = 1; t < kBW; ++t) {
+        float acc = x[t * kLdD];
+        const float* Lt = D + t * kLdD;
+#pragma unroll 8
+        for (int q = 0; q < t; ++q) acc = fmaf(-Lt[q], x[q * kLdD], acc);
+        x[t * kLdD] = acc;
+      }
+    } else {
+      float* x = X + tid * kLdD;  // row tid
+      for (int t = 0; t < kBW; ++t) {
+        float acc = x[t];
+#pragma unroll 8
+        for (int q = 0; q < t; ++q) acc = fmaf(-x[q], D[q * kLdD + t], acc);
+        x[t] = acc * dinv[t];
+      }
+    }
+    __syncthreads();
+    if (cols) {
+      for (int e = tid; e < kBW * 128; e += 128) {
+        const int t = e >> 7, c = e & 127;
+        if (c < cnt) F[(k0 + t) * m + base + c] = X[t * kLdD + c];
+      }
+    } else {
+      for (int e = tid; e < 128 * kBW; e += 128) {
+        const int r = e / kBW, t = e % kBW;
+        if (r < cnt) F[(base + r) * m + k0 + t] = X[r * kLdD + t];
+      }
+    }
+  }
+}
+
+size_t large_trsm_smem() { return (size_t)2 * kBW * kLdD * 4 + kBW * 4; }
+
+// A22 -= L21 U12: 128 x 128 output tiles; thread (ty, tx) owns rows
+// {4ty..4ty+3, 64+4ty..64+4ty+3} and the same pattern of columns with tx.
+__global__ void __launch_bounds__(256, 2) k_large_update(SolveArgs a, int k0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* As = reinterpret_cast<float*>(smraw);  // kUpdK x kLdS: As[k][r] = L21[r][k]
+  float* Bs = As + kUpdK * kLdS;                // kUpdK x kLdS: Bs[k][c] = U12[k][c]
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  int n, m;
+  if (!large_live(a, b, n, m)) return;
+  const int k1 = k0 + kBW;
+  if (k1 >= m) return;
+  const int rest = m - k1, nt = (rest + 127) >> 7, tiles = nt * nt;
+  float* F = a.LU + bt.mat_off[b];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int t = blockIdx.y; t < tiles; t += gridDim.y) {
+    const int r0 = k1 + (t / nt) * 128, c0 = k1 + (t % nt) * 128;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int kc = 0; kc < kBW; kc += kUpdK) {
+      __syncthreads();
+      for (int e = tid; e < 128 * kUpdK; e += 256) {
+        const int rr = e / kUpdK, kk = e % kUpdK;
+        const int r = r0 + rr;
+        As[kk * kLdS + rr] = (r < m) ? F[r * m + k0 + kc + kk] : 0.0f;
+      }
+      for (int e = tid; e < kUpdK * 128; e += 256) {
+        const int kk = e >> 7, cc = e & 127;
+        const int c = c0 + cc;
+        Bs[kk * kLdS + cc] = (c < m) ? F[(k0 + kc + kk) * m + c] : 0.0f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < kUpdK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(As + kk * kLdS + 4 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(As + kk * kLdS + 64 + 4 * ty);
+        const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * kLdS + 4 * tx);
+        const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * kLdS + 64 + 4 * tx);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+    }
+    const int ca = c0 + 4 * tx, cb = ca + 64;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + ((i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4);
+      if (r >= m) continue;
+      float* Cr = F + r * m;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (ca + j < m) Cr[ca + j] -= acc[i][j];
+        if (cb + j < m) Cr[cb + j] -= acc[i][j + 4];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t large_update_smem() { return (size_t)2 * kUpdK * kLdS * 4; }
+
+__global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  int n, m;
+  if (!large_live(a, b, n, m)) return;
+  invert_diagonal_blocks(a.LU + bt.mat_off[b], m, m);
+}
+
+// gridDim.y per airfoil: enough blocks for ~4 per SM over the whole batch.
+static int split_for(int B, int per_airfoil_max) {
+  const int want = (4 * 152 + B - 1) / max(B, 1);
+  return max(1, min(want, per_airfoil_max));
+}
+
+cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
+  const Batch& bt = a.bt;
+  const int B = bt.B, m_max = bt.n_max + 1;
+  if (B == 0 || m_max <= kLargeM) return cudaSuccess;
+  cudaError_t e;
+  e = ensure_smem(k_large_diag, large_diag_smem());
+  if (e != cudaSuccess) return e;
+  e = ensure_smem(k_large_trsm, large_trsm_smem());
+  if (e != cudaSuccess) return e;
+  e = ensure_smem(k_large_update, large_update_smem());
+  if (e != cudaSuccess) return e;
+  k_large_init<<<dim3(B, split_for(B, 64)), 256, 0, s>>>(a);
+  for (int k0 = 0; k0 < m_max; k0 += kBW) {
+    k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, k0);
+    const int rest = m_max - (k0 + kBW);
+    if (rest <= 0) break;
+    const int ns = (rest + 127) / 128;
+    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 128, large_trsm_smem(), s>>>(a, k0);
+    k_large_update<<<dim3(B, split_for(B, ns * ns)), 256, large_update_smem(), s>>>(a, k0);
+  }
+  k_large_finish<<<B, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace panel

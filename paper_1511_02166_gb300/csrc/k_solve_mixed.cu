@@ -28,51 +28,9 @@
 //    with the stored factor (read through L1/L2) and the refinement residuals
 //    (one pass over the rows for M u, one over the columns for M^T lambda).
 #include "df.cuh"
-#include "panel_common.cuh"
+#include "lu_mixed.cuh"
 
 namespace panel {
-
-constexpr int kSmemM = 230;  // largest m = n + 1 factored in shared memory
-constexpr int kNB = 32;      // panel width
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
-struct SolveArgs {
-  Batch bt;
-  const float* A_hi;
-  const float* A_lo;
-  float* LU;
-  int32_t* piv;
-  const double* rhs;
-  const double* vinf;
-  const double* chord;
-  double* u;         // forward solution (may be NULL: no forward system)
-  double* lam;       // transposed solution (may be NULL: no transposed system)
-  int max_iter;
-  double tol;
-  int32_t* info;
-  int32_t* iters;
-  int force_global;  // k_lu_global takes every airfoil, not only m > kSmemM
-};
-
-__device__ __forceinline__ double block_absmax_d(double v, double* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double r = 0.0;
-  for (int w = 0; w < kWarps; ++w) r = fmax(r, red[w]);
-  __syncthreads();
-  return r;
-}
-
-// border scale s = mean |A_jj| over the influence block (hi plane)
-__device__ __forceinline__ double border_scale(const float* Ah, int n, int m, double* red) {
-  double sdiag = 0.0;
-  for (int j = threadIdx.x; j < n; j += kThreads) sdiag += fabs((double)Ah[j * m + j]);
-  return block_sum(sdiag, red) / n;
-}
 
 // ---------------------------------------------------------------------------
 // Pieces shared by both factorisations (all indices fit in 32 bits)
@@ -253,48 +211,6 @@ __device__ int lu_rowpanel(float* F, int ld, int m, int* ipiv, float* prow, floa
   return 0;
 }
 
-// ---------------------------------------------------------------------------
-// Inverted diagonal blocks, in place, one warp per 32 x 32 block (lane j =
-// column j of the inverse).  X = L_dd^{-1} (unit lower) replaces the part
-// below the diagonal row by row (row i is written after every lane has read
-// it); Y = U_dd^{-1} (upper) replaces the rest row by row from the bottom.
-// ---------------------------------------------------------------------------
-__device__ void invert_diagonal_blocks(float* F, int ld, int m) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb = (m + 31) >> 5;
-  for (int d = warp; d < nb; d += kWarps) {
-    const int k0 = 32 * d;
-    const int kb = min(32, m - k0);
-    float* B = F + k0 * ld + k0;
-    const int j = lane;
-    // X[i][j] = -(L[i][j] + sum_{j<k<i} L[i][k] X[k][j]),  i > j
-    for (int i = 1; i < kb; ++i) {
-      float x = 0.0f;
-      if (j < i) {
-        x = -B[i * ld + j];
-        for (int k = j + 1; k < i; ++k) x = fmaf(-B[i * ld + k], B[k * ld + j], x);
-      }
-      __syncwarp();
-      if (j < i) B[i * ld + j] = x;
-      __syncwarp();
-    }
-    // Y[i][j] = -(sum_{i<k<=j} U[i][k] Y[k][j]) / U[i][i] (i < j), Y[j][j] = 1/U[j][j]
-    for (int i = kb - 1; i >= 0; --i) {
-      float y = 0.0f;
-      const float uii = B[i * ld + i];
-      if (j == i) {
-        y = 1.0f / uii;
-      } else if (j > i && j < kb) {
-        float acc = 0.0f;
-        for (int k = i + 1; k <= j; ++k) acc = fmaf(B[i * ld + k], B[k * ld + j], acc);
-        y = -acc / uii;
-      }
-      __syncwarp();
-      if (j >= i && j < kb) B[i * ld + j] = y;
-      __syncwarp();
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // The LU kernel, factor in shared memory (m <= kSmemM)
@@ -381,10 +297,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
   const int m = n + 1;
   if (a.info[b] != 0) return;
   if (m <= kSmemM && !a.force_global) return;  // taken by k_lu_mixed
-  if (n > bt.n_max) {
+  if (n > a.n_cap) {
     if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
     return;
   }
+  if (m > kLargeM) return;  // taken by the blocked factor (k_lu_large.cu)
   const int mv = bt.n_max + 1;
   float* P = reinterpret_cast<float*>(smraw);           // mv x LDP panel
   float* U = P + mv * LDP;                              // NB x CW slab of U12
@@ -930,6 +847,7 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.info = info;
   a.iters = iters;
   a.force_global = 0;
+  a.n_cap = bt.n_max;
   return a;
 }
 
@@ -941,18 +859,17 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
                           nullptr, 0, 0.0, info, iters);
   a.force_global = force_global ? 1 : 0;
   cudaError_t e;
+  if (bt.n_max + 1 > kLargeM) {
+    e = launch_lu_large(a, s);
+    if (e != cudaSuccess) return e;
+  }
   if (bt.n_max + 1 > kSmemM || force_global) {
-    if (lu_global_smem<32>(bt.n_max) <= kMaxSmem) {
-      const size_t smem = lu_global_smem<32>(bt.n_max);
-      e = ensure_smem(k_lu_global<32>, smem);
-      if (e != cudaSuccess) return e;
-      k_lu_global<32><<<bt.B, kThreads, smem, s>>>(a);
-    } else {
-      const size_t smem = lu_global_smem<16>(bt.n_max);
-      e = ensure_smem(k_lu_global<16>, smem);
-      if (e != cudaSuccess) return e;
-      k_lu_global<16><<<bt.B, kThreads, smem, s>>>(a);
-    }
+    SolveArgs g = a;
+    g.bt.n_max = min(bt.n_max, kLargeM - 1);
+    const size_t smem = lu_global_smem<32>(g.bt.n_max);
+    e = ensure_smem(k_lu_global<32>, smem);
+    if (e != cudaSuccess) return e;
+    k_lu_global<32><<<bt.B, kThreads, smem, s>>>(g);
     e = cudaGetLastError();
     if (e != cudaSuccess || force_global) return e;
   }

@@ -50,10 +50,12 @@ def _store_tune_cache(cache):
         pass
 
 
-def size_buckets(sorted_sizes, width):
+def size_buckets(sorted_sizes, width, min_count=1):
     """Contiguous runs of the (descending) sizes with equal ceil(n / width):
-    a list of (start, count, n_max)."""
-    out = []
+    a list of (start, count, n_max).  Runs shorter than ``min_count`` airfoils
+    are merged with the following ones (a launch of a few blocks would leave
+    most SMs idle), and a short last run joins the one before it."""
+    runs = []
     start = 0
     B = len(sorted_sizes)
     while start < B:
@@ -61,8 +63,18 @@ def size_buckets(sorted_sizes, width):
         end = start + 1
         while end < B and -(-int(sorted_sizes[end]) // width) == key:
             end += 1
-        out.append((start, end - start, max(int(sorted_sizes[start]), 3)))
+        runs.append((start, end - start, max(int(sorted_sizes[start]), 3)))
         start = end
+    out = []
+    for r in runs:
+        if out and out[-1][1] < min_count:
+            s0, c0, n0 = out[-1]
+            out[-1] = (s0, c0 + r[1], n0)
+        else:
+            out.append(r)
+    if len(out) > 1 and out[-1][1] < min_count:
+        s0, c0, n0 = out[-2]
+        out[-2:] = [(s0, c0 + out[-1][1], n0)]
     return out
 
 MODES = {"fp64": bd.PANEL_FP64, "mixed": bd.PANEL_MIXED}
@@ -85,7 +97,7 @@ class PanelBatch:
 
     def __init__(self, nodes, offsets, alpha, mode: str = "mixed", vinf=None, chord=None,
                  device="cuda", max_iter: int = 10, tol: float = 1e-12,
-                 bucket_width: int | None = 64):
+                 bucket_width: int | None = 64, bucket_min: int = 608):
         self.device = _require_cuda(device)
         if mode not in MODES:
             raise ValueError("mode must be one of %s" % sorted(MODES))
@@ -140,7 +152,7 @@ class PanelBatch:
         if bucket_width is None or self.B == 0:
             self.buckets = [(0, self.B, self.n_max)] if self.B else []
         else:
-            self.buckets = size_buckets(sorted_sizes, int(bucket_width))
+            self.buckets = size_buckets(sorted_sizes, int(bucket_width), int(bucket_min))
         self.lu_global = [False] * len(self.buckets)
         self.graph = None
 

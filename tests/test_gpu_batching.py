@@ -38,7 +38,8 @@ def test_buckets_match_single_launch():
     from paper_1511_02166_gb300.solver import PanelBatch
     pop = _ragged(5, SIZES)
     one = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=None)
-    many = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64)
+    many = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64,
+                      bucket_min=1)
     assert len(one.buckets) == 1 and len(many.buckets) == 6
     one.run(with_grad=True)
     many.run(with_grad=True)
@@ -61,7 +62,8 @@ def test_forced_global_lu_in_every_bucket():
     import torch
     from paper_1511_02166_gb300.solver import PanelBatch
     pop = _ragged(6, SIZES)
-    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64,
+                    bucket_min=1)
     pb.lu_global = [True] * len(pb.buckets)
     pb.run(with_grad=False)
     torch.cuda.synchronize()
@@ -76,7 +78,7 @@ def test_autotune_then_graph_replay_with_new_inputs(tmp_path, monkeypatch):
     monkeypatch.setenv("PANEL_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     sizes = [64 + (37 * k) % 449 for k in range(40)]
     pop = _ragged(7, sizes)
-    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_min=4)
     chosen = pb.autotune(reps=1)
     assert (tmp_path / "tune.json").exists() and len(chosen) >= 1
     pb.capture(with_grad=True)
@@ -94,5 +96,5 @@ def test_autotune_then_graph_replay_with_new_inputs(tmp_path, monkeypatch):
         s = slice(pop2.offsets[b], pop2.offsets[b + 1])
         assert rel_inf(g[s], ref[s]) < 1e-9, b
     # a second instance reads the cached choice instead of timing again
-    pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_min=4)
     assert pb2.autotune(reps=1) == chosen and pb2.lu_global == pb.lu_global

@@ -1,0 +1,96 @@
+"""GPU parity of large airfoils (n > 639: the step-synchronous blocked FP32
+factor with the pivot search inside the 128-row diagonal blocks, refined in
+double-float) against the FP64 oracle.
+
+Tolerances.  Cl within 1e-10 (relative to max(|Cl|, 1)).  At these sizes the
+bordered system is ill conditioned (condition numbers 1e6..4e6 at n ~ 2000),
+so two FP64-class evaluations whose matrix entries differ by one rounding
+(1e-16) already differ in gamma by up to ~1e-9; gamma is therefore held to
+5e-9 of the oracle, and the backward error of the GPU solution against the
+oracle's matrix, |b - M u| / (|M| |u|) in the inf norm evaluated in long
+double, to 1e-14.  Gradients within 1e-9 of the forward-tangent oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_02166_gb300 import inputs
+from tests.gpu_util import cl_err, need_gpu, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(seed, sizes):
+    rng = np.random.default_rng(seed)
+    air = [inputs.naca4(rng.uniform(0, .06), rng.uniform(.2, .6), rng.uniform(.08, .18), n)
+           for n in sizes]
+    return inputs.pack(air, rng.uniform(-0.07, 0.17, len(air)))
+
+
+def _run(pop, grad=False):
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    pb.run(with_grad=grad)
+    torch.cuda.synchronize()
+    return pb
+
+
+def _backward_error(nodes, alpha, u):
+    M, b = oracle.assemble(nodes, alpha)
+    Ml = M.astype(np.longdouble)
+    r = b.astype(np.longdouble) - Ml @ u.astype(np.longdouble)
+    scale = np.abs(Ml).sum(axis=1).max() * np.abs(u.astype(np.longdouble)).max()
+    return float(np.abs(r).max() / scale)
+
+
+def _check(pop, pb):
+    ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    assert np.all(ref["info"] == 0)
+    u = pb.u.cpu().numpy()
+    for b in range(pop.batch):
+        o = pop.offsets[b] + b
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 5e-9, (b, n)
+        s = slice(pop.offsets[b], pop.offsets[b + 1])
+        assert _backward_error(pop.nodes[s], pop.alpha[b], u[o:o + n + 1]) < 1e-14, (b, n)
+    assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < 1e-10
+    assert np.max(np.abs(pb.cp.cpu().numpy() - ref["cp"])) < 1e-7
+
+
+def test_large_blocked_factor_sizes():
+    # ragged edges of the 128-wide block columns and of the 128 x 128 tiles
+    need_gpu()
+    pop = _ragged(11, [640, 641, 767, 768, 1025, 1300, 2048])
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    assert np.all(pb.iters.cpu().numpy() <= 6)
+    _check(pop, pb)
+
+
+def test_large_and_small_airfoils_in_one_batch():
+    # one launch spans all three factorisations (shared memory, one block in
+    # global memory, step-synchronous blocked)
+    need_gpu()
+    pop = _ragged(12, [1500, 700, 639, 300, 229, 100, 3])
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop, pb)
+
+
+def test_large_population_sample():
+    need_gpu()
+    pop = inputs.make_population("large_b1024_n1024_2048", batch=4)
+    pb = _run(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop, pb)
+
+
+def test_large_gradient_matches_tangent_oracle():
+    need_gpu()
+    pop = _ragged(13, [700, 3])
+    pb = _run(pop, grad=True)
+    s = slice(pop.offsets[0], pop.offsets[1])
+    ref, info = oracle.cl_gradient(pop.nodes[s], pop.alpha[0])
+    assert info == 0
+    assert rel_inf(pb.grad.cpu().numpy()[s], ref) < 1e-9
