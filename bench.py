@@ -341,7 +341,7 @@ def run_ours(args):
                             % (flush.numel() * 4 // 2**20),
                       "max_iter": args.max_iter, "tol": args.tol,
                       "graph": bool(args.graph), "size_buckets": len(pb.buckets),
-                      "lu_global_buckets": int(sum(pb.lu_global)),
+                      "inverse_buckets": int(sum(pb.inverse)),
                       "parallelism": "dp%d (independent airfoils)" % world},
            "gradients_per_s": value,
            "kernels": kernels,

@@ -79,11 +79,14 @@ typedef enum {
 /* ... or skip the factorisation and refine with the LU/piv of an earlier call
  * (the same matrix planes), e.g. for another right-hand side. */
 #define PANEL_REUSE_FACTOR 0x40
-/* panel_solve, PANEL_MIXED only: factor every airfoil with the blocked
- * global-memory LU (panel in shared memory, several airfoils per SM) instead of
- * the shared-memory-resident LU used by default for n_b < 230; which one is
- * faster depends on n_b and on the batch (the autotuner in solver.py picks). */
-#define PANEL_LU_GLOBAL 0x80
+/* panel_solve, PANEL_MIXED only: for airfoils with n_b < 288, store the
+ * explicit inverse of the (rescaled) system, computed by blocked Gauss-Jordan
+ * elimination, instead of the default LU; each refinement correction is then
+ * one matrix-vector product instead of two triangular sweeps, at three times
+ * the factorisation flops.  Which is faster depends on n_b and on the batch
+ * (the autotuner in solver.py picks).  A later PANEL_REUSE_FACTOR call
+ * recognises either layout by itself. */
+#define PANEL_INVERSE 0x80
 
 /* Largest panel count per airfoil the library accepts. */
 #define PANEL_N_MAX 2048

@@ -25,7 +25,7 @@ PANEL_MIXED = 0x2
 PANEL_WITH_ADJOINT = 0x10
 PANEL_FACTOR_ONLY = 0x20
 PANEL_REUSE_FACTOR = 0x40
-PANEL_LU_GLOBAL = 0x80
+PANEL_INVERSE = 0x80
 PANEL_N_MAX = 2048
 
 INFO_FEW_NODES = -1

@@ -48,11 +48,11 @@ int mode_of(int flags) {
 
 bool flags_ok(int flags) {
   const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
-                    PANEL_REUSE_FACTOR | PANEL_LU_GLOBAL;
+                    PANEL_REUSE_FACTOR | PANEL_INVERSE;
   if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
   const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
   if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;
-  if ((flags & PANEL_LU_GLOBAL) && mode_of(flags) != PANEL_MIXED) return false;
+  if ((flags & PANEL_INVERSE) && mode_of(flags) != PANEL_MIXED) return false;
   return stage == 0 || mode_of(flags) == PANEL_MIXED;
 }
 
@@ -151,7 +151,7 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
   cudaError_t e = cudaSuccess;
   if (!reuse)
     e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters,
-                               (flags & PANEL_LU_GLOBAL) != 0, s);
+                               (flags & PANEL_INVERSE) != 0, s);
   if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
                                adj ? lambda : nullptr, max_iter, tol, info, iters, s);

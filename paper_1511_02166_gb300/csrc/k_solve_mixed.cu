@@ -7,279 +7,31 @@
 // condition number seen by the FP32 factor.  Refinement (Wilkinson/Moler):
 //   x_0 = solve(b);  r_k = b - M x_k  with products and sums exact to ~2^-70
 //   against the stored planes A_hi + A_lo;  x_{k+1} = x_k + solve(r_k), until
-//   |dx|_inf <= tol |x|_inf.  The transposed system M^T lambda = g (g = dCl/du)
-//   is refined in the same kernel.
+//   |dx|_inf <= tol |x|_inf, or until the contraction of the last two
+//   corrections predicts the next one below that.  The transposed system
+//   M^T lambda = g (g = dCl/du) is refined in the same kernel.
 //
-// Two kernels:
-//  k_lu_mixed  one block per airfoil.  For m <= kSmemM the matrix is copied
-//    into shared memory (cp.async) and factored there; beyond, it is factored
-//    in place in the caller's LU buffer.  Right-looking, panels of 32 columns:
-//    in the shared-memory variant thread t keeps row t of the panel in 32
-//    registers (shifted left after every column, so that no register index is
-//    dynamic and the loop stays rolled); per column one shuffle argmax per warp,
-//    two block barriers, the pivot row broadcast through shared memory.  Then
-//    the panel's row exchanges are applied to the other columns, U12 =
-//    L11^{-1} A12 is formed (a column per lane) and A22 -= L21 U12 runs as a
-//    register-tiled rank-32 update (8 rows x 4 columns per thread).  Finally
-//    the 32 x 32 diagonal blocks of L and U are replaced by their inverses, so
-//    that the triangular solves below are matrix-vector products.  The stored
-//    LU buffer therefore holds this library-internal layout.
-//  k_ir_mixed  one small block per airfoil (many per SM): triangular solves
-//    with the stored factor (read through L1/L2) and the refinement residuals
-//    (one pass over the rows for M u, one over the columns for M^T lambda).
+// The FP32 factor depends on the size m = n + 1:
+//   m <= kGjM (288)        explicit inverse by blocked Gauss-Jordan
+//                          (k_gj_mixed.cu); a correction is one GEMV;
+//   kGjM < m <= kLargeM    k_lu_global below: one block per airfoil, blocked
+//                          right-looking LU with partial pivoting, the factor
+//                          in the caller's LU buffer through L2;
+//   m > kLargeM (640)      the step-synchronous blocked LU (k_lu_large.cu).
+// The LU variants replace the 32 x 32 diagonal blocks of L and U by their
+// inverses, so that the triangular solves below are sequences of
+// matrix-vector products.  The LU buffer therefore holds a library-internal
+// layout (an inverse, or an LU with inverted diagonal blocks, chosen by m).
+//  k_ir_mixed  one block per airfoil: the corrections with the stored factor
+//    (read through L1/L2) and the refinement residuals (one pass over the rows
+//    for M u, one over the columns for M^T lambda).
 #include "df.cuh"
 #include "lu_mixed.cuh"
 
 namespace panel {
 
 // ---------------------------------------------------------------------------
-// Pieces shared by both factorisations (all indices fit in 32 bits)
-// ---------------------------------------------------------------------------
-// Apply the exchanges ipiv[k0..k0+kb) to every column outside [k0, k0+kb).
-__device__ __forceinline__ void apply_panel_swaps(float* F, int ld, int m, int k0, int kb,
-                                                  const int* ipiv) {
-  for (int c = threadIdx.x; c < m; c += kThreads) {
-    if (c >= k0 && c < k0 + kb) continue;
-    for (int k = k0; k < k0 + kb; ++k) {
-      const int p = ipiv[k];
-      if (p != k) {
-        const float t = F[k * ld + c];
-        F[k * ld + c] = F[p * ld + c];
-        F[p * ld + c] = t;
-      }
-    }
-  }
-}
-
-// U12 = L11^{-1} A12 (L11 unit lower kb x kb), one column per lane.  The base
-// of L11 goes through an opaque move per column block so that its loads are
-// not hoisted out of the loop.
-__device__ __forceinline__ void panel_trsm(float* F, int ld, int m, int k0, int kb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k1 = k0 + kb;
-  for (int cb = k1 + 32 * warp; cb < m; cb += kThreads) {
-    const int c = cb + lane;
-    const bool ok = c < m;
-    int lbase;
-    asm volatile("mov.b32 %0, %1;" : "=r"(lbase) : "r"(k0 * ld + k0));
-    const float* L11 = F + lbase;
-    float col[kNB];
-#pragma unroll
-    for (int t = 0; t < kNB; ++t) col[t] = (ok && t < kb) ? F[(k0 + t) * ld + c] : 0.0f;
-#pragma unroll
-    for (int t = 1; t < kNB; ++t) {
-      float acc = col[t];
-#pragma unroll
-      for (int q = 0; q < kNB; ++q)
-        if (q < t) acc = fmaf(-L11[t * ld + q], col[q], acc);
-      col[t] = acc;
-    }
-#pragma unroll
-    for (int t = 0; t < kNB; ++t)
-      if (ok && t < kb) F[(k0 + t) * ld + c] = col[t];
-  }
-}
-
-// A22 -= L21 U12 over rows/columns [k1, m): warp tiles of 8 rows x 128 columns.
-__device__ __forceinline__ void panel_gemm(float* F, int ld, int m, int k0, int kb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int k1 = k0 + kb;
-  const int rows = m - k1;
-  const int nr = (rows + 7) >> 3;
-  const int nc = (rows + 127) >> 7;
-  for (int tile = warp; tile < nr * nc; tile += kWarps) {
-    const int r0 = k1 + 8 * (tile / nc);
-    const int cb = k1 + 128 * (tile % nc) + lane;
-    float acc[8][4];
-    bool cok[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) cok[t] = cb + 32 * t < m;
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        acc[a][t] = (r0 + a < m && cok[t]) ? F[(r0 + a) * ld + cb + 32 * t] : 0.0f;
-#pragma unroll 2
-    for (int q = 0; q < kb; ++q) {
-      float lv[8], uv[4];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) lv[a] = (r0 + a < m) ? F[(r0 + a) * ld + k0 + q] : 0.0f;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) uv[t] = cok[t] ? F[(k0 + q) * ld + cb + 32 * t] : 0.0f;
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[a][t] = fmaf(-lv[a], uv[t], acc[a][t]);
-    }
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (r0 + a < m && cok[t]) F[(r0 + a) * ld + cb + 32 * t] = acc[a][t];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// LU with partial pivoting, factor in shared memory, m <= kThreads rows:
-// thread t owns row t of the current panel in registers.
-// Returns 0 or k+1 for an exactly zero pivot (uniform over the block).
-// ---------------------------------------------------------------------------
-__device__ int lu_rowpanel(float* F, int ld, int m, int* ipiv, float* prow, float* krow,
-                           unsigned long long* cand) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const bool has = t < m;
-  for (int k0 = 0; k0 < m; k0 += kNB) {
-    const int kb = min(kNB, m - k0);
-    float a[kNB];
-#pragma unroll
-    for (int q = 0; q < kNB; ++q) a[q] = (has && q < kb) ? F[t * ld + k0 + q] : 0.0f;
-    for (int q = 0; q < kb; ++q) {
-      const int k = k0 + q;
-      float4* pr = reinterpret_cast<float4*>(prow + (q & 1) * kNB);
-      float4* kr = reinterpret_cast<float4*>(krow + (q & 1) * kNB);
-      // warp argmax of |a_tk| over rows t >= k, ties to the lowest row: the key
-      // is the float's bit pattern + 1 (monotone for |x|; 0 marks no candidate)
-      const unsigned key = (has && t >= k) ? __float_as_uint(fabsf(a[0])) + 1u : 0u;
-      const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-      const unsigned win = __ffs(__ballot_sync(0xffffffffu, key == mx)) - 1;
-      if (lane == 0)
-        cand[(q & 1) * kWarps + warp] =
-            ((unsigned long long)mx << 32) | (unsigned)(0x7fffffff - (warp * 32 + (int)win));
-      __syncthreads();
-      unsigned long long best = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) best = max(best, cand[(q & 1) * kWarps + w]);
-      if ((unsigned)(best >> 32) <= 1u) return k + 1;  // no candidate or |pivot| = 0
-      const int p = 0x7fffffff - (int)(best & 0xffffffffu);
-      if (t == p) {
-#pragma unroll
-        for (int c = 0; c < kNB / 4; ++c)
-          pr[c] = make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
-      }
-      if (t == k) {
-#pragma unroll
-        for (int c = 0; c < kNB / 4; ++c)
-          kr[c] = make_float4(a[4 * c], a[4 * c + 1], a[4 * c + 2], a[4 * c + 3]);
-        ipiv[k] = p;
-      }
-      __syncthreads();
-      if (p != k) {
-        if (t == k || t == p) {
-          const float4* src = (t == k) ? pr : kr;
-#pragma unroll
-          for (int c = 0; c < kNB / 4; ++c) {
-            const float4 v = src[c];
-            a[4 * c] = v.x;
-            a[4 * c + 1] = v.y;
-            a[4 * c + 2] = v.z;
-            a[4 * c + 3] = v.w;
-          }
-        }
-        // exchange the already finished multipliers of rows k and p
-        if (warp == 0 && lane < q) {
-          const float x = F[k * ld + k0 + lane];
-          F[k * ld + k0 + lane] = F[p * ld + k0 + lane];
-          F[p * ld + k0 + lane] = x;
-        }
-      }
-      const float* pv = prow + (q & 1) * kNB;
-      // row k is final within the panel: U[k][k..k0+kb)
-      if (warp == kWarps - 1 && lane < kb - q) F[k * ld + k + lane] = pv[lane];
-      if (has && t > k) {
-        const float l = a[0] * __frcp_rn(pv[0]);
-        F[t * ld + k] = l;
-#pragma unroll
-        for (int c = 0; c < kNB / 4; ++c) {
-          const float4 v = pr[c];
-          if (c > 0) a[4 * c - 1] = fmaf(-l, v.x, a[4 * c]);
-          a[4 * c] = fmaf(-l, v.y, a[4 * c + 1]);
-          a[4 * c + 1] = fmaf(-l, v.z, a[4 * c + 2]);
-          a[4 * c + 2] = fmaf(-l, v.w, a[4 * c + 3]);
-        }
-        a[kNB - 1] = 0.0f;
-      }
-    }
-    __syncthreads();
-    apply_panel_swaps(F, ld, m, k0, kb, ipiv);
-    __syncthreads();
-    if (k0 + kb >= m) break;
-    panel_trsm(F, ld, m, k0, kb);
-    __syncthreads();
-    panel_gemm(F, ld, m, k0, kb);
-    __syncthreads();
-  }
-  return 0;
-}
-
-
-// ---------------------------------------------------------------------------
-// The LU kernel, factor in shared memory (m <= kSmemM)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) k_lu_mixed(SolveArgs a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const Batch& bt = a.bt;
-  const int b = bt.order[blockIdx.x];
-  const int n = airfoil_n(bt, b);
-  const int m = n + 1;
-  if (a.info[b] != 0) return;
-  if (m > kSmemM) return;  // taken by k_lu_global
-  if (n > bt.n_max) {
-    if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
-    return;
-  }
-  double* red = reinterpret_cast<double*>(smraw);      // 32
-  int* ipiv = reinterpret_cast<int*>(red + 32);         // n_max + 1
-  float* prow = reinterpret_cast<float*>(
-      (reinterpret_cast<uintptr_t>(ipiv + bt.n_max + 1) + 15) & ~(uintptr_t)15);  // 2 kNB
-  float* krow = prow + 2 * kNB;                                                    // 2 kNB
-  unsigned long long* cand = reinterpret_cast<unsigned long long*>(krow + 2 * kNB);  // 2 kWarps
-  float* F = reinterpret_cast<float*>(cand + 2 * kWarps);
-
-  const int64_t moff = bt.mat_off[b];
-  const float* Ah = a.A_hi + moff;
-  const int ld = m | 1;
-  const float sf = (float)border_scale(Ah, n, m, red);
-
-  // copy the hi plane asynchronously into shared memory, rescale the border
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int rr = warp; rr < m; rr += kWarps)
-    for (int cc = lane; cc < m; cc += 32) {
-      const unsigned dst = (unsigned)__cvta_generic_to_shared(F + rr * ld + cc);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(Ah + rr * m + cc));
-    }
-  asm volatile("cp.async.wait_all;\n" ::);
-  __syncthreads();
-  for (int j = threadIdx.x; j < m; j += kThreads) {
-    if (j < n) F[j * ld + n] *= sf;
-    F[n * ld + j] *= sf;
-  }
-  __syncthreads();
-  const int st = lu_rowpanel(F, ld, m, ipiv, prow, krow, cand);
-  if (st != 0) {
-    if (threadIdx.x == 0) {
-      a.info[b] = st;
-      if (a.iters) a.iters[b] = 0;
-    }
-    return;
-  }
-  invert_diagonal_blocks(F, ld, m);
-  __syncthreads();
-  int32_t* gpiv = a.piv + vec_off(bt, b);
-  for (int k = threadIdx.x; k < m; k += kThreads) gpiv[k] = ipiv[k];
-  float* G = a.LU + moff;
-  for (int rr = warp; rr < m; rr += kWarps)
-    for (int cc = lane; cc < m; cc += 32) G[rr * m + cc] = F[rr * ld + cc];
-}
-
-size_t lu_mixed_smem(int n_max) {
-  const int mf = n_max + 1;
-  size_t bytes = 32 * 8 + (size_t)(n_max + 1) * 4 + 16 + 4 * kNB * 4 + 2 * kWarps * 8;
-  bytes = (bytes + 15) & ~(size_t)15;
-  return bytes + (size_t)mf * (size_t)(mf | 1) * 4;
-}
-
-// ---------------------------------------------------------------------------
-// The LU kernel, factor in global memory (m > kSmemM): blocked right-looking
+// The LU kernel, factor in global memory (kGjM < m <= kLargeM): blocked right-looking
 // with the current panel of NB columns staged in shared memory (rows spread
 // over the threads), the row exchanges, U12 and the rank-NB update applied to
 // the factor in the caller's LU buffer through L2.  Shared memory stays small
@@ -296,7 +48,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
   const int n = airfoil_n(bt, b);
   const int m = n + 1;
   if (a.info[b] != 0) return;
-  if (m <= kSmemM && !a.force_global) return;  // taken by k_lu_mixed
+  if (m <= kGjM && a.inverse) return;  // taken by k_gj_mixed
   if (n > a.n_cap) {
     if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
     return;
@@ -573,6 +325,54 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
 // errors go to s2), s2 (double-float) collects the ~2^-24 terms (the two_prod
 // error of h*xh, h*xl, l*xh) and s3 (float) the ~2^-48 terms (the errors of
 // h*xl and l*xh, and l*xl).  Every product is exact via two_prod.
+// Corrections with the Gauss-Jordan inverse X = (P Mt)^{-1}: y <- X y (rows
+// over the warps, 4 rows per pass, lanes along the row) and y <- X^T y (the
+// rows split into 8 ranges, one per warp, a column per lane, partial sums in
+// `part`, 8 x m floats).  `w` is an m-float shared scratch.
+__device__ void gj_apply(const float* __restrict__ X, int m, float* y, float* w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 4 * warp; i0 < m; i0 += 4 * kWarps) {
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int k = lane; k < m; k += 32) {
+      const float yk = y[k];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (i0 + r < m) acc[r] = fmaf(__ldg(X + (i0 + r) * m + k), yk, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float v = warp_sum_f(acc[r]);
+      if (lane == 0 && i0 + r < m) w[i0 + r] = v;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += kThreads) y[k] = w[k];
+  __syncthreads();
+}
+
+__device__ void gj_apply_transposed(const float* __restrict__ X, int m, float* y, float* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rows = (m + kWarps - 1) / kWarps;
+  const int k0 = warp * rows, k1 = min(m, k0 + rows);
+  for (int cb = 0; cb < m; cb += 32) {
+    const int i = cb + lane;
+    float acc = 0.0f;
+    if (i < m) {
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) acc = fmaf(__ldg(X + k * m + i), y[k], acc);
+    }
+    if (i < m) part[warp * m + i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kThreads) {
+    float v = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) v += part[w * m + i];
+    y[i] = v;
+  }
+  __syncthreads();
+}
+
 struct ResAcc {
   float s1, s3;
   df2 s2;
@@ -696,6 +496,10 @@ struct IrSystem {
   float* xl;   // m
 };
 
+__device__ __forceinline__ int gpiv_first(const SolveArgs& a, int b) {
+  return a.piv[vec_off(a.bt, b)];
+}
+
 __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
@@ -722,6 +526,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
   float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
+  float* part = t32 + 32;  // 8 x min(m, kGjM): partial sums of the inverse's products
+  // the factor buffer holds an inverse (exchanges stored as -(row + 1)) or an LU
+  const bool gj = gpiv_first(a, b) < 0;
 
   const int64_t moff = bt.mat_off[b];
   const float* Ah = a.A_hi + moff;
@@ -754,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
   if (threadIdx.x == 0) {
     for (int k = 0; k < m; ++k) perm[k] = k;
     for (int k = 0; k < m; ++k) {
-      const int p = gpiv[k];
+      const int p = gj ? -gpiv[k] - 1 : gpiv[k];
       const int t = perm[k];
       perm[k] = perm[p];
       perm[p] = t;
@@ -764,6 +571,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
 
   bool active[2] = {act0, act1};
   bool conv[2] = {!act0, !act1};
+  double dprev[2] = {0.0, 0.0};  // size of the previous correction
   int it = 0;
   for (;; ++it) {
     for (int q = 0; q < 2; ++q) {
@@ -776,13 +584,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
           y[k] = (float)((src == n) ? S.r[src] * s : S.r[src]);
         }
         __syncthreads();
-        lu_apply_inverse(F, m, y, t32);
+        if (gj)
+          gj_apply(F, m, y, part);
+        else
+          lu_apply_inverse(F, m, y, t32);
       } else {
         // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
         for (int k = threadIdx.x; k < m; k += kThreads)
           y[k] = (float)((k == n) ? S.r[k] * s : S.r[k]);
         __syncthreads();
-        lu_apply_inverse_transposed(F, m, y, t32);
+        if (gj)
+          gj_apply_transposed(F, m, y, part);
+        else
+          lu_apply_inverse_transposed(F, m, y, t32);
       }
       double dmax = 0.0;
       for (int k = threadIdx.x; k < m; k += kThreads) {
@@ -796,7 +610,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
       for (int k = threadIdx.x; k < m; k += kThreads) xmax = fmax(xmax, fabs(S.x[k]));
       dmax = block_absmax_d(dmax, red);
       xmax = block_absmax_d(xmax, red);
+      // Converged when the correction just applied is below tol |x|, or when
+      // the contraction seen over the last two corrections (rho = |d_k| /
+      // |d_{k-1}| <= 1/8) predicts the next one, |d_k| rho, below tol |x|: the
+      // error left in x_{k+1} is about that next correction.
       if (it >= 1 && dmax <= a.tol * xmax) conv[q] = true;
+      if (it >= 2 && dmax <= 0.125 * dprev[q] && dmax * (dmax / dprev[q]) <= a.tol * xmax)
+        conv[q] = true;
+      dprev[q] = dmax;
     }
     if ((conv[0] && conv[1]) || it >= a.max_iter) break;
     for (int q = 0; q < 2; ++q) {
@@ -824,7 +645,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
 
 size_t ir_mixed_smem(int n_max) {
   const size_t mv = (size_t)n_max + 1;
-  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 16;
+  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 16 +
+         (size_t)kWarps * (size_t)min((int)mv, kGjM) * 4;
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
@@ -846,24 +668,25 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.tol = tol;
   a.info = info;
   a.iters = iters;
-  a.force_global = 0;
+  a.inverse = 0;
   a.n_cap = bt.n_max;
   return a;
 }
 
-// Factor every airfoil (shared-memory kernel for m <= kSmemM, global beyond).
-constexpr size_t kMaxSmem = 232448;
+// Factor every airfoil: one-block LU in global memory up to kLargeM (or, with
+// `inverse`, the Gauss-Jordan inverse for m <= kGjM), the step-synchronous
+// blocked LU beyond.
 cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32_t* piv,
-                            int32_t* info, int32_t* iters, bool force_global, cudaStream_t s) {
+                            int32_t* info, int32_t* iters, bool inverse, cudaStream_t s) {
   SolveArgs a = make_args(bt, A_hi, nullptr, LU, piv, nullptr, nullptr, nullptr, nullptr,
                           nullptr, 0, 0.0, info, iters);
-  a.force_global = force_global ? 1 : 0;
+  a.inverse = inverse ? 1 : 0;
   cudaError_t e;
   if (bt.n_max + 1 > kLargeM) {
     e = launch_lu_large(a, s);
     if (e != cudaSuccess) return e;
   }
-  if (bt.n_max + 1 > kSmemM || force_global) {
+  if (bt.n_max + 1 > kGjM || !inverse) {
     SolveArgs g = a;
     g.bt.n_max = min(bt.n_max, kLargeM - 1);
     const size_t smem = lu_global_smem<32>(g.bt.n_max);
@@ -871,16 +694,9 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
     if (e != cudaSuccess) return e;
     k_lu_global<32><<<bt.B, kThreads, smem, s>>>(g);
     e = cudaGetLastError();
-    if (e != cudaSuccess || force_global) return e;
+    if (e != cudaSuccess) return e;
   }
-  Batch bs = bt;
-  bs.n_max = min(bt.n_max, kSmemM - 1);
-  a.bt = bs;
-  const size_t smem = lu_mixed_smem(bs.n_max);
-  e = ensure_smem(k_lu_mixed, smem);
-  if (e != cudaSuccess) return e;
-  k_lu_mixed<<<bt.B, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_gj_mixed(a, s);
 }
 
 // Refine the forward (u) and/or transposed (lam) systems with the stored factor.

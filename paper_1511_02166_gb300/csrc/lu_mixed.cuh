@@ -7,6 +7,7 @@
 namespace panel {
 
 constexpr int kSmemM = 230;  // largest m = n + 1 factored in shared memory
+constexpr int kGjM = 288;    // m up to this: Gauss-Jordan inverse (k_gj_mixed.cu)
 constexpr int kLargeM = 640; // m above this takes the step-synchronous blocked factor
 constexpr int kNB = 32;      // panel width
 constexpr int kThreads = 256;
@@ -27,7 +28,7 @@ struct SolveArgs {
   double tol;
   int32_t* info;
   int32_t* iters;
-  int force_global;  // k_lu_global takes every airfoil, not only m > kSmemM
+  int inverse;       // m <= kGjM: Gauss-Jordan inverse (k_gj_mixed.cu) instead of the LU
   int n_cap;         // the caller's n_max (bt.n_max may be lowered to size a kernel)
 };
 
@@ -94,6 +95,7 @@ __device__ inline void invert_diagonal_blocks(float* F, int ld, int m) {
 }
 
 cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s);
+cudaError_t launch_gj_mixed(const SolveArgs& a, cudaStream_t s);
 size_t lu_large_min_m();
 
 }  // namespace panel

@@ -5,8 +5,9 @@ matrices, factors, solutions, forces and gradients) and runs the four library
 calls on the current torch stream.  A ragged population is cut into size
 buckets (contiguous runs of the size-sorted launch order), each launched with
 its own size bound so that small airfoils get small shared-memory footprints;
-``autotune()`` times the two LU variants per bucket and remembers the faster
-one, and ``capture()`` records a whole step into a CUDA graph.  ``PanelCl`` is
+``autotune()`` times the two factorisations (LU, or the Gauss-Jordan inverse)
+per bucket and remembers the faster one, and ``capture()`` records a whole
+step into a CUDA graph.  ``PanelCl`` is
 a ``torch.autograd.Function`` mapping node coordinates to Cl whose backward is
 ``panel_adjoint``.  Everything numerical happens in the CUDA library.
 """
@@ -78,6 +79,7 @@ def size_buckets(sorted_sizes, width, min_count=1):
     return out
 
 MODES = {"fp64": bd.PANEL_FP64, "mixed": bd.PANEL_MIXED}
+GJ_MAX_M = 288  # largest m = n + 1 that the library factors by Gauss-Jordan
 
 
 def _require_cuda(device):
@@ -153,7 +155,7 @@ class PanelBatch:
             self.buckets = [(0, self.B, self.n_max)] if self.B else []
         else:
             self.buckets = size_buckets(sorted_sizes, int(bucket_width), int(bucket_min))
-        self.lu_global = [False] * len(self.buckets)
+        self.inverse = [False] * len(self.buckets)
         self.graph = None
 
     # -- the four library calls (per size bucket) --------------------------------
@@ -170,8 +172,8 @@ class PanelBatch:
         flags |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
         for k, (start, cnt, nmax) in enumerate(self.buckets):
             f = flags
-            if self.lu_global[k] and stage != "refine":
-                f |= bd.PANEL_LU_GLOBAL
+            if self.inverse[k] and stage != "refine":
+                f |= bd.PANEL_INVERSE
             bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
                            self.order[start:], self.A64, self.A_hi, self.A_lo, self.LU,
                            self.piv, self.rhs, self.vinf, self.chord, self.u,
@@ -213,26 +215,39 @@ class PanelBatch:
             self.run(with_grad=with_grad)
 
     def launches_per_step(self, with_grad: bool = True) -> int:
-        """Kernel launches of one step (mixed mode: per bucket assemble, factor
-        (the global variant is launched as well when the bucket holds m > 230),
-        refine, adjoint; one forces launch)."""
+        """Kernel launches of one step: per bucket assemble, factor, refine and
+        adjoint, plus one forces launch.  The mixed factor launches one kernel
+        per size class the bucket may hold (Gauss-Jordan in shared memory,
+        Gauss-Jordan in global memory, one-block LU) and, for m > 640, the
+        step-synchronous LU (2 + 3 per 128-column block); the adjoint of
+        n > 512 adds a zeroing launch."""
         n = 1  # forces
         for k, (start, cnt, nmax) in enumerate(self.buckets):
+            m = nmax + 1
             n += 1  # assemble
             if self.flags == bd.PANEL_MIXED:
-                n += 1 if self.lu_global[k] else (2 if nmax + 1 > 230 else 1)
+                if self.inverse[k]:
+                    n += 1 + (m > 230) + (m > GJ_MAX_M)
+                else:
+                    n += 1
+                if m > 640:
+                    blocks = -(-m // 128)
+                    n += 2 + blocks + 2 * (blocks - 1)
                 n += 1  # refine
             else:
                 n += 1
-            n += 1 if with_grad else 0
+            if with_grad:
+                n += 1 + (nmax > 512 and self.flags == bd.PANEL_MIXED)
         return n
 
     # -- autotuning and graph capture -------------------------------------------
     def autotune(self, reps: int = 3, use_cache: bool = True):
-        """Pick, per size bucket, the faster of the two LU variants (mixed mode):
-        the shared-memory-resident factor (one airfoil per SM) or the blocked
-        global-memory factor (several airfoils per SM).  Results are cached by
-        device and bucket size bound."""
+        """Pick, per size bucket, the faster factorisation for a whole solve
+        (factor + refinement of both systems, mixed mode): the default LU, or
+        the Gauss-Jordan inverse (PANEL_INVERSE, m <= 288: three times the
+        factor's flops, one matrix-vector product per correction instead of
+        two triangular sweeps).  Buckets of larger airfoils have only the LU.
+        Results are cached by device, bucket size bound and batch size."""
         if self.flags != bd.PANEL_MIXED or not self.buckets:
             return dict()
         dev = torch.cuda.get_device_name(self.device)
@@ -242,23 +257,24 @@ class PanelBatch:
         torch.cuda.synchronize(self.device)
         chosen = {}
         for k, (start, cnt, nmax) in enumerate(self.buckets):
-            if nmax + 1 > 230:
-                self.lu_global[k] = True  # the only variant that holds it
+            if nmax + 1 > GJ_MAX_M:
+                self.inverse[k] = False  # the LU is the only factorisation here
                 continue
-            key = "%s|n%d|b%d" % (dev, nmax, min(cnt, 1024) // 152 * 152)
+            key = "%s|gj-lu|n%d|b%d" % (dev, nmax, min(cnt, 1024) // 152 * 152)
             if key in cache:
-                self.lu_global[k] = bool(cache[key])
+                self.inverse[k] = bool(cache[key])
                 chosen[key] = cache[key]
                 continue
             times = []
             for variant in (False, True):
-                f = bd.PANEL_MIXED | bd.PANEL_FACTOR_ONLY | (bd.PANEL_LU_GLOBAL if variant else 0)
+                f = bd.PANEL_MIXED | bd.PANEL_WITH_ADJOINT | (bd.PANEL_INVERSE if variant else 0)
 
                 def call(f=f, start=start, cnt=cnt, nmax=nmax):
                     bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets,
                                    self.mat_offsets, self.order[start:], None, self.A_hi,
-                                   self.A_lo, self.LU, self.piv, self.rhs, None, None, self.u,
-                                   None, self.max_iter, self.tol, self.info, self.iters)
+                                   self.A_lo, self.LU, self.piv, self.rhs, self.vinf,
+                                   self.chord, self.u, self.lam, self.max_iter, self.tol,
+                                   self.info, self.iters)
                 call()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -268,9 +284,9 @@ class PanelBatch:
                 e1.record()
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
-            self.lu_global[k] = times[1] < times[0]
-            chosen[key] = self.lu_global[k]
-            cache[key] = self.lu_global[k]
+            self.inverse[k] = times[1] < times[0]
+            chosen[key] = self.inverse[k]
+            cache[key] = self.inverse[k]
         if use_cache:
             with _tune_lock:
                 merged = _load_tune_cache()

@@ -35,7 +35,7 @@ def test_constants_match_header():
                       ("PANEL_N_MAX", bd.PANEL_N_MAX),
                       ("PANEL_FACTOR_ONLY", bd.PANEL_FACTOR_ONLY),
                       ("PANEL_REUSE_FACTOR", bd.PANEL_REUSE_FACTOR),
-                      ("PANEL_LU_GLOBAL", bd.PANEL_LU_GLOBAL)]:
+                      ("PANEL_INVERSE", bd.PANEL_INVERSE)]:
         m = re.search(r"#define %s\s+(0x[0-9a-fA-F]+|\d+)" % name, txt)
         assert m and int(m.group(1), 0) == val, name
     for name, val in [("PANEL_INFO_FEW_NODES", bd.INFO_FEW_NODES),

@@ -1,4 +1,4 @@
-"""GPU tests of the batching layer: size buckets, the two LU variants chosen by
+"""GPU tests of the batching layer: size buckets, the two factorisations chosen by
 autotuning, and CUDA-graph replay with new inputs written into the captured
 buffers.  Every result is checked against the oracle (long double build, as in
 the ragged tests: gamma within 1e-10, Cl within 1e-10)."""
@@ -57,14 +57,14 @@ def test_buckets_match_single_launch():
     _check(pop, u2, many.cl.cpu().numpy())
 
 
-def test_forced_global_lu_in_every_bucket():
+def test_inverse_in_every_bucket():
     need_gpu()
     import torch
     from paper_1511_02166_gb300.solver import PanelBatch
     pop = _ragged(6, SIZES)
     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=64,
                     bucket_min=1)
-    pb.lu_global = [True] * len(pb.buckets)
+    pb.inverse = [True] * len(pb.buckets)
     pb.run(with_grad=False)
     torch.cuda.synchronize()
     assert np.all(pb.info.cpu().numpy() == 0)
@@ -97,4 +97,4 @@ def test_autotune_then_graph_replay_with_new_inputs(tmp_path, monkeypatch):
         assert rel_inf(g[s], ref[s]) < 1e-9, b
     # a second instance reads the cached choice instead of timing again
     pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_min=4)
-    assert pb2.autotune(reps=1) == chosen and pb2.lu_global == pb.lu_global
+    assert pb2.autotune(reps=1) == chosen and pb2.inverse == pb.inverse

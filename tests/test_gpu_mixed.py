@@ -2,9 +2,11 @@
 double-float refinement) against the FP64 oracle.
 
 Tolerances (stated per result): after refinement |dgamma|_inf/|gamma|_inf and
-|dCl|/max(|Cl|,1) <= 1e-10; unrefined (max_iter = 0) <= 1e-4; gradients
-<= 1e-9 relative (inf norm) against the forward-tangent oracle; matrix entries
-(A_hi + A_lo) within 2e-15 absolute of the oracle's FP64 entries.
+|dCl|/max(|Cl|,1) <= 1e-10; unrefined (max_iter = 0) 5e-4 for the LU and 2e-2
+for the Gauss-Jordan inverse (derived in test_mixed_unrefined_within_bounds: a
+1e-4 target is below what one FP32 solve reaches at condition numbers ~3e4);
+gradients <= 1e-9 relative (inf norm) against the forward-tangent oracle;
+matrix entries (A_hi + A_lo) within 2e-15 absolute of the oracle's FP64 entries.
 """
 import math
 
@@ -130,31 +132,60 @@ def test_mixed_small_config_matches_oracle():
     _check_solution(pop, pb)
 
 
-def test_mixed_unrefined_within_5e4():
-    # FP32 LU with partial pivoting and FP32 triangular solves alone (no
-    # refinement): the measured worst case over these airfoils is ~2.4e-4
-    # (cond ~3e4 after the border rescaling, times the FP32 rounding)
-    need_gpu()
-    pop = inputs.make_population("naca_b4096_n200", batch=32)
-    pb = _run(pop, max_iter=0)
-    info = pb.info.cpu().numpy()
-    assert np.all(info == -5)  # no refinement step was allowed: flagged not converged
+def _unrefined_worst(pop, inverse):
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", max_iter=0)
+    pb.inverse = [inverse] * len(pb.buckets)
+    pb.run()
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == -5)  # no refinement step allowed: not converged
     ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
     u = pb.u.cpu().numpy()
+    worst = 0.0
     for b in range(pop.batch):
         o = pop.offsets[b] + b
         n = pop.offsets[b + 1] - pop.offsets[b]
-        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 5e-4
+        worst = max(worst, rel_inf(u[o:o + n], ref["u"][o:o + n]))
+    return worst
 
 
-def test_mixed_ragged_spans_both_factor_paths():
+def test_mixed_unrefined_within_bounds():
+    # The FP32 factor alone (no refinement step).  The rescaled bordered
+    # systems have condition numbers ~3e4, so one FP32 solve is good to about
+    # cond x 2^-24 x a small growth factor: the partially pivoted LU measures
+    # <= 3.5e-4 on these airfoils (bound 5e-4).  The Gauss-Jordan inverse
+    # (PANEL_INVERSE, m <= 288) is not backward stable: its entries carry relative
+    # errors ~2e-5 (32 block steps of FP32 rank-32 updates of the whole
+    # matrix), and |X| |b| / |x| ~ 300 here, so the first correction is good to
+    # ~6e-3 (measured <= 3.2e-3; bound 2e-2).  Refinement removes the
+    # difference: the refined results are held to 1e-10 elsewhere.
     need_gpu()
-    sizes = [3, 4, 31, 32, 33, 64, 100, 199, 228, 229, 230, 231, 257, 300, 512]
+    pop = inputs.make_population("naca_b4096_n200", batch=32)
+    e_lu = _unrefined_worst(pop, False)
+    e_gj = _unrefined_worst(pop, True)
+    print("unrefined worst: LU %.2e, inverse %.2e" % (e_lu, e_gj))
+    assert e_lu < 5e-4
+    assert e_gj < 2e-2
+
+
+@pytest.mark.parametrize("inverse", [False, True])
+def test_mixed_ragged_both_factorisations(inverse):
+    # sizes across the block edges of every factor kernel: the one-block LU,
+    # and with PANEL_INVERSE the Gauss-Jordan inverse in shared memory
+    # (m <= 230) and in global memory (m <= 288), the LU above
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    sizes = [3, 4, 31, 32, 33, 64, 100, 199, 228, 229, 230, 231, 257, 287, 288, 300, 512]
     rng = np.random.default_rng(1)
     air = [inputs.naca4(rng.uniform(0, .06), rng.uniform(.2, .6), rng.uniform(.08, .18), n)
            for n in sizes]
     pop = inputs.pack(air, rng.uniform(-0.07, 0.17, len(air)))
-    pb = _run(pop)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    pb.inverse = [inverse] * len(pb.buckets)
+    pb.run()
+    torch.cuda.synchronize()
     assert np.all(pb.info.cpu().numpy() == 0)
     _check_solution(pop, pb, extended=True)
 
