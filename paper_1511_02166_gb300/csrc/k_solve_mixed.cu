@@ -39,7 +39,7 @@ namespace panel {
 // and hide each other's latencies.
 // ---------------------------------------------------------------------------
 template <int NB>
-__global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LDP = NB + 1;
   constexpr int CW = 128;  // GEMM column slab
@@ -81,41 +81,62 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
     for (int r = warp; r < rows; r += kWarps)
       if (lane < kb) P[r * LDP + lane] = F[(k0 + r) * m + k0 + lane];
     __syncthreads();
-    // ---- factor the panel (rows over the threads) ----
-    for (int q = 0; q < kb; ++q) {
-      unsigned bk = 0;
-      int br = 0x7fffffff;
-      for (int r = q + tid; r < rows; r += kThreads) {
-        const unsigned key = __float_as_uint(fabsf(P[r * LDP + q])) + 1u;
-        if (key > bk) { bk = key; br = r; }
-      }
-      const unsigned mx = __reduce_max_sync(0xffffffffu, bk);
-      const unsigned rmin = __reduce_min_sync(0xffffffffu, bk == mx ? (unsigned)br : 0xffffffffu);
-      if (lane == 0) cand[warp] = ((unsigned long long)mx << 32) | (0x7fffffffu - rmin);
-      __syncthreads();
-      unsigned long long best = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) best = max(best, cand[w]);
-      if ((unsigned)(best >> 32) <= 1u) {
-        if (tid == 0) {
-          a.info[b] = k0 + q + 1;
-          if (a.iters) a.iters[b] = 0;
+    // ---- factor the panel: LU of the diagonal block by warp 0 (pivot search
+    // inside the block's rows, lane = column), then L21 = A21 U11^{-1} with a
+    // thread per row below the block ----
+    if (warp == 0) {
+      int fz = 0;
+      for (int q = 0; q < kb; ++q) {
+        const float v = (lane >= q && lane < kb) ? fabsf(P[lane * LDP + q]) : -1.0f;
+        const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;  // |x| bits are monotone
+        const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+        if (mx <= 1u) {  // exactly zero (or NaN) pivot column
+          fz = q + 1;
+          break;
         }
-        return;
+        const int p = __ffs(__ballot_sync(0xffffffffu, key == mx)) - 1;  // lowest row on ties
+        if (lane == 0) ipiv[k0 + q] = k0 + p;
+        if (p != q && lane < NB) {
+          const float t = P[q * LDP + lane];
+          P[q * LDP + lane] = P[p * LDP + lane];
+          P[p * LDP + lane] = t;
+        }
+        __syncwarp();
+        const float inv = 1.0f / P[q * LDP + q];
+        const float uq = (lane < NB) ? P[q * LDP + lane] : 0.0f;
+        for (int r = q + 1; r < kb; ++r) {
+          const float l = P[r * LDP + q] * inv;
+          __syncwarp();
+          if (lane > q && lane < NB) P[r * LDP + lane] = fmaf(-l, uq, P[r * LDP + lane]);
+          if (lane == q) P[r * LDP + q] = l;
+        }
+        __syncwarp();
       }
-      const int p = (int)(0x7fffffffu - (unsigned)(best & 0xffffffffu));
-      if (p != q && tid < kb) {
-        const float t = P[q * LDP + tid];
-        P[q * LDP + tid] = P[p * LDP + tid];
-        P[p * LDP + tid] = t;
+      if (lane == 0) cand[0] = (unsigned long long)fz;
+      if (lane < kb) red[lane] = (double)(1.0f / P[lane * LDP + lane]);
+    }
+    __syncthreads();
+    if (cand[0] != 0ull) {
+      if (tid == 0) {
+        a.info[b] = k0 + (int)cand[0];
+        if (a.iters) a.iters[b] = 0;
       }
-      if (tid == 0) ipiv[k0 + q] = k0 + p;
-      __syncthreads();
-      const float inv = 1.0f / P[q * LDP + q];
-      for (int r = q + 1 + tid; r < rows; r += kThreads) {
-        const float l = P[r * LDP + q] * inv;
-        P[r * LDP + q] = l;
-        for (int c = q + 1; c < kb; ++c) P[r * LDP + c] = fmaf(-l, P[q * LDP + c], P[r * LDP + c]);
+      return;
+    }
+    if (rows > kb) {  // then kb == NB
+      for (int r = kb + tid; r < rows; r += kThreads) {
+        float x[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) x[t] = P[r * LDP + t];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          float acc = x[t];
+#pragma unroll
+          for (int q = 0; q < t; ++q) acc = fmaf(-x[q], P[q * LDP + t], acc);
+          x[t] = acc * (float)red[t];
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) P[r * LDP + t] = x[t];
       }
       __syncthreads();
     }
@@ -485,6 +506,57 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
   }
 }
 
+// Both residuals in one pass over the matrix (m <= kFuseM), each entry loaded
+// once: warp w takes the rows j = w, w + 8, ...; lane l owns the columns
+// c = l + 32 t.  The row sums (forward system, x) are reduced across the warp
+// per row; the column sums (transposed system, lam) stay in per-lane
+// accumulators and are merged across the warps through `part` (kWarps x m).
+constexpr int kFuseM = 288;
+constexpr int kFuseT = (kFuseM + 31) / 32;
+__device__ void residual_both(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
+                              const float* xh, const float* xl, const float* yh, const float* yl,
+                              const double* b, const double* g, double* rf, double* rt,
+                              ResAcc* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ResAcc cacc[kFuseT];
+#pragma unroll
+  for (int t = 0; t < kFuseT; ++t) resacc_init(cacc[t]);
+  for (int j = warp; j < m; j += kWarps) {
+    float h[kFuseT], l[kFuseT];
+#pragma unroll
+    for (int t = 0; t < kFuseT; ++t) {
+      const int c = lane + 32 * t;
+      const bool ok = c < m;
+      h[t] = ok ? __ldg(Ah + j * m + c) : 0.0f;
+      l[t] = ok ? __ldg(Al + j * m + c) : 0.0f;
+    }
+    const float yjh = yh[j], yjl = yl[j];
+    ResAcc racc;
+    resacc_init(racc);
+#pragma unroll
+    for (int t = 0; t < kFuseT; ++t) {
+      const int c = lane + 32 * t;
+      if (c < m) {
+        resacc_add(racc, h[t], l[t], xh[c], xl[c]);
+        resacc_add(cacc[t], h[t], l[t], yjh, yjl);
+      }
+    }
+    racc = warp_sum_res(racc);
+    if (lane == 0) rf[j] = resacc_sub_from(b[j], racc);
+  }
+#pragma unroll
+  for (int t = 0; t < kFuseT; ++t) {
+    const int c = lane + 32 * t;
+    if (c < m) part[warp * m + c] = cacc[t];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < m; c += kThreads) {
+    ResAcc acc = part[c];
+    for (int w = 1; w < kWarps; ++w) resacc_merge(acc, part[w * m + c]);
+    rt[c] = resacc_sub_from(g[c], acc);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // The refinement kernel: forward and/or transposed system of one airfoil
 // ---------------------------------------------------------------------------
@@ -526,7 +598,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
   float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
-  float* part = t32 + 32;  // 8 x min(m, kGjM): partial sums of the inverse's products
+  // kWarps x min(m, kFuseM) partial sums: of the inverse's products (floats),
+  // or of the fused residual pass (ResAcc)
+  float* part = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(t32 + 32) + 15) & ~(uintptr_t)15);
   // the factor buffer holds an inverse (exchanges stored as -(row + 1)) or an LU
   const bool gj = gpiv_first(a, b) < 0;
 
@@ -629,8 +704,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
       }
     }
     __syncthreads();
-    if (active[0] && !conv[0]) residual_rows(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
-    if (active[1] && !conv[1]) residual_cols(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
+    const bool both = active[0] && !conv[0] && active[1] && !conv[1];
+    if (both && m <= kFuseM) {
+      residual_both(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb, sys[1].bb,
+                    sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
+    } else {
+      if (active[0] && !conv[0]) residual_rows(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
+      if (active[1] && !conv[1]) residual_cols(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
+    }
     __syncthreads();
   }
   for (int k = threadIdx.x; k < m; k += kThreads) {
@@ -645,8 +726,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
 
 size_t ir_mixed_smem(int n_max) {
   const size_t mv = (size_t)n_max + 1;
-  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 16 +
-         (size_t)kWarps * (size_t)min((int)mv, kGjM) * 4;
+  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 32 +
+         (size_t)kWarps * (size_t)min((int)mv, kFuseM) * sizeof(ResAcc);
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
