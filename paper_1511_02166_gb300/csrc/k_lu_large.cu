@@ -8,9 +8,9 @@
 //                   in shared memory, with the pivot search restricted to the
 //                   rows of D; its row exchanges are applied to the rest of
 //                   those rows.
-//   k_large_trsm    U12 = L11^{-1} A12 (a column per thread) and
-//                   L21 = A21 U11^{-1} (a row per thread), in slabs of 128
-//                   columns / rows staged in shared memory.
+//   k_large_trsm    U12 = L11^{-1} A12 and L21 = A21 U11^{-1}: the two
+//                   triangles of the diagonal block are inverted in shared
+//                   memory, then 128-wide slabs are multiplied by them.
 //   k_large_update  A22 -= L21 U12 in 128 x 128 tiles, K in chunks of 64,
 //                   8 x 8 outputs per thread (FP32 FMA).
 // Each of the three takes gridDim.y blocks per airfoil striding over its
@@ -165,14 +165,27 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int k0) {
 
 size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + kBW * 4; }
 
-// U12 = L11^{-1} A12 and L21 = A21 U11^{-1}.  Tasks 0..ns-1 are 128-column
-// slabs of A12, tasks ns..2ns-1 are 128-row slabs of A21; the slab is staged in
-// shared memory and every thread solves its own column (row) there.
-__global__ void __launch_bounds__(128) k_large_trsm(SolveArgs a, int k0) {
+// U12 = L11^{-1} A12 and L21 = A21 U11^{-1} as products with the explicit
+// inverses of the two triangles of the factored diagonal block.  Per block:
+//   1. the block D = L11 \ U11 is staged; thread j < 128 forms column j of
+//      L11^{-1} (forward substitution on e_j), thread 128 + i row i of
+//      U11^{-1} (from X U = I, so each row needs only its own earlier
+//      entries); four partial sums per dot product keep the chains short;
+//   2. tasks 0..ns-1 are 128-column slabs of A12, tasks ns..2ns-1 128-row
+//      slabs of A21: the slab is staged in shared memory and multiplied by the
+//      inverse, 8 x 8 outputs per thread, written straight back to the factor.
+// Li holds L11^{-1} transposed (Li[k][t] = (L11^{-1})[t][k]) and Ui holds
+// U11^{-1} by rows, both with an odd row stride (conflict-free while they are
+// formed); the slab has 16-byte rows for vector reads.
+constexpr int kLdI = kBW + 1;
+constexpr int kLdX = kBW + 4;
+
+__global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* D = reinterpret_cast<float*>(smraw);  // kBW x kLdD: L11 \ U11
-  float* X = D + kBW * kLdD;                   // kBW x kLdD slab
-  float* dinv = X + kBW * kLdD;                // kBW
+  float* X = reinterpret_cast<float*>(smraw);  // kBW x kLdX: D (stride kLdI), then the slab
+  float* Li = X + kBW * kLdX;                  // kBW x kLdI
+  float* Ui = Li + kBW * kLdI;                 // kBW x kLdI
+  float* dinv = Ui + kBW * kLdI;               // kBW
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   int n, m;
@@ -181,65 +194,145 @@ __global__ void __launch_bounds__(128) k_large_trsm(SolveArgs a, int k0) {
   if (k1 >= m) return;
   const int tid = threadIdx.x;
   float* F = a.LU + bt.mat_off[b];
-  for (int e = tid; e < kBW * kBW; e += 128) {
+  float* D = X;
+  for (int e = tid; e < kBW * kBW; e += 256) {
     const int r = e / kBW, c = e % kBW;
-    D[r * kLdD + c] = F[(k0 + r) * m + k0 + c];
+    D[r * kLdI + c] = F[(k0 + r) * m + k0 + c];
   }
-  if (tid < kBW) dinv[tid] = 1.0f / F[(k0 + tid) * m + k0 + tid];
+  __syncthreads();
+  if (tid < kBW) dinv[tid] = 1.0f / D[tid * kLdI + tid];
+  __syncthreads();
+  if (tid < kBW) {
+    // column j of L11^{-1}: x_j = 1, x_t = -sum_{j <= q < t} L[t][q] x_q
+    const int j = tid;
+    float* x = Li + j * kLdI;
+    for (int t = 0; t < j; ++t) x[t] = 0.0f;
+    x[j] = 1.0f;
+    for (int t = j + 1; t < kBW; ++t) {
+      const float* Lt = D + t * kLdI;
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+      int q = j;
+      for (; q + 3 < t; q += 4) {
+        s0 = fmaf(Lt[q], x[q], s0);
+        s1 = fmaf(Lt[q + 1], x[q + 1], s1);
+        s2 = fmaf(Lt[q + 2], x[q + 2], s2);
+        s3 = fmaf(Lt[q + 3], x[q + 3], s3);
+      }
+      for (; q < t; ++q) s0 = fmaf(Lt[q], x[q], s0);
+      x[t] = -((s0 + s1) + (s2 + s3));
+    }
+  } else {
+    // row i of U11^{-1}: y_i = 1 / U_ii, y_t = -(sum_{i <= q < t} y_q U[q][t]) / U_tt
+    const int i = tid - kBW;
+    float* y = Ui + i * kLdI;
+    for (int t = 0; t < i; ++t) y[t] = 0.0f;
+    y[i] = dinv[i];
+    for (int t = i + 1; t < kBW; ++t) {
+      float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+      int q = i;
+      for (; q + 3 < t; q += 4) {
+        s0 = fmaf(y[q], D[q * kLdI + t], s0);
+        s1 = fmaf(y[q + 1], D[(q + 1) * kLdI + t], s1);
+        s2 = fmaf(y[q + 2], D[(q + 2) * kLdI + t], s2);
+        s3 = fmaf(y[q + 3], D[(q + 3) * kLdI + t], s3);
+      }
+      for (; q < t; ++q) s0 = fmaf(y[q], D[q * kLdI + t], s0);
+      y[t] = -((s0 + s1) + (s2 + s3)) * dinv[t];
+    }
+  }
   const int rest = m - k1, ns = (rest + 127) >> 7;
+  const int tx = tid & 15, ty = tid >> 4;
   for (int task = blockIdx.y; task < 2 * ns; task += gridDim.y) {
     const bool cols = task < ns;
     const int base = k1 + (cols ? task : task - ns) * 128;
     const int cnt = min(128, m - base);
     __syncthreads();
     if (cols) {
-      // X[t][c] = A12[k0 + t][base + c]
-      for (int e = tid; e < kBW * 128; e += 128) {
-        const int t = e >> 7, c = e & 127;
-        X[t * kLdD + c] = (c < cnt) ? F[(k0 + t) * m + base + c] : 0.0f;
+      // X[k][c] = A12[k0 + k][base + c]
+      for (int e = tid; e < kBW * 128; e += 256) {
+        const int k = e >> 7, c = e & 127;
+        X[k * kLdX + c] = (c < cnt) ? F[(k0 + k) * m + base + c] : 0.0f;
       }
     } else {
-      // X[r][t] = A21[base + r][k0 + t]
-      for (int e = tid; e < 128 * kBW; e += 128) {
-        const int r = e / kBW, t = e % kBW;
-        X[r * kLdD + t] = (r < cnt) ? F[(base + r) * m + k0 + t] : 0.0f;
+      // X[k][r] = A21[base + r][k0 + k]
+      for (int e = tid; e < 128 * kBW; e += 256) {
+        const int r = e / kBW, k = e % kBW;
+        X[k * kLdX + r] = (r < cnt) ? F[(base + r) * m + k0 + k] : 0.0f;
       }
     }
     __syncthreads();
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    // rows 4ty.., 64+4ty.. and columns 4tx.., 64+4tx.. of the 128 x 128 result
     if (cols) {
-      float* x = X + tid;  // column tid, stride kLdD
-      for (int t = 1; t < kBW; ++t) {
-        float acc = x[t * kLdD];
-        const float* Lt = D + t * kLdD;
-#pragma unroll 8
-        for (int q = 0; q < t; ++q) acc = fmaf(-Lt[q], x[q * kLdD], acc);
-        x[t * kLdD] = acc;
+      // U12[t][c] = sum_k (L11^{-1})[t][k] X[k][c]
+#pragma unroll 2
+      for (int k = 0; k < kBW; ++k) {
+        const float* lk = Li + k * kLdI;
+        float av[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          av[i] = lk[4 * ty + i];
+          av[i + 4] = lk[64 + 4 * ty + i];
+        }
+        const float4 b0 = *reinterpret_cast<const float4*>(X + k * kLdX + 4 * tx);
+        const float4 b1 = *reinterpret_cast<const float4*>(X + k * kLdX + 64 + 4 * tx);
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int t = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
+        float* row = F + (k0 + t) * m + base;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
+          if (c < cnt) row[c] = acc[i][j];
+        }
       }
     } else {
-      float* x = X + tid * kLdD;  // row tid
-      for (int t = 0; t < kBW; ++t) {
-        float acc = x[t];
-#pragma unroll 8
-        for (int q = 0; q < t; ++q) acc = fmaf(-x[q], D[q * kLdD + t], acc);
-        x[t] = acc * dinv[t];
+      // L21[r][t] = sum_k X[k][r] (U11^{-1})[k][t]
+#pragma unroll 2
+      for (int k = 0; k < kBW; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(X + k * kLdX + 4 * ty);
+        const float4 a1 = *reinterpret_cast<const float4*>(X + k * kLdX + 64 + 4 * ty);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float* uk = Ui + k * kLdI;
+        float bv[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          bv[j] = uk[4 * tx + j];
+          bv[j + 4] = uk[64 + 4 * tx + j];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
-    }
-    __syncthreads();
-    if (cols) {
-      for (int e = tid; e < kBW * 128; e += 128) {
-        const int t = e >> 7, c = e & 127;
-        if (c < cnt) F[(k0 + t) * m + base + c] = X[t * kLdD + c];
-      }
-    } else {
-      for (int e = tid; e < 128 * kBW; e += 128) {
-        const int r = e / kBW, t = e % kBW;
-        if (r < cnt) F[(base + r) * m + k0 + t] = X[r * kLdD + t];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
+        if (r >= cnt) continue;
+        float* row = F + (base + r) * m + k0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int t = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
+          row[t] = acc[i][j];
+        }
       }
     }
   }
 }
 
-size_t large_trsm_smem() { return (size_t)2 * kBW * kLdD * 4 + kBW * 4; }
+size_t large_trsm_smem() {
+  return ((size_t)kBW * kLdX + 2 * (size_t)kBW * kLdI + kBW) * 4;
+}
 
 // A22 -= L21 U12: 128 x 128 output tiles; thread (ty, tx) owns rows
 // {4ty..4ty+3, 64+4ty..64+4ty+3} and the same pattern of columns with tx.
@@ -339,7 +432,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     const int rest = m_max - (k0 + kBW);
     if (rest <= 0) break;
     const int ns = (rest + 127) / 128;
-    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 128, large_trsm_smem(), s>>>(a, k0);
+    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, k0);
     k_large_update<<<dim3(B, split_for(B, ns * ns)), 256, large_update_smem(), s>>>(a, k0);
   }
   k_large_finish<<<B, 256, 0, s>>>(a);
