@@ -119,6 +119,8 @@ __device__ __forceinline__ int load_and_check_geometry(const double* nodes, int 
 // Raise a kernel's dynamic shared-memory limit only when a launch needs more
 // than any earlier one on the current device: after a warm-up call no
 // attribute is set any more, so later calls can be captured into CUDA graphs.
+// The attribute is set even below 48 KB: a kernel's static shared memory
+// counts against the default 48 KB as well.
 inline cudaError_t ensure_smem_impl(const void* kernel, size_t bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, size_t> granted;
@@ -127,7 +129,7 @@ inline cudaError_t ensure_smem_impl(const void* kernel, size_t bytes) {
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
   size_t& g = granted[std::make_pair(dev, kernel)];
-  if (bytes <= g || bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes <= g) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) g = bytes;
   return e;

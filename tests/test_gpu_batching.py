@@ -98,3 +98,18 @@ def test_autotune_then_graph_replay_with_new_inputs(tmp_path, monkeypatch):
     # a second instance reads the cached choice instead of timing again
     pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_min=4)
     assert pb2.autotune(reps=1) == chosen and pb2.inverse == pb.inverse
+
+
+def test_inverse_small_airfoils_with_static_shared_memory():
+    # n = 100: the Gauss-Jordan kernel's dynamic shared memory (41 KB) plus its
+    # static arrays cross the default 48 KB, so the launch needs the opt-in
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = inputs.make_population("naca_b64_n100", batch=16)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    pb.inverse = [True] * len(pb.buckets)
+    pb.run()
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop, pb.u.cpu().numpy(), pb.cl.cpu().numpy())
