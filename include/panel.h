@@ -98,6 +98,10 @@ typedef enum {
 #define PANEL_INFO_NONFINITE (-4)
 #define PANEL_INFO_NOCONV (-5)
 #define PANEL_INFO_TOO_LARGE (-6) /* n_b exceeds the n_max given to the call */
+/* A bounded device-side wait (tensor-core completion) ran out; the airfoil's
+ * factor is incomplete.  Not expected in operation: it turns a stalled
+ * pipeline into an error instead of a hang. */
+#define PANEL_INFO_DEVICE_TIMEOUT (-7)
 
 /*
  * panel_plan (HOST memory only, no GPU work).

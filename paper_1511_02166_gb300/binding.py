@@ -34,6 +34,7 @@ INFO_ZERO_PANEL = -3
 INFO_NONFINITE = -4
 INFO_NOCONV = -5
 INFO_TOO_LARGE = -6
+INFO_DEVICE_TIMEOUT = -7
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

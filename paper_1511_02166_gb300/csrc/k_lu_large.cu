@@ -424,7 +424,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = ensure_smem(k_large_trsm, large_trsm_smem());
   if (e != cudaSuccess) return e;
-  e = ensure_smem(k_large_update, large_update_smem());
+  e = ensure_smem(k_update_tc, update_tc_smem());
   if (e != cudaSuccess) return e;
   k_large_init<<<dim3(B, split_for(B, 64)), 256, 0, s>>>(a);
   for (int k0 = 0; k0 < m_max; k0 += kBW) {
@@ -433,7 +433,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     if (rest <= 0) break;
     const int ns = (rest + 127) / 128;
     k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, k0);
-    k_large_update<<<dim3(B, split_for(B, ns * ns)), 256, large_update_smem(), s>>>(a, k0);
+    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 256, update_tc_smem(), s>>>(a, k0);
   }
   k_large_finish<<<B, 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -43,7 +43,8 @@ def test_constants_match_header():
                       ("PANEL_INFO_ZERO_PANEL", bd.INFO_ZERO_PANEL),
                       ("PANEL_INFO_NONFINITE", bd.INFO_NONFINITE),
                       ("PANEL_INFO_NOCONV", bd.INFO_NOCONV),
-                      ("PANEL_INFO_TOO_LARGE", bd.INFO_TOO_LARGE)]:
+                      ("PANEL_INFO_TOO_LARGE", bd.INFO_TOO_LARGE),
+                      ("PANEL_INFO_DEVICE_TIMEOUT", bd.INFO_DEVICE_TIMEOUT)]:
         m = re.search(r"#define %s \((-\d+)\)" % name, txt)
         assert m and int(m.group(1)) == val, name
 
