@@ -433,7 +433,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     if (rest <= 0) break;
     const int ns = (rest + 127) / 128;
     k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, k0);
-    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 256, update_tc_smem(), s>>>(a, k0);
+    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 288, update_tc_smem(), s>>>(a, k0);
   }
   k_large_finish<<<B, 256, 0, s>>>(a);
   return cudaGetLastError();

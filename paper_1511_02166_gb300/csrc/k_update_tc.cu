@@ -2,9 +2,20 @@
 // blocked LU of large airfoils (k_lu_large.cu) on the 5th-generation tensor
 // cores: tcgen05.mma (kind::tf32) with the accumulator in tensor memory.
 //
-// One block of 256 threads takes 128 x 128 output tiles of one airfoil (block
-// y of gridDim.y strides over the airfoil's tiles); K = 128 (the block column)
-// in chunks of kKC = 16, double-buffered in shared memory.
+// One block takes 128 x 128 output tiles of one airfoil (block y of gridDim.y
+// strides over the airfoil's tiles); K = 128 (the block column) is fed in
+// chunks of kKC = 16.  The block is warp-specialised (288 threads):
+//   warps 0-3  epilogue: wait for a finished accumulator, read it from tensor
+//              memory (warp w owns TMEM lanes 32w..32w+31 = tile rows) and
+//              subtract it from A22;
+//   warps 4-7  producers: load a chunk of L21 and U12 into registers (the
+//              next chunk is in flight while the current one is stored), split
+//              it into TF32 hi / lo parts and store them in shared memory;
+//   warp 8     one lane issues the MMAs.
+// Producers and the MMA lane pass kStages shared-memory stages through
+// full / empty mbarriers; the MMA lane and the epilogue pass two tensor-memory
+// accumulators (2 x 128 columns) through tfull / tempty mbarriers, so the
+// epilogue of one tile overlaps the MMAs of the next.
 //
 // Precision.  The factor is FP32; a TF32 product alone (11 significant bits)
 // would make the LU far less accurate than FP32 and the refinement would stall
@@ -15,22 +26,17 @@
 // tensor memory.  The rank-128 product is accumulated on its own and
 // subtracted from A22 once, in the epilogue.
 //
-// Data movement.  The airfoil's row stride m is arbitrary, so rows are not
-// 16-byte aligned and a tensor map cannot describe them: operand chunks are
-// copied by cp.async (4 bytes per copy, zero-filled outside the matrix) into a
-// ring of raw stages two chunks ahead, then split into hi / lo and written in
-// the canonical K-major, non-swizzled layout:
-// 8-row x 16-byte core matrices, 128 contiguous bytes each; core matrices
-// adjacent in K are 128 B apart (leading byte offset), those adjacent in M / N
-// are kKC / 4 x 128 B apart (stride byte offset).  A generic-to-async proxy
-// fence orders the stores before the MMAs that read them; tcgen05.commit
-// arrives on one mbarrier per buffer when the MMAs that read it are done.
-// The epilogue reads the accumulator with tcgen05.ld (warp w reads TMEM lanes
-// 32 (w % 4) .. + 31, i.e. rows of the tile, and columns 64 (w / 4) .. + 63).
+// Layout.  The airfoil's row stride m is arbitrary, so rows are not 16-byte
+// aligned and a tensor map cannot describe them; the producers write the
+// canonical K-major, non-swizzled layout themselves: 8-row x 16-byte core
+// matrices, 128 contiguous bytes each; core matrices adjacent in K are 128 B
+// apart (leading byte offset), those adjacent in M / N are kKC / 4 x 128 B
+// apart (stride byte offset).  A generic-to-async proxy fence orders the
+// stores before the MMAs that read them.
 //
-// Every wait is bounded: a block that gives up sets info[b] =
-// PANEL_INFO_DEVICE_TIMEOUT, stops issuing work, waits (bounded) for its own
-// MMAs, frees its tensor memory and returns.
+// Every wait is bounded and polls a shared failure flag: a block that gives up
+// sets info[b] = PANEL_INFO_DEVICE_TIMEOUT, stops issuing work, waits
+// (bounded) for its own MMAs, frees its tensor memory and returns.
 #include "lu_mixed.cuh"
 
 namespace panel {
@@ -39,16 +45,16 @@ namespace {
 
 constexpr int kTM = 128;               // tile rows (MMA M)
 constexpr int kTN = 128;               // tile columns (MMA N)
-constexpr int kKC = 16;                // K per staged chunk
+constexpr int kKC = 16;                // K per chunk
 constexpr int kBWc = 128;              // block column width (K of the update)
 constexpr int kChunks = kBWc / kKC;    // 8
+constexpr int kStages = 3;             // shared-memory stages
 constexpr int kOpBytes = kTM * kKC * 4;            // one operand plane of a chunk: 8 KB
 constexpr int kBufBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
-constexpr int kRawStages = 3;                      // raw chunks in flight (cp.async)
-constexpr int kRawBytes = 2 * kOpBytes;            // raw A and B^T of one chunk
-constexpr int kSmemBytes = 2 * kBufBytes + kRawStages * kRawBytes + 64;
-constexpr uint32_t kTmemCols = 128;                // FP32 accumulator, 128 x 128
-constexpr long long kSpinLimit = 1ll << 22;        // bounded waits (well under a second per wait)
+constexpr int kSmemBytes = kStages * kBufBytes + 128;  // stages + barriers + flags
+constexpr uint32_t kTmemCols = 2 * kTN;            // two FP32 accumulators, 128 x 128 each
+constexpr int kThreadsTc = 288;                    // 4 epilogue + 4 producer + 1 MMA warps
+constexpr long long kSpinLimit = 1ll << 22;        // bounded waits (well under a second each)
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
@@ -84,8 +90,16 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// Waits for the phase with the given parity; false if the bounded spin ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+      : "memory");
+}
+
+// Waits for the phase with the given parity; false if the bounded spin ran out
+// or another thread of the block has already given up (*fail).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
   for (long long it = 0; it < kSpinLimit; ++it) {
     uint32_t done;
     asm volatile(
@@ -96,7 +110,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 255) == 255 && *fail) return false;
   }
+  *fail = 1;
   return false;
 }
 
@@ -144,7 +160,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 2) k_update_tc(SolveArgs a, int k0) {
+__global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
@@ -157,14 +173,17 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(SolveArgs a, int k0) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* F = a.LU + bt.mat_off[b];
-  unsigned char* raw = smraw + 2 * kBufBytes;  // kRawStages x (A rows, B^T rows)
-  unsigned char* misc = raw + kRawStages * kRawBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);  // 2 barriers
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 16);
-  int* fail = reinterpret_cast<int*>(misc + 20);
+  unsigned char* misc = smraw + kStages * kBufBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);  // full[3] empty[3] tfull[2] tempty[2] done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 96);
+  volatile int* fail = reinterpret_cast<volatile int*>(misc + 100);
   const uint32_t sbase = smem_u32(smraw);
-  const uint32_t rbase = smem_u32(raw);
-  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
+  const uint32_t bar_base = smem_u32(bars);
+  auto full_bar = [&](int st) { return bar_base + 8u * st; };
+  auto empty_bar = [&](int st) { return bar_base + 8u * (kStages + st); };
+  auto tfull_bar = [&](int ac) { return bar_base + 8u * (2 * kStages + ac); };
+  auto tempty_bar = [&](int ac) { return bar_base + 8u * (2 * kStages + 2 + ac); };
+  const uint32_t done_bar = bar_base + 8u * (2 * kStages + 4);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -174,8 +193,15 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(SolveArgs a, int k0) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(full_bar(st), 4);   // one arrival per producer warp
+      mbar_init(empty_bar(st), 1);  // tcgen05.commit
+    }
+    for (int ac = 0; ac < 2; ++ac) {
+      mbar_init(tfull_bar(ac), 1);   // tcgen05.commit
+      mbar_init(tempty_bar(ac), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(done_bar, 1);
     *fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -183,145 +209,122 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(SolveArgs a, int k0) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  bool ok = true;
 
-  // The chunks of all this block's tiles form one sequence q = 0 .. nq - 1
-  // (kChunks per tile).  Raw copies (cp.async, 4 bytes each: rows are not
-  // 16-byte aligned) run kRawStages - 1 chunks ahead of the MMAs.
   const int my_tiles = (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;
   const int nq = my_tiles * kChunks;
-  constexpr int kPer = kTM * kKC / 256;  // elements of A (and of B^T) per thread per chunk
-  auto tile_of = [&](int q, int& r0, int& c0) {
-    const int t = (int)blockIdx.y + (q / kChunks) * (int)gridDim.y;
+  auto tile_rc = [&](int tau, int& r0, int& c0) {
+    const int t = (int)blockIdx.y + tau * (int)gridDim.y;
     r0 = k1 + (t / nt) * kTM;
     c0 = k1 + (t % nt) * kTN;
   };
-  auto issue = [&](int q) {
-    if (q < nq) {
+
+  if (warp >= 4 && warp < 8) {
+    // ---------------- producers ----------------
+    const int pt = tid - 128;
+    constexpr int kPer = kTM * kKC / 128;  // 16 values of A and 16 of B^T per thread
+    auto load = [&](int q, float (&ra)[kPer], float (&rb)[kPer]) {
       int r0, c0;
-      tile_of(q, r0, c0);
+      tile_rc(q / kChunks, r0, c0);
       const int kg = k0 + (q % kChunks) * kKC;
-      const uint32_t dst = rbase + (uint32_t)((q % kRawStages) * kRawBytes);
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
-        const int e = tid + 256 * j;
-        const int r = r0 + e / kKC;                    // A[row][k], k fastest
-        const bool va = r < m;
-        const float* sa = va ? F + r * m + kg + e % kKC : F;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * e), "l"(sa),
-                     "r"(va ? 4 : 0)
-                     : "memory");
-        const int c = c0 + e % kTN;                    // B^T raw as U12[k][col], col fastest
-        const bool vb = c < m;
-        const float* sb = vb ? F + (kg + e / kTN) * m + c : F;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + kOpBytes + 4 * e),
-                     "l"(sb), "r"(vb ? 4 : 0)
-                     : "memory");
+        const int e = pt + 128 * j;
+        const int r = r0 + (e >> 4);          // A[row][k], k fastest
+        ra[j] = (r < m) ? F[r * m + kg + (e & 15)] : 0.0f;
+        const int c = c0 + (e & 127);         // U12[k][col], col fastest
+        rb[j] = (c < m) ? F[(kg + (e >> 7)) * m + c] : 0.0f;
       }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-
-  for (int q = 0; q < kRawStages - 1; ++q) issue(q);
-  for (int q = 0; q < nq && ok; ++q) {
-    const int kc = q % kChunks, buf = q & 1;
-    asm volatile("cp.async.wait_group %0;" ::"n"(kRawStages - 2) : "memory");
-    __syncthreads();  // chunk q's raw copy is visible to every thread
-    if (pending[buf]) {  // the MMAs that read this buffer two chunks ago
-      if (!mbar_wait(buf ? bar1 : bar0, phase[buf])) *fail = 1;
-      phase[buf] ^= 1u;
-      pending[buf] = false;
-    }
-    {
-      const float* ra = reinterpret_cast<const float*>(raw + (q % kRawStages) * kRawBytes);
-      const float* rb = ra + kTM * kKC;
-      unsigned char* B = smraw + buf * kBufBytes;
+    };
+    auto store = [&](int q, const float (&ra)[kPer], const float (&rb)[kPer]) -> bool {
+      const int st = q % kStages, u = q / kStages;
+      if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail)) return false;
+      unsigned char* B = smraw + st * kBufBytes;
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
-        const int e = tid + 256 * j;
-        const float xa = ra[e];
-        const float ha = tf32_hi(xa);
-        const uint32_t oa = core_off(e / kKC, e % kKC);
+        const int e = pt + 128 * j;
+        const uint32_t oa = core_off(e >> 4, e & 15);
+        const float ha = tf32_hi(ra[j]);
         *reinterpret_cast<float*>(B + oa) = ha;
-        *reinterpret_cast<float*>(B + kOpBytes + oa) = xa - ha;
-        const float xb = rb[e];
-        const float hb = tf32_hi(xb);
-        const uint32_t ob = core_off(e % kTN, e / kTN);
+        *reinterpret_cast<float*>(B + kOpBytes + oa) = ra[j] - ha;
+        const uint32_t ob = core_off(e & 127, e >> 7);
+        const float hb = tf32_hi(rb[j]);
         *reinterpret_cast<float*>(B + 2 * kOpBytes + ob) = hb;
-        *reinterpret_cast<float*>(B + 3 * kOpBytes + ob) = xb - hb;
+        *reinterpret_cast<float*>(B + 3 * kOpBytes + ob) = rb[j] - hb;
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full_bar(st));
+      return true;
+    };
+    float a0[kPer], b0[kPer], a1[kPer], b1[kPer];
+    load(0, a0, b0);
+    for (int q = 0; q < nq; q += 2) {
+      if (q + 1 < nq) load(q + 1, a1, b1);
+      if (!store(q, a0, b0)) break;
+      if (q + 1 >= nq) break;
+      if (q + 2 < nq) load(q + 2, a0, b0);
+      if (!store(q + 1, a1, b1)) break;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (*fail) {
-      ok = false;
-      break;
+  } else if (warp == 8) {
+    // ---------------- MMA issue (one lane) ----------------
+    if (lane == 0) {
+      for (int q = 0; q < nq; ++q) {
+        const int st = q % kStages, u = q / kStages;
+        const int kc = q % kChunks, tau = q / kChunks, ac = tau & 1, v = tau >> 1;
+        if (kc == 0 && v >= 1 && !mbar_wait(tempty_bar(ac), (v - 1) & 1, fail)) break;
+        if (!mbar_wait(full_bar(st), u & 1, fail)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ac * kTN);
+        const uint32_t ah = sbase + st * kBufBytes, al = ah + kOpBytes;
+        const uint32_t bh = ah + 2 * kOpBytes, bl = ah + 3 * kOpBytes;
+#pragma unroll
+        for (int s = 0; s < kKC / 8; ++s) {  // K = 8 per MMA: two core matrices
+          const uint32_t ko = s * 2 * 128;
+          const uint32_t acc0 = (kc > 0 || s > 0) ? 1u : 0u;
+          tc_mma(d, smem_desc(ah + ko), smem_desc(bh + ko), acc0);
+          tc_mma(d, smem_desc(ah + ko), smem_desc(bl + ko), 1u);
+          tc_mma(d, smem_desc(al + ko), smem_desc(bh + ko), 1u);
+        }
+        tc_commit(empty_bar(st));
+        if (kc == kChunks - 1) tc_commit(tfull_bar(ac));
+      }
+      tc_commit(done_bar);  // arrives once every MMA issued above has completed
     }
-    if (tid == 0) {
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: A22 -= D ----------------
+    for (int tau = 0; tau < my_tiles; ++tau) {
+      const int ac = tau & 1, v = tau >> 1;
+      if (!mbar_wait(tfull_bar(ac), v & 1, fail)) break;
       tc_fence_after();
-      const uint32_t ah = sbase + buf * kBufBytes, al = ah + kOpBytes;
-      const uint32_t bh = ah + 2 * kOpBytes, bl = ah + 3 * kOpBytes;
-#pragma unroll
-      for (int s = 0; s < kKC / 8; ++s) {  // K = 8 per MMA: two core matrices
-        const uint32_t ko = s * 2 * 128;
-        const uint32_t acc0 = (kc > 0 || s > 0) ? 1u : 0u;
-        tc_mma(tmem, smem_desc(ah + ko), smem_desc(bh + ko), acc0);
-        tc_mma(tmem, smem_desc(ah + ko), smem_desc(bl + ko), 1u);
-        tc_mma(tmem, smem_desc(al + ko), smem_desc(bh + ko), 1u);
-      }
-      tc_commit(buf ? bar1 : bar0);
-    }
-    pending[buf] = true;
-    issue(q + kRawStages - 1);
-    if (kc != kChunks - 1) continue;
-
-    // end of a tile: wait for all its MMAs, then A22 -= D
-    for (int p = 0; p < 2; ++p) {
-      if (pending[p]) {
-        if (!mbar_wait(p ? bar1 : bar0, phase[p])) *fail = 1;
-        phase[p] ^= 1u;
-        pending[p] = false;
-      }
-    }
-    tc_fence_after();
-    __syncthreads();
-    if (*fail) {
-      ok = false;
-      break;
-    }
-    int r0, c0;
-    tile_of(q, r0, c0);
-    const int g = warp & 3, h = warp >> 2;
-    const int r = r0 + 32 * g + lane;
+      int r0, c0;
+      tile_rc(tau, r0, c0);
+      const int r = r0 + 32 * warp + lane;
 #pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
-      const int cb = 64 * h + 32 * s;
-      float v[32];
-      tc_ld32(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)cb, v);
-      if (r < m) {
-        float* row = F + r * m + c0 + cb;
-        const int cn = min(32, m - (c0 + cb));
-        float c[32];
+      for (int s = 0; s < kTN / 32; ++s) {
+        float v32[32];
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * kTN + 32 * s), v32);
+        if (r < m) {
+          float* row = F + r * m + c0 + 32 * s;
+          const int cn = min(32, m - (c0 + 32 * s));
+          float c[32];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) c[i] = (i < cn) ? row[i] : 0.0f;
+          for (int i = 0; i < 32; ++i) c[i] = (i < cn) ? row[i] : 0.0f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (i < cn) row[i] = c[i] - v[i];
+          for (int i = 0; i < 32; ++i)
+            if (i < cn) row[i] = c[i] - v32[i];
+        }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(ac));
     }
-    tc_fence_before();
-    __syncthreads();
   }
 
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  if (!ok) {
-    // give the MMAs already issued a bounded chance to finish before the
-    // tensor memory is released
+  // every MMA this block issued has completed once done_bar has flipped
+  __syncthreads();
+  if (!mbar_wait(done_bar, 0, fail) || *fail) {
     if (tid == 0) a.info[b] = PANEL_INFO_DEVICE_TIMEOUT;
-    for (int p = 0; p < 2; ++p)
-      if (pending[p]) mbar_wait(p ? bar1 : bar0, phase[p]);
   }
   tc_fence_before();
   __syncthreads();
