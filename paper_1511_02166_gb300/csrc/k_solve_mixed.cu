@@ -572,7 +572,11 @@ __device__ __forceinline__ int gpiv_first(const SolveArgs& a, int b) {
   return a.piv[vec_off(a.bt, b)];
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_ir_mixed(SolveArgs a) {
+// MINB blocks per SM: 4 for small airfoils (more airfoils in flight to hide the
+// latency of the dependent sweeps, at the cost of a few spilled registers), 3
+// when shared memory allows no more anyway.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
@@ -789,9 +793,16 @@ cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_l
   SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
                           rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
   const size_t smem = ir_mixed_smem(bt.n_max);
-  cudaError_t e = ensure_smem(k_ir_mixed, smem);
-  if (e != cudaSuccess) return e;
-  k_ir_mixed<<<bt.B, kThreads, smem, s>>>(a);
+  cudaError_t e;
+  if (bt.n_max + 1 <= kFuseM) {
+    e = ensure_smem(k_ir_mixed<4>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<4><<<bt.B, kThreads, smem, s>>>(a);
+  } else {
+    e = ensure_smem(k_ir_mixed<3>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<3><<<bt.B, kThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

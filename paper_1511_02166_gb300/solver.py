@@ -165,20 +165,22 @@ class PanelBatch:
                               self.mat_offsets, self.order[start:], self.alpha, self.vinf,
                               self.A64, self.A_hi, self.A_lo, self.rhs, self.info)
 
+    def _solve_bucket(self, k, start, cnt, nmax, with_adjoint, stage, stream=None):
+        f = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
+        f |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
+        if self.inverse[k] and stage != "refine":
+            f |= bd.PANEL_INVERSE
+        bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
+                       self.order[start:], self.A64, self.A_hi, self.A_lo, self.LU,
+                       self.piv, self.rhs, self.vinf, self.chord, self.u,
+                       self.lam if with_adjoint else None, self.max_iter, self.tol,
+                       self.info, self.iters, stream=stream)
+
     def solve(self, with_adjoint: bool = False, stage: str = "all"):
         """stage 'all' (factor + refine), 'factor' (LU only) or 'refine' (reuse the
         stored LU; mixed mode only)."""
-        flags = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
-        flags |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
         for k, (start, cnt, nmax) in enumerate(self.buckets):
-            f = flags
-            if self.inverse[k] and stage != "refine":
-                f |= bd.PANEL_INVERSE
-            bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
-                           self.order[start:], self.A64, self.A_hi, self.A_lo, self.LU,
-                           self.piv, self.rhs, self.vinf, self.chord, self.u,
-                           self.lam if with_adjoint else None, self.max_iter, self.tol,
-                           self.info, self.iters)
+            self._solve_bucket(k, start, cnt, nmax, with_adjoint, stage)
         if stage != "factor":
             self.have_lambda = with_adjoint
 
@@ -186,16 +188,20 @@ class PanelBatch:
         bd.panel_forces(self.B, self.nodes, self.node_offsets, self.u, self.alpha, self.vinf,
                         self.chord, self.info, self.cp, self.cl, self.cl_p, self.cd_p)
 
+    def _adjoint_bucket(self, start, cnt, nmax, gc, have_lambda, stream=None):
+        bd.panel_adjoint(cnt, nmax, self.flags, self.nodes, self.node_offsets,
+                         self.mat_offsets, self.order[start:], self.A64, self.A_hi,
+                         self.A_lo, self.LU, self.piv, self.u,
+                         self.lam if have_lambda else None,
+                         None if have_lambda else self.lam, self.alpha, self.vinf,
+                         self.chord, gc, self.grad, self.max_iter, self.tol, self.info,
+                         stream=stream)
+
     def adjoint(self, grad_cl=None):
         gc = None if grad_cl is None else torch.as_tensor(
             grad_cl, dtype=torch.float64, device=self.device).contiguous()
         for start, cnt, nmax in self.buckets:
-            bd.panel_adjoint(cnt, nmax, self.flags, self.nodes, self.node_offsets,
-                             self.mat_offsets, self.order[start:], self.A64, self.A_hi,
-                             self.A_lo, self.LU, self.piv, self.u,
-                             self.lam if self.have_lambda else None,
-                             None if self.have_lambda else self.lam, self.alpha, self.vinf,
-                             self.chord, gc, self.grad, self.max_iter, self.tol, self.info)
+            self._adjoint_bucket(start, cnt, nmax, gc, self.have_lambda)
         self.have_lambda = True
 
     def run(self, with_grad: bool = False):
@@ -296,9 +302,10 @@ class PanelBatch:
         return chosen
 
     def capture(self, with_grad: bool = True):
-        """Record one step into a CUDA graph (after a warm-up step outside it)."""
+        """Record one step into a CUDA graph (after a warm-up step outside it);
+        with a pipeline the graph holds one branch per part."""
         self.graph = None
-        self.run(with_grad=with_grad)
+        self.run_pipelined(with_grad=with_grad)
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
