@@ -302,10 +302,9 @@ class PanelBatch:
         return chosen
 
     def capture(self, with_grad: bool = True):
-        """Record one step into a CUDA graph (after a warm-up step outside it);
-        with a pipeline the graph holds one branch per part."""
+        """Record one step into a CUDA graph (after a warm-up step outside it)."""
         self.graph = None
-        self.run_pipelined(with_grad=with_grad)
+        self.run(with_grad=with_grad)
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
