@@ -11,8 +11,8 @@
 //   k_large_trsm    U12 = L11^{-1} A12 and L21 = A21 U11^{-1}: the two
 //                   triangles of the diagonal block are inverted in shared
 //                   memory, then 128-wide slabs are multiplied by them.
-//   k_large_update  A22 -= L21 U12 in 128 x 128 tiles, K in chunks of 64,
-//                   8 x 8 outputs per thread (FP32 FMA).
+//   k_update_tc     A22 -= L21 U12 in 128 x 128 tiles on the tcgen05 tensor
+//                   cores (k_update_tc.cu).
 // Each of the three takes gridDim.y blocks per airfoil striding over its
 // slabs / tiles, so a batch of few airfoils still fills the GPU.
 //
@@ -37,8 +37,6 @@ namespace panel {
 
 constexpr int kBW = 128;      // block column width
 constexpr int kLdD = kBW + 1;
-constexpr int kUpdK = 64;     // K chunk of the update
-constexpr int kLdS = 132;     // row stride of the update's staged operands
 
 size_t lu_large_min_m() { return kLargeM + 1; }
 
@@ -333,73 +331,6 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
 size_t large_trsm_smem() {
   return ((size_t)kBW * kLdX + 2 * (size_t)kBW * kLdI + kBW) * 4;
 }
-
-// A22 -= L21 U12: 128 x 128 output tiles; thread (ty, tx) owns rows
-// {4ty..4ty+3, 64+4ty..64+4ty+3} and the same pattern of columns with tx.
-__global__ void __launch_bounds__(256, 2) k_large_update(SolveArgs a, int k0) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* As = reinterpret_cast<float*>(smraw);  // kUpdK x kLdS: As[k][r] = L21[r][k]
-  float* Bs = As + kUpdK * kLdS;                // kUpdK x kLdS: Bs[k][c] = U12[k][c]
-  const Batch& bt = a.bt;
-  const int b = bt.order[blockIdx.x];
-  int n, m;
-  if (!large_live(a, b, n, m)) return;
-  const int k1 = k0 + kBW;
-  if (k1 >= m) return;
-  const int rest = m - k1, nt = (rest + 127) >> 7, tiles = nt * nt;
-  float* F = a.LU + bt.mat_off[b];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int t = blockIdx.y; t < tiles; t += gridDim.y) {
-    const int r0 = k1 + (t / nt) * 128, c0 = k1 + (t % nt) * 128;
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    for (int kc = 0; kc < kBW; kc += kUpdK) {
-      __syncthreads();
-      for (int e = tid; e < 128 * kUpdK; e += 256) {
-        const int rr = e / kUpdK, kk = e % kUpdK;
-        const int r = r0 + rr;
-        As[kk * kLdS + rr] = (r < m) ? F[r * m + k0 + kc + kk] : 0.0f;
-      }
-      for (int e = tid; e < kUpdK * 128; e += 256) {
-        const int kk = e >> 7, cc = e & 127;
-        const int c = c0 + cc;
-        Bs[kk * kLdS + cc] = (c < m) ? F[(k0 + kc + kk) * m + c] : 0.0f;
-      }
-      __syncthreads();
-#pragma unroll 4
-      for (int kk = 0; kk < kUpdK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(As + kk * kLdS + 4 * ty);
-        const float4 a1 = *reinterpret_cast<const float4*>(As + kk * kLdS + 64 + 4 * ty);
-        const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * kLdS + 4 * tx);
-        const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * kLdS + 64 + 4 * tx);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-      }
-    }
-    const int ca = c0 + 4 * tx, cb = ca + 64;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = r0 + ((i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4);
-      if (r >= m) continue;
-      float* Cr = F + r * m;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (ca + j < m) Cr[ca + j] -= acc[i][j];
-        if (cb + j < m) Cr[cb + j] -= acc[i][j + 4];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-size_t large_update_smem() { return (size_t)2 * kUpdK * kLdS * 4; }
 
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   const Batch& bt = a.bt;
