@@ -35,7 +35,7 @@ METRIC = "airfoil solves/sec and dCl/dx gradients/sec on 1 GB300 at <=1e-10 Cl e
 DEFAULT_CONFIG = "naca_b4096_n200"
 L2_BYTES = 135528448
 
-# Algorithmic work per unit (derivations in the design doc):
+# Algorithmic work per unit:
 #  * assembly: one (control point, panel) pair = the FP32 flops (FMA = 2) of the
 #    double-float far-field evaluation, ASSEMBLY_FLOP_PER_PAIR;
 #  * factor: 2/3 m^3 FP32 flops per airfoil (m = n + 1);
@@ -115,6 +115,45 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def kernel_source_digest() -> str:
+    """sha256 over the CUDA sources (csrc/*.cu, *.cuh): a DRAM-traffic figure
+    recorded with another digest was taken on different kernels."""
+    import hashlib
+    import glob
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1511_02166_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(call, workload, mode, batch, digest):
+    """DRAM bytes per launch of `call` from the table in profiles/ (one ncu
+    capture per row, scaled to `batch` airfoils as the row says), or None if
+    there is no row for this call and workload or the kernels have changed."""
+    try:
+        with open(TRAFFIC_TABLE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        cells = [c.strip().strip("`") for c in ln.strip().strip("|").split("|")]
+        if len(cells) < 7 or cells[0] != call or cells[1] != workload or cells[2] != mode:
+            continue
+        try:
+            cap_batch = int(cells[3])
+            per_airfoil = float(cells[5]) / cap_batch
+        except ValueError:
+            continue
+        return per_airfoil * batch if cells[6] == digest else None
+    return None
 
 
 def _dist():
@@ -325,8 +364,12 @@ def run_ours(args):
                        "unit": unit, "frac": ach / peak}
     dom = max(kms, key=kms.get)
     dk = kernels[dom]
+    digest = kernel_source_digest()
+    traffic = recorded_traffic(dom, args.config, args.mode, B, digest)
     roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"],
-                "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"], "traffic": None,
+                "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"],
+                "traffic": traffic, "traffic_unit": "bytes per launch",
+                "kernel_digest": digest,
                 "peak_source": alu_src if dk["bound"] == "alu"
                 else "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     launches_per_step = pb.launches_per_step(with_grad=True)
