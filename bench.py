@@ -330,6 +330,30 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = float(np.mean(e2e_ms))
 
+    # ---- polar: Cl at POLAR_ANGLES angles per airfoil from one factorisation ----
+    polar = None
+    if args.mode == "mixed" and args.polar > 0:
+        K = int(args.polar)
+        alphas = torch.linspace(math.radians(-4.0), math.radians(10.0), K, dtype=torch.float64,
+                                device=dev).repeat(B, 1).contiguous()
+        pb.polar(alphas)
+        torch.cuda.synchronize()
+        pms = []
+        for it in range(args.warmup + max(2, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.polar(alphas)  # assemble + factor + two basis refinements + combination
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                pms.append(e0.elapsed_time(e1))
+        pm = float(np.mean(pms))
+        polar = {"angles": K, "ms": pm, "cl_per_s": world * B * K / (pm * 1e-3),
+                 "airfoil_polars_per_s": world * B / (pm * 1e-3),
+                 "what": "panel_assemble + panel_solve(factor) + panel_polar per step"}
+
     # ---- roofline of the dominant kernel ----
     kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
     sizes = pop.sizes.astype(np.float64)
@@ -387,6 +411,7 @@ def run_ours(args):
                       "inverse_buckets": int(sum(pb.inverse)),
                       "parallelism": "dp%d (independent airfoils)" % world},
            "gradients_per_s": value,
+           "polar": polar,
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
@@ -417,6 +442,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--polar", type=int, default=16,
+                    help="also time Cl at this many angles per airfoil from one factorisation "
+                         "(0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the calls one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

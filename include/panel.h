@@ -195,6 +195,28 @@ int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_
                   int32_t* info, void* stream);
 
 /*
+ * panel_polar -- Cl at K angles of attack per airfoil from one factorisation
+ * (PANEL_MIXED only; PANEL_FP64 returns PANEL_ENOTSUP).
+ *   The right-hand side of Section 2's system is linear in (cos a, sin a):
+ *   b(a) = cos(a) b_y + sin(a) b_x with b_y,j = v m_j,y and b_x,j = -v m_j,x
+ *   (m_j the control point, 0 in the Kutta row), so the strengths are
+ *   u(a) = cos(a) u_y + sin(a) u_x and Cl(a) = cos(a) Cl_y + sin(a) Cl_x.
+ *   The call refines the two basis systems against the matrix planes with the
+ *   factor (LU, piv) stored by an earlier panel_solve of the same planes (e.g.
+ *   with PANEL_FACTOR_ONLY), then combines them.
+ *   alphas [B][K] f64 radians by airfoil index; u_y, u_x [sum m_b] f64
+ *   outputs packed like u; cl [B][K] f64 output (NaN where info[b] != 0).
+ *   vinf, chord as in panel_solve.  info / iters as in panel_solve (iters is
+ *   that of the second basis system).  K = 0 solves the basis only.
+ */
+int panel_polar(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                const int64_t* mat_offsets, const int32_t* order, const float* A_hi,
+                const float* A_lo, const void* LU, const int32_t* piv, const double* vinf,
+                const double* chord, int K, const double* alphas, double* u_y, double* u_x,
+                double* cl, int max_iter, double tol, int32_t* info, int32_t* iters,
+                void* stream);
+
+/*
  * panel_df_eval -- diagnostic: evaluate the double-float primitives of the
  * PANEL_MIXED assembly on `count` device inputs (results rounded to f64):
  *   op 0: out[k] = log(a[k])                      (a[k] > 0)

@@ -49,6 +49,8 @@ SIGNATURES = {
     "panel_forces": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_adjoint": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                            _P, _P, _P, _I, _D, _P, _P]),
+    "panel_polar": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P,
+                         _P, _I, _D, _P, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
@@ -149,6 +151,15 @@ def panel_adjoint(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64,
                                 _ptr(lambda_out), _ptr(alpha), _ptr(vinf), _ptr(chord),
                                 _ptr(grad_cl), _ptr(grad_nodes), int(max_iter), float(tol),
                                 _ptr(info), _stream(stream)), "panel_adjoint")
+
+
+def panel_polar(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, A_lo, LU, piv,
+                vinf, chord, K, alphas, u_y, u_x, cl, max_iter, tol, info, iters, stream=None):
+    _check(load().panel_polar(B, n_max, flags, _ptr(nodes), _ptr(node_offsets),
+                              _ptr(mat_offsets), _ptr(order), _ptr(A_hi), _ptr(A_lo), _ptr(LU),
+                              _ptr(piv), _ptr(vinf), _ptr(chord), int(K), _ptr(alphas),
+                              _ptr(u_y), _ptr(u_x), _ptr(cl), int(max_iter), float(tol),
+                              _ptr(info), _ptr(iters), _stream(stream)), "panel_polar")
 
 
 def panel_df_eval(op, count, a, b, out, stream=None):

@@ -27,7 +27,11 @@ cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_
                             bool, cudaStream_t);
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
-                            double*, int, double, int32_t*, int32_t*, cudaStream_t);
+                            double*, int, double, int32_t*, int32_t*, cudaStream_t,
+                            int rhs_kind = 0);
+cudaError_t launch_polar_cl(const Batch&, const double*, const double*, const double*,
+                            const double*, int, const double*, const int32_t*, double*,
+                            cudaStream_t);
 cudaError_t launch_df_eval(int, int, const double*, const double*, double*, cudaStream_t);
 size_t adjoint_df_smem(int n_max);
 constexpr size_t kMaxDynSmem = 232448;
@@ -155,6 +159,31 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
   if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
                                adj ? lambda : nullptr, max_iter, tol, info, iters, s);
+  return status_of(e);
+}
+
+int panel_polar(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+                const int64_t* mat_offsets, const int32_t* order, const float* A_hi,
+                const float* A_lo, const void* LU, const int32_t* piv, const double* vinf,
+                const double* chord, int K, const double* alphas, double* u_y, double* u_x,
+                double* cl, int max_iter, double tol, int32_t* info, int32_t* iters,
+                void* stream) {
+  if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX || K < 0) return PANEL_EINVAL;
+  if (mode_of(flags) == PANEL_FP64) return PANEL_ENOTSUP;
+  if (mode_of(flags) != PANEL_MIXED || (flags & ~PANEL_MIXED) != 0) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !mat_offsets || !order || !A_hi || !A_lo || !LU || !piv ||
+      !u_y || !u_x || !info || (K > 0 && (!alphas || !cl)) || max_iter < 0 || !(tol > 0.0))
+    return PANEL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch bt = make_batch(B, n_max, nodes, node_offsets, mat_offsets, order);
+  cudaError_t e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, nullptr, vinf,
+                                         chord, u_y, nullptr, max_iter, tol, info, iters, s, 1);
+  if (e == cudaSuccess)
+    e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, nullptr, vinf, chord,
+                               u_x, nullptr, max_iter, tol, info, iters, s, 2);
+  if (e == cudaSuccess && K > 0)
+    e = panel::launch_polar_cl(bt, u_y, u_x, vinf, chord, K, alphas, info, cl, s);
   return status_of(e);
 }
 

@@ -71,4 +71,55 @@ cudaError_t launch_forces(const Batch& bt, const double* u, const double* alpha,
   return cudaGetLastError();
 }
 
+// Polar: with the basis solutions u_y (right-hand side v m_y) and u_x (-v m_x)
+// of the same factored system, u(alpha) = cos(alpha) u_y + sin(alpha) u_x by
+// linearity, so Cl(alpha) = cos(alpha) Cl_y + sin(alpha) Cl_x.  One warp per
+// airfoil of this call (size order); cl is [B][K] by airfoil index.
+__global__ void __launch_bounds__(256) k_polar_cl(Batch bt, const double* __restrict__ uy,
+                                                  const double* __restrict__ ux,
+                                                  const double* __restrict__ vinf,
+                                                  const double* __restrict__ chord, int K,
+                                                  const double* __restrict__ alphas,
+                                                  const int32_t* __restrict__ info,
+                                                  double* __restrict__ cl) {
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= bt.B) return;
+  const int b = bt.order[w];
+  const int n = airfoil_n(bt, b);
+  double* out = cl + (int64_t)b * K;
+  if ((info && info[b] != 0) || n < 3 || n > bt.n_max) {
+    for (int k = lane; k < K; k += 32) out[k] = nan("");
+    return;
+  }
+  const double* x = bt.nodes + 2 * bt.node_off[b];
+  const double* gy = uy + vec_off(bt, b);
+  const double* gx = ux + vec_off(bt, b);
+  double cy = 0.0, cx = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    const int j1 = (j + 1 == n) ? 0 : j + 1;
+    const double hx = x[2 * j1] - x[2 * j], hy = x[2 * j1 + 1] - x[2 * j + 1];
+    const double L = sqrt(hx * hx + hy * hy);
+    cy = fma(gy[j], L, cy);
+    cx = fma(gx[j], L, cx);
+  }
+  cy = warp_sum(cy);
+  cx = warp_sum(cx);
+  const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
+  const double f = 2.0 / (v * c);
+  for (int k = lane; k < K; k += 32) {
+    const double al = alphas[(int64_t)b * K + k];
+    out[k] = f * (cos(al) * cy + sin(al) * cx);
+  }
+}
+
+cudaError_t launch_polar_cl(const Batch& bt, const double* uy, const double* ux,
+                            const double* vinf, const double* chord, int K, const double* alphas,
+                            const int32_t* info, double* cl, cudaStream_t s) {
+  const int wpb = 8;
+  const int grid = (bt.B + wpb - 1) / wpb;
+  k_polar_cl<<<grid, wpb * 32, 0, s>>>(bt, uy, ux, vinf, chord, K, alphas, info, cl);
+  return cudaGetLastError();
+}
+
 }  // namespace panel

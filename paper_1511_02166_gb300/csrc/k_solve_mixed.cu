@@ -621,7 +621,21 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
   const double* nd = bt.nodes + 2 * bt.node_off[b];
   const double v = a.vinf ? a.vinf[b] : 1.0, cc = a.chord ? a.chord[b] : 1.0;
   for (int k = threadIdx.x; k < m; k += kThreads) {
-    if (act0) sys[0].bb[k] = a.rhs[vec_off(bt, b) + k];
+    if (act0) {
+      if (a.rhs_kind == 0) {
+        sys[0].bb[k] = a.rhs[vec_off(bt, b) + k];
+      } else {
+        // the basis right-hand sides of a polar: b(alpha) = cos(alpha) b_y +
+        // sin(alpha) b_x with b_y = v m_y, b_x = -v m_x (m the control point)
+        double bk = 0.0;
+        if (k < n) {
+          const int k1 = (k + 1 == n) ? 0 : k + 1;
+          bk = (a.rhs_kind == 1) ? 0.5 * v * (nd[2 * k + 1] + nd[2 * k1 + 1])
+                                 : -0.5 * v * (nd[2 * k] + nd[2 * k1]);
+        }
+        sys[0].bb[k] = bk;
+      }
+    }
     if (act1) {
       double g = 0.0;
       if (k < n) {
@@ -755,6 +769,7 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.iters = iters;
   a.inverse = 0;
   a.n_cap = bt.n_max;
+  a.rhs_kind = 0;
   return a;
 }
 
@@ -789,9 +804,10 @@ cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_l
                             const float* LU, const int32_t* piv, const double* rhs,
                             const double* vinf, const double* chord, double* u, double* lam,
                             int max_iter, double tol, int32_t* info, int32_t* iters,
-                            cudaStream_t s) {
+                            cudaStream_t s, int rhs_kind) {
   SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
                           rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
+  a.rhs_kind = rhs_kind;
   const size_t smem = ir_mixed_smem(bt.n_max);
   cudaError_t e;
   if (bt.n_max + 1 <= kFuseM) {

@@ -30,6 +30,7 @@ struct SolveArgs {
   int32_t* iters;
   int inverse;       // m <= kGjM: Gauss-Jordan inverse (k_gj_mixed.cu) instead of the LU
   int n_cap;         // the caller's n_max (bt.n_max may be lowered to size a kernel)
+  int rhs_kind;      // forward right-hand side: 0 rhs, 1 v m_y, 2 -v m_x (polar basis)
 };
 
 __device__ __forceinline__ double block_absmax_d(double v, double* red) {

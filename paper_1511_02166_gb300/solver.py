@@ -204,6 +204,33 @@ class PanelBatch:
             self._adjoint_bucket(start, cnt, nmax, gc, self.have_lambda)
         self.have_lambda = True
 
+    def polar(self, alphas, factor: bool = True):
+        """Cl at K angles per airfoil, alphas [B][K] radians (by airfoil index),
+        from one factorisation: the two basis systems (right-hand sides v m_y
+        and -v m_x) are refined with the stored factor and combined,
+        Cl(a) = cos(a) Cl_y + sin(a) Cl_x.  Returns cl [B][K] (and keeps the basis
+        strengths in self.u_y, self.u_x).  factor=False reuses the factor of an
+        earlier solve of the same matrices."""
+        if self.flags != bd.PANEL_MIXED:
+            raise ValueError("polars need the mixed-precision path")
+        al = torch.as_tensor(alphas, dtype=torch.float64, device=self.device).contiguous()
+        if al.dim() != 2 or al.shape[0] != self.B:
+            raise ValueError("alphas must be [B][K]")
+        K = int(al.shape[1])
+        if factor:
+            self.assemble()
+            self.solve(stage="factor")
+        if getattr(self, "u_y", None) is None:
+            self.u_y = torch.empty_like(self.u)
+            self.u_x = torch.empty_like(self.u)
+        cl = torch.empty(self.B, K, dtype=torch.float64, device=self.device)
+        for start, cnt, nmax in self.buckets:
+            bd.panel_polar(cnt, nmax, self.flags, self.nodes, self.node_offsets,
+                           self.mat_offsets, self.order[start:], self.A_hi, self.A_lo, self.LU,
+                           self.piv, self.vinf, self.chord, K, al, self.u_y, self.u_x, cl,
+                           self.max_iter, self.tol, self.info, self.iters)
+        return cl
+
     def run(self, with_grad: bool = False):
         """Assemble, solve, forces (and the adjoint for unit upstream gradient)."""
         self.assemble()

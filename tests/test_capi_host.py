@@ -85,6 +85,12 @@ def test_argument_validation_before_any_launch():
                            None, None, None) == bd.PANEL_EINVAL
     assert lib.panel_solve(1, 10, bd.PANEL_MIXED | bd.PANEL_FACTOR_ONLY | bd.PANEL_REUSE_FACTOR,
                            *([None] * 14), 3, 1e-12, None, None, None) == bd.PANEL_EINVAL
+    # polars: mixed path only, pointers checked, an empty batch is a no-op
+    args = [None] * 10 + [0, None, None, None, None, 3, 1e-12, None, None, None]
+    assert lib.panel_polar(1, 10, bd.PANEL_FP64, *args) == bd.PANEL_ENOTSUP
+    assert lib.panel_polar(1, 10, bd.PANEL_MIXED, *args) == bd.PANEL_EINVAL
+    assert lib.panel_polar(1, 10, bd.PANEL_MIXED | bd.PANEL_INVERSE, *args) == bd.PANEL_EINVAL
+    assert lib.panel_polar(0, 10, bd.PANEL_MIXED, *args) == bd.PANEL_OK
     # an empty batch is a no-op
     assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
     assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"
