@@ -76,6 +76,9 @@ def _bind(lib):
     lib.oracle_cl_gradient.restype = ctypes.c_int
     lib.oracle_cl_gradient.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, _D]
+    lib.oracle_vjp.restype = ctypes.c_int
+    lib.oracle_vjp.argtypes = [ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, _D, _D, _D]
     lib.oracle_evaluate_batch.restype = None
     lib.oracle_evaluate_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _D, _D,
                                           _D, _D, _I32, ctypes.c_int]
@@ -206,6 +209,20 @@ def cl_gradient(nodes, alpha: float, vinf: float = 1.0, chord: float = 1.0):
     g = np.zeros((n, 2))
     info = _load().oracle_cl_gradient(n, _dp(nodes), float(alpha), float(vinf), float(chord),
                                       _dp(g))
+    return g, info
+
+
+def vjp(nodes, alpha: float, w_cl: float = 0.0, w_gamma=None, w_cp=None, vinf: float = 1.0,
+        chord: float = 1.0):
+    """Gradient w.r.t. the nodes [n][2] of w_cl Cl + w_gamma . gamma + w_cp . Cp by
+    forward tangents; returns (grad, info)."""
+    nodes = _f64(nodes)
+    n = len(nodes)
+    g = np.zeros((n, 2))
+    wg = None if w_gamma is None else _f64(w_gamma)
+    wc = None if w_cp is None else _f64(w_cp)
+    info = _load().oracle_vjp(n, _dp(nodes), float(alpha), float(vinf), float(chord),
+                              float(w_cl), _dp(wg), _dp(wc), _dp(g))
     return g, info
 
 

@@ -430,16 +430,20 @@ static void node_dual(const double *nodes, int n, int i, int k, int coord, dual 
 }
 
 /*
- * dCl/d(node coordinates) for one airfoil by forward tangents:
- *   M du/ds = db/ds - (dM/ds) u,   dCl/ds = 2/(v_inf c) sum_i (du_i/ds |h_i| + u_i d|h_i|/ds)
+ * Vector-Jacobian product for one airfoil by forward tangents: the gradient
+ * with respect to the node coordinates of
+ *   L = w_cl Cl + sum_j w_gamma[j] gamma_j + sum_j w_cp[j] Cp_j
+ * (w_gamma, w_cp of length n, either may be NULL = 0), through
+ *   M du/ds = db/ds - (dM/ds) u,   dCl/ds = 2/(v_inf c) sum_i (du_i/ds |h_i| + u_i d|h_i|/ds),
+ *   dCp_j/ds = -2 gamma_j dgamma_j/ds / v_inf^2,
  * for each of the 2n coordinates s, reusing the LU of M.  dM/ds is formed
  * entry by entry from the dual panel integral; entries that do not involve
  * node k (neither the control point nor the panel touches it) have zero
- * derivative and are skipped.  grad[2k+c] = dCl/d(x_k)_c.  Returns the LU info
+ * derivative and are skipped.  grad[2k+c] = dL/d(x_k)_c.  Returns the LU info
  * (0 on success) or a negative geometry code.
  */
-int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, double chord,
-                       double *grad) {
+int oracle_vjp(int n, const double *nodes, double alpha, double vinf, double chord, double w_cl,
+               const double *w_gamma, const double *w_cp, double *grad) {
   if (n < 3) return -1;
   if (!(oracle_signed_area(n, nodes) > 0.0)) return -2;
   int m = n + 1;
@@ -491,7 +495,12 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
           dual len = dsqrt(dadd(dmul(hx, hx), dmul(hy, hy)));
           dcl += r[i] * len.v + u[i] * len.d;
         }
-        grad[2 * k + coord] = (double)(2.0 * dcl / (rv * rc));
+        real dl = (real)w_cl * 2.0 * dcl / (rv * rc);
+        for (int j = 0; j < n; ++j) {
+          if (w_gamma) dl += (real)w_gamma[j] * r[j];
+          if (w_cp) dl += (real)w_cp[j] * (-2.0 * u[j] * r[j] / (rv * rv));
+        }
+        grad[2 * k + coord] = (double)dl;
       }
     }
   }
@@ -502,6 +511,12 @@ int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, do
   free(r);
   free(piv);
   return info;
+}
+
+/* dCl/d(node coordinates): the product above with w_cl = 1 alone. */
+int oracle_cl_gradient(int n, const double *nodes, double alpha, double vinf, double chord,
+                       double *grad) {
+  return oracle_vjp(n, nodes, alpha, vinf, chord, 1.0, NULL, NULL, grad);
 }
 
 /* ------------------------------------------------------------------------ */

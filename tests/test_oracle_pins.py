@@ -508,6 +508,38 @@ def test_gradient_matches_central_differences():
     assert rel_inf(g, fd) < 1e-5
 
 
+def test_vjp_matches_central_differences():
+    # L = w_cl Cl + w_gamma . gamma + w_cp . Cp with random weights: the tangent
+    # product against central differences of L from full re-evaluations
+    nodes = inputs.naca4(0.02, 0.35, 0.13, 20)
+    al = math.radians(4.0)
+    rng = np.random.default_rng(5)
+    n = len(nodes)
+    w_cl, w_g, w_cp = 0.7, rng.normal(size=n), rng.normal(size=n)
+
+    def L(x):
+        r = oracle.evaluate(x, al)
+        return w_cl * r["cl"] + w_g @ r["gamma"] + w_cp @ r["cp"]
+
+    g, info = oracle.vjp(nodes, al, w_cl, w_g, w_cp)
+    assert info == 0
+    h = 1e-6
+    fd = np.zeros_like(nodes)
+    for k in range(n):
+        for c in range(2):
+            xp = nodes.copy()
+            xm = nodes.copy()
+            xp[k, c] += h
+            xm[k, c] -= h
+            fd[k, c] = (L(xp) - L(xm)) / (2 * h)
+    assert rel_inf(g, fd) < 1e-5
+    # the three parts are additive, and w_cl alone is the Cl gradient
+    gc, _ = oracle.cl_gradient(nodes, al)
+    gg, _ = oracle.vjp(nodes, al, 0.0, w_g, None)
+    gp, _ = oracle.vjp(nodes, al, 0.0, None, w_cp)
+    assert rel_inf(w_cl * gc + gg + gp, g) < 1e-12
+
+
 def test_gradient_invariances():
     # Cl does not change under a rigid translation: the node gradients sum to zero.
     nodes = inputs.naca4(0.02, 0.3, 0.12, 40)
