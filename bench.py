@@ -354,6 +354,32 @@ def run_ours(args):
                  "airfoil_polars_per_s": world * B / (pm * 1e-3),
                  "what": "panel_assemble + panel_solve(factor) + panel_polar per step"}
 
+    # ---- vector-Jacobian product of (Cl, u, Cp) on the solved population ----
+    vjp = None
+    if args.mode == "mixed" and args.vjp:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1511)
+        w_cl = torch.randn(B, dtype=torch.float64, device=dev, generator=gen)
+        w_u = torch.randn(pb.total_vec, dtype=torch.float64, device=dev, generator=gen)
+        w_cp = torch.randn(pb.total_nodes, dtype=torch.float64, device=dev, generator=gen)
+        pb.run()
+        pb.vjp(w_cl, w_u, w_cp)
+        torch.cuda.synchronize()
+        vms = []
+        for it in range(args.warmup + max(2, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.vjp(w_cl, w_u, w_cp)  # transposed refinement + dM/dx contraction
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                vms.append(e0.elapsed_time(e1))
+        vm = float(np.mean(vms))
+        vjp = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
+               "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
+
     # ---- roofline of the dominant kernel ----
     kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
     sizes = pop.sizes.astype(np.float64)
@@ -412,6 +438,7 @@ def run_ours(args):
                       "parallelism": "dp%d (independent airfoils)" % world},
            "gradients_per_s": value,
            "polar": polar,
+           "vjp": vjp,
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
@@ -445,6 +472,8 @@ def main():
     ap.add_argument("--polar", type=int, default=16,
                     help="also time Cl at this many angles per airfoil from one factorisation "
                          "(0: skip)")
+    ap.add_argument("--no-vjp", dest="vjp", action="store_false",
+                    help="skip timing the vector-Jacobian product of (Cl, u, Cp)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the calls one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

@@ -217,6 +217,29 @@ int panel_polar(int B, int n_max, int flags, const double* nodes, const int64_t*
                 void* stream);
 
 /*
+ * panel_vjp -- vector-Jacobian product of the strengths, Cp and Cl with
+ * respect to the node coordinates (PANEL_MIXED only; PANEL_FP64 returns
+ * PANEL_ENOTSUP): grad_nodes = dL/dx for
+ *   L = sum_b w_cl[b] Cl_b + sum_j w_u[j] u_j + sum_j w_cp[j] Cp_j,
+ *   u = (gamma, C) per airfoil as solved by panel_solve, Cp_j = 1 - (gamma_j / v)^2
+ *   (Section 2's strengths and Cp, as panel_forces).
+ *   lambda solves M^T lambda = dL/du (refined with the stored factor LU/piv of
+ *   an earlier panel_solve of the same matrix planes), then
+ *   dL/dx_k = w_cl dCl/dx_k|_u + lambda^T (db/dx_k - (dM/dx_k) u), with the pair
+ *   derivatives of panel_adjoint.
+ *   u [sum m_b] the solved strengths; w_cl [B] (NULL = 0); w_u [sum m_b] packed
+ *   like u and w_cp [sum n_b] packed like the nodes (NULL = 0); lambda
+ *   [sum m_b] f64 output;
+ *   grad_nodes [sum n_b][2] f64 output (NaN where info[b] != 0).
+ */
+int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+              const int64_t* mat_offsets, const int32_t* order, const float* A_hi,
+              const float* A_lo, const void* LU, const int32_t* piv, const double* u,
+              const double* alpha, const double* vinf, const double* chord, const double* w_cl,
+              const double* w_u, const double* w_cp, double* lambda, double* grad_nodes,
+              int max_iter, double tol, int32_t* info, void* stream);
+
+/*
  * panel_df_eval -- diagnostic: evaluate the double-float primitives of the
  * PANEL_MIXED assembly on `count` device inputs (results rounded to f64):
  *   op 0: out[k] = log(a[k])                      (a[k] > 0)

@@ -212,14 +212,14 @@ def cl_gradient(nodes, alpha: float, vinf: float = 1.0, chord: float = 1.0):
     return g, info
 
 
-def vjp(nodes, alpha: float, w_cl: float = 0.0, w_gamma=None, w_cp=None, vinf: float = 1.0,
+def vjp(nodes, alpha: float, w_cl: float = 0.0, w_u=None, w_cp=None, vinf: float = 1.0,
         chord: float = 1.0):
-    """Gradient w.r.t. the nodes [n][2] of w_cl Cl + w_gamma . gamma + w_cp . Cp by
-    forward tangents; returns (grad, info)."""
+    """Gradient w.r.t. the nodes [n][2] of w_cl Cl + w_u . u + w_cp . Cp by forward
+    tangents, u = (gamma, C) (w_u of length n + 1); returns (grad, info)."""
     nodes = _f64(nodes)
     n = len(nodes)
     g = np.zeros((n, 2))
-    wg = None if w_gamma is None else _f64(w_gamma)
+    wg = None if w_u is None else _f64(w_u)
     wc = None if w_cp is None else _f64(w_cp)
     info = _load().oracle_vjp(n, _dp(nodes), float(alpha), float(vinf), float(chord),
                               float(w_cl), _dp(wg), _dp(wc), _dp(g))

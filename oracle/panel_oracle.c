@@ -432,8 +432,9 @@ static void node_dual(const double *nodes, int n, int i, int k, int coord, dual 
 /*
  * Vector-Jacobian product for one airfoil by forward tangents: the gradient
  * with respect to the node coordinates of
- *   L = w_cl Cl + sum_j w_gamma[j] gamma_j + sum_j w_cp[j] Cp_j
- * (w_gamma, w_cp of length n, either may be NULL = 0), through
+ *   L = w_cl Cl + sum_j w_u[j] u_j + sum_j w_cp[j] Cp_j
+ * with u = (gamma_0 .. gamma_{n-1}, C) (w_u of length n + 1, w_cp of length n,
+ * either may be NULL = 0), through
  *   M du/ds = db/ds - (dM/ds) u,   dCl/ds = 2/(v_inf c) sum_i (du_i/ds |h_i| + u_i d|h_i|/ds),
  *   dCp_j/ds = -2 gamma_j dgamma_j/ds / v_inf^2,
  * for each of the 2n coordinates s, reusing the LU of M.  dM/ds is formed
@@ -443,7 +444,7 @@ static void node_dual(const double *nodes, int n, int i, int k, int coord, dual 
  * (0 on success) or a negative geometry code.
  */
 int oracle_vjp(int n, const double *nodes, double alpha, double vinf, double chord, double w_cl,
-               const double *w_gamma, const double *w_cp, double *grad) {
+               const double *w_u, const double *w_cp, double *grad) {
   if (n < 3) return -1;
   if (!(oracle_signed_area(n, nodes) > 0.0)) return -2;
   int m = n + 1;
@@ -496,10 +497,10 @@ int oracle_vjp(int n, const double *nodes, double alpha, double vinf, double cho
           dcl += r[i] * len.v + u[i] * len.d;
         }
         real dl = (real)w_cl * 2.0 * dcl / (rv * rc);
-        for (int j = 0; j < n; ++j) {
-          if (w_gamma) dl += (real)w_gamma[j] * r[j];
+        for (int j = 0; j < m; ++j)
+          if (w_u) dl += (real)w_u[j] * r[j];
+        for (int j = 0; j < n; ++j)
           if (w_cp) dl += (real)w_cp[j] * (-2.0 * u[j] * r[j] / (rv * rv));
-        }
         grad[2 * k + coord] = (double)dl;
       }
     }

@@ -51,6 +51,8 @@ SIGNATURES = {
                            _P, _P, _P, _I, _D, _P, _P]),
     "panel_polar": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P,
                          _P, _I, _D, _P, _P, _P]),
+    "panel_vjp": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                       _P, _P, _I, _D, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
@@ -160,6 +162,16 @@ def panel_polar(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, 
                               _ptr(piv), _ptr(vinf), _ptr(chord), int(K), _ptr(alphas),
                               _ptr(u_y), _ptr(u_x), _ptr(cl), int(max_iter), float(tol),
                               _ptr(info), _ptr(iters), _stream(stream)), "panel_polar")
+
+
+def panel_vjp(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, A_lo, LU, piv, u,
+              alpha, vinf, chord, w_cl, w_u, w_cp, lam, grad_nodes, max_iter, tol, info,
+              stream=None):
+    _check(load().panel_vjp(B, n_max, flags, _ptr(nodes), _ptr(node_offsets), _ptr(mat_offsets),
+                            _ptr(order), _ptr(A_hi), _ptr(A_lo), _ptr(LU), _ptr(piv), _ptr(u),
+                            _ptr(alpha), _ptr(vinf), _ptr(chord), _ptr(w_cl), _ptr(w_u),
+                            _ptr(w_cp), _ptr(lam), _ptr(grad_nodes), int(max_iter), float(tol),
+                            _ptr(info), _stream(stream)), "panel_vjp")
 
 
 def panel_df_eval(op, count, a, b, out, stream=None):

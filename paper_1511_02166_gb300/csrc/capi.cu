@@ -37,7 +37,11 @@ size_t adjoint_df_smem(int n_max);
 constexpr size_t kMaxDynSmem = 232448;
 cudaError_t launch_adjoint_df(const Batch&, const double*, const double*, const double*,
                               const double*, const double*, const double*, double*,
-                              const int32_t*, cudaStream_t);
+                              const int32_t*, cudaStream_t, bool lam_weighted = false);
+cudaError_t launch_ir_vjp(const Batch&, const float*, const float*, const float*,
+                          const int32_t*, const double*, const double*, const double*,
+                          const double*, const double*, const double*, double*, int, double,
+                          int32_t*, cudaStream_t);
 }  // namespace panel
 
 using panel::Batch;
@@ -185,6 +189,29 @@ int panel_polar(int B, int n_max, int flags, const double* nodes, const int64_t*
   if (e == cudaSuccess && K > 0)
     e = panel::launch_polar_cl(bt, u_y, u_x, vinf, chord, K, alphas, info, cl, s);
   return status_of(e);
+}
+
+int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
+              const int64_t* mat_offsets, const int32_t* order, const float* A_hi,
+              const float* A_lo, const void* LU, const int32_t* piv, const double* u,
+              const double* alpha, const double* vinf, const double* chord, const double* w_cl,
+              const double* w_u, const double* w_cp, double* lambda, double* grad_nodes,
+              int max_iter, double tol, int32_t* info, void* stream) {
+  if (B < 0 || n_max < 3 || n_max > PANEL_N_MAX) return PANEL_EINVAL;
+  if (mode_of(flags) == PANEL_FP64) return PANEL_ENOTSUP;
+  if (mode_of(flags) != PANEL_MIXED || (flags & ~PANEL_MIXED) != 0) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !mat_offsets || !order || !A_hi || !A_lo || !LU || !piv ||
+      !u || !alpha || !lambda || !grad_nodes || !info || max_iter < 0 || !(tol > 0.0))
+    return PANEL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Batch bt = make_batch(B, n_max, nodes, node_offsets, mat_offsets, order);
+  cudaError_t e = panel::launch_ir_vjp(bt, A_hi, A_lo, (const float*)LU, piv, vinf, chord, u,
+                                       w_cl, w_u, w_cp, lambda, max_iter, tol, info, s);
+  if (e != cudaSuccess) return status_of(e);
+  if (panel::adjoint_df_smem(n_max) > panel::kMaxDynSmem) return PANEL_ENOTSUP;
+  return status_of(panel::launch_adjoint_df(bt, u, lambda, alpha, vinf, chord, w_cl,
+                                            grad_nodes, info, s, true));
 }
 
 int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const double* u,

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
     const double* __restrict__ alpha, const double* __restrict__ vinf,
     const double* __restrict__ chord, const double* __restrict__ grad_cl,
-    double* __restrict__ grad, const int32_t* __restrict__ info) {
+    double* __restrict__ grad, const int32_t* __restrict__ info, int lam_weighted) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = bt.n_max;
   float4* tlog = reinterpret_cast<float4*>(smraw);        // 257
@@ -274,7 +274,11 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
   __syncthreads();
   const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
   const double ca = cos(alpha[b]), sa = sin(alpha[b]);
-  const double gscale = grad_cl ? grad_cl[b] : 1.0;
+  // se scales the explicit dCl/dx term, sl the lambda terms: the upstream
+  // dL/dCl for both when lambda solves M^T lambda = dCl/du, or (w_cl, 1) when
+  // lambda already carries the weights of a vector-Jacobian product
+  const double se = grad_cl ? grad_cl[b] : (lam_weighted ? 0.0 : 1.0);
+  const double sl = lam_weighted ? 1.0 : se;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int km = (k == 0) ? n - 1 : k - 1;
     const int k1 = (k + 1 == n) ? 0 : k + 1;
@@ -282,16 +286,16 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     const double hkx = xs[k1] - xs[k], hky = ys[k1] - ys[k];
     const double hmx = xs[k] - xs[km], hmy = ys[k] - ys[km];
     const double Lk = sqrt(hkx * hkx + hky * hky), Lm = sqrt(hmx * hmx + hmy * hmy);
-    double gx = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
-    double gy = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
-    gx += 0.5 * v * (-sa) * (lb[km] + lb[k]);
-    gy += 0.5 * v * ca * (lb[km] + lb[k]);
+    const double ex = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
+    const double ey = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
+    double gx = 0.5 * v * (-sa) * (lb[km] + lb[k]);
+    double gy = 0.5 * v * ca * (lb[km] + lb[k]);
     gx += kInvTwoPi * (0.5 * (lb[km] * P[2 * km] + lb[k] * P[2 * k]) + ub[k] * Ac[2 * k] +
                        ub[km] * Bc[2 * km]);
     gy += kInvTwoPi * (0.5 * (lb[km] * P[2 * km + 1] + lb[k] * P[2 * k + 1]) +
                        ub[k] * Ac[2 * k + 1] + ub[km] * Bc[2 * km + 1]);
-    gout[2 * k] = gscale * gx;
-    gout[2 * k + 1] = gscale * gy;
+    gout[2 * k] = se * ex + sl * gx;
+    gout[2 * k + 1] = se * ey + sl * gy;
   }
 }
 
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
     Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,
     const double* __restrict__ alpha, const double* __restrict__ vinf,
     const double* __restrict__ chord, const double* __restrict__ grad_cl,
-    double* __restrict__ grad, const int32_t* __restrict__ info) {
+    double* __restrict__ grad, const int32_t* __restrict__ info, int lam_weighted) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = bt.n_max;
   float4* tlog = reinterpret_cast<float4*>(smraw);        // 257
@@ -363,8 +367,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
                     nodes[2 * i1 + 1]);
   }
   const double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
-  const double gscale = grad_cl ? grad_cl[b] : 1.0;
-  const double w2pi = gscale * kInvTwoPi;
+  // se scales the explicit dCl/dx term, sl the lambda terms (as in k_adjoint_df)
+  const double se = grad_cl ? grad_cl[b] : (lam_weighted ? 0.0 : 1.0);
+  const double sl = lam_weighted ? 1.0 : se;
+  const double w2pi = sl * kInvTwoPi;
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -446,12 +452,12 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
       const double hkx = nodes[2 * k1] - nodes[2 * k], hky = nodes[2 * k1 + 1] - nodes[2 * k + 1];
       const double hmx = nodes[2 * k] - nodes[2 * km], hmy = nodes[2 * k + 1] - nodes[2 * km + 1];
       const double Lk = sqrt(hkx * hkx + hky * hky), Lm = sqrt(hmx * hmx + hmy * hmy);
-      double gx = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
-      double gy = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
-      gx += 0.5 * v * (-sa) * (lb[km] + lb[k]);
-      gy += 0.5 * v * ca * (lb[km] + lb[k]);
-      atomicAdd(&gout[2 * k], gscale * gx);
-      atomicAdd(&gout[2 * k + 1], gscale * gy);
+      const double ex = 2.0 / (v * c) * (ub[km] * hmx / Lm - ub[k] * hkx / Lk);
+      const double ey = 2.0 / (v * c) * (ub[km] * hmy / Lm - ub[k] * hky / Lk);
+      const double bx = 0.5 * v * (-sa) * (lb[km] + lb[k]);
+      const double by = 0.5 * v * ca * (lb[km] + lb[k]);
+      atomicAdd(&gout[2 * k], se * ex + sl * bx);
+      atomicAdd(&gout[2 * k + 1], se * ey + sl * by);
     }
   }
 }
@@ -467,20 +473,21 @@ size_t adjoint_df_smem(int n_max) {
 cudaError_t launch_adjoint_df(const Batch& bt, const double* u, const double* lambda,
                               const double* alpha, const double* vinf, const double* chord,
                               const double* grad_cl, double* grad, const int32_t* info,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool lam_weighted) {
   const size_t smem = adjoint_df_smem(bt.n_max);
   cudaError_t e;
   if (bt.n_max <= kPartialsN) {
     e = ensure_smem(k_adjoint_df, smem);
     if (e != cudaSuccess) return e;
-    k_adjoint_df<<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad, info);
+    k_adjoint_df<<<bt.B, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad, info,
+                                         lam_weighted ? 1 : 0);
   } else {
     e = ensure_smem(k_adjoint_df_split, smem);
     if (e != cudaSuccess) return e;
     k_adjoint_prepare<<<bt.B, 256, 0, s>>>(bt, grad, info);
     const dim3 grid(bt.B, (bt.n_max + kSplitChunk - 1) / kSplitChunk);
     k_adjoint_df_split<<<grid, 256, smem, s>>>(bt, u, lambda, alpha, vinf, chord, grad_cl, grad,
-                                               info);
+                                               info, lam_weighted ? 1 : 0);
   }
   return cudaGetLastError();
 }

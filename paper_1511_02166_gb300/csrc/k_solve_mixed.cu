@@ -641,7 +641,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
       if (k < n) {
         const int k1 = (k + 1 == n) ? 0 : k + 1;
         const double hx = nd[2 * k1] - nd[2 * k], hy = nd[2 * k1 + 1] - nd[2 * k + 1];
-        g = 2.0 * sqrt(hx * hx + hy * hy) / (v * cc);
+        g = 2.0 * sqrt(hx * hx + hy * hy) / (v * cc);  // dCl/dgamma_k
+      }
+      if (a.vjp) {
+        // dL/du for L = w_cl Cl + w_u . u + w_cp . Cp, Cp_k = 1 - (gamma_k / v)^2
+        g *= a.w_cl ? a.w_cl[b] : 0.0;
+        if (a.w_u) g += a.w_u[vec_off(bt, b) + k];
+        if (a.w_cp && k < n)
+          g += a.w_cp[bt.node_off[b] + k] * (-2.0 * a.u_in[vec_off(bt, b) + k] / (v * v));
       }
       sys[1].bb[k] = g;
     }
@@ -770,6 +777,8 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.inverse = 0;
   a.n_cap = bt.n_max;
   a.rhs_kind = 0;
+  a.vjp = 0;
+  a.w_cl = a.w_u = a.w_cp = a.u_in = nullptr;
   return a;
 }
 
@@ -797,6 +806,34 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
     if (e != cudaSuccess) return e;
   }
   return launch_gj_mixed(a, s);
+}
+
+// lambda of a vector-Jacobian product: M^T lambda = w_cl dCl/du + w_u +
+// w_cp dCp/du (refined), with the forward strengths u.
+cudaError_t launch_ir_vjp(const Batch& bt, const float* A_hi, const float* A_lo,
+                          const float* LU, const int32_t* piv, const double* vinf,
+                          const double* chord, const double* u, const double* w_cl,
+                          const double* w_u, const double* w_cp, double* lam, int max_iter,
+                          double tol, int32_t* info, cudaStream_t s) {
+  SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
+                          nullptr, vinf, chord, nullptr, lam, max_iter, tol, info, nullptr);
+  a.vjp = 1;
+  a.w_cl = w_cl;
+  a.w_u = w_u;
+  a.w_cp = w_cp;
+  a.u_in = u;
+  const size_t smem = ir_mixed_smem(bt.n_max);
+  cudaError_t e;
+  if (bt.n_max + 1 <= kFuseM) {
+    e = ensure_smem(k_ir_mixed<4>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<4><<<bt.B, kThreads, smem, s>>>(a);
+  } else {
+    e = ensure_smem(k_ir_mixed<3>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<3><<<bt.B, kThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
 }
 
 // Refine the forward (u) and/or transposed (lam) systems with the stored factor.

@@ -231,6 +231,26 @@ class PanelBatch:
                            self.max_iter, self.tol, self.info, self.iters)
         return cl
 
+    def vjp(self, w_cl=None, w_u=None, w_cp=None):
+        """Gradient w.r.t. the nodes of sum w_cl Cl + w_u . u + w_cp . Cp (w_cl [B],
+        w_u [sum m] packed like self.u = (gamma, C) per airfoil, w_cp [sum n]
+        packed like the nodes; None = 0), after run() of the mixed path; returns
+        self.grad [sum n][2]."""
+        if self.flags != bd.PANEL_MIXED:
+            raise ValueError("vector-Jacobian products need the mixed-precision path")
+
+        def dev(w):
+            return None if w is None else torch.as_tensor(
+                w, dtype=torch.float64, device=self.device).contiguous()
+        wc, wg, wp = dev(w_cl), dev(w_u), dev(w_cp)
+        for start, cnt, nmax in self.buckets:
+            bd.panel_vjp(cnt, nmax, self.flags, self.nodes, self.node_offsets, self.mat_offsets,
+                         self.order[start:], self.A_hi, self.A_lo, self.LU, self.piv, self.u,
+                         self.alpha, self.vinf, self.chord, wc, wg, wp, self.lam, self.grad,
+                         self.max_iter, self.tol, self.info)
+        self.have_lambda = False  # lambda now belongs to this product
+        return self.grad
+
     def run(self, with_grad: bool = False):
         """Assemble, solve, forces (and the adjoint for unit upstream gradient)."""
         self.assemble()
@@ -354,6 +374,31 @@ class PanelBatch:
 
     def gamma(self, b):
         return self.vec(self.u, b)[:-1]
+
+
+class PanelSolve(torch.autograd.Function):
+    """Strengths, Cp and Cl of every airfoil of a batch as differentiable
+    functions of the nodes (mixed path).
+
+    forward(nodes [sum n][2] f64 cuda, offsets (host int64 [B+1]), alpha [B])
+    -> (u [sum (n+1)] = (gamma, C) per airfoil, packed at offsets[b] + b;
+        cp [sum n]; cl [B]).  backward is one panel_vjp: a transposed solve with
+    the stored factor for dL/du assembled from all three upstream gradients,
+    then the dM/dx contraction.
+    """
+
+    @staticmethod
+    def forward(ctx, nodes, offsets, alpha):
+        pb = PanelBatch(nodes.detach(), offsets, alpha.detach(), mode="mixed",
+                        device=nodes.device)
+        pb.run(with_grad=False)
+        ctx.pb = pb
+        return pb.u.clone(), pb.cp.clone(), pb.cl.clone()
+
+    @staticmethod
+    def backward(ctx, g_u, g_cp, g_cl):
+        grad = ctx.pb.vjp(w_cl=g_cl, w_u=g_u, w_cp=g_cp)
+        return grad.clone(), None, None
 
 
 class PanelCl(torch.autograd.Function):

@@ -509,17 +509,17 @@ def test_gradient_matches_central_differences():
 
 
 def test_vjp_matches_central_differences():
-    # L = w_cl Cl + w_gamma . gamma + w_cp . Cp with random weights: the tangent
+    # L = w_cl Cl + w_u . (gamma, C) + w_cp . Cp with random weights: the tangent
     # product against central differences of L from full re-evaluations
     nodes = inputs.naca4(0.02, 0.35, 0.13, 20)
     al = math.radians(4.0)
     rng = np.random.default_rng(5)
     n = len(nodes)
-    w_cl, w_g, w_cp = 0.7, rng.normal(size=n), rng.normal(size=n)
+    w_cl, w_g, w_cp = 0.7, rng.normal(size=n + 1), rng.normal(size=n)
 
     def L(x):
         r = oracle.evaluate(x, al)
-        return w_cl * r["cl"] + w_g @ r["gamma"] + w_cp @ r["cp"]
+        return w_cl * r["cl"] + w_g @ r["u"] + w_cp @ r["cp"]
 
     g, info = oracle.vjp(nodes, al, w_cl, w_g, w_cp)
     assert info == 0
