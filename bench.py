@@ -380,6 +380,38 @@ def run_ours(args):
         vjp = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
                "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
 
+    # ---- genetic optimisation: sample -> evaluate -> select/crossover/mutate on the device ----
+    ga = None
+    if args.mode == "mixed" and args.ga > 0:
+        from paper_1511_02166_gb300.ga import GeneticOptimizer
+        n_ga = int(np.clip(int(pop.sizes.max()), 16, 1024))
+        opt = GeneticOptimizer(B=B - (B % 2), n=n_ga, alpha=math.radians(4.0), seed=1511 + rank,
+                               device=dev)
+        opt.evaluate()  # nodes of the first population, then pick each bucket's factorisation
+        if args.autotune:
+            opt.pb.autotune()
+        for _ in range(args.warmup):
+            opt.evaluate()
+            opt.step()
+        torch.cuda.synchronize()
+        gms = []
+        for _ in range(int(args.ga)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            opt.evaluate()  # panel_ga_sample + assemble + solve + forces
+            opt.step()      # uniforms + panel_ga_step
+            e1.record(stream)
+            e1.synchronize()
+            gms.append(e0.elapsed_time(e1))
+        gm = float(np.mean(gms))
+        best = float(torch.nan_to_num(opt.evaluate(), nan=-np.inf).max())
+        ga = {"population": opt.B, "nodes": n_ga, "control_points": opt.P, "generations": len(gms),
+              "ms_per_generation": gm, "generations_per_s": 1e3 / gm,
+              "airfoils_per_s": world * opt.B / (gm * 1e-3), "best_cl": best,
+              "what": "panel_ga_sample + assemble + solve + forces + panel_ga_step per generation"}
+
     # ---- roofline of the dominant kernel ----
     kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
     sizes = pop.sizes.astype(np.float64)
@@ -439,6 +471,7 @@ def run_ours(args):
            "gradients_per_s": value,
            "polar": polar,
            "vjp": vjp,
+           "ga": ga,
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
@@ -474,6 +507,9 @@ def main():
                          "(0: skip)")
     ap.add_argument("--no-vjp", dest="vjp", action="store_false",
                     help="skip timing the vector-Jacobian product of (Cl, u, Cp)")
+    ap.add_argument("--ga", type=int, default=5,
+                    help="also time this many generations of the device genetic optimiser on a "
+                         "population of the configured batch (0: skip)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the calls one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

@@ -240,6 +240,37 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
               int max_iter, double tol, int32_t* info, void* stream);
 
 /*
+ * Genetic algorithm around the evaluator (the genetic optimisation of
+ * Section 2; the paper leaves the spline, the sampling, k, p and the mutation
+ * unspecified -- the choices below are this library's).
+ *
+ * panel_ga_sample -- nodes of B airfoils from their B-spline genomes.
+ *   The airfoil is a clamped uniform cubic B-spline over P >= 4 control points
+ *   with x coordinates ctrl_x [P] shared by the population (trailing edge,
+ *   upper surface, leading edge, lower surface, trailing edge) and y
+ *   coordinates genome [B][P].  Node i of n is the curve at
+ *   t_i = (1 - cos(pi i / n_u)) / 4 for i <= n_u = ceil(n/2), else
+ *   1/2 + (1 - cos(pi (i - n_u) / (n - n_u))) / 4.  nodes [B*n][2] f64 output
+ *   (airfoil b at rows b n .. b n + n - 1, the layout panel_plan expects with
+ *   node_offsets[b] = b n).
+ *
+ * panel_ga_step -- one generation: genome_out [B][P] from genome_in [B][P]
+ *   and fitness [B] (higher is better, NaN never preferred), B even, by
+ *   B/2 x (two tournaments of size k <= 16 accepting the j-th ranked
+ *   candidate with probability p (1-p)^j, one-point crossover into two
+ *   children, per child a mutation with probability pm of one gene by
+ *   sigma_g (2u - 1), clamped to [lo_g, hi_g]).  Every random number is an
+ *   input: rand [B/2][4k + 5] uniform in [0, 1), per pair: k candidate draws
+ *   and k - 1 acceptance draws per tournament, the crossover point, then per
+ *   child the mutation decision, gene and amount.  lo, hi, sigma [P].
+ */
+int panel_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
+                    double* nodes, void* stream);
+int panel_ga_step(int B, int P, int k, double p, double pm, const double* lo, const double* hi,
+                  const double* sigma, const double* genome_in, const double* fitness,
+                  const double* rand, double* genome_out, void* stream);
+
+/*
  * panel_df_eval -- diagnostic: evaluate the double-float primitives of the
  * PANEL_MIXED assembly on `count` device inputs (results rounded to f64):
  *   op 0: out[k] = log(a[k])                      (a[k] > 0)

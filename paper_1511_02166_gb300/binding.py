@@ -53,6 +53,8 @@ SIGNATURES = {
                          _P, _I, _D, _P, _P, _P]),
     "panel_vjp": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                        _P, _P, _I, _D, _P, _P]),
+    "panel_ga_sample": (_I, [_I, _I, _I, _P, _P, _P, _P]),
+    "panel_ga_step": (_I, [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
@@ -172,6 +174,18 @@ def panel_vjp(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, A_
                             _ptr(alpha), _ptr(vinf), _ptr(chord), _ptr(w_cl), _ptr(w_u),
                             _ptr(w_cp), _ptr(lam), _ptr(grad_nodes), int(max_iter), float(tol),
                             _ptr(info), _stream(stream)), "panel_vjp")
+
+
+def panel_ga_sample(B, P, n, ctrl_x, genome, nodes, stream=None):
+    _check(load().panel_ga_sample(int(B), int(P), int(n), _ptr(ctrl_x), _ptr(genome),
+                                  _ptr(nodes), _stream(stream)), "panel_ga_sample")
+
+
+def panel_ga_step(B, P, k, p, pm, lo, hi, sigma, genome_in, fitness, rand, genome_out,
+                  stream=None):
+    _check(load().panel_ga_step(int(B), int(P), int(k), float(p), float(pm), _ptr(lo), _ptr(hi),
+                                _ptr(sigma), _ptr(genome_in), _ptr(fitness), _ptr(rand),
+                                _ptr(genome_out), _stream(stream)), "panel_ga_step")
 
 
 def panel_df_eval(op, count, a, b, out, stream=None):

@@ -29,6 +29,11 @@ cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const floa
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t,
                             int rhs_kind = 0);
+cudaError_t launch_ga_sample(int, int, int, const double*, const double*, double*, cudaStream_t);
+cudaError_t launch_ga_step(int, int, int, double, double, const double*, const double*,
+                           const double*, const double*, const double*, const double*, double*,
+                           cudaStream_t);
+int ga_max_tournament();
 cudaError_t launch_polar_cl(const Batch&, const double*, const double*, const double*,
                             const double*, int, const double*, const int32_t*, double*,
                             cudaStream_t);
@@ -212,6 +217,28 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
   if (panel::adjoint_df_smem(n_max) > panel::kMaxDynSmem) return PANEL_ENOTSUP;
   return status_of(panel::launch_adjoint_df(bt, u, lambda, alpha, vinf, chord, w_cl,
                                             grad_nodes, info, s, true));
+}
+
+int panel_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
+                    double* nodes, void* stream) {
+  if (B < 0 || P < 4 || n < 3 || n > PANEL_N_MAX) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!ctrl_x || !genome || !nodes) return PANEL_EINVAL;
+  return status_of(panel::launch_ga_sample(B, P, n, ctrl_x, genome, nodes, (cudaStream_t)stream));
+}
+
+int panel_ga_step(int B, int P, int k, double p, double pm, const double* lo, const double* hi,
+                  const double* sigma, const double* genome_in, const double* fitness,
+                  const double* rand, double* genome_out, void* stream) {
+  if (B < 0 || (B & 1) || P < 2 || k < 1 || k > panel::ga_max_tournament() || !(p >= 0.0) ||
+      !(p <= 1.0) || !(pm >= 0.0) || !(pm <= 1.0))
+    return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!lo || !hi || !sigma || !genome_in || !fitness || !rand || !genome_out ||
+      genome_in == genome_out)
+    return PANEL_EINVAL;
+  return status_of(panel::launch_ga_step(B, P, k, p, pm, lo, hi, sigma, genome_in, fitness, rand,
+                                         genome_out, (cudaStream_t)stream));
 }
 
 int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const double* u,

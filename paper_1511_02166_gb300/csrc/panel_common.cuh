@@ -16,6 +16,7 @@
 
 namespace panel {
 
+constexpr double kPiF64 = 3.1415926535897932384626433832795;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
 // Node coordinates must be finite and below this magnitude (the split of
