@@ -120,16 +120,44 @@ class ClockSampler:
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
 
-def kernel_source_digest() -> str:
-    """sha256 over the CUDA sources (csrc/*.cu, *.cuh): a DRAM-traffic figure
-    recorded with another digest was taken on different kernels."""
+CALL_SOURCES = {
+    "mixed": {"assemble": ["k_assemble_df.cu"],
+              "factor": ["k_solve_mixed.cu", "k_gj_mixed.cu", "k_lu_large.cu", "k_update_tc.cu"],
+              "refine": ["k_solve_mixed.cu"],
+              "forces": ["k_forces.cu"],
+              "adjoint": ["k_adjoint_df.cu"]},
+    "fp64": {"assemble": ["k_assemble_f64.cu"], "solve": ["k_solve_f64.cu"],
+             "forces": ["k_forces.cu"], "adjoint": ["k_solve_f64.cu"]},
+}
+
+
+def kernel_source_digest(call=None, mode="mixed") -> str:
+    """sha256 over the CUDA sources of the kernels one library call launches
+    (the .cu files and the csrc headers they include, transitively), or over
+    every source when `call` is None: a DRAM-traffic figure recorded with
+    another digest was taken on different kernels."""
     import hashlib
     import glob
-    h = hashlib.sha256()
+    import re
     csrc = os.path.join(ROOT, "paper_1511_02166_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    if call is None:
+        files = sorted(os.path.basename(f) for f in
+                       glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    else:
+        todo, seen = list(CALL_SOURCES[mode][call]), set()
+        while todo:
+            f = todo.pop()
+            if f in seen:
+                continue
+            seen.add(f)
+            with open(os.path.join(csrc, f)) as fh:
+                for inc in re.findall(r'^#include "([^"/]+)"', fh.read(), flags=re.M):
+                    todo.append(inc)
+        files = sorted(seen)
+    h = hashlib.sha256()
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -446,7 +474,7 @@ def run_ours(args):
                        "unit": unit, "frac": ach / peak}
     dom = max(kms, key=kms.get)
     dk = kernels[dom]
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(dom, args.mode)
     traffic = recorded_traffic(dom, args.config, args.mode, B, digest)
     roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"],
                 "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"],
