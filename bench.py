@@ -43,11 +43,15 @@ L2_BYTES = 135528448
 #    once per system) + 16 per refinement step (both planes once, the factor
 #    once per system);
 #  * adjoint contraction: one pair = ADJOINT_FLOP_PER_PAIR FP32 flops;
+#  * viscous correction: VISCOUS_BYTES_PER_NODE per node;
 #  * plain FP64 path: FP64 flops of the same formulas (ASSEMBLY_F64_FLOP_PER_PAIR,
 #    2/3 m^3 for the LU, ADJOINT_F64_FLOP_PER_PAIR).
 ASSEMBLY_FLOP_PER_PAIR = 350
 ADJOINT_FLOP_PER_PAIR = 480
 ASSEMBLY_F64_FLOP_PER_PAIR = 90
+# viscous correction: per node the node (16 B) and its strength (8 B) read, theta
+# and cf (16 B) written
+VISCOUS_BYTES_PER_NODE = 40
 ADJOINT_F64_FLOP_PER_PAIR = 110
 # FP32 peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -408,6 +412,32 @@ def run_ours(args):
         vjp = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
                "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
 
+    # ---- viscous correction (Thwaites boundary layer, drag, L/D) on the solved population ----
+    viscous = None
+    if args.mode == "mixed" and args.viscous:
+        pb.run()
+        pb.viscous(1.0e6)
+        torch.cuda.synchronize()
+        vis = []
+        for it in range(args.warmup + max(2, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pb.viscous()
+            e1.record(stream)
+            e1.synchronize()
+            if it >= args.warmup:
+                vis.append(e0.elapsed_time(e1))
+        vm_ = float(np.mean(vis))
+        vbytes = float(pop.sizes.sum()) * VISCOUS_BYTES_PER_NODE
+        sep = pb.sep.cpu().numpy()
+        viscous = {"ms": vm_, "airfoils_per_s": world * B / (vm_ * 1e-3),
+                   "reynolds": 1.0e6, "bound": "hbm", "achieved_gbs": vbytes / (vm_ * 1e-3) / 1e9,
+                   "attached_surfaces": float((sep == -1).mean()),
+                   "what": "panel_viscous: Thwaites march, separation, Squire-Young and friction "
+                           "drag, L/D per airfoil, after a solve"}
+
     # ---- genetic optimisation: sample -> evaluate -> select/crossover/mutate on the device ----
     ga = None
     if args.mode == "mixed" and args.ga > 0:
@@ -500,6 +530,7 @@ def run_ours(args):
            "polar": polar,
            "vjp": vjp,
            "ga": ga,
+           "viscous": viscous,
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
@@ -535,6 +566,8 @@ def main():
                          "(0: skip)")
     ap.add_argument("--no-vjp", dest="vjp", action="store_false",
                     help="skip timing the vector-Jacobian product of (Cl, u, Cp)")
+    ap.add_argument("--no-viscous", dest="viscous", action="store_false",
+                    help="skip timing the viscous correction (boundary layer and drag)")
     ap.add_argument("--ga", type=int, default=5,
                     help="also time this many generations of the device genetic optimiser on a "
                          "population of the configured batch (0: skip)")

@@ -15,6 +15,9 @@
  *                   mixed-precision mode;
  *   panel_forces    Cp at the control points and the lift coefficient
  *                   (Section 2, Figure 2 report C_L);
+ *   panel_viscous   Thwaites's boundary layer on the surface speed: momentum
+ *                   thickness, skin friction, separation and the drag
+ *                   (Section 2's viscous correction);
  *   panel_adjoint   dCl/d(node coordinates) by a transposed solve with the
  *                   stored LU and a contraction with dM/dx (the method has no
  *                   gradient in the paper; the formulas are the chain rule of
@@ -173,6 +176,40 @@ int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const 
                  const double* alpha, const double* vinf, const double* chord,
                  const int32_t* info, double* cp, double* cl, double* cl_p, double* cd_p,
                  void* stream);
+
+/*
+ * panel_viscous -- the viscous correction of Section 2 (Thwaites's laminar
+ * boundary-layer method on the inviscid surface speed; the paper names the
+ * method for the drag and prints no formulas, the textbook ones are used):
+ *   U_j = |gamma_j| / v_inf at the control points; the stagnation point lies
+ *   between control points j and j+1 for the first j with gamma_j > 0 >=
+ *   gamma_{j+1} (linear zero of gamma); the upper surface runs through control
+ *   points j..0, the lower through j+1..n-1, each to the trailing edge;
+ *   theta^2 U^6 = (0.45 / Re) int U^5 ds (U piecewise linear, lengths in chords),
+ *   lambda = Re theta^2 dU/ds, Thwaites's shear and shape functions l, H
+ *   (Cebeci-Bradshaw fits, lambda clamped to [-0.09, 0.1]); laminar separation
+ *   at the first control point with lambda < -0.09, past which the wall shear
+ *   is zero and H keeps its separation value while theta follows the integral.
+ *   u [sum m_b] f64 from panel_solve; alpha [B] f64; vinf, chord [B] f64 or NULL
+ *   (1.0); reynolds [B] f64, Re = v_inf c / nu.
+ *   Outputs: cd [B] f64 profile drag by Squire and Young,
+ *   sum over both surfaces of 2 theta U^((H + 5) / 2) at the trailing edge;
+ *   cd_f [B] f64 or NULL, skin-friction drag (cf = 2 l U / (Re theta)
+ *   integrated along the freestream direction); theta [sum n_b] f64 or NULL,
+ *   momentum thickness / c at the control points; cf [sum n_b] f64 or NULL,
+ *   skin-friction coefficient at the control points; sep [B][2] i32 or NULL,
+ *   the separating control point of the upper and lower surface (-1: attached
+ *   to the trailing edge); ld [B] f64 or NULL, the lift-to-drag ratio
+ *   cl[b] / cd[b] (cl [B] f64 from panel_forces, required with ld; the fitness
+ *   of Section 3's optimisation).  Airfoils with info[b] != 0, no stagnation
+ *   point, or Re not positive and finite get NaN outputs and sep = -2.  FP64;
+ *   one warp per surface (prefix sums for the integral).
+ */
+int panel_viscous(int B, const double* nodes, const int64_t* node_offsets, const double* u,
+                  const double* alpha, const double* vinf, const double* chord,
+                  const double* reynolds, const int32_t* info, const double* cl, double* ld,
+                  double* cd, double* cd_f, double* theta, double* cf, int32_t* sep,
+                  void* stream);
 
 /*
  * panel_adjoint -- grad_nodes = grad_cl[b] * dCl/d(nodes of airfoil b).

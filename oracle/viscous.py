@@ -27,14 +27,18 @@ choice it leaves open is a reading of this library:
     point's lambda;
   * the Cebeci-Bradshaw fits of Thwaites's shear and shape functions l(lambda),
     H(lambda), with lambda clamped to [-0.09, 0.1];
-  * laminar separation at the first point with lambda < -0.09 (or U = 0):
-    the surface ends there;
+  * laminar separation at the first control point with lambda < -0.09 (or
+    U = 0); from there to the trailing edge the wall shear is zero and the
+    shape factor keeps its separation value H(-0.09), while theta follows the
+    same integral (an early separation, with the speed falling behind it,
+    raises theta at the trailing edge);
   * skin friction cf = 2 l U / (Re theta) (per 1/2 rho v_inf^2), friction drag
     Cd_f = sum over both surfaces of the integral of cf along the freestream
     direction (trapezoid between consecutive points);
-  * profile drag by Squire and Young, Cd = sum over both surfaces of
-    2 theta_e U_e^((H_e + 5) / 2) at the surface's end point e (trailing edge or
-    separation).
+  * profile drag by Squire and Young at the trailing edge, Cd = sum over both
+    surfaces of 2 theta_TE U_TE^((H_TE + 5) / 2).  It falls with the inviscid
+    trailing-edge speed, which tends to zero at a blunt trailing edge: shapes
+    are meant to keep a small trailing-edge angle.
 """
 from __future__ import annotations
 
@@ -126,7 +130,7 @@ def _surfaces(n, xy, q):
 def viscous_airfoil(xy, gamma, alpha, Re, vinf=1.0, chord=1.0):
     """One airfoil: xy [n][2] nodes (counter-clockwise, x_0 at the trailing
     edge), gamma [n] panel strengths.  Returns dict(cd, cd_f, theta [n],
-    cf [n], sep (upper, lower))."""
+    cf [n], sep (upper, lower): the separating control point, -1 if attached)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     out = dict(cd=math.nan, cd_f=math.nan, theta=np.full(n, math.nan), cf=np.full(n, math.nan),
@@ -177,18 +181,19 @@ def viscous_airfoil(xy, gamma, alpha, Re, vinf=1.0, chord=1.0):
         U[K + 1] = U[K]
         P[K + 1] = te
         theta, lam, e = march(h, U, Re)
+        separated = e <= K
         cf = np.zeros(K + 2)
-        for k in range(1, e + 1):
-            l, _ = shear_shape(lam[k])
-            cf[k] = 2.0 * l * U[k] / (Re * theta[k])
-        for k in range(1, e + 1):
+        for k in range(1, K + 2):
+            if not (separated and k >= e):
+                l, _ = shear_shape(lam[k])
+                cf[k] = 2.0 * l * U[k] / (Re * theta[k])
+        for k in range(1, K + 2):
             cd_f += 0.5 * (cf[k - 1] + cf[k]) * float(np.dot(P[k] - P[k - 1], ehat))
-        _, He = shear_shape(lam[e])
-        cd += 2.0 * theta[e] * U[e] ** ((He + 5.0) / 2.0)
+        _, He = shear_shape(LAMBDA_SEP if separated else lam[K + 1])
+        cd += 2.0 * theta[K + 1] * U[K + 1] ** ((He + 5.0) / 2.0)
         for k, c in enumerate(cps, start=1):
-            if k <= e:
-                out["theta"][c] = theta[k]
-                out["cf"][c] = cf[k]
+            out["theta"][c] = theta[k]
+            out["cf"][c] = cf[k]
         if side == "lower" and q[j + 1] == 0.0:
             out["theta"][j + 1] = theta[0]
             out["cf"][j + 1] = 0.0

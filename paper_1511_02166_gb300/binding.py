@@ -47,6 +47,8 @@ SIGNATURES = {
     "panel_solve": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                          _I, _D, _P, _P, _P]),
     "panel_forces": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "panel_viscous": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                           _P]),
     "panel_adjoint": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                            _P, _P, _P, _I, _D, _P, _P]),
     "panel_polar": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P,
@@ -155,6 +157,15 @@ def panel_adjoint(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64,
                                 _ptr(lambda_out), _ptr(alpha), _ptr(vinf), _ptr(chord),
                                 _ptr(grad_cl), _ptr(grad_nodes), int(max_iter), float(tol),
                                 _ptr(info), _stream(stream)), "panel_adjoint")
+
+
+def panel_viscous(B, nodes, node_offsets, u, alpha, vinf, chord, reynolds, info, cl, ld, cd,
+                  cd_f=None, theta=None, cf=None, sep=None, stream=None):
+    _check(load().panel_viscous(B, _ptr(nodes), _ptr(node_offsets), _ptr(u), _ptr(alpha),
+                                _ptr(vinf), _ptr(chord), _ptr(reynolds), _ptr(info), _ptr(cl),
+                                _ptr(ld), _ptr(cd), _ptr(cd_f), _ptr(theta), _ptr(cf), _ptr(sep),
+                                _stream(stream)),
+           "panel_viscous")
 
 
 def panel_polar(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, A_lo, LU, piv,

@@ -38,6 +38,9 @@ cudaError_t launch_polar_cl(const Batch&, const double*, const double*, const do
                             const double*, int, const double*, const int32_t*, double*,
                             cudaStream_t);
 cudaError_t launch_df_eval(int, int, const double*, const double*, double*, cudaStream_t);
+cudaError_t launch_viscous(const Batch&, const double*, const double*, const double*,
+                           const double*, const double*, const int32_t*, const double*, double*,
+                           double*, double*, double*, double*, int32_t*, cudaStream_t);
 size_t adjoint_df_smem(int n_max);
 constexpr size_t kMaxDynSmem = 232448;
 cudaError_t launch_adjoint_df(const Batch&, const double*, const double*, const double*,
@@ -251,6 +254,20 @@ int panel_forces(int B, const double* nodes, const int64_t* node_offsets, const 
   Batch bt = make_batch(B, 0, nodes, node_offsets, nullptr, nullptr);
   return status_of(panel::launch_forces(bt, u, alpha, vinf, chord, info, cp, cl, cl_p, cd_p,
                                         (cudaStream_t)stream));
+}
+
+int panel_viscous(int B, const double* nodes, const int64_t* node_offsets, const double* u,
+                  const double* alpha, const double* vinf, const double* chord,
+                  const double* reynolds, const int32_t* info, const double* cl, double* ld,
+                  double* cd, double* cd_f, double* theta, double* cf, int32_t* sep,
+                  void* stream) {
+  if (B < 0) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!nodes || !node_offsets || !u || !alpha || !reynolds || !cd || (ld && !cl))
+    return PANEL_EINVAL;
+  Batch bt = make_batch(B, 0, nodes, node_offsets, nullptr, nullptr);
+  return status_of(panel::launch_viscous(bt, u, alpha, vinf, chord, reynolds, info, cl, ld, cd,
+                                         cd_f, theta, cf, sep, (cudaStream_t)stream));
 }
 
 int panel_adjoint(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,

@@ -1,9 +1,11 @@
 """Genetic optimisation around the batched evaluator (the genetic optimisation
 of Section 2): a population of B-spline airfoils lives on the device, each
 generation is panel_ga_sample -> the panel method (assemble, solve, forces) ->
-panel_ga_step.  Fitness is the lift coefficient at the population's angle of
-attack (an airfoil the library flags -- invalid geometry, no convergence --
-has fitness NaN and is never preferred).  Random numbers are drawn on the
+panel_ga_step.  Fitness is the lift-to-drag ratio at the population's angle
+of attack and Reynolds number (Section 3's fitness; the drag from the viscous
+correction, panel_viscous), or the lift coefficient alone.  An airfoil the
+library flags -- invalid geometry, no convergence, no stagnation point -- has
+fitness NaN and is never preferred.  Random numbers are drawn on the
 device from a seeded torch generator and passed to the library as inputs."""
 from __future__ import annotations
 
@@ -24,23 +26,35 @@ def default_control_x(half: int = 7) -> np.ndarray:
 
 def default_bounds(ctrl_x: np.ndarray):
     """y bounds per control point: 0 at the two trailing-edge points, an upper
-    band over the first half and a lower band over the second."""
+    band over the first half and a lower band over the second, both narrowing
+    linearly towards the trailing edge (|y| <= 0.25 (1 - x) above, 0.2 (1 - x)
+    below, sign-definite behind x = 0.8).  The narrowing keeps the
+    trailing-edge angle small: the drag of the viscous correction is taken at
+    the trailing edge, where a blunt edge would drive the inviscid speed, and
+    with it the drag estimate, to zero."""
+    ctrl_x = np.asarray(ctrl_x, dtype=np.float64)
     P = len(ctrl_x)
     lo = np.zeros(P)
     hi = np.zeros(P)
     for j in range(1, P - 1):
+        taper = 1.0 - ctrl_x[j]
+        aft = ctrl_x[j] > 0.8
         if j < P // 2:
-            lo[j], hi[j] = 0.005, 0.12
+            lo[j], hi[j] = (0.0 if aft else 0.005), min(0.12, 0.25 * taper)
         else:
-            lo[j], hi[j] = -0.10, 0.02
+            lo[j], hi[j] = max(-0.10, -0.2 * taper), (0.0 if aft else 0.02)
     return lo, hi
 
 
 class GeneticOptimizer:
     def __init__(self, B: int, n: int, alpha: float, ctrl_x=None, lo=None, hi=None, sigma=None,
-                 k: int = 4, p: float = 0.8, pm: float = 0.3, seed: int = 0, device="cuda"):
+                 k: int = 4, p: float = 0.8, pm: float = 0.3, seed: int = 0, device="cuda",
+                 fitness: str = "ld", reynolds: float = 1.0e6):
         if B % 2:
             raise ValueError("the population size must be even")
+        if fitness not in ("ld", "cl"):
+            raise ValueError("fitness is 'ld' (lift over drag) or 'cl'")
+        self.fitness_kind = fitness
         self.device = torch.device(device)
         self.B, self.n = int(B), int(n)
         cx = default_control_x() if ctrl_x is None else np.asarray(ctrl_x, dtype=np.float64)
@@ -63,6 +77,7 @@ class GeneticOptimizer:
         offsets = np.arange(self.B + 1, dtype=np.int64) * self.n
         self.pb = PanelBatch(np.zeros((self.B * self.n, 2)), offsets, np.full(self.B, alpha),
                              mode="mixed", device=self.device)
+        self.pb.reynolds.fill_(float(reynolds))
         self.fitness = None
         self.generation = 0
 
@@ -70,7 +85,11 @@ class GeneticOptimizer:
         bd.panel_ga_sample(self.B, self.P, self.n, self.ctrl_x, self.genome, self.pb.nodes)
         self.pb.info.zero_()
         self.pb.run(with_grad=False)
-        self.fitness = self.pb.cl
+        if self.fitness_kind == "ld":
+            self.pb.viscous()
+            self.fitness = self.pb.ld
+        else:
+            self.fitness = self.pb.cl
         return self.fitness
 
     def draw(self):

@@ -148,6 +148,13 @@ class PanelBatch:
         self.cl_p = torch.empty(self.B, **f64)
         self.cd_p = torch.empty(self.B, **f64)
         self.grad = torch.empty(total, 2, **f64)
+        self.reynolds = torch.full((self.B,), 1.0e6, **f64)
+        self.cd = torch.empty(self.B, **f64)
+        self.cd_f = torch.empty(self.B, **f64)
+        self.ld = torch.empty(self.B, **f64)
+        self.theta = torch.empty(total, **f64)
+        self.cf = torch.empty(total, **f64)
+        self.sep = torch.empty(self.B, 2, **i32)
         self.have_lambda = False
         sizes = np.diff(offsets_h)
         sorted_sizes = sizes[order_h] if self.B else sizes
@@ -187,6 +194,17 @@ class PanelBatch:
     def forces(self):
         bd.panel_forces(self.B, self.nodes, self.node_offsets, self.u, self.alpha, self.vinf,
                         self.chord, self.info, self.cp, self.cl, self.cl_p, self.cd_p)
+
+    def viscous(self, reynolds=None):
+        """Thwaites's boundary layer on the solved surface speed (after forces()):
+        cd (Squire-Young), cd_f (skin friction), ld = cl / cd, theta and cf at the
+        control points, sep (separating control point per surface, -1 attached).
+        `reynolds` (scalar or [B], v_inf c / nu) replaces the stored values."""
+        if reynolds is not None:
+            self.reynolds.copy_(torch.as_tensor(reynolds, dtype=torch.float64).expand(self.B))
+        bd.panel_viscous(self.B, self.nodes, self.node_offsets, self.u, self.alpha, self.vinf,
+                         self.chord, self.reynolds, self.info, self.cl, self.ld, self.cd,
+                         self.cd_f, self.theta, self.cf, self.sep)
 
     def _adjoint_bucket(self, start, cnt, nmax, gc, have_lambda, stream=None):
         bd.panel_adjoint(cnt, nmax, self.flags, self.nodes, self.node_offsets,

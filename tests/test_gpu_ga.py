@@ -53,20 +53,29 @@ def test_step_bit_exact(k, p, pm):
     assert np.array_equal(out.cpu().numpy(), ref)
 
 
-def test_device_generation_matches_oracle():
+@pytest.mark.parametrize("fitness", ["cl", "ld"])
+def test_device_generation_matches_oracle(fitness):
     need_gpu()
     import torch
+    from oracle import viscous as ov
     from paper_1511_02166_gb300.ga import GeneticOptimizer
-    opt = GeneticOptimizer(B=16, n=120, alpha=np.radians(2.0), seed=7)
+    alpha, Re = np.radians(2.0), 1.0e6
+    opt = GeneticOptimizer(B=16, n=120, alpha=alpha, seed=7, fitness=fitness, reynolds=Re)
     fit0 = opt.evaluate().cpu().numpy().copy()
     g0 = opt.genome.cpu().numpy().copy()
     cx = opt.ctrl_x.cpu().numpy()
     nodes = oga.sample(cx, g0, opt.n)
     offs = np.arange(opt.B + 1, dtype=np.int64) * opt.n
-    ref = oracle.evaluate_batch(nodes, offs, np.full(opt.B, np.radians(2.0)))
-    ok = ref["info"] == 0
+    al = np.full(opt.B, alpha)
+    ref = oracle.evaluate_batch(nodes, offs, al)
+    want = ref["cl"].copy()
+    if fitness == "ld":
+        want = want / ov.viscous_batch(nodes, offs, ref["u"], al, Re, info=ref["info"])["cd"]
+    want[ref["info"] != 0] = np.nan
+    ok = np.isfinite(want)
+    assert ok.sum() >= opt.B // 2
     assert np.array_equal(ok, np.isfinite(fit0))
-    assert np.max(np.abs(fit0[ok] - ref["cl"][ok]) / np.maximum(np.abs(ref["cl"][ok]), 1)) < 1e-10
+    assert np.max(np.abs(fit0[ok] - want[ok]) / np.maximum(np.abs(want[ok]), 1)) < 1e-9
     rand = opt.step()
     nxt = oga.step(g0, fit0, rand.cpu().numpy(), opt.k, opt.p, opt.pm, opt.lo.cpu().numpy(),
                    opt.hi.cpu().numpy(), opt.sigma.cpu().numpy())
