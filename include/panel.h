@@ -289,7 +289,7 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
  *   t_i = (1 - cos(pi i / n_u)) / 4 for i <= n_u = ceil(n/2), else
  *   1/2 + (1 - cos(pi (i - n_u) / (n - n_u))) / 4.  nodes [B*n][2] f64 output
  *   (airfoil b at rows b n .. b n + n - 1, the layout panel_plan expects with
- *   node_offsets[b] = b n).
+ *   node_offsets[b] = b n).  B <= 65535 * 64.
  *
  * panel_ga_step -- one generation: genome_out [B][P] from genome_in [B][P]
  *   and fitness [B] (higher is better, NaN never preferred), B even, by

@@ -224,7 +224,7 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
 
 int panel_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
                     double* nodes, void* stream) {
-  if (B < 0 || P < 4 || n < 3 || n > PANEL_N_MAX) return PANEL_EINVAL;
+  if (B < 0 || B > 65535 * 64 || P < 4 || n < 3 || n > PANEL_N_MAX) return PANEL_EINVAL;
   if (B == 0) return PANEL_OK;
   if (!ctrl_x || !genome || !nodes) return PANEL_EINVAL;
   return status_of(panel::launch_ga_sample(B, P, n, ctrl_x, genome, nodes, (cudaStream_t)stream));

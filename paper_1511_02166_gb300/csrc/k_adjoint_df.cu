@@ -14,7 +14,9 @@
 //  H = log P - sum_n u^n / (2n (2n+1)):
 //     2pi dG/dp     = L conj(F1(u) / P),    F1(u) = 1 + u/3 + u^2/5 + ... = atanh(w)/w,
 //     2pi dG/dDelta = t (log|P| + Re(log(1 - u))/2 + i Im F1(u)),
-//     dG/db = -dG/dp / 2 + dG/dDelta.
+//     dG/db = -dG/dp / 2 + dG/dDelta;
+//  u and the first-order terms in double-float, the terms of second and higher
+//  order in u (below 5e-5 of the leading one) in float32.
 //  near field (panel frame: xi = (p-a).t, eta = (p-a).n, l1 = log|p-a|^2,
 //  l2 = log|p-b|^2, theta the subtended angle):
 //     2pi dG/dp = (l1 - l2)/2 t + theta n,
@@ -22,8 +24,9 @@
 //  On the own panel theta (+-pi) cancels between the terms and is set to 0.
 //
 // Layout: one block per airfoil; each warp owns 32 consecutive columns (panels
-// i, one per lane) and sweeps all rows j: A_i, B_i accumulate in the lane's
-// registers (double-float), the row sums P_j are warp-reduced and kept as one
+// i, one per lane) and sweeps all rows j: S_i = sum_j lambda_j dG_ji/dp and B_i
+// accumulate in the lane's registers (double-float; A_i = -S_i - B_i by
+// translation invariance), the row sums P_j are warp-reduced and kept as one
 // double-float partial per warp in shared memory, summed at the end
 // (n <= kPartialsN).  Larger airfoils take k_adjoint_df_split: the panels are
 // cut into chunks of 256, one block per (airfoil, chunk), and every term of the
@@ -33,16 +36,6 @@
 #include "panel_df.cuh"
 
 namespace panel {
-
-struct cdf {
-  df2 re, im;
-};
-__device__ __forceinline__ cdf cmul(const cdf& a, const cdf& b) {
-  cdf r;
-  r.re = df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im));
-  r.im = df_add(df_mul(a.re, b.im), df_mul(a.im, b.re));
-  return r;
-}
 
 // 2pi dG/dp and 2pi dG/db for the pair (p; panel i).
 __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __restrict__ s, int ld,
@@ -66,47 +59,39 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
     const df2 c2 = pf(s, ld, kC2, i), s2 = pf(s, ld, kS2, i);
     const df2 inv = df_rcp(rho2);
     const df2 q = df_mul(df_mul_f(pf(s, ld, kQ6, i), 6.0f), inv);  // L^2 / (4 |P|^2)
-    // u = q (cos 2phi + i sin(2beta - 2phi)...) = q (Z + i W) / |P|^2
-    cdf u;
-    u.re = df_mul(q, df_mul(df_add(df_mul(c2, X), df_mul(s2, Y)), inv));
-    u.im = df_mul(q, df_mul(df_sub(df_mul(s2, X), df_mul(c2, Y)), inv));
-    const cdf u2 = cmul(u, u);
-    // F1 - 1 = u/3 + u^2/5 + [u^3/7 + u^4/9 + u^5/11 + u^6/13 + u^7/15 in float32]
-    // Re log(1 - u) = -Re(u) - Re(u^2)/2 - [Re(u^3)/3 + ... in float32]
-    const float ur = u.re.hi, ui = u.im.hi, u2r = u2.re.hi, u2i = u2.im.hi;
-    const float u3r = u2r * ur - u2i * ui, u3i = u2r * ui + u2i * ur;
-    const float u4r = u2r * u2r - u2i * u2i, u4i = 2.0f * u2r * u2i;
-    const float u5r = u4r * ur - u4i * ui, u5i = u4r * ui + u4i * ur;
-    const float u6r = u4r * u2r - u4i * u2i, u6i = u4r * u2i + u4i * u2r;
-    const float u7r = u6r * ur - u6i * ui, u7i = u6r * ui + u6i * ur;
-    const float tFr = u3r * (1.0f / 7.0f) + u4r * (1.0f / 9.0f) + u5r * (1.0f / 11.0f) +
-                      u6r * (1.0f / 13.0f) + u7r * (1.0f / 15.0f);
-    const float tFi = u3i * (1.0f / 7.0f) + u4i * (1.0f / 9.0f) + u5i * (1.0f / 11.0f) +
-                      u6i * (1.0f / 13.0f) + u7i * (1.0f / 15.0f);
-    const float tLr = u3r * (1.0f / 3.0f) + u4r * 0.25f + u5r * 0.2f + u6r * (1.0f / 6.0f) +
-                      u7r * (1.0f / 7.0f);
+    // u = q (cos 2beta + i sin 2beta) conj(P)^2 / |P|^2 in double-float
+    const df2 ure = df_mul(q, df_mul(df_add(df_mul(c2, X), df_mul(s2, Y)), inv));
+    const df2 uim = df_mul(q, df_mul(df_sub(df_mul(s2, X), df_mul(c2, Y)), inv));
+    // the first-order terms in double-float, the rest (below 5e-5 of the leading
+    // term) in float32 from the leading word of u:
+    //   F1 - 1 = u/3 + u^2 (1/5 + u (1/7 + u (1/9 + u/11))),
+    //   -Re log(1 - u) = Re u + Re u^2 (1/2 + u (1/3 + u (1/4 + u/5)))
+    const float ur = ure.hi, ui = uim.hi;
+    const float u2r = ur * ur - ui * ui, u2i = 2.0f * ur * ui;
+    float ar = (1.0f / 9.0f) + ur * (1.0f / 11.0f), ai = ui * (1.0f / 11.0f), tr;
+    tr = (1.0f / 7.0f) + ur * ar - ui * ai; ai = ur * ai + ui * ar; ar = tr;
+    tr = (1.0f / 5.0f) + ur * ar - ui * ai; ai = ur * ai + ui * ar; ar = tr;
+    const float hFr = u2r * ar - u2i * ai, hFi = u2r * ai + u2i * ar;
+    float br = 0.25f + ur * 0.2f, bi = ui * 0.2f;
+    tr = (1.0f / 3.0f) + ur * br - ui * bi; bi = ur * bi + ui * br; br = tr;
+    tr = 0.5f + ur * br - ui * bi; bi = ur * bi + ui * br; br = tr;
+    const float hL = u2r * br - u2i * bi;
     const df2 third = df_const(kThird);
-    cdf F;  // F1 - 1
-    F.re = df_add(df_mul(u.re, third), df_mul_f(u2.re, 0.2f));
-    F.re = fast_two_sum(F.re.hi, __fadd_rn(F.re.lo, tFr));
-    F.im = df_add(df_mul(u.im, third), df_mul_f(u2.im, 0.2f));
-    F.im = fast_two_sum(F.im.hi, __fadd_rn(F.im.lo, tFi));
-    // 2pi dG/dp = L inv conj(F1) P,  conj(F1) P = P + conj(F - 0) P
-    const df2 fr = df_add_f(F.re, 1.0f);
+    const df2 Fre = df_add_f(df_mul(ure, third), hFr);
+    const df2 Fim = df_add_f(df_mul(uim, third), hFi);
+    // 2pi dG/dp = L inv conj(F1) P
+    const df2 fr = df_add_f(Fre, 1.0f);
     const df2 Li = df_mul(L, inv);
-    gpx = df_mul(Li, df_add(df_mul(fr, px), df_mul(F.im, py)));
-    gpy = df_mul(Li, df_sub(df_mul(fr, py), df_mul(F.im, px)));
-    // K = log|P| + Re log(1 - u)/2 + i Im F1
+    gpx = df_mul(Li, df_add(df_mul(fr, px), df_mul(Fim, py)));
+    gpy = df_mul(Li, df_sub(df_mul(fr, py), df_mul(Fim, px)));
+    // K = log|P| + Re log(1 - u)/2 + i Im F1;  2pi dG/db = t K - gp / 2
     df2 lg = df_log(rho2, tlog);
     lg.hi *= 0.5f;
     lg.lo *= 0.5f;
-    df2 rl = df_add(u.re, mkdf(0.5f * u2.re.hi, 0.5f * u2.re.lo));
-    rl = fast_two_sum(rl.hi, __fadd_rn(rl.lo, tLr));  // -Re log(1 - u)
+    const df2 rl = df_add_f(ure, hL);  // -Re log(1 - u)
     const df2 Kr = df_sub(lg, mkdf(0.5f * rl.hi, 0.5f * rl.lo));
-    const df2 Ki = F.im;
-    // dG/db = -gp/2 + t K
-    gbx = df_sub(df_sub(df_mul(tx, Kr), df_mul(ty, Ki)), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo));
-    gby = df_sub(df_add(df_mul(ty, Kr), df_mul(tx, Ki)), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo));
+    gbx = df_sub(df_sub(df_mul(tx, Kr), df_mul(ty, Fim)), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo));
+    gby = df_sub(df_add(df_mul(ty, Kr), df_mul(tx, Fim)), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo));
     return;
   }
   // near field, panel frame (n = t rotated by +90 degrees)
@@ -218,7 +203,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     const bool ok = i < n;
     const int ii = ok ? i : n - 1;
     const df2 ui = ok ? df_from_double(ub[ii]) : mkdf(0.0f);
-    df2 sAx = mkdf(0.0f), sAy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+    df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
     // rows in windows of 4: the lane's u_i dG/dp terms are shifted into rx/ry
     // (static register indices with a rolled loop) and reduced per window
     df2 rx[4], ry[4];
@@ -232,11 +217,11 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
           df2 gpx, gpy, gbx, gby;
           panel_dG_df(pj, pc, ld, ii, ii == j, tlog, tatan, gpx, gpy, gbx, gby);
           const df2 lj = mkdf(lamh[j], laml[j]);
-          // A_i += lambda_j (-gp - gb), B_i += lambda_j gb
+          // S_i += lambda_j gp, B_i += lambda_j gb  (A_i = -S_i - B_i)
           sBx = df_add(sBx, df_mul(lj, gbx));
           sBy = df_add(sBy, df_mul(lj, gby));
-          sAx = df_sub(sAx, df_mul(lj, df_add(gpx, gbx)));
-          sAy = df_sub(sAy, df_mul(lj, df_add(gpy, gby)));
+          sSx = df_add(sSx, df_mul(lj, gpx));
+          sSy = df_add(sSy, df_mul(lj, gpy));
           if (ok) {
             vx = df_mul(ui, gpx);
             vy = df_mul(ui, gpy);
@@ -254,10 +239,11 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
       }
     }
     if (ok) {
-      Ac[2 * i] = df_to_double(sAx);
-      Ac[2 * i + 1] = df_to_double(sAy);
-      Bc[2 * i] = df_to_double(sBx);
-      Bc[2 * i + 1] = df_to_double(sBy);
+      const double bx = df_to_double(sBx), by = df_to_double(sBy);
+      Ac[2 * i] = -(df_to_double(sSx) + bx);
+      Ac[2 * i + 1] = -(df_to_double(sSy) + by);
+      Bc[2 * i] = bx;
+      Bc[2 * i + 1] = by;
     }
   }
   __syncthreads();
@@ -380,7 +366,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
   const bool warp_on = 32 * warp < nc;
   const int ic = ok ? il : 0;
   const df2 ui = ok ? df_from_double(ub[i]) : mkdf(0.0f);
-  df2 sAx = mkdf(0.0f), sAy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+  df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
     if (warp_on) {
@@ -397,8 +383,8 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
             const df2 lj = mkdf(lamh[j], laml[j]);
             sBx = df_add(sBx, df_mul(lj, gbx));
             sBy = df_add(sBy, df_mul(lj, gby));
-            sAx = df_sub(sAx, df_mul(lj, df_add(gpx, gbx)));
-            sAy = df_sub(sAy, df_mul(lj, df_add(gpy, gby)));
+            sSx = df_add(sSx, df_mul(lj, gpx));
+            sSy = df_add(sSy, df_mul(lj, gpy));
             if (ok) {
               vx = df_mul(ui, gpx);
               vy = df_mul(ui, gpy);
@@ -438,10 +424,11 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
     // u_i A_i belongs to node i (start of panel i), u_i B_i to node i + 1
     const int i1 = (i + 1 == n) ? 0 : i + 1;
     const double f = w2pi * ub[i];
-    atomicAdd(&gout[2 * i], f * df_to_double(sAx));
-    atomicAdd(&gout[2 * i + 1], f * df_to_double(sAy));
-    atomicAdd(&gout[2 * i1], f * df_to_double(sBx));
-    atomicAdd(&gout[2 * i1 + 1], f * df_to_double(sBy));
+    const double bx = df_to_double(sBx), by = df_to_double(sBy);
+    atomicAdd(&gout[2 * i], -f * (df_to_double(sSx) + bx));
+    atomicAdd(&gout[2 * i + 1], -f * (df_to_double(sSy) + by));
+    atomicAdd(&gout[2 * i1], f * bx);
+    atomicAdd(&gout[2 * i1 + 1], f * by);
   }
   if (blockIdx.y == 0) {
     // the terms that need no pair sums, once per node

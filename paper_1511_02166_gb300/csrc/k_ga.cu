@@ -97,24 +97,51 @@ __device__ int tournament(int B, int k, double p, const double* __restrict__ fit
 
 }  // namespace
 
-__global__ void k_ga_sample(int B, int P, int n, const double* __restrict__ ctrl_x,
-                            const double* __restrict__ genome, double* __restrict__ nodes) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)B * n) return;
-  const int b = (int)(e / n), i = (int)(e % n);
-  const int nu = (n + 1) / 2;
-  const double t = (i <= nu) ? 0.25 * (1.0 - cos(kPiF64 * i / nu))
-                             : 0.5 + 0.25 * (1.0 - cos(kPiF64 * (i - nu) / (n - nu)));
-  double N[4];
-  const int s = bspline_basis3(t, P, N);
-  const double* y = genome + (int64_t)b * P;
-  double px = 0.0, py = 0.0;
-  for (int r = 0; r < 4; ++r) {
-    px = fma(N[r], ctrl_x[s - 3 + r], px);
-    py = fma(N[r], y[s - 3 + r], py);
+// Nodes of a tile of kTileN nodes x kTileB airfoils per block: the basis of the
+// tile's nodes (and their x, shared by the population) is evaluated once into
+// shared memory, then every airfoil of the tile applies it to its genome.
+constexpr int kTileN = 64, kTileB = 64, kSampleThreads = 256;
+
+__global__ void __launch_bounds__(kSampleThreads) k_ga_sample(int B, int P, int n,
+                                                              const double* __restrict__ ctrl_x,
+                                                              const double* __restrict__ genome,
+                                                              double* __restrict__ nodes) {
+  __shared__ double sN[kTileN][4];
+  __shared__ double sx[kTileN];
+  __shared__ int ss[kTileN];
+  const int i0 = blockIdx.x * kTileN, b0 = blockIdx.y * kTileB;
+  const int t = threadIdx.x;
+  if (t < kTileN && i0 + t < n) {
+    const int i = i0 + t;
+    const int nu = (n + 1) / 2;
+    const double tp = (i <= nu) ? 0.25 * (1.0 - cos(kPiF64 * i / nu))
+                                : 0.5 + 0.25 * (1.0 - cos(kPiF64 * (i - nu) / (n - nu)));
+    double N[4];
+    const int sp = bspline_basis3(tp, P, N);
+    double px = 0.0;
+    for (int r = 0; r < 4; ++r) {
+      sN[t][r] = N[r];
+      px = fma(N[r], ctrl_x[sp - 3 + r], px);
+    }
+    sx[t] = px;
+    ss[t] = sp;
   }
-  nodes[2 * e] = px;
-  nodes[2 * e + 1] = py;
+  __syncthreads();
+  const int li = t % kTileN;
+  const int i = i0 + li;
+  if (i >= n) return;
+  const int sp = ss[li];
+  const double px = sx[li];
+  for (int lb = t / kTileN; lb < kTileB; lb += kSampleThreads / kTileN) {
+    const int b = b0 + lb;
+    if (b >= B) break;
+    const double* y = genome + (int64_t)b * P + sp - 3;
+    double py = 0.0;
+    for (int r = 0; r < 4; ++r) py = fma(sN[li][r], y[r], py);
+    const int64_t e = (int64_t)b * n + i;
+    nodes[2 * e] = px;
+    nodes[2 * e + 1] = py;
+  }
 }
 
 __global__ void k_ga_step(int B, int P, int k, double p, double pm, const double* __restrict__ lo,
@@ -152,8 +179,8 @@ __global__ void k_ga_step(int B, int P, int k, double p, double pm, const double
 
 cudaError_t launch_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
                              double* nodes, cudaStream_t s) {
-  const int64_t total = (int64_t)B * n;
-  k_ga_sample<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(B, P, n, ctrl_x, genome, nodes);
+  const dim3 grid((n + kTileN - 1) / kTileN, (B + kTileB - 1) / kTileB);
+  k_ga_sample<<<grid, kSampleThreads, 0, s>>>(B, P, n, ctrl_x, genome, nodes);
   return cudaGetLastError();
 }
 

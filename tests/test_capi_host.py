@@ -91,6 +91,21 @@ def test_argument_validation_before_any_launch():
     assert lib.panel_polar(1, 10, bd.PANEL_MIXED, *args) == bd.PANEL_EINVAL
     assert lib.panel_polar(1, 10, bd.PANEL_MIXED | bd.PANEL_INVERSE, *args) == bd.PANEL_EINVAL
     assert lib.panel_polar(0, 10, bd.PANEL_MIXED, *args) == bd.PANEL_OK
+    # viscous correction: required pointers, cl required with ld
+    assert lib.panel_viscous(1, *([None] * 16)) == bd.PANEL_EINVAL
+    assert lib.panel_viscous(-1, *([None] * 16)) == bd.PANEL_EINVAL
+    assert lib.panel_viscous(0, *([None] * 16)) == bd.PANEL_OK
+    # genetic algorithm: sizes, probabilities and buffers checked before any launch
+    assert lib.panel_ga_sample(1, 3, 10, None, None, None, None) == bd.PANEL_EINVAL
+    assert lib.panel_ga_sample(65535 * 64 + 1, 18, 10, None, None, None, None) == bd.PANEL_EINVAL
+    assert lib.panel_ga_sample(0, 18, 10, None, None, None, None) == bd.PANEL_OK
+    ga = [None] * 8
+    assert lib.panel_ga_step(3, 18, 4, 0.8, 0.3, *ga) == bd.PANEL_EINVAL  # odd population
+    assert lib.panel_ga_step(4, 18, 17, 0.8, 0.3, *ga) == bd.PANEL_EINVAL  # tournament > 16
+    assert lib.panel_ga_step(4, 18, 4, 1.5, 0.3, *ga) == bd.PANEL_EINVAL
+    assert lib.panel_ga_step(4, 18, 4, 0.8, -0.1, *ga) == bd.PANEL_EINVAL
+    assert lib.panel_ga_step(4, 18, 4, 0.8, 0.3, *ga) == bd.PANEL_EINVAL  # NULL buffers
+    assert lib.panel_ga_step(0, 18, 4, 0.8, 0.3, *ga) == bd.PANEL_OK
     # an empty batch is a no-op
     assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
     assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"

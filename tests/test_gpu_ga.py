@@ -13,7 +13,9 @@ from tests.gpu_util import need_gpu
 pytestmark = pytest.mark.gpu
 
 
-def test_sampler_matches_oracle():
+@pytest.mark.parametrize("B,n", [(5, 137), (130, 64), (67, 3)])
+def test_sampler_matches_oracle(B, n):
+    # tiles of 64 nodes x 64 airfoils: ragged in both directions, one exact tile, n = 3
     need_gpu()
     import torch
     from paper_1511_02166_gb300 import binding as bd
@@ -21,7 +23,6 @@ def test_sampler_matches_oracle():
     cx = default_control_x()
     lo, hi = default_bounds(cx)
     rng = np.random.default_rng(4)
-    B, n = 5, 137
     g = lo + rng.random((B, len(cx))) * (hi - lo)
     out = torch.empty(B * n, 2, dtype=torch.float64, device="cuda")
     bd.panel_ga_sample(B, len(cx), n, torch.tensor(cx, device="cuda"),
