@@ -16,7 +16,11 @@
 //     2pi dG/dDelta = t (log|P| + Re(log(1 - u))/2 + i Im F1(u)),
 //     dG/db = -dG/dp / 2 + dG/dDelta;
 //  u and the first-order terms in double-float, the terms of second and higher
-//  order in u (below 5e-5 of the leading one) in float32.
+//  order in u (below 5e-5 of the leading one) in float32; when every lane of a
+//  warp has |P| >= 32 L (|u| <= 1/4096) only the leading terms L P / |P|^2 and
+//  t log|P| are double-float and the whole series is float32.
+//  The caller's lanes must all call this function together (a warp vote picks
+//  the branch).
 //  near field (panel frame: xi = (p-a).t, eta = (p-a).n, l1 = log|p-a|^2,
 //  l2 = log|p-b|^2, theta the subtended angle):
 //     2pi dG/dp = (l1 - l2)/2 t + theta n,
@@ -51,6 +55,41 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
   const float Lh = s[kL * ld + i];
   const df2 tx = pf(s, ld, kTx, i), ty = pf(s, ld, kTy, i);
   const df2 L = pf(s, ld, kL, i);
+  if (__all_sync(0xffffffffu, rho2.hi >= 1024.0f * Lh * Lh)) {
+    // every lane of the warp at |P| >= 32 L (warp-uniform branch): |u| <= 1/4096,
+    // the leading terms L P / |P|^2 and t log|P| in double-float, the whole
+    // series in u in float32 (below 1/12288 of the leading term: ~3e-11 of it)
+    const df2 inv = df_rcp(rho2);
+    const df2 Li = df_mul(L, inv);
+    gpx = df_mul(Li, px);
+    gpy = df_mul(Li, py);
+    df2 lg = df_log(rho2, tlog);
+    lg.hi *= 0.5f;
+    lg.lo *= 0.5f;
+    const float pxh = px.hi, pyh = py.hi, invf = inv.hi;
+    const float X = pxh * pxh - pyh * pyh, Y = 2.0f * pxh * pyh;
+    const float q = 6.0f * s[kQ6 * ld + i] * invf;  // L^2 / (4 |P|^2)
+    const float c2 = s[kC2 * ld + i], s2 = s[kS2 * ld + i];
+    const float ur = q * (c2 * X + s2 * Y) * invf, ui = q * (s2 * X - c2 * Y) * invf;
+    // F1 - 1 = u (1/3 + u (1/5 + u (1/7 + u / 9))): the u^5 term is below 1e-19
+    float ar = (1.0f / 7.0f) + ur * (1.0f / 9.0f), ai = ui * (1.0f / 9.0f), tr;
+    tr = (1.0f / 5.0f) + ur * ar - ui * ai; ai = ur * ai + ui * ar; ar = tr;
+    tr = (1.0f / 3.0f) + ur * ar - ui * ai; ai = ur * ai + ui * ar; ar = tr;
+    const float Fr = ur * ar - ui * ai, Fi = ur * ai + ui * ar;
+    // -Re log(1 - u) = Re u (1 + u (1/2 + u (1/3 + u / 4)))
+    float br = (1.0f / 3.0f) + ur * 0.25f, bi = ui * 0.25f;
+    tr = 0.5f + ur * br - ui * bi; bi = ur * bi + ui * br; br = tr;
+    tr = 1.0f + ur * br - ui * bi; bi = ur * bi + ui * br; br = tr;
+    const float rl = ur * br - ui * bi;
+    const float Lif = Li.hi;
+    gpx = df_add_f(gpx, Lif * (Fr * pxh + Fi * pyh));
+    gpy = df_add_f(gpy, Lif * (Fr * pyh - Fi * pxh));
+    const float dK = -0.5f * rl;
+    const float txh = tx.hi, tyh = ty.hi;
+    gbx = df_add_f(df_sub(df_mul(tx, lg), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo)), txh * dK - tyh * Fi);
+    gby = df_add_f(df_sub(df_mul(ty, lg), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo)), tyh * dK + txh * Fi);
+    return;
+  }
   if (rho2.hi >= 16.0f * Lh * Lh) {
     const df2 X = df_sub(px2, py2);
     df2 Y = df_mul(px, py);
