@@ -85,35 +85,55 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
     // inside the block's rows, lane = column), then L21 = A21 U11^{-1} with a
     // thread per row below the block ----
     if (warp == 0) {
+      // register-resident: lane r holds row r of the diagonal block (x[t] =
+      // column t); rows keep their lanes and pos tracks their current position,
+      // so an exchange of positions q and p is bookkeeping plus one ipiv entry
+      float x[NB];
+#pragma unroll
+      for (int t = 0; t < NB; ++t) x[t] = (lane < kb && t < kb) ? P[lane * LDP + t] : 0.0f;
+      int pos = lane;
+      bool done = lane >= kb;  // already a pivot row (or outside the block)
       int fz = 0;
-      for (int q = 0; q < kb; ++q) {
-        const float v = (lane >= q && lane < kb) ? fabsf(P[lane * LDP + q]) : -1.0f;
-        const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;  // |x| bits are monotone
-        const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-        if (mx <= 1u) {  // exactly zero (or NaN) pivot column
-          fz = q + 1;
-          break;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < kb && fz == 0) {
+          const float v = done ? -1.0f : fabsf(x[q]);
+          const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;  // |x| bits are monotone
+          const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+          if (mx <= 1u) {  // exactly zero (or NaN) pivot column
+            fz = q + 1;
+          } else {
+            // the lowest current position among the maxima
+            const unsigned pm = __reduce_min_sync(0xffffffffu, key == mx ? (unsigned)pos : 0xffu);
+            const int pl = __ffs(__ballot_sync(0xffffffffu, key == mx && pos == (int)pm)) - 1;
+            const int ql = __ffs(__ballot_sync(0xffffffffu, pos == q)) - 1;  // the row now at q
+            if (lane == 0) ipiv[k0 + q] = k0 + (int)pm;
+            if (lane == ql) pos = (int)pm;
+            if (lane == pl) {
+              pos = q;
+              done = true;
+            }
+            const float inv = 1.0f / __shfl_sync(0xffffffffu, x[q], pl);
+            const float l = x[q] * inv;
+            const bool elim = !done;
+#pragma unroll
+            for (int c = q + 1; c < NB; ++c) {
+              const float uc = __shfl_sync(0xffffffffu, x[c], pl);
+              if (elim) x[c] = fmaf(-l, uc, x[c]);
+            }
+            if (elim) x[q] = l;
+          }
         }
-        const int p = __ffs(__ballot_sync(0xffffffffu, key == mx)) - 1;  // lowest row on ties
-        if (lane == 0) ipiv[k0 + q] = k0 + p;
-        if (p != q && lane < NB) {
-          const float t = P[q * LDP + lane];
-          P[q * LDP + lane] = P[p * LDP + lane];
-          P[p * LDP + lane] = t;
-        }
-        __syncwarp();
-        const float inv = 1.0f / P[q * LDP + q];
-        const float uq = (lane < NB) ? P[q * LDP + lane] : 0.0f;
-        for (int r = q + 1; r < kb; ++r) {
-          const float l = P[r * LDP + q] * inv;
-          __syncwarp();
-          if (lane > q && lane < NB) P[r * LDP + lane] = fmaf(-l, uq, P[r * LDP + lane]);
-          if (lane == q) P[r * LDP + q] = l;
-        }
-        __syncwarp();
       }
+      __syncwarp();
+      if (lane < kb) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t)
+          if (t < kb) P[pos * LDP + t] = x[t];
+      }
+      __syncwarp();
       if (lane == 0) cand[0] = (unsigned long long)fz;
-      if (lane < kb) red[lane] = (double)(1.0f / P[lane * LDP + lane]);
+      if (lane < kb && fz == 0) red[lane] = (double)(1.0f / P[lane * LDP + lane]);
     }
     __syncthreads();
     if (cand[0] != 0ull) {
