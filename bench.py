@@ -195,6 +195,33 @@ def _dist():
     return world, rank, local
 
 
+def rank_population_spec(spec, rank):
+    """Weak scaling: rank r evaluates its own population of the configured size
+    (the seed index shifted by 1000 r); airfoils are independent, so no data
+    crosses ranks."""
+    from paper_1511_02166_gb300 import inputs
+    return inputs.PopulationSpec(spec.name, spec.batch, spec.n_min, spec.n_max, spec.perturbed,
+                                 spec.seed_index + 1000 * rank)
+
+
+def max_over_ranks(x, device=None):
+    """The largest x over the ranks of the default process group (x itself
+    without one): the slowest rank sets the whole job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, ms):
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
@@ -226,16 +253,49 @@ def cpu_baseline(config, seconds=15.0, max_airfoils=None):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: W untimed and K timed steps,
+    each the solve and forward-tangent gradient of the same bounded sample of
+    the workload (sized so that the whole run takes about args.ref_seconds).
+    Under torchrun only rank 0 runs; the other ranks exit without work."""
     world, rank, _ = _dist()
     if rank != 0:
         return
-    cb = cpu_baseline(args.config, seconds=max(5.0, 20.0 / max(args.steps, 1)))
-    out = {"metric": METRIC, "value": cb["value"], "unit": "airfoils/s", "impl": "reference",
+    import oracle
+    from paper_1511_02166_gb300 import inputs
+    spec = inputs.SPECS[args.config]
+    threads = oracle.max_threads()
+    pop_all = inputs.make_population(spec)
+    per_step = max(1.0, args.ref_seconds / max(args.steps + args.warmup, 1))
+
+    def one(sub):
+        t0 = time.perf_counter()
+        oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
+        oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
+        return time.perf_counter() - t0
+
+    # size the sample: grow it until one step takes about per_step seconds
+    k = 2 * threads
+    while True:
+        sub = pop_all.subset(np.arange(min(k, pop_all.batch)))
+        dt = one(sub)
+        if dt > per_step / 2 or sub.batch >= pop_all.batch:
+            break
+        k = min(pop_all.batch, int(k * max(2.0, per_step / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        one(sub)
+    times = [one(sub) for _ in range(args.steps)]
+    sec = float(np.mean(times))
+    value = sub.batch / sec
+    sample = ("%d of %d airfoils of %s per step (solve + forward-tangent gradient), "
+              "%d threads" % (sub.batch, spec.batch, args.config, threads))
+    out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "impl": "reference",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.config}, "cpu_baseline": cb,
-           "e2e": {"value": cb["value"], "unit": "airfoils/s", "h2d_bytes_per_step": 0,
+           "config": {"workload": args.config, "batch_per_step": int(sub.batch)},
+           "cpu_baseline": {"value": value, "unit": "airfoils/s", "cores": int(threads),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "airfoils/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -257,10 +317,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    spec = inputs.SPECS[args.config]
-    # weak scaling: each rank evaluates its own batch of the configured size
-    spec_r = inputs.PopulationSpec(spec.name, spec.batch, spec.n_min, spec.n_max, spec.perturbed,
-                                   spec.seed_index + 1000 * rank)
+    spec_r = rank_population_spec(inputs.SPECS[args.config], rank)
     pop = inputs.make_population(spec_r, batch=args.batch)
     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=args.mode, device=dev,
                     max_iter=args.max_iter, tol=args.tol)
@@ -331,14 +388,9 @@ def run_ours(args):
         totals.append(e0.elapsed_time(e1))
     barrier()
     clocks = clk.stop()
-    ms = float(np.mean(totals))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(totals)), dev)
     B = pop.batch
-    value = world * B / (ms * 1e-3)
+    value = whole_job_rate(world, B, ms)
 
     # ---- e2e through the public API with host buffers ----
     nodes_h = torch.from_numpy(pop.nodes).pin_memory()
@@ -360,7 +412,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = float(np.mean(e2e_ms))
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), dev)
 
     # ---- polar: Cl at POLAR_ANGLES angles per airfoil from one factorisation ----
     polar = None
@@ -534,7 +586,7 @@ def run_ours(args):
            "kernels": kernels,
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
            "info_nonzero": int((info != 0).sum()),
-           "e2e": {"value": world * B / (e2e * 1e-3), "unit": "airfoils/s",
+           "e2e": {"value": whole_job_rate(world, B, e2e), "unit": "airfoils/s",
                    "ms_per_step": e2e, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "roofline": roofline,
@@ -560,6 +612,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=10)
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: about this many seconds for the whole run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--polar", type=int, default=16,
                     help="also time Cl at this many angles per airfoil from one factorisation "
