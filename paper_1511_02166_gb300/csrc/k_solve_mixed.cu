@@ -459,14 +459,42 @@ __device__ __forceinline__ double resacc_sub_from(double c, const ResAcc& a) {
   return ((c - (double)a.s1) - ((double)a.s2.hi + (double)a.s2.lo)) - (double)a.s3;
 }
 
+// The first residual of the refinement only has to carry the ~1e-4 error of
+// the float32 solve to the next correction: a double-float sum of the products
+// (each exact to ~2^-48 of itself, the sum to ~2^-44 of sum |p|) suffices there.
+struct LiteAcc {
+  df2 s;
+};
+__device__ __forceinline__ void resacc_init(LiteAcc& a) { a.s = mkdf(0.0f); }
+__device__ __forceinline__ void resacc_add(LiteAcc& a, float h, float l, float xh, float xl) {
+  const df2 p = two_prod(h, xh);
+  const float e = __fmaf_rn(h, xl, __fmaf_rn(l, xh, p.lo));
+  a.s = df_add(a.s, mkdf(p.hi, e));
+}
+__device__ __forceinline__ void resacc_merge(LiteAcc& a, const LiteAcc& b) { a.s = df_add(a.s, b.s); }
+__device__ __forceinline__ LiteAcc warp_sum_res(LiteAcc a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    LiteAcc b;
+    b.s.hi = __shfl_xor_sync(0xffffffffu, a.s.hi, o);
+    b.s.lo = __shfl_xor_sync(0xffffffffu, a.s.lo, o);
+    resacc_merge(a, b);
+  }
+  return a;
+}
+__device__ __forceinline__ double resacc_sub_from(double c, const LiteAcc& a) {
+  return c - ((double)a.s.hi + (double)a.s.lo);
+}
+
 // r_j = b_j - sum_i M_ji x_i for all rows j; x given as float pairs (xh, xl).
 // A warp takes two rows at a time and issues all loads of a 256-column chunk
 // before accumulating.
+template <class Acc>
 __device__ void residual_rows(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const double* b, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 2 * warp; j0 < m; j0 += 2 * kWarps) {
-    ResAcc acc0, acc1;
+    Acc acc0, acc1;
     resacc_init(acc0);
     resacc_init(acc1);
     const bool two = j0 + 1 < m;
@@ -502,13 +530,14 @@ __device__ void residual_rows(const float* __restrict__ Ah, const float* __restr
 
 // r_i = g_i - sum_j M_ji x_j for all columns i: each warp owns 32 consecutive
 // columns (one per lane) and walks all rows, 8 rows of loads in flight.
+template <class Acc>
 __device__ void residual_cols(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const double* g, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = 32 * warp; cb < m; cb += kThreads) {
     const int c = cb + lane;
     const bool ok = c < m;
-    ResAcc acc;
+    Acc acc;
     resacc_init(acc);
     for (int jb = 0; jb < m; jb += 8) {
       float h[8], l[8];
@@ -533,12 +562,13 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
 // accumulators and are merged across the warps through `part` (kWarps x m).
 constexpr int kFuseM = 288;
 constexpr int kFuseT = (kFuseM + 31) / 32;
+template <class Acc>
 __device__ void residual_both(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const float* yh, const float* yl,
                               const double* b, const double* g, double* rf, double* rt,
-                              ResAcc* part) {
+                              Acc* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ResAcc cacc[kFuseT];
+  Acc cacc[kFuseT];
 #pragma unroll
   for (int t = 0; t < kFuseT; ++t) resacc_init(cacc[t]);
   for (int j = warp; j < m; j += kWarps) {
@@ -551,7 +581,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
       l[t] = ok ? __ldg(Al + j * m + c) : 0.0f;
     }
     const float yjh = yh[j], yjl = yl[j];
-    ResAcc racc;
+    Acc racc;
     resacc_init(racc);
 #pragma unroll
     for (int t = 0; t < kFuseT; ++t) {
@@ -571,7 +601,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
   }
   __syncthreads();
   for (int c = threadIdx.x; c < m; c += kThreads) {
-    ResAcc acc = part[c];
+    Acc acc = part[c];
     for (int w = 1; w < kWarps; ++w) resacc_merge(acc, part[w * m + c]);
     rt[c] = resacc_sub_from(g[c], acc);
   }
@@ -734,7 +764,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
       // the contraction seen over the last two corrections (rho = |d_k| /
       // |d_{k-1}| <= 1/8) predicts the next one, |d_k| rho, below tol |x|: the
       // error left in x_{k+1} is about that next correction.
-      if (it >= 1 && dmax <= a.tol * xmax) conv[q] = true;
+      // (the correction of iteration 1 comes from the double-float residual,
+      // so the first test waits for iteration 2)
+      if (it >= 2 && dmax <= a.tol * xmax) conv[q] = true;
       if (it >= 2 && dmax <= 0.125 * dprev[q] && dmax * (dmax / dprev[q]) <= a.tol * xmax)
         conv[q] = true;
       dprev[q] = dmax;
@@ -750,12 +782,24 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
     }
     __syncthreads();
     const bool both = active[0] && !conv[0] && active[1] && !conv[1];
-    if (both && m <= kFuseM) {
-      residual_both(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb, sys[1].bb,
-                    sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
+    if (it == 0) {
+      if (both && m <= kFuseM) {
+        residual_both<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
+                               sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<LiteAcc*>(part));
+      } else {
+        if (active[0] && !conv[0])
+          residual_rows<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
+        if (active[1] && !conv[1])
+          residual_cols<LiteAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
+      }
+    } else if (both && m <= kFuseM) {
+      residual_both<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
+                            sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
     } else {
-      if (active[0] && !conv[0]) residual_rows(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
-      if (active[1] && !conv[1]) residual_cols(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
+      if (active[0] && !conv[0])
+        residual_rows<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
+      if (active[1] && !conv[1])
+        residual_cols<ResAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
     }
     __syncthreads();
   }
