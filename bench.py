@@ -518,9 +518,11 @@ def run_ours(args):
         gm = float(np.mean(gms))
         best = float(torch.nan_to_num(opt.evaluate(), nan=-np.inf).max())
         ga = {"population": opt.B, "nodes": n_ga, "control_points": opt.P, "generations": len(gms),
+              "fitness": "lift over drag (Re 1e6, alpha 4 deg)", "best_fitness": best,
               "ms_per_generation": gm, "generations_per_s": 1e3 / gm,
-              "airfoils_per_s": world * opt.B / (gm * 1e-3), "best_cl": best,
-              "what": "panel_ga_sample + assemble + solve + forces + panel_ga_step per generation"}
+              "airfoils_per_s": world * opt.B / (gm * 1e-3),
+              "what": "panel_ga_sample + assemble + solve + forces + panel_viscous + "
+                      "panel_ga_step per generation"}
 
     # ---- roofline of the dominant kernel ----
     kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
