@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
       (reinterpret_cast<uintptr_t>(U + NB * CW) + 15) & ~(uintptr_t)15);  // 32
   unsigned long long* cand = reinterpret_cast<unsigned long long*>(red + 32);  // kWarps
   int* ipiv = reinterpret_cast<int*>(cand + kWarps);    // mv
+  int* bperm = ipiv + mv;  // NB: final row q of the block = row k0 + bperm[q] before its exchanges
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t moff = bt.mat_off[b];
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
 #pragma unroll
         for (int t = 0; t < NB; ++t)
           if (t < kb) P[pos * LDP + t] = x[t];
+        bperm[pos] = lane;
       }
       __syncwarp();
       if (lane == 0) cand[0] = (unsigned long long)fz;
@@ -163,16 +165,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
     // ---- write the panel back, exchange rows outside it ----
     for (int r = warp; r < rows; r += kWarps)
       if (lane < kb) F[(k0 + r) * m + k0 + lane] = P[r * LDP + lane];
-    for (int c = tid; c < m; c += kThreads) {
-      if (c >= k0 && c < k0 + kb) continue;
-      for (int k = k0; k < k0 + kb; ++k) {
-        const int pk = ipiv[k];
-        if (pk != k) {
-          const float t = F[k * m + c];
-          F[k * m + c] = F[pk * m + c];
-          F[pk * m + c] = t;
-        }
-      }
+    // the exchanges of this block's rows: composed into bperm, all loads of a
+    // column in flight at once; the columns right of the panel read their rows
+    // through bperm in the U12 solve below instead
+    for (int c = tid; c < k0; c += kThreads) {
+      float v[NB];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) v[q] = (q < kb) ? F[(k0 + bperm[q]) * m + c] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < kb) F[(k0 + q) * m + c] = v[q];
     }
     __syncthreads();
     const int k1 = k0 + kb;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
       const bool ok = c < m;
       float col[NB];
 #pragma unroll
-      for (int t = 0; t < NB; ++t) col[t] = (ok && t < kb) ? F[(k0 + t) * m + c] : 0.0f;
+      for (int t = 0; t < NB; ++t) col[t] = (ok && t < kb) ? F[(k0 + bperm[t]) * m + c] : 0.0f;
       for (int q = 0; q < kb; ++q) {
         const float x = col[0];
         if (ok) F[(k0 + q) * m + c] = x;
@@ -250,7 +252,7 @@ size_t lu_global_smem(int n_max) {
   const size_t mv = (size_t)n_max + 1;
   size_t bytes = mv * (NB + 1) * 4 + (size_t)NB * 128 * 4;
   bytes = (bytes + 15) & ~(size_t)15;
-  return bytes + 32 * 8 + kWarps * 8 + mv * 4;
+  return bytes + 32 * 8 + kWarps * 8 + mv * 4 + NB * 4;
 }
 
 // ---------------------------------------------------------------------------
