@@ -273,7 +273,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k0 = 0; k0 < m; k0 += 32) {
     const int kb = min(32, m - k0);
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
       const float* row = F + i * m;
       float acc = 0.0f;
@@ -282,7 +282,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
       if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
       // z_i = t_i + sum_{k<i} X[i][k] t_k  (X unit lower, stored below the diagonal)
       float v = (lane < q) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
@@ -293,7 +293,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
   }
   for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
     const int kb = min(32, m - k0);
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
       const float* row = F + i * m;
       float acc = 0.0f;
@@ -302,7 +302,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
       if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
       // x_i = sum_{k>=i} Y[i][k] t_k  (Y upper with diagonal)
       float v = (lane >= q && lane < kb) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
@@ -322,7 +322,7 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
     const int kb = min(32, m - k0);
     if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
     __syncthreads();
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       // z_i = sum_{k<=i} Y[k][i] t_k
       const int i = k0 + q;
       float v = (lane <= q) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
@@ -330,7 +330,7 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
       if (lane == 0) y[i] = v;
     }
     __syncthreads();
-    for (int r = k0 + kb + threadIdx.x; r < m; r += kThreads) {
+    for (int r = k0 + kb + threadIdx.x; r < m; r += (int)blockDim.x) {
       float acc = y[r];
 #pragma unroll 8
       for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
@@ -342,7 +342,7 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
     const int kb = min(32, m - k0);
     if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
     __syncthreads();
-    for (int q = warp; q < kb; q += kWarps) {
+    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       // z_i = t_i + sum_{k>i} X[k][i] t_k
       const int i = k0 + q;
       float v = (lane > q && lane < kb) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
@@ -350,7 +350,7 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
       if (lane == 0) y[i] = t32[q] + v;
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < k0; r += kThreads) {
+    for (int r = threadIdx.x; r < k0; r += (int)blockDim.x) {
       float acc = y[r];
 #pragma unroll 8
       for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
@@ -374,7 +374,7 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
 // `part`, 8 x m floats).  `w` is an m-float shared scratch.
 __device__ void gj_apply(const float* __restrict__ X, int m, float* y, float* w) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 4 * warp; i0 < m; i0 += 4 * kWarps) {
+  for (int i0 = 4 * warp; i0 < m; i0 += 4 * (int)(blockDim.x >> 5)) {
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int k = lane; k < m; k += 32) {
       const float yk = y[k];
@@ -389,13 +389,13 @@ __device__ void gj_apply(const float* __restrict__ X, int m, float* y, float* w)
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < m; k += kThreads) y[k] = w[k];
+  for (int k = threadIdx.x; k < m; k += (int)blockDim.x) y[k] = w[k];
   __syncthreads();
 }
 
 __device__ void gj_apply_transposed(const float* __restrict__ X, int m, float* y, float* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int rows = (m + kWarps - 1) / kWarps;
+  const int rows = (m + (int)(blockDim.x >> 5) - 1) / (int)(blockDim.x >> 5);
   const int k0 = warp * rows, k1 = min(m, k0 + rows);
   for (int cb = 0; cb < m; cb += 32) {
     const int i = cb + lane;
@@ -407,10 +407,10 @@ __device__ void gj_apply_transposed(const float* __restrict__ X, int m, float* y
     if (i < m) part[warp * m + i] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += kThreads) {
+  for (int i = threadIdx.x; i < m; i += (int)blockDim.x) {
     float v = 0.0f;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) v += part[w * m + i];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += part[w * m + i];
     y[i] = v;
   }
   __syncthreads();
@@ -495,7 +495,7 @@ template <class Acc>
 __device__ void residual_rows(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const double* b, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j0 = 2 * warp; j0 < m; j0 += 2 * kWarps) {
+  for (int j0 = 2 * warp; j0 < m; j0 += 2 * (int)(blockDim.x >> 5)) {
     Acc acc0, acc1;
     resacc_init(acc0);
     resacc_init(acc1);
@@ -536,7 +536,7 @@ template <class Acc>
 __device__ void residual_cols(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const double* g, double* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 32 * warp; cb < m; cb += kThreads) {
+  for (int cb = 32 * warp; cb < m; cb += (int)blockDim.x) {
     const int c = cb + lane;
     const bool ok = c < m;
     Acc acc;
@@ -561,7 +561,7 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
 // once: warp w takes the rows j = w, w + 8, ...; lane l owns the columns
 // c = l + 32 t.  The row sums (forward system, x) are reduced across the warp
 // per row; the column sums (transposed system, lam) stay in per-lane
-// accumulators and are merged across the warps through `part` (kWarps x m).
+// accumulators and are merged across the warps through `part` ((int)(blockDim.x >> 5) x m).
 constexpr int kFuseM = 288;
 constexpr int kFuseT = (kFuseM + 31) / 32;
 template <class Acc>
@@ -573,7 +573,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
   Acc cacc[kFuseT];
 #pragma unroll
   for (int t = 0; t < kFuseT; ++t) resacc_init(cacc[t]);
-  for (int j = warp; j < m; j += kWarps) {
+  for (int j = warp; j < m; j += (int)(blockDim.x >> 5)) {
     float h[kFuseT], l[kFuseT];
 #pragma unroll
     for (int t = 0; t < kFuseT; ++t) {
@@ -602,9 +602,9 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
     if (c < m) part[warp * m + c] = cacc[t];
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < m; c += kThreads) {
+  for (int c = threadIdx.x; c < m; c += (int)blockDim.x) {
     Acc acc = part[c];
-    for (int w = 1; w < kWarps; ++w) resacc_merge(acc, part[w * m + c]);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) resacc_merge(acc, part[w * m + c]);
     rt[c] = resacc_sub_from(g[c], acc);
   }
 }
@@ -624,11 +624,9 @@ __device__ __forceinline__ int gpiv_first(const SolveArgs& a, int b) {
   return a.piv[vec_off(a.bt, b)];
 }
 
-// MINB blocks per SM: 4 for small airfoils (more airfoils in flight to hide the
-// latency of the dependent sweeps, at the cost of a few spilled registers), 3
-// when shared memory allows no more anyway.
-template <int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
+// NT threads, MINB blocks per SM (see launch_ir_kernel).
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
@@ -654,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
   float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
-  // kWarps x min(m, kFuseM) partial sums: of the inverse's products (floats),
+  // (int)(blockDim.x >> 5) x min(m, kFuseM) partial sums: of the inverse's products (floats),
   // or of the fused residual pass (ResAcc)
   float* part = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(t32 + 32) + 15) & ~(uintptr_t)15);
@@ -672,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
   // right-hand sides: b, and g = dCl/du = 2 |h_k| / (v c) (0 for C)
   const double* nd = bt.nodes + 2 * bt.node_off[b];
   const double v = a.vinf ? a.vinf[b] : 1.0, cc = a.chord ? a.chord[b] : 1.0;
-  for (int k = threadIdx.x; k < m; k += kThreads) {
+  for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
     if (act0) {
       if (a.rhs_kind == 0) {
         sys[0].bb[k] = a.rhs[vec_off(bt, b) + k];
@@ -731,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
       IrSystem& S = sys[q];
       if (q == 0) {
         // y = P S_r r;  solve;  dx = S_c y
-        for (int k = threadIdx.x; k < m; k += kThreads) {
+        for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
           const int src = perm[k];
           y[k] = (float)((src == n) ? S.r[src] * s : S.r[src]);
         }
@@ -742,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
           lu_apply_inverse(F, m, y, t32);
       } else {
         // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
-        for (int k = threadIdx.x; k < m; k += kThreads)
+        for (int k = threadIdx.x; k < m; k += (int)blockDim.x)
           y[k] = (float)((k == n) ? S.r[k] * s : S.r[k]);
         __syncthreads();
         if (gj)
@@ -751,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
           lu_apply_inverse_transposed(F, m, y, t32);
       }
       double dmax = 0.0;
-      for (int k = threadIdx.x; k < m; k += kThreads) {
+      for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
         const int dst = (q == 0) ? k : perm[k];
         const double d = (dst == n) ? (double)y[k] * s : (double)y[k];
         S.x[dst] += d;
@@ -759,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
       }
       __syncthreads();
       double xmax = 0.0;
-      for (int k = threadIdx.x; k < m; k += kThreads) xmax = fmax(xmax, fabs(S.x[k]));
+      for (int k = threadIdx.x; k < m; k += (int)blockDim.x) xmax = fmax(xmax, fabs(S.x[k]));
       dmax = block_absmax_d(dmax, red);
       xmax = block_absmax_d(xmax, red);
       // Converged when the correction just applied is below tol |x|, or when
@@ -776,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
     if ((conv[0] && conv[1]) || it >= a.max_iter) break;
     for (int q = 0; q < 2; ++q) {
       if (!active[q] || conv[q]) continue;
-      for (int k = threadIdx.x; k < m; k += kThreads) {
+      for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
         const df2 d = df_from_double(sys[q].x[k]);
         sys[q].xh[k] = d.hi;
         sys[q].xl[k] = d.lo;
@@ -805,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < m; k += kThreads) {
+  for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
     if (act0) a.u[vec_off(bt, b) + k] = sys[0].x[k];
     if (act1) a.lam[vec_off(bt, b) + k] = sys[1].x[k];
   }
@@ -815,10 +813,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_ir_mixed(SolveArgs a) {
   }
 }
 
-size_t ir_mixed_smem(int n_max) {
+size_t ir_mixed_smem(int n_max, int nt) {
   const size_t mv = (size_t)n_max + 1;
   return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 32 +
-         (size_t)kWarps * (size_t)min((int)mv, kFuseM) * sizeof(ResAcc);
+         (size_t)(nt / 32) * (size_t)min((int)mv, kFuseM) * sizeof(ResAcc);
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
@@ -876,6 +874,33 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
 
 // lambda of a vector-Jacobian product: M^T lambda = w_cl dCl/du + w_u +
 // w_cp dCp/du (refined), with the forward strengths u.
+// Blocks of 128 threads, 8 per SM, while the shared memory of 8 fits in the SM's
+// 228 KB (1 KB of it reserved per block; m <= 204): more airfoils in flight to
+// hide the latency of the dependent sweeps.  Then 256 threads, 4 per SM up to
+// kFuseM unknowns (a few spilled registers) and 3 above.
+static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
+  const Batch& bt = a.bt;
+  const int mv = bt.n_max + 1;
+  cudaError_t e;
+  if (8 * (ir_mixed_smem(bt.n_max, 128) + 1024) <= 233472) {
+    const size_t smem = ir_mixed_smem(bt.n_max, 128);
+    e = ensure_smem(k_ir_mixed<128, 8>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<128, 8><<<bt.B, 128, smem, s>>>(a);
+  } else if (mv <= kFuseM) {
+    const size_t smem = ir_mixed_smem(bt.n_max, kThreads);
+    e = ensure_smem(k_ir_mixed<kThreads, 4>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<kThreads, 4><<<bt.B, kThreads, smem, s>>>(a);
+  } else {
+    const size_t smem = ir_mixed_smem(bt.n_max, kThreads);
+    e = ensure_smem(k_ir_mixed<kThreads, 3>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<kThreads, 3><<<bt.B, kThreads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ir_vjp(const Batch& bt, const float* A_hi, const float* A_lo,
                           const float* LU, const int32_t* piv, const double* vinf,
                           const double* chord, const double* u, const double* w_cl,
@@ -888,18 +913,7 @@ cudaError_t launch_ir_vjp(const Batch& bt, const float* A_hi, const float* A_lo,
   a.w_u = w_u;
   a.w_cp = w_cp;
   a.u_in = u;
-  const size_t smem = ir_mixed_smem(bt.n_max);
-  cudaError_t e;
-  if (bt.n_max + 1 <= kFuseM) {
-    e = ensure_smem(k_ir_mixed<4>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<4><<<bt.B, kThreads, smem, s>>>(a);
-  } else {
-    e = ensure_smem(k_ir_mixed<3>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<3><<<bt.B, kThreads, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  return launch_ir_kernel(a, s);
 }
 
 // Refine the forward (u) and/or transposed (lam) systems with the stored factor.
@@ -911,18 +925,7 @@ cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_l
   SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
                           rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
   a.rhs_kind = rhs_kind;
-  const size_t smem = ir_mixed_smem(bt.n_max);
-  cudaError_t e;
-  if (bt.n_max + 1 <= kFuseM) {
-    e = ensure_smem(k_ir_mixed<4>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<4><<<bt.B, kThreads, smem, s>>>(a);
-  } else {
-    e = ensure_smem(k_ir_mixed<3>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<3><<<bt.B, kThreads, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  return launch_ir_kernel(a, s);
 }
 
 }  // namespace panel

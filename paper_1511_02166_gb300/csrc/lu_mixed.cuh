@@ -48,7 +48,8 @@ __device__ __forceinline__ double block_absmax_d(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double r = 0.0;
-  for (int w = 0; w < kWarps; ++w) r = fmax(r, red[w]);
+  const int nw = blockDim.x >> 5;
+  for (int w = 0; w < nw; ++w) r = fmax(r, red[w]);
   __syncthreads();
   return r;
 }
@@ -56,7 +57,7 @@ __device__ __forceinline__ double block_absmax_d(double v, double* red) {
 // border scale s = mean |A_jj| over the influence block (hi plane)
 __device__ __forceinline__ double border_scale(const float* Ah, int n, int m, double* red) {
   double sdiag = 0.0;
-  for (int j = threadIdx.x; j < n; j += kThreads) sdiag += fabs((double)Ah[j * m + j]);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sdiag += fabs((double)Ah[j * m + j]);
   return block_sum(sdiag, red) / n;
 }
 
