@@ -113,3 +113,15 @@ def test_inverse_small_airfoils_with_static_shared_memory():
     torch.cuda.synchronize()
     assert np.all(pb.info.cpu().numpy() == 0)
     _check(pop, pb.u.cpu().numpy(), pb.cl.cpu().numpy())
+
+
+def test_empty_batch_is_a_no_op():
+    # B = 0 through every call of the Python layer: nothing launched, nothing raised
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pb = PanelBatch(np.zeros((0, 2)), np.zeros(1, dtype=np.int64), np.zeros(0), mode="mixed")
+    pb.run(with_grad=True)
+    pb.viscous(1.0e6)
+    assert pb.cl.numel() == 0 and pb.grad.numel() == 0 and pb.cd.numel() == 0
+    torch.cuda.synchronize()
