@@ -652,8 +652,8 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
   float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
-  // (int)(blockDim.x >> 5) x min(m, kFuseM) partial sums: of the inverse's products (floats),
-  // or of the fused residual pass (ResAcc)
+  // per-warp partial sums: of the inverse's products (floats, m <= kGjM), or of
+  // the fused residual pass (ResAcc, launches with n_max + 1 <= kFuseM)
   float* part = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(t32 + 32) + 15) & ~(uintptr_t)15);
   // the factor buffer holds an inverse (exchanges stored as -(row + 1)) or an LU
@@ -666,6 +666,8 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   const int32_t* gpiv = a.piv + vec_off(bt, b);
   const double s = border_scale(Ah, n, m, red);
   const bool act0 = a.u != nullptr, act1 = a.lam != nullptr;
+  // the fused residual pass needs `part`, allocated when the launch's n_max fits
+  const bool fuse = bt.n_max + 1 <= kFuseM;
 
   // right-hand sides: b, and g = dCl/du = 2 |h_k| / (v c) (0 for C)
   const double* nd = bt.nodes + 2 * bt.node_off[b];
@@ -783,7 +785,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
     __syncthreads();
     const bool both = active[0] && !conv[0] && active[1] && !conv[1];
     if (it == 0) {
-      if (both && m <= kFuseM) {
+      if (both && fuse) {
         residual_both<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
                                sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<LiteAcc*>(part));
       } else {
@@ -792,7 +794,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
         if (active[1] && !conv[1])
           residual_cols<LiteAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
       }
-    } else if (both && m <= kFuseM) {
+    } else if (both && fuse) {
       residual_both<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
                             sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
     } else {
@@ -813,10 +815,15 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   }
 }
 
+// `part` (per-warp partial sums) serves the fused residual pass of launches with
+// n_max + 1 <= kFuseM (nt/32 x m accumulators) and, in any launch, the
+// Gauss-Jordan products of airfoils with m <= kGjM (nt/32 x m floats): the
+// factor of a refinement launch may hold inverses whatever its n_max.
 size_t ir_mixed_smem(int n_max, int nt) {
   const size_t mv = (size_t)n_max + 1;
-  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 32 +
-         (size_t)(nt / 32) * (size_t)min((int)mv, kFuseM) * sizeof(ResAcc);
+  const size_t part = (mv <= (size_t)kFuseM) ? (size_t)(nt / 32) * mv * sizeof(ResAcc)
+                                             : (size_t)(nt / 32) * kGjM * sizeof(float);
+  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 32 + part;
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
@@ -877,28 +884,26 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
 // Blocks of 128 threads, 8 per SM, while the shared memory of 8 fits in the SM's
 // 228 KB (1 KB of it reserved per block; m <= 204): more airfoils in flight to
 // hide the latency of the dependent sweeps.  Then 256 threads, 4 per SM up to
-// kFuseM unknowns (a few spilled registers) and 3 above.
-static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
-  const Batch& bt = a.bt;
-  const int mv = bt.n_max + 1;
-  cudaError_t e;
-  if (8 * (ir_mixed_smem(bt.n_max, 128) + 1024) <= 233472) {
-    const size_t smem = ir_mixed_smem(bt.n_max, 128);
-    e = ensure_smem(k_ir_mixed<128, 8>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<128, 8><<<bt.B, 128, smem, s>>>(a);
-  } else if (mv <= kFuseM) {
-    const size_t smem = ir_mixed_smem(bt.n_max, kThreads);
-    e = ensure_smem(k_ir_mixed<kThreads, 4>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<kThreads, 4><<<bt.B, kThreads, smem, s>>>(a);
-  } else {
-    const size_t smem = ir_mixed_smem(bt.n_max, kThreads);
-    e = ensure_smem(k_ir_mixed<kThreads, 3>, smem);
-    if (e != cudaSuccess) return e;
-    k_ir_mixed<kThreads, 3><<<bt.B, kThreads, smem, s>>>(a);
-  }
+// kFuseM unknowns (a few spilled registers), and above it the most warps per
+// airfoil that shared memory allows: 4 x 256, 2 x 512 or 1 x 1024 threads.
+template <int NT, int MINB>
+static cudaError_t launch_ir_shape(const SolveArgs& a, cudaStream_t s) {
+  const size_t smem = ir_mixed_smem(a.bt.n_max, NT);
+  const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB>, smem);
+  if (e != cudaSuccess) return e;
+  k_ir_mixed<NT, MINB><<<a.bt.B, NT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
+  const int n_max = a.bt.n_max;
+  auto fits = [&](int nt, int blocks) {
+    return (size_t)blocks * (ir_mixed_smem(n_max, nt) + 1024) <= 233472;
+  };
+  if (fits(128, 8)) return launch_ir_shape<128, 8>(a, s);
+  if (n_max + 1 <= kFuseM || fits(kThreads, 4)) return launch_ir_shape<kThreads, 4>(a, s);
+  if (fits(512, 2)) return launch_ir_shape<512, 2>(a, s);
+  return launch_ir_shape<1024, 1>(a, s);
 }
 
 cudaError_t launch_ir_vjp(const Batch& bt, const float* A_hi, const float* A_lo,
