@@ -119,6 +119,20 @@ int panel_plan(int B, const int64_t* node_offsets, int64_t* mat_offsets, int32_t
                int32_t* n_max);
 
 /*
+ * panel_workspace_size (HOST memory only, no GPU work).
+ * Bytes of the device arrays the calls below need besides their inputs and
+ * outputs, for a batch with host node_offsets[B+1] and the precision flag in
+ * `flags` (PANEL_FP64 or PANEL_MIXED): the matrix plane(s) (A64, or A_hi and
+ * A_lo) and the factor buffer (sum m_b^2 elements each, m_b = n_b + 1), the
+ * pivots, the right-hand side and lambda (sum m_b each).  The library allocates
+ * nothing: the caller provides these as separate arrays with the layouts given
+ * at each call, and this is their total, for budgeting device memory.  Returns
+ * 0 for B == 0 and (size_t)-1 for B < 0, a NULL pointer, decreasing offsets,
+ * n_b > PANEL_N_MAX or a bad flag.
+ */
+size_t panel_workspace_size(int B, const int64_t* node_offsets, int flags);
+
+/*
  * panel_assemble -- Section 2: influence matrix, C column, Kutta row, rhs.
  *   nodes [sum n_b][2] f64, node_offsets [B+1] i64, mat_offsets [B+1] i64,
  *   order [B] i32 (from panel_plan), alpha [B] f64 (radians),

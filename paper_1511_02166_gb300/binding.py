@@ -43,6 +43,7 @@ _D = ctypes.c_double
 #: symbol -> (restype, argtypes); mirrors include/panel.h
 SIGNATURES = {
     "panel_plan": (_I, [_I, _P, _P, _P, _P]),
+    "panel_workspace_size": (ctypes.c_size_t, [_I, _P, _I]),
     "panel_assemble": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_solve": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                          _I, _D, _P, _P, _P]),
@@ -122,6 +123,15 @@ def panel_plan(node_offsets: np.ndarray):
     _check(load().panel_plan(B, _ptr(node_offsets), _ptr(mat), _ptr(order), _ptr(nmax)),
            "panel_plan")
     return mat, order[:B], int(nmax[0])
+
+
+def panel_workspace_size(node_offsets: np.ndarray, flags: int) -> int:
+    """Host: bytes of the planes, factor, pivots, rhs and lambda of a batch."""
+    node_offsets = np.ascontiguousarray(node_offsets, dtype=np.int64)
+    n = load().panel_workspace_size(len(node_offsets) - 1, _ptr(node_offsets), int(flags))
+    if n == ctypes.c_size_t(-1).value:
+        raise ValueError("panel_workspace_size: invalid offsets or flags")
+    return int(n)
 
 
 def panel_assemble(B, n_max, flags, nodes, node_offsets, mat_offsets, order, alpha, vinf,

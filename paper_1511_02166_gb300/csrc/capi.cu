@@ -124,6 +124,24 @@ int panel_plan(int B, const int64_t* node_offsets, int64_t* mat_offsets, int32_t
   return PANEL_OK;
 }
 
+size_t panel_workspace_size(int B, const int64_t* node_offsets, int flags) {
+  const size_t bad = (size_t)-1;
+  if (B < 0 || (B > 0 && !node_offsets)) return bad;
+  const int mode = flags & (PANEL_FP64 | PANEL_MIXED);
+  if (mode != PANEL_FP64 && mode != PANEL_MIXED) return bad;
+  size_t mat = 0, vec = 0;
+  for (int b = 0; b < B; ++b) {
+    const int64_t n = node_offsets[b + 1] - node_offsets[b];
+    if (n < 0 || n > PANEL_N_MAX) return bad;
+    mat += (size_t)(n + 1) * (size_t)(n + 1);
+    vec += (size_t)(n + 1);
+  }
+  // planes + factor: FP64 plane and FP64 factor, or two FP32 planes and an FP32 factor
+  const size_t mat_bytes = (mode == PANEL_FP64) ? mat * (8 + 8) : mat * (4 + 4 + 4);
+  // pivots (i32), rhs and lambda (f64)
+  return mat_bytes + vec * (4 + 8 + 8);
+}
+
 int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
                    const int64_t* mat_offsets, const int32_t* order, const double* alpha,
                    const double* vinf, double* A64, float* A_hi, float* A_lo, double* rhs,

@@ -110,3 +110,16 @@ def test_argument_validation_before_any_launch():
     assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
     assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"
     assert "sm_103a" in bd.panel_version()
+
+
+def test_workspace_size_counts_the_work_arrays():
+    offs = np.array([0, 100, 300, 303], dtype=np.int64)
+    m = np.diff(offs) + 1
+    mat, vec = int((m * m).sum()), int(m.sum())
+    assert bd.panel_workspace_size(offs, bd.PANEL_MIXED) == mat * 12 + vec * 20
+    assert bd.panel_workspace_size(offs, bd.PANEL_FP64) == mat * 16 + vec * 20
+    assert bd.panel_workspace_size(np.zeros(1, dtype=np.int64), bd.PANEL_MIXED) == 0
+    with pytest.raises(ValueError):
+        bd.panel_workspace_size(offs, 0)
+    with pytest.raises(ValueError):
+        bd.panel_workspace_size(np.array([0, bd.PANEL_N_MAX + 1]), bd.PANEL_MIXED)
