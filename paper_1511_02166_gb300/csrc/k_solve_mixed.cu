@@ -38,6 +38,45 @@ namespace panel {
 // (the panel plus a 128-column slab of U12), so several airfoils share an SM
 // and hide each other's latencies.
 // ---------------------------------------------------------------------------
+// A22 -= L21 U12 over the columns [cc, cc + 32 J) of the staged U12 slab: warp
+// w takes the 8-row tiles w, w + 8, ...; lane l the columns cc + l + 32 j.
+template <int J, int LDP, int CW>
+__device__ __forceinline__ void update_tiles(float* __restrict__ F, const float* __restrict__ P,
+                                             const float* __restrict__ U, int m, int k0, int k1,
+                                             int kb, int cc, int nrt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int rt = warp; rt < nrt; rt += kWarps) {
+    const int r0 = k1 + 8 * rt;
+    float acc[8][J];
+#pragma unroll
+    for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int r = r0 + aa, c = cc + lane + 32 * j;
+        acc[aa][j] = (r < m && c < m) ? F[r * m + c] : 0.0f;
+      }
+#pragma unroll 4
+    for (int q = 0; q < kb; ++q) {
+      float lv[8], uv[J];
+#pragma unroll
+      for (int aa = 0; aa < 8; ++aa) lv[aa] = (r0 + aa < m) ? P[(r0 + aa - k0) * LDP + q] : 0.0f;
+#pragma unroll
+      for (int j = 0; j < J; ++j) uv[j] = U[q * CW + lane + 32 * j];
+#pragma unroll
+      for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[aa][j] = fmaf(-lv[aa], uv[j], acc[aa][j]);
+    }
+#pragma unroll
+    for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int r = r0 + aa, c = cc + lane + 32 * j;
+        if (r < m && c < m) F[r * m + c] = acc[aa][j];
+      }
+  }
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -179,22 +218,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
     __syncthreads();
     const int k1 = k0 + kb;
     if (k1 >= m) break;
-    // ---- U12 = L11^{-1} A12, a column per lane, shifted registers ----
+    // ---- U12 = L11^{-1} A12, a column per lane, unrolled forward substitution
+    // (here kb == NB: a panel with columns right of it is full) ----
     for (int cb = k1 + 32 * warp; cb < m; cb += kThreads) {
       const int c = cb + lane;
       const bool ok = c < m;
       float col[NB];
 #pragma unroll
-      for (int t = 0; t < NB; ++t) col[t] = (ok && t < kb) ? F[(k0 + bperm[t]) * m + c] : 0.0f;
-      for (int q = 0; q < kb; ++q) {
-        const float x = col[0];
+      for (int t = 0; t < NB; ++t) col[t] = ok ? F[(k0 + bperm[t]) * m + c] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const float x = col[q];
         if (ok) F[(k0 + q) * m + c] = x;
 #pragma unroll
-        for (int t = 1; t < NB; ++t) {
-          const float l = (q + t < kb) ? P[(q + t) * LDP + q] : 0.0f;
-          col[t - 1] = fmaf(-l, x, col[t]);
-        }
-        col[NB - 1] = 0.0f;
+        for (int t = q + 1; t < NB; ++t) col[t] = fmaf(-P[t * LDP + q], x, col[t]);
       }
     }
     __syncthreads();
@@ -208,36 +245,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
           U[t * CW + lane + 32 * j] = (c < m) ? F[(k0 + t) * m + c] : 0.0f;
         }
       __syncthreads();
-      for (int rt = warp; rt < nrt; rt += kWarps) {
-        const int r0 = k1 + 8 * rt;
-        float acc[8][4];
-#pragma unroll
-        for (int aa = 0; aa < 8; ++aa)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int r = r0 + aa, c = cc + lane + 32 * j;
-            acc[aa][j] = (r < m && c < m) ? F[r * m + c] : 0.0f;
-          }
-#pragma unroll 4
-        for (int q = 0; q < kb; ++q) {
-          float lv[8], uv[4];
-#pragma unroll
-          for (int aa = 0; aa < 8; ++aa) lv[aa] = (r0 + aa < m) ? P[(r0 + aa - k0) * LDP + q] : 0.0f;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) uv[j] = U[q * CW + lane + 32 * j];
-#pragma unroll
-          for (int aa = 0; aa < 8; ++aa)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[aa][j] = fmaf(-lv[aa], uv[j], acc[aa][j]);
-        }
-#pragma unroll
-        for (int aa = 0; aa < 8; ++aa)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int r = r0 + aa, c = cc + lane + 32 * j;
-            if (r < m && c < m) F[r * m + c] = acc[aa][j];
-          }
-      }
+      // register tiles 8 rows x 32 J columns, J = 1..4 by the width of the slab
+      const int J = min(CW / 32, (m - cc + 31) >> 5);
+      if (J == 4)
+        update_tiles<4, LDP, CW>(F, P, U, m, k0, k1, kb, cc, nrt);
+      else if (J == 3)
+        update_tiles<3, LDP, CW>(F, P, U, m, k0, k1, kb, cc, nrt);
+      else if (J == 2)
+        update_tiles<2, LDP, CW>(F, P, U, m, k0, k1, kb, cc, nrt);
+      else
+        update_tiles<1, LDP, CW>(F, P, U, m, k0, k1, kb, cc, nrt);
       __syncthreads();
     }
   }
