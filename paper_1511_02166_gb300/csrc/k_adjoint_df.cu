@@ -18,9 +18,10 @@
 //  u and the first-order terms in double-float, the terms of second and higher
 //  order in u (below 5e-5 of the leading one) in float32; when every lane of a
 //  warp has |P| >= 32 L (|u| <= 1/4096) only the leading terms L P / |P|^2 and
-//  t log|P| are double-float and the whole series is float32.
-//  The caller's lanes must all call this function together (a warp vote picks
-//  the branch).
+//  t log|P| are double-float and the whole series is float32.  A warp with a
+//  near-field lane and every lane within 64 L takes the near-field form on all
+//  lanes.  The caller's lanes must all call this function together (warp votes
+//  pick the branches).
 //  near field (panel frame: xi = (p-a).t, eta = (p-a).n, l1 = log|p-a|^2,
 //  l2 = log|p-b|^2, theta the subtended angle):
 //     2pi dG/dp = (l1 - l2)/2 t + theta n,
@@ -90,7 +91,13 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
     gby = df_add_f(df_sub(df_mul(ty, lg), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo)), tyh * dK + txh * Fi);
     return;
   }
-  if (rho2.hi >= 16.0f * Lh * Lh) {
+  // A warp with a lane in the near field (|P| < 4 L) and every lane within 64 L
+  // evaluates the closed form on all lanes (warp-uniform): its log difference
+  // loses at most ~64x to cancellation (~1e-12 of the pair's value), and the
+  // warp runs one branch instead of both.
+  const bool near_all = __any_sync(0xffffffffu, rho2.hi < 16.0f * Lh * Lh) &&
+                        __all_sync(0xffffffffu, rho2.hi < 4096.0f * Lh * Lh);
+  if (!near_all && rho2.hi >= 16.0f * Lh * Lh) {
     const df2 X = df_sub(px2, py2);
     df2 Y = df_mul(px, py);
     Y.hi *= 2.0f;
