@@ -258,7 +258,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
       __syncthreads();
     }
   }
-  invert_diagonal_blocks(F, m, m);
+  // the diagonal blocks inverted in shared memory (the panel and slab buffers
+  // are free now: a 32 x LDP slot per warp), then written back
+  {
+    float* S = P + warp * (NB * LDP);
+    const int nb = (m + NB - 1) / NB;
+    for (int d = warp; d < nb; d += kWarps) {
+      const int d0 = NB * d, kbd = min(NB, m - d0);
+      for (int r = 0; r < kbd; ++r)
+        if (lane < kbd) S[r * LDP + lane] = F[(d0 + r) * m + d0 + lane];
+      __syncwarp();
+      invert_block(S, LDP, kbd);
+      for (int r = 0; r < kbd; ++r)
+        if (lane < kbd) F[(d0 + r) * m + d0 + lane] = S[r * LDP + lane];
+      __syncwarp();
+    }
+  }
   __syncthreads();
   int32_t* gpiv = a.piv + vec_off(bt, b);
   for (int k = tid; k < m; k += kThreads) gpiv[k] = ipiv[k];

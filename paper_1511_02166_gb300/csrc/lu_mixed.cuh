@@ -66,41 +66,45 @@ __device__ __forceinline__ double border_scale(const float* Ah, int n, int m, do
 // column j of the inverse).  X = L_dd^{-1} (unit lower) replaces the part
 // below the diagonal row by row (row i is written after every lane has read
 // it); Y = U_dd^{-1} (upper) replaces the rest row by row from the bottom.
+// invert_block takes one kb x kb block (kb <= 32) at B with row stride ld,
+// called by all lanes of one warp.
 // ---------------------------------------------------------------------------
+__device__ inline void invert_block(float* B, int ld, int kb) {
+  const int j = threadIdx.x & 31;
+  // X[i][j] = -(L[i][j] + sum_{j<k<i} L[i][k] X[k][j]),  i > j
+  for (int i = 1; i < kb; ++i) {
+    float x = 0.0f;
+    if (j < i) {
+      x = -B[i * ld + j];
+      for (int k = j + 1; k < i; ++k) x = fmaf(-B[i * ld + k], B[k * ld + j], x);
+    }
+    __syncwarp();
+    if (j < i) B[i * ld + j] = x;
+    __syncwarp();
+  }
+  // Y[i][j] = -(sum_{i<k<=j} U[i][k] Y[k][j]) / U[i][i] (i < j), Y[j][j] = 1/U[j][j]
+  for (int i = kb - 1; i >= 0; --i) {
+    float y = 0.0f;
+    const float uii = B[i * ld + i];
+    if (j == i) {
+      y = 1.0f / uii;
+    } else if (j > i && j < kb) {
+      float acc = 0.0f;
+      for (int k = i + 1; k <= j; ++k) acc = fmaf(B[i * ld + k], B[k * ld + j], acc);
+      y = -acc / uii;
+    }
+    __syncwarp();
+    if (j >= i && j < kb) B[i * ld + j] = y;
+    __syncwarp();
+  }
+}
+
 __device__ inline void invert_diagonal_blocks(float* F, int ld, int m) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const int nb = (m + 31) >> 5;
   for (int d = warp; d < nb; d += kWarps) {
     const int k0 = 32 * d;
-    const int kb = min(32, m - k0);
-    float* B = F + k0 * ld + k0;
-    const int j = lane;
-    // X[i][j] = -(L[i][j] + sum_{j<k<i} L[i][k] X[k][j]),  i > j
-    for (int i = 1; i < kb; ++i) {
-      float x = 0.0f;
-      if (j < i) {
-        x = -B[i * ld + j];
-        for (int k = j + 1; k < i; ++k) x = fmaf(-B[i * ld + k], B[k * ld + j], x);
-      }
-      __syncwarp();
-      if (j < i) B[i * ld + j] = x;
-      __syncwarp();
-    }
-    // Y[i][j] = -(sum_{i<k<=j} U[i][k] Y[k][j]) / U[i][i] (i < j), Y[j][j] = 1/U[j][j]
-    for (int i = kb - 1; i >= 0; --i) {
-      float y = 0.0f;
-      const float uii = B[i * ld + i];
-      if (j == i) {
-        y = 1.0f / uii;
-      } else if (j > i && j < kb) {
-        float acc = 0.0f;
-        for (int k = i + 1; k <= j; ++k) acc = fmaf(B[i * ld + k], B[k * ld + j], acc);
-        y = -acc / uii;
-      }
-      __syncwarp();
-      if (j >= i && j < kb) B[i * ld + j] = y;
-      __syncwarp();
-    }
+    invert_block(F + k0 * ld + k0, ld, min(32, m - k0));
   }
 }
 
