@@ -914,10 +914,12 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
 // lambda of a vector-Jacobian product: M^T lambda = w_cl dCl/du + w_u +
 // w_cp dCp/du (refined), with the forward strengths u.
 // Blocks of 128 threads, 8 per SM, while the shared memory of 8 fits in the SM's
-// 228 KB (1 KB of it reserved per block; m <= 204): more airfoils in flight to
-// hide the latency of the dependent sweeps.  Then 256 threads, 4 per SM up to
-// kFuseM unknowns (a few spilled registers), and above it the most warps per
-// airfoil that shared memory allows: 4 x 256, 2 x 512 or 1 x 1024 threads.
+// 228 KB (1 KB of it reserved per block; m <= 204) and the batch fills 8 blocks
+// on every SM: more airfoils in flight to hide the latency of the dependent
+// sweeps (a smaller batch is better served by more warps per airfoil).  Then 256
+// threads, 4 per SM up to kFuseM unknowns (a few spilled registers), and above
+// it the most warps per airfoil that shared memory allows: 4 x 256, 2 x 512 or
+// 1 x 1024 threads.
 template <int NT, int MINB>
 static cudaError_t launch_ir_shape(const SolveArgs& a, cudaStream_t s) {
   const size_t smem = ir_mixed_smem(a.bt.n_max, NT);
@@ -932,7 +934,7 @@ static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
   auto fits = [&](int nt, int blocks) {
     return (size_t)blocks * (ir_mixed_smem(n_max, nt) + 1024) <= 233472;
   };
-  if (fits(128, 8)) return launch_ir_shape<128, 8>(a, s);
+  if (fits(128, 8) && a.bt.B >= 8 * sm_count()) return launch_ir_shape<128, 8>(a, s);
   if (n_max + 1 <= kFuseM || fits(kThreads, 4)) return launch_ir_shape<kThreads, 4>(a, s);
   if (fits(512, 2)) return launch_ir_shape<512, 2>(a, s);
   return launch_ir_shape<1024, 1>(a, s);

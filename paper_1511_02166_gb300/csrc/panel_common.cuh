@@ -140,4 +140,20 @@ inline cudaError_t ensure_smem(K kernel, size_t bytes) {
   return ensure_smem_impl(reinterpret_cast<const void*>(kernel), bytes);
 }
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 0 if the query fails).
+inline int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> count;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = count.find(dev);
+  if (it != count.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+  count[dev] = n;
+  return n;
+}
+
 }  // namespace panel
