@@ -72,3 +72,26 @@ def test_uneven_full_population_samples():
         e64 = rel_inf(ref64["u"][os_:os_ + n], ref["u"][os_:os_ + n])
         assert rel_inf(u[o:o + n], ref["u"][os_:os_ + n]) < max(1e-10, 3 * e64), b
     assert cl_err(pb.cl.cpu().numpy()[idx], ref["cl"]) < 1e-10
+
+
+def test_large_full_population_samples():
+    # all 1024 airfoils of 1024..2048 panels (the step-synchronous factor with
+    # the tcgen05 update, the 1024-thread refinement); tolerances of
+    # test_gpu_large.py: gamma within 5e-9, the backward error against the
+    # oracle's matrix (long double) within 1e-13, Cl within 1e-10
+    need_gpu()
+    from tests.test_gpu_large import _backward_error
+    pop = inputs.make_population("large_b1024_n1024_2048")
+    pb = _bench_step(pop)
+    assert np.all(pb.info.cpu().numpy() == 0)
+    idx = _sample(pop, 3, 13)
+    sub = pop.subset(idx)
+    ref = oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
+    u = pb.u.cpu().numpy()
+    for s, b in enumerate(idx):
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        o, os_ = pop.offsets[b] + b, sub.offsets[s] + s
+        assert rel_inf(u[o:o + n], ref["u"][os_:os_ + n]) < 5e-9, b
+        gs = slice(pop.offsets[b], pop.offsets[b + 1])
+        assert _backward_error(pop.nodes[gs], pop.alpha[b], u[o:o + n + 1]) < 1e-13, b
+    assert cl_err(pb.cl.cpu().numpy()[idx], ref["cl"]) < 1e-10
