@@ -99,7 +99,7 @@ class PanelBatch:
 
     def __init__(self, nodes, offsets, alpha, mode: str = "mixed", vinf=None, chord=None,
                  device="cuda", max_iter: int = 10, tol: float = 1e-12,
-                 bucket_width: int | None = 64, bucket_min: int = 608):
+                 bucket_width: int | None = 192, bucket_min: int = 608):
         self.device = _require_cuda(device)
         if mode not in MODES:
             raise ValueError("mode must be one of %s" % sorted(MODES))
