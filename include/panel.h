@@ -314,7 +314,18 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
  *   input: rand [B/2][4k + 5] uniform in [0, 1), per pair: k candidate draws
  *   and k - 1 acceptance draws per tournament, the crossover point, then per
  *   child the mutation decision, gene and amount.  lo, hi, sigma [P].
+ *
+ * panel_ga_genome_grad -- genome gradient of a loss L from its node gradient
+ *   (gradient-refined GA steps; e.g. L = Cl with grad_nodes from panel_adjoint):
+ *   the nodes of panel_ga_sample have y_i = sum_r N_r(t_i) g_r with x fixed, so
+ *   dL/dg_r = sum_i N_r(t_i) dL/dy_i.  grad_nodes [B*n][2] f64 (only the y
+ *   components are read); grad_genome [B][P] f64 output or NULL; with lr != 0
+ *   the genome [B][P] (in/out) takes the ascent step g <- clamp(g + lr dL/dg,
+ *   lo, hi) (lo, hi [P]).  Sums in node order (deterministic).
  */
+int panel_ga_genome_grad(int B, int P, int n, const double* grad_nodes, double lr,
+                         const double* lo, const double* hi, double* genome, double* grad_genome,
+                         void* stream);
 int panel_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
                     double* nodes, void* stream);
 int panel_ga_step(int B, int P, int k, double p, double pm, const double* lo, const double* hi,

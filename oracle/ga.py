@@ -1,5 +1,6 @@
-"""Genetic-algorithm oracle (test infrastructure): the B-spline genome sampler
-and one generation of tournament selection, one-point crossover and mutation,
+"""Genetic-algorithm oracle (test infrastructure): the B-spline genome sampler,
+the genome gradient of a node-gradient (gradient-refined steps), and one
+generation of tournament selection, one-point crossover and mutation,
 written from the genetic optimisation of Section 2 with plain numpy / scipy and
 Python loops.  Only tests/ (and the CPU legs of bench.py) use it; it shares no
 code with the CUDA library.
@@ -58,6 +59,16 @@ def sample(ctrl_x, genome, n: int) -> np.ndarray:
         pts = curve(np.minimum(t, 1.0))
         out[b * n:(b + 1) * n] = pts
     return out
+
+
+def genome_grad(ctrl_x, grad_nodes, n: int) -> np.ndarray:
+    """dL/dgenome [B][P] from dL/dnodes [B*n][2]: the nodes' y coordinates are
+    the B-spline's design matrix (scipy) times the genome, x is fixed."""
+    P = len(ctrl_x)
+    t = np.minimum(sample_parameters(n), 1.0)
+    J = BSpline.design_matrix(t, knots(P), 3).toarray()  # [n][P]
+    gy = np.asarray(grad_nodes, dtype=np.float64)[:, 1].reshape(-1, n)
+    return gy @ J
 
 
 def _rank_key(fitness, idx, pos):

@@ -58,6 +58,7 @@ SIGNATURES = {
                        _P, _P, _I, _D, _P, _P]),
     "panel_ga_sample": (_I, [_I, _I, _I, _P, _P, _P, _P]),
     "panel_ga_step": (_I, [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "panel_ga_genome_grad": (_I, [_I, _I, _I, _P, _D, _P, _P, _P, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
@@ -200,6 +201,12 @@ def panel_vjp(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A_hi, A_
 def panel_ga_sample(B, P, n, ctrl_x, genome, nodes, stream=None):
     _check(load().panel_ga_sample(int(B), int(P), int(n), _ptr(ctrl_x), _ptr(genome),
                                   _ptr(nodes), _stream(stream)), "panel_ga_sample")
+
+
+def panel_ga_genome_grad(B, P, n, grad_nodes, lr, lo, hi, genome, grad_genome, stream=None):
+    _check(load().panel_ga_genome_grad(B, P, n, _ptr(grad_nodes), float(lr), _ptr(lo), _ptr(hi),
+                                       _ptr(genome), _ptr(grad_genome), _stream(stream)),
+           "panel_ga_genome_grad")
 
 
 def panel_ga_step(B, P, k, p, pm, lo, hi, sigma, genome_in, fitness, rand, genome_out,

@@ -34,6 +34,8 @@ cudaError_t launch_ga_step(int, int, int, double, double, const double*, const d
                            const double*, const double*, const double*, const double*, double*,
                            cudaStream_t);
 int ga_max_tournament();
+cudaError_t launch_ga_genome_grad(int, int, int, const double*, double, const double*,
+                                  const double*, double*, double*, cudaStream_t);
 cudaError_t launch_polar_cl(const Batch&, const double*, const double*, const double*,
                             const double*, int, const double*, const int32_t*, double*,
                             cudaStream_t);
@@ -246,6 +248,17 @@ int panel_ga_sample(int B, int P, int n, const double* ctrl_x, const double* gen
   if (B == 0) return PANEL_OK;
   if (!ctrl_x || !genome || !nodes) return PANEL_EINVAL;
   return status_of(panel::launch_ga_sample(B, P, n, ctrl_x, genome, nodes, (cudaStream_t)stream));
+}
+
+int panel_ga_genome_grad(int B, int P, int n, const double* grad_nodes, double lr,
+                         const double* lo, const double* hi, double* genome, double* grad_genome,
+                         void* stream) {
+  if (B < 0 || P < 4 || n < 3 || n > PANEL_N_MAX || !(lr == lr)) return PANEL_EINVAL;
+  if (B == 0) return PANEL_OK;
+  if (!grad_nodes || (!grad_genome && lr == 0.0)) return PANEL_EINVAL;
+  if (lr != 0.0 && (!lo || !hi || !genome)) return PANEL_EINVAL;
+  return status_of(panel::launch_ga_genome_grad(B, P, n, grad_nodes, lr, lo, hi, genome,
+                                                grad_genome, (cudaStream_t)stream));
 }
 
 int panel_ga_step(int B, int P, int k, double p, double pm, const double* lo, const double* hi,

@@ -177,6 +177,59 @@ __global__ void k_ga_step(int B, int P, int k, double p, double pm, const double
   }
 }
 
+// Genome gradient of a loss whose node gradient is grad_nodes: the nodes' y
+// coordinates are linear in the genome, y_i = sum_r N_r(t_i) g_r (x fixed), so
+// dL/dg_r = sum_i N_r(t_i) dL/dy_i.  One block per airfoil: the basis of every
+// node into shared memory, then thread r sums over the nodes in the support of
+// control point r in node order (deterministic).  With lr != 0 the genome also
+// takes the ascent step g_r <- min(max(g_r + lr dL/dg_r, lo_r), hi_r).
+constexpr int kGradThreads = 128;
+
+__global__ void __launch_bounds__(kGradThreads) k_ga_genome_grad(
+    int P, int n, const double* __restrict__ grad_nodes, double lr, const double* __restrict__ lo,
+    const double* __restrict__ hi, double* __restrict__ genome, double* __restrict__ grad_genome) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  double* Nb = reinterpret_cast<double*>(gsm);      // n x 4
+  double* gy = Nb + 4 * n;                          // n
+  int* sp = reinterpret_cast<int*>(gy + n);         // n
+  const int b = blockIdx.x;
+  const int nu = (n + 1) / 2;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double t = (i <= nu) ? 0.25 * (1.0 - cos(kPiF64 * i / nu))
+                               : 0.5 + 0.25 * (1.0 - cos(kPiF64 * (i - nu) / (n - nu)));
+    double N[4];
+    sp[i] = bspline_basis3(t, P, N);
+    for (int r = 0; r < 4; ++r) Nb[4 * i + r] = N[r];
+    gy[i] = grad_nodes[2 * ((int64_t)b * n + i) + 1];
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < P; r += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int q = r - (sp[i] - 3);  // index of control point r in node i's four
+      if (q >= 0 && q < 4) acc = fma(Nb[4 * i + q], gy[i], acc);
+    }
+    if (grad_genome) grad_genome[(int64_t)b * P + r] = acc;
+    if (lr != 0.0) {
+      double* g = genome + (int64_t)b * P + r;
+      *g = fmin(fmax(*g + lr * acc, lo[r]), hi[r]);
+    }
+  }
+}
+
+size_t ga_grad_smem(int n) { return (size_t)n * (4 * 8 + 8 + 4); }
+
+cudaError_t launch_ga_genome_grad(int B, int P, int n, const double* grad_nodes, double lr,
+                                  const double* lo, const double* hi, double* genome,
+                                  double* grad_genome, cudaStream_t s) {
+  const size_t smem = ga_grad_smem(n);
+  const cudaError_t e = ensure_smem(k_ga_genome_grad, smem);
+  if (e != cudaSuccess) return e;
+  k_ga_genome_grad<<<B, kGradThreads, smem, s>>>(P, n, grad_nodes, lr, lo, hi, genome,
+                                                 grad_genome);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ga_sample(int B, int P, int n, const double* ctrl_x, const double* genome,
                              double* nodes, cudaStream_t s) {
   const dim3 grid((n + kTileN - 1) / kTileN, (B + kTileB - 1) / kTileB);

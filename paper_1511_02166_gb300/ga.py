@@ -92,6 +92,20 @@ class GeneticOptimizer:
             self.fitness = self.pb.cl
         return self.fitness
 
+    def refine(self, lr: float):
+        """One gradient-ascent step of every genome on Cl (gradient-refined GA
+        step): dCl/dnodes by the adjoint, mapped to the genome by the transpose
+        of the B-spline sampling, g <- clamp(g + lr dCl/dg, lo, hi), then the
+        fitness of the refined population.  Needs fitness 'cl'."""
+        if self.fitness_kind != "cl":
+            raise ValueError("gradient refinement follows dCl/dgenome: use fitness='cl'")
+        bd.panel_ga_sample(self.B, self.P, self.n, self.ctrl_x, self.genome, self.pb.nodes)
+        self.pb.info.zero_()
+        self.pb.run(with_grad=True)
+        bd.panel_ga_genome_grad(self.B, self.P, self.n, self.pb.grad, float(lr), self.lo,
+                                self.hi, self.genome, None)
+        return self.evaluate()
+
     def draw(self):
         return torch.rand(self.B // 2, 4 * self.k + 5, generator=self.gen, dtype=torch.float64,
                           device=self.device)
@@ -105,10 +119,12 @@ class GeneticOptimizer:
         self.generation += 1
         return rand
 
-    def run(self, generations: int):
+    def run(self, generations: int, refine_lr: float = 0.0):
+        """`generations` steps; with refine_lr > 0 each generation first takes
+        one gradient-ascent step on Cl (refine())."""
         best = []
         for _ in range(generations):
-            f = self.evaluate()
+            f = self.refine(refine_lr) if refine_lr > 0 else self.evaluate()
             best.append(float(torch.nan_to_num(f, nan=-np.inf).max()))
             self.step()
         self.evaluate()

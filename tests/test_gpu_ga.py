@@ -82,3 +82,44 @@ def test_device_generation_matches_oracle(fitness):
                    opt.hi.cpu().numpy(), opt.sigma.cpu().numpy())
     assert np.array_equal(opt.genome.cpu().numpy(), nxt)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n,lr", [(120, 0.0), (301, 1e-3)])
+def test_genome_gradient_and_ascent_step(n, lr):
+    # the transpose of the sampler on the device against scipy's design matrix;
+    # with lr != 0 the clamped ascent step on the genome
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300 import binding as bd
+    from paper_1511_02166_gb300.ga import default_bounds, default_control_x
+    cx = default_control_x()
+    lo, hi = default_bounds(cx)
+    rng = np.random.default_rng(n)
+    B, P = 9, len(cx)
+    g = lo + rng.random((B, P)) * (hi - lo)
+    w = rng.normal(size=(B * n, 2)) * 50.0
+    ref = oga.genome_grad(cx, w, n)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    gd, out = dev(g), torch.empty(B, P, dtype=torch.float64, device="cuda")
+    bd.panel_ga_genome_grad(B, P, n, dev(w), lr, dev(lo), dev(hi), gd, out)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
+    want = np.minimum(np.maximum(g + lr * ref, lo), hi) if lr else g
+    assert np.max(np.abs(gd.cpu().numpy() - want)) <= 1e-14
+
+
+def test_gradient_refined_generation_raises_lift():
+    # one refinement step on Cl (adjoint gradient through the sampler) raises the
+    # population's lift where the bounds allow, and its fitness is the oracle's Cl
+    need_gpu()
+    from paper_1511_02166_gb300.ga import GeneticOptimizer
+    opt = GeneticOptimizer(B=32, n=120, alpha=np.radians(3.0), seed=5, fitness="cl")
+    f0 = opt.evaluate().cpu().numpy().copy()
+    f1 = opt.refine(2e-3).cpu().numpy()
+    ok = np.isfinite(f0) & np.isfinite(f1)
+    assert ok.sum() >= 24 and np.mean(f1[ok] > f0[ok]) > 0.9
+    nodes = oga.sample(opt.ctrl_x.cpu().numpy(), opt.genome.cpu().numpy(), opt.n)
+    offs = np.arange(opt.B + 1, dtype=np.int64) * opt.n
+    ref = oracle.evaluate_batch(nodes, offs, np.full(opt.B, np.radians(3.0)))
+    good = ok & (ref["info"] == 0)
+    assert np.max(np.abs(f1[good] - ref["cl"][good]) / np.maximum(np.abs(ref["cl"][good]), 1)) < 1e-9

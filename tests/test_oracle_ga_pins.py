@@ -95,3 +95,25 @@ def test_crossover_segments_and_mutation_bounds():
     changed = out1[diff]
     assert np.all((changed >= 0.2) & (changed <= 0.8))
     assert np.all(np.abs(out1 - out0) <= 0.05 + 1e-15)
+
+
+def test_genome_gradient_is_the_adjoint_of_the_sampler():
+    # the sampler is linear in the genome: the gradient of L = <w, y(g)> is J^T w,
+    # checked by central differences of L and by the partition of unity
+    # (sum over control points of dL/dg = sum over nodes of dL/dy)
+    cx = default_control_x()
+    lo, hi = default_bounds(cx)
+    rng = np.random.default_rng(21)
+    n, B = 57, 3
+    g = lo + rng.random((B, len(cx))) * (hi - lo)
+    w = rng.normal(size=(B * n, 2))
+    grad = ga.genome_grad(cx, w, n)
+    L = lambda gg: float(np.sum(w[:, 1] * ga.sample(cx, gg, n)[:, 1]))
+    h = 1e-6
+    for b in range(B):
+        for r in range(len(cx)):
+            gp, gm = g.copy(), g.copy()
+            gp[b, r] += h
+            gm[b, r] -= h
+            assert abs((L(gp) - L(gm)) / (2 * h) - grad[b, r]) < 1e-8 * max(1.0, abs(grad[b, r]))
+    assert np.allclose(grad.sum(axis=1), w[:, 1].reshape(B, n).sum(axis=1), rtol=1e-13, atol=1e-13)
