@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) k_assemble_df(Batch bt, const double* __r
                                                      float* __restrict__ A_hi,
                                                      float* __restrict__ A_lo,
                                                      double* __restrict__ rhs,
-                                                     int32_t* __restrict__ info) {
+                                                     int32_t* __restrict__ info, int rounds) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = bt.n_max;
   float4* tlog = reinterpret_cast<float4*>(smraw);                   // 257
@@ -67,29 +67,82 @@ __global__ void __launch_bounds__(256) k_assemble_df(Batch bt, const double* __r
     Ah[(int64_t)n * m + j] = (j == 0 || j == n - 1) ? 1.0f : 0.0f;
     Al[(int64_t)n * m + j] = 0.0f;
   }
-  // pairs (j, i), j, i < n, row-major over the threads of the block
+  // pairs (j, i), j, i < n, row-major over the threads of the block, in rounds of
+  // `rounds` pairs per thread: the far-field pairs are evaluated at once, the
+  // near-field ones (|P| < 4 L) queued and then evaluated by all threads
+  // together, so that no warp runs both forms for a mix of its lanes
+  // (rounds == 0: both forms inline, for the largest airfoils, whose one block
+  // per SM cannot afford the barriers)
+  int* queue = reinterpret_cast<int*>(pc + kPanelFields * ld);  // blockDim.x * rounds
+  int* qn = queue + blockDim.x * rounds;
   const int stride = blockDim.x;
   const int dj = stride / n, di = stride % n;
   int j = threadIdx.x / n, i = threadIdx.x % n;
   point3 pj = load_point(pc, ld, j < n ? j : 0);
-  while (j < n) {
-    const df2 g = panel_G_df(pj, pc, ld, i, tlog, tatan);
-    const int64_t e = (int64_t)j * m + i;
-    Ah[e] = -g.hi;
-    Al[e] = -g.lo;
-    const int jo = j;
-    i += di;
-    j += dj;
-    if (i >= n) {
-      i -= n;
-      ++j;
+  if (rounds == 0) {
+    while (j < n) {
+      const df2 g = panel_G_df<0>(pair_geom(pj, pc, ld, i), pc, ld, i, tlog, tatan);
+      const int64_t e = (int64_t)j * m + i;
+      Ah[e] = -g.hi;
+      Al[e] = -g.lo;
+      const int jo = j;
+      i += di;
+      j += dj;
+      if (i >= n) {
+        i -= n;
+        ++j;
+      }
+      if (j != jo && j < n) pj = load_point(pc, ld, j);
     }
-    if (j != jo && j < n) pj = load_point(pc, ld, j);
+    return;
+  }
+  const int np = n * n;
+  for (int p0 = 0; p0 < np; p0 += stride * rounds) {
+    if (threadIdx.x == 0) *qn = 0;
+    __syncthreads();
+    for (int r = 0; r < rounds && j < n; ++r) {
+      const PairGeom gm = pair_geom(pj, pc, ld, i);
+      if (gm.far()) {
+        const df2 g = panel_G_df<1>(gm, pc, ld, i, tlog, tatan);
+        const int64_t e = (int64_t)j * m + i;
+        Ah[e] = -g.hi;
+        Al[e] = -g.lo;
+      } else {
+        queue[atomicAdd(qn, 1)] = j * n + i;
+      }
+      const int jo = j;
+      i += di;
+      j += dj;
+      if (i >= n) {
+        i -= n;
+        ++j;
+      }
+      if (j != jo && j < n) pj = load_point(pc, ld, j);
+    }
+    __syncthreads();
+    const int cnt = *qn;
+    for (int t = threadIdx.x; t < cnt; t += stride) {
+      const int pq = queue[t];
+      const int jq = pq / n, iq = pq - jq * n;
+      const PairGeom gm = pair_geom(load_point(pc, ld, jq), pc, ld, iq);
+      const df2 g = panel_G_df<2>(gm, pc, ld, iq, tlog, tatan);
+      const int64_t e = (int64_t)jq * m + iq;
+      Ah[e] = -g.hi;
+      Al[e] = -g.lo;
+    }
+    __syncthreads();
   }
 }
 
+// Pairs per thread between two near-field passes (the queue holds 256 x rounds
+// pair indices, 16 KB); 0 above 1024 panels: there the panel constants take
+// most of the shared memory, one block fits an SM, and the barriers of the
+// deferred pass cost more than the mixed branches (C5 assembly 36 -> 49 ms).
+static int assemble_rounds(int n_max) { return n_max <= 1024 ? 16 : 0; }
+
 size_t assemble_df_smem(int n_max) {
-  return 257 * 16 + 34 * 8 + (size_t)(2 * n_max + 32) * 8 + (size_t)kPanelFields * n_max * 4;
+  return 257 * 16 + 34 * 8 + (size_t)(2 * n_max + 32) * 8 + (size_t)kPanelFields * n_max * 4 +
+         ((size_t)256 * assemble_rounds(n_max) + 1) * 4;
 }
 
 cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const double* vinf,
@@ -98,7 +151,8 @@ cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const doubl
   const size_t smem = assemble_df_smem(bt.n_max);
   cudaError_t e = ensure_smem(k_assemble_df, smem);
   if (e != cudaSuccess) return e;
-  k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info);
+  k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info,
+                                        assemble_rounds(bt.n_max));
   return cudaGetLastError();
 }
 

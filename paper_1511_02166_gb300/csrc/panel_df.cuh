@@ -119,18 +119,36 @@ __device__ __forceinline__ point3 make_point(double x, double y) {
   return p;
 }
 
-// G(p; panel i) in double-float for the control point p.
-__device__ __forceinline__ df2 panel_G_df(const point3& p, const float* __restrict__ s, int ld,
-                                          int i, const float4* __restrict__ tlog,
+// P = p - c_i (exactly formed from the split coordinates) and |P|^2.
+struct PairGeom {
+  df2 px, py, px2, py2, rho2;
+  float Lh;
+  __device__ __forceinline__ bool far() const { return rho2.hi >= 16.0f * Lh * Lh; }
+};
+__device__ __forceinline__ PairGeom pair_geom(const point3& p, const float* __restrict__ s,
+                                              int ld, int i) {
+  PairGeom g;
+  g.px = split_diff(p.xh, p.xm, p.xl, s[kCx * ld + i], s[(kCx + 1) * ld + i],
+                    s[(kCx + 2) * ld + i]);
+  g.py = split_diff(p.yh, p.ym, p.yl, s[kCy * ld + i], s[(kCy + 1) * ld + i],
+                    s[(kCy + 2) * ld + i]);
+  g.px2 = df_sqr(g.px);
+  g.py2 = df_sqr(g.py);
+  g.rho2 = df_add(g.px2, g.py2);
+  g.Lh = s[kL * ld + i];
+  return g;
+}
+
+// G(p; panel i) in double-float for the control point p.  WHICH = 0: the far or
+// the near form by |P| >= 4 L; 1: the far form; 2: the near form (the caller has
+// made the choice with PairGeom::far).
+template <int WHICH = 0>
+__device__ __forceinline__ df2 panel_G_df(const PairGeom& gm, const float* __restrict__ s,
+                                          int ld, int i, const float4* __restrict__ tlog,
                                           const float2* __restrict__ tatan) {
-  const df2 px = split_diff(p.xh, p.xm, p.xl, s[kCx * ld + i], s[(kCx + 1) * ld + i],
-                            s[(kCx + 2) * ld + i]);
-  const df2 py = split_diff(p.yh, p.ym, p.yl, s[kCy * ld + i], s[(kCy + 1) * ld + i],
-                            s[(kCy + 2) * ld + i]);
-  const df2 px2 = df_sqr(px), py2 = df_sqr(py);
-  const df2 rho2 = df_add(px2, py2);
-  const float Lh = s[kL * ld + i];
-  if (rho2.hi >= 16.0f * Lh * Lh) {
+  const df2 px = gm.px, py = gm.py, px2 = gm.px2, py2 = gm.py2, rho2 = gm.rho2;
+  const float Lh = gm.Lh;
+  if (WHICH == 1 || (WHICH == 0 && gm.far())) {
     // ---- far field: multipole series about the panel midpoint ----
     const df2 X = df_sub(px2, py2);
     df2 Y = df_mul(px, py);
@@ -166,6 +184,7 @@ __device__ __forceinline__ df2 panel_G_df(const point3& p, const float* __restri
     lg.lo *= 0.5f;
     return df_mul(pf(s, ld, kLg, i), df_sub(lg, S));
   }
+  if (WHICH == 1) return mkdf(0.0f);
   // ---- near field: exact closed form in the panel frame ----
   const df2 tx = pf(s, ld, kTx, i), ty = pf(s, ld, kTy, i);
   const df2 L = pf(s, ld, kL, i);
@@ -183,6 +202,12 @@ __device__ __forceinline__ df2 panel_G_df(const point3& p, const float* __restri
   br = df_add(br, df_mul(eta, th));
   br = df_sub(br, L);
   return df_mul(br, df_const(kInv2Pi));
+}
+
+__device__ __forceinline__ df2 panel_G_df(const point3& p, const float* __restrict__ s, int ld,
+                                          int i, const float4* __restrict__ tlog,
+                                          const float2* __restrict__ tatan) {
+  return panel_G_df<0>(pair_geom(p, s, ld, i), s, ld, i, tlog, tatan);
 }
 
 }  // namespace panel
