@@ -63,6 +63,12 @@ def shear_shape(lam):
     return l, H
 
 
+def squire_young(theta, U, H):
+    """Momentum thickness far downstream (one surface's share of Cd / 2), the
+    closed form of Squire and Young: theta U^((H + 5) / 2) at the trailing edge."""
+    return theta * U ** ((H + 5.0) / 2.0)
+
+
 def march(h, U, Re):
     """Thwaites's method along one surface.
 
@@ -190,7 +196,7 @@ def viscous_airfoil(xy, gamma, alpha, Re, vinf=1.0, chord=1.0):
         for k in range(1, K + 2):
             cd_f += 0.5 * (cf[k - 1] + cf[k]) * float(np.dot(P[k] - P[k - 1], ehat))
         _, He = shear_shape(LAMBDA_SEP if separated else lam[K + 1])
-        cd += 2.0 * theta[K + 1] * U[K + 1] ** ((He + 5.0) / 2.0)
+        cd += 2.0 * squire_young(theta[K + 1], U[K + 1], He)
         for k, c in enumerate(cps, start=1):
             out["theta"][c] = theta[k]
             out["cf"][c] = cf[k]

@@ -188,3 +188,20 @@ def test_degenerate_inputs_give_nan():
     assert math.isnan(v["cd"]) and v["sep"] == (-2, -2)
     v = ov.viscous_airfoil(xy, u[:60], 0.0, 0.0)
     assert math.isnan(v["cd"]) and np.all(np.isnan(v["theta"]))
+
+
+@pytest.mark.parametrize("U_te,H_te", [(0.9, 2.6), (0.75, 3.55), (1.1, 2.3)])
+def test_squire_young_from_the_wake_momentum_equation(U_te, H_te):
+    # Squire and Young's closed form is the wake momentum integral without wall
+    # shear, d ln(theta) / d ln(U) = -(H + 2), with H - 1 falling linearly in
+    # ln U from H_te - 1 at the trailing edge to 0 far downstream (U = 1);
+    # integrated here numerically, independently of the closed form
+    s0 = math.log(U_te)
+
+    def rhs(s, y):
+        H = 1.0 + (H_te - 1.0) * s / s0
+        return [-(H + 2.0)]
+
+    sol = scipy_integrate.solve_ivp(rhs, [s0, 0.0], [math.log(0.01)], rtol=1e-12, atol=1e-14)
+    theta_inf = math.exp(sol.y[0, -1])
+    assert abs(ov.squire_young(0.01, U_te, H_te) / theta_inf - 1) < 1e-9
