@@ -246,10 +246,24 @@ def cpu_baseline(config, seconds=15.0, max_airfoils=None):
         if dt > seconds / 4 or sub.batch >= pop_all.batch:
             break
         k = min(pop_all.batch, int(k * max(2.0, seconds / 4 / max(dt, 1e-3))))
+    # library-solve reference: LAPACK (numpy.linalg.solve) on the oracle's assembled
+    # matrices of the first airfoils of the sample, the solve alone
+    ls = pop_all.subset(np.arange(min(64, pop_all.batch)))
+    mats = []
+    for b in range(ls.batch):
+        s0, s1 = ls.offsets[b], ls.offsets[b + 1]
+        mats.append(oracle.assemble(ls.nodes[s0:s1], float(ls.alpha[b])))
+    t0 = time.perf_counter()
+    for M, rhs in mats:
+        np.linalg.solve(M, rhs)
+    lapack = ls.batch / (time.perf_counter() - t0)
     return {"value": done / elapsed, "unit": "airfoils/s", "cores": int(threads),
             "host_cores": int(cores), "kind": "oracle",
             "sample": "%d of %d airfoils of %s (solve + forward-tangent gradient), %.1f s"
-                      % (done, spec.batch, config, elapsed)}
+                      % (done, spec.batch, config, elapsed),
+            "lapack_solves_per_s": lapack,
+            "lapack_sample": "numpy.linalg.solve of the oracle's assembled systems, first %d "
+                             "airfoils" % ls.batch}
 
 
 def run_reference(args):
