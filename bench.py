@@ -339,6 +339,22 @@ def run_ours(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    def timed_ms(fn, reps, warmup):
+        """Mean CUDA-event time of fn() on the launching stream over `reps` calls
+        after `warmup` untimed ones, with the L2 flushed before each call."""
+        ts = []
+        for it in range(warmup + reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if it >= warmup:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts)), len(ts)
+
     if args.mode == "mixed":
         names = ["assemble", "factor", "refine", "forces", "adjoint"]
         fns = [pb.assemble, lambda: pb.solve(stage="factor"),
@@ -436,18 +452,8 @@ def run_ours(args):
                                 device=dev).repeat(B, 1).contiguous()
         pb.polar(alphas)
         torch.cuda.synchronize()
-        pms = []
-        for it in range(args.warmup + max(2, args.steps // 2)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.polar(alphas)  # assemble + factor + two basis refinements + combination
-            e1.record(stream)
-            e1.synchronize()
-            if it >= args.warmup:
-                pms.append(e0.elapsed_time(e1))
-        pm = float(np.mean(pms))
+        # assemble + factor + two basis refinements + combination
+        pm, _ = timed_ms(lambda: pb.polar(alphas), max(2, args.steps // 2), args.warmup)
         polar = {"angles": K, "ms": pm, "cl_per_s": world * B * K / (pm * 1e-3),
                  "airfoil_polars_per_s": world * B / (pm * 1e-3),
                  "what": "panel_assemble + panel_solve(factor) + panel_polar per step"}
@@ -463,18 +469,8 @@ def run_ours(args):
         pb.run()
         pb.vjp(w_cl, w_u, w_cp)
         torch.cuda.synchronize()
-        vms = []
-        for it in range(args.warmup + max(2, args.steps // 2)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.vjp(w_cl, w_u, w_cp)  # transposed refinement + dM/dx contraction
-            e1.record(stream)
-            e1.synchronize()
-            if it >= args.warmup:
-                vms.append(e0.elapsed_time(e1))
-        vm = float(np.mean(vms))
+        # transposed refinement + dM/dx contraction
+        vm, _ = timed_ms(lambda: pb.vjp(w_cl, w_u, w_cp), max(2, args.steps // 2), args.warmup)
         vjp = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
                "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
 
@@ -484,18 +480,7 @@ def run_ours(args):
         pb.run()
         pb.viscous(1.0e6)
         torch.cuda.synchronize()
-        vis = []
-        for it in range(args.warmup + max(2, args.steps // 2)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pb.viscous()
-            e1.record(stream)
-            e1.synchronize()
-            if it >= args.warmup:
-                vis.append(e0.elapsed_time(e1))
-        vm_ = float(np.mean(vis))
+        vm_, _ = timed_ms(pb.viscous, max(2, args.steps // 2), args.warmup)
         vbytes = float(pop.sizes.sum()) * VISCOUS_BYTES_PER_NODE
         sep = pb.sep.cpu().numpy()
         viscous = {"ms": vm_, "airfoils_per_s": world * B / (vm_ * 1e-3),
@@ -518,20 +503,14 @@ def run_ours(args):
             opt.evaluate()
             opt.step()
         torch.cuda.synchronize()
-        gms = []
-        for _ in range(int(args.ga)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            opt.evaluate()  # panel_ga_sample + assemble + solve + forces
+
+        def generation():
+            opt.evaluate()  # panel_ga_sample + assemble + solve + forces + viscous
             opt.step()      # uniforms + panel_ga_step
-            e1.record(stream)
-            e1.synchronize()
-            gms.append(e0.elapsed_time(e1))
-        gm = float(np.mean(gms))
+
+        gm, ngen = timed_ms(generation, int(args.ga), 0)
         best = float(torch.nan_to_num(opt.evaluate(), nan=-np.inf).max())
-        ga = {"population": opt.B, "nodes": n_ga, "control_points": opt.P, "generations": len(gms),
+        ga = {"population": opt.B, "nodes": n_ga, "control_points": opt.P, "generations": ngen,
               "fitness": "lift over drag (Re 1e6, alpha 4 deg)", "best_fitness": best,
               "ms_per_generation": gm, "generations_per_s": 1e3 / gm,
               "airfoils_per_s": world * opt.B / (gm * 1e-3),
