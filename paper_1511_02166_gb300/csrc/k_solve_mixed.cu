@@ -596,19 +596,19 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
 // accumulators and are merged across the warps through `part` ((int)(blockDim.x >> 5) x m).
 constexpr int kFuseM = 288;
 constexpr int kFuseT = (kFuseM + 31) / 32;
-template <class Acc>
+template <class Acc, int FT = kFuseT>
 __device__ void residual_both(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const float* yh, const float* yl,
                               const double* b, const double* g, double* rf, double* rt,
                               Acc* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Acc cacc[kFuseT];
+  Acc cacc[FT];
 #pragma unroll
-  for (int t = 0; t < kFuseT; ++t) resacc_init(cacc[t]);
+  for (int t = 0; t < FT; ++t) resacc_init(cacc[t]);
   for (int j = warp; j < m; j += (int)(blockDim.x >> 5)) {
-    float h[kFuseT], l[kFuseT];
+    float h[FT], l[FT];
 #pragma unroll
-    for (int t = 0; t < kFuseT; ++t) {
+    for (int t = 0; t < FT; ++t) {
       const int c = lane + 32 * t;
       const bool ok = c < m;
       h[t] = ok ? __ldg(Ah + j * m + c) : 0.0f;
@@ -618,7 +618,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
     Acc racc;
     resacc_init(racc);
 #pragma unroll
-    for (int t = 0; t < kFuseT; ++t) {
+    for (int t = 0; t < FT; ++t) {
       const int c = lane + 32 * t;
       if (c < m) {
         resacc_add(racc, h[t], l[t], xh[c], xl[c]);
@@ -629,7 +629,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
     if (lane == 0) rf[j] = resacc_sub_from(b[j], racc);
   }
 #pragma unroll
-  for (int t = 0; t < kFuseT; ++t) {
+  for (int t = 0; t < FT; ++t) {
     const int c = lane + 32 * t;
     if (c < m) part[warp * m + c] = cacc[t];
   }
@@ -657,7 +657,7 @@ __device__ __forceinline__ int gpiv_first(const SolveArgs& a, int b) {
 }
 
 // NT threads, MINB blocks per SM (see launch_ir_kernel).
-template <int NT, int MINB>
+template <int NT, int MINB, int FT>
 __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
     const bool both = active[0] && !conv[0] && active[1] && !conv[1];
     if (it == 0) {
       if (both && fuse) {
-        residual_both<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
+        residual_both<LiteAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
                                sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<LiteAcc*>(part));
       } else {
         if (active[0] && !conv[0])
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
           residual_cols<LiteAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
       }
     } else if (both && fuse) {
-      residual_both<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
+      residual_both<ResAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
                             sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
     } else {
       if (active[0] && !conv[0])
@@ -920,12 +920,14 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
 // threads, 4 per SM up to kFuseM unknowns (a few spilled registers), and above
 // it the most warps per airfoil that shared memory allows: 4 x 256, 2 x 512 or
 // 1 x 1024 threads.
-template <int NT, int MINB>
+// FT: columns per lane of the fused residual pass (ceil(n_max + 1 / 32) at most;
+// fewer registers for the smaller airfoils of the 128-thread shape, m <= 204).
+template <int NT, int MINB, int FT = kFuseT>
 static cudaError_t launch_ir_shape(const SolveArgs& a, cudaStream_t s) {
   const size_t smem = ir_mixed_smem(a.bt.n_max, NT);
-  const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB>, smem);
+  const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB, FT>, smem);
   if (e != cudaSuccess) return e;
-  k_ir_mixed<NT, MINB><<<a.bt.B, NT, smem, s>>>(a);
+  k_ir_mixed<NT, MINB, FT><<<a.bt.B, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -934,7 +936,8 @@ static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
   auto fits = [&](int nt, int blocks) {
     return (size_t)blocks * (ir_mixed_smem(n_max, nt) + 1024) <= 233472;
   };
-  if (fits(128, 8) && a.bt.B >= 8 * sm_count()) return launch_ir_shape<128, 8>(a, s);
+  if (fits(128, 8) && n_max + 1 <= 7 * 32 && a.bt.B >= 8 * sm_count())
+    return launch_ir_shape<128, 8, 7>(a, s);
   if (n_max + 1 <= kFuseM || fits(kThreads, 4)) return launch_ir_shape<kThreads, 4>(a, s);
   if (fits(512, 2)) return launch_ir_shape<512, 2>(a, s);
   return launch_ir_shape<1024, 1>(a, s);
