@@ -136,11 +136,12 @@ def _surfaces(n, xy, q):
 def viscous_airfoil(xy, gamma, alpha, Re, vinf=1.0, chord=1.0):
     """One airfoil: xy [n][2] nodes (counter-clockwise, x_0 at the trailing
     edge), gamma [n] panel strengths.  Returns dict(cd, cd_f, theta [n],
-    cf [n], sep (upper, lower): the separating control point, -1 if attached)."""
+    cf [n], sep (upper, lower): the separating control point, -1 if attached,
+    stagnation: the stagnation point's coordinates)."""
     xy = np.asarray(xy, dtype=np.float64)
     n = len(xy)
     out = dict(cd=math.nan, cd_f=math.nan, theta=np.full(n, math.nan), cf=np.full(n, math.nan),
-               sep=(-2, -2))
+               sep=(-2, -2), stagnation=None)
     if not (Re > 0.0 and math.isfinite(Re)):
         return out
     q = np.asarray(gamma, dtype=np.float64) / vinf
@@ -207,6 +208,7 @@ def viscous_airfoil(xy, gamma, alpha, Re, vinf=1.0, chord=1.0):
     out["cd"] = cd
     out["cd_f"] = cd_f
     out["sep"] = tuple(sep)
+    out["stagnation"] = p0 * chord
     return out
 
 

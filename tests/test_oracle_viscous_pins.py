@@ -205,3 +205,19 @@ def test_squire_young_from_the_wake_momentum_equation(U_te, H_te):
     sol = scipy_integrate.solve_ivp(rhs, [s0, 0.0], [math.log(0.01)], rtol=1e-12, atol=1e-14)
     theta_inf = math.exp(sol.y[0, -1])
     assert abs(ov.squire_young(0.01, U_te, H_te) / theta_inf - 1) < 1e-9
+
+
+@pytest.mark.parametrize("alpha_deg", [0.0, 3.0, 8.0])
+def test_cylinder_stagnation_point_under_incidence(alpha_deg):
+    # With the Kutta condition at its rear point a cylinder carries the
+    # circulation that keeps the rear stagnation point there; the front one then
+    # sits at the polar angle pi + 2 alpha (potential flow); the linear zero of
+    # gamma between two control points must find it well inside one panel
+    # (spacing 2 pi / n: 0.031 rad at n = 200)
+    a = math.radians(alpha_deg)
+    for n in (200, 400, 800):
+        xy = inputs.cylinder(n)
+        u = oracle.evaluate(xy, a)["u"]
+        p0 = ov.viscous_airfoil(xy, u[:n], a, 1e6)["stagnation"]
+        ang = math.atan2(p0[1], p0[0] - 0.5) % (2 * math.pi)
+        assert abs(ang - (math.pi + 2 * a)) < 1e-4, n
