@@ -106,6 +106,20 @@ def test_argument_validation_before_any_launch():
     assert lib.panel_ga_step(4, 18, 4, 0.8, -0.1, *ga) == bd.PANEL_EINVAL
     assert lib.panel_ga_step(4, 18, 4, 0.8, 0.3, *ga) == bd.PANEL_EINVAL  # NULL buffers
     assert lib.panel_ga_step(0, 18, 4, 0.8, 0.3, *ga) == bd.PANEL_OK
+    # genome gradient: sizes, NaN step, and the buffers each mode needs
+    gg = lambda B, P, n, lr, *ptrs: lib.panel_ga_genome_grad(B, P, n, None, lr, *ptrs, None)
+    assert gg(1, 3, 10, 0.0, None, None, None, None) == bd.PANEL_EINVAL      # P < 4
+    assert gg(1, 18, 2, 0.0, None, None, None, None) == bd.PANEL_EINVAL      # n < 3
+    assert gg(1, 18, 10, float("nan"), None, None, None, None) == bd.PANEL_EINVAL
+    assert gg(1, 18, 10, 0.0, None, None, None, None) == bd.PANEL_EINVAL     # no node gradient
+    assert gg(0, 18, 10, 0.0, None, None, None, None) == bd.PANEL_OK
+    # vector-Jacobian products: mixed path only, pointers checked
+    vj = [None] * 17 + [3, 1e-12, None, None]
+    assert lib.panel_vjp(1, 10, bd.PANEL_FP64, *vj) == bd.PANEL_ENOTSUP
+    assert lib.panel_vjp(1, 10, bd.PANEL_MIXED | bd.PANEL_INVERSE, *vj) == bd.PANEL_EINVAL
+    assert lib.panel_vjp(1, 10, bd.PANEL_MIXED, *vj) == bd.PANEL_EINVAL
+    assert lib.panel_vjp(1, bd.PANEL_N_MAX + 1, bd.PANEL_MIXED, *vj) == bd.PANEL_EINVAL
+    assert lib.panel_vjp(0, 10, bd.PANEL_MIXED, *vj) == bd.PANEL_OK
     # an empty batch is a no-op
     assert lib.panel_forces(0, *([None] * 11), None) == bd.PANEL_OK
     assert bd.panel_strerror(bd.PANEL_EINVAL) == "invalid argument"
