@@ -321,7 +321,10 @@ int panel_vjp(int B, int n_max, int flags, const double* nodes, const int64_t* n
  *   dL/dg_r = sum_i N_r(t_i) dL/dy_i.  grad_nodes [B*n][2] f64 (only the y
  *   components are read); grad_genome [B][P] f64 output or NULL; with lr != 0
  *   the genome [B][P] (in/out) takes the ascent step g <- clamp(g + lr dL/dg,
- *   lo, hi) (lo, hi [P]).  Sums in node order (deterministic).
+ *   lo, hi) (lo, hi [P]) for every gene whose dL/dg is finite; a gene with a
+ *   non-finite gradient (e.g. an airfoil whose solve failed, whose node
+ *   gradients panel_adjoint sets to NaN) keeps its value.  Sums in node order
+ *   (deterministic).
  */
 int panel_ga_genome_grad(int B, int P, int n, const double* grad_nodes, double lr,
                          const double* lo, const double* hi, double* genome, double* grad_genome,
@@ -344,6 +347,22 @@ int panel_ga_step(int B, int P, int k, double p, double pm, const double* lo, co
  */
 int panel_df_eval(int op, int count, const double* a, const double* b, double* out,
                   void* stream);
+
+/*
+ * panel_debug_wait_limit (HOST, diagnostic) -- the number of polls after which
+ * a pipeline wait inside the tensor-core trailing update of the large-airfoil
+ * factor (n_b >= 640, PANEL_MIXED) gives up.  A wait that runs out stops the
+ * airfoil's factorisation: the kernel waits for the tensor-core operations it
+ * has already issued, releases its tensor memory, writes
+ * info[b] = PANEL_INFO_DEVICE_TIMEOUT and returns, and the later stages skip
+ * that airfoil.  The default (2^22 polls, far above any wait of a working
+ * pipeline) turns a stalled pipeline into that error instead of a hang; a test
+ * lowers it to exercise the error path.  polls <= 0 restores the default.
+ * Returns the previous limit.  The value is process-wide and read when a
+ * panel_solve call launches its kernels (not synchronised with calls in flight
+ * on other host threads).  Not part of the paper's method.
+ */
+int64_t panel_debug_wait_limit(int64_t polls);
 
 /* Human-readable name of a panel_status value (static string). */
 const char* panel_strerror(int status);

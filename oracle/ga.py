@@ -71,6 +71,22 @@ def genome_grad(ctrl_x, grad_nodes, n: int) -> np.ndarray:
     return gy @ J
 
 
+def ascent_step(genome, grad_genome, lr: float, lo, hi) -> np.ndarray:
+    """One clamped gradient-ascent step of the genomes [B][P]:
+    g <- min(max(g + lr dL/dg, lo), hi) for every gene whose gradient is
+    finite; a gene with a non-finite gradient (an airfoil whose solve failed)
+    keeps its value (the library's reading; the paper has no gradient steps)."""
+    g = np.array(genome, dtype=np.float64, copy=True)
+    d = np.asarray(grad_genome, dtype=np.float64)
+    out = g.copy()
+    B, P = g.shape
+    for b in range(B):
+        for r in range(P):
+            if math.isfinite(d[b, r]):
+                out[b, r] = min(max(g[b, r] + lr * d[b, r], lo[r]), hi[r])
+    return out
+
+
 def _rank_key(fitness, idx, pos):
     f = fitness[idx]
     return (1, 0.0, idx, pos) if math.isnan(f) else (0, -f, idx, pos)

@@ -60,6 +60,7 @@ SIGNATURES = {
     "panel_ga_step": (_I, [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_ga_genome_grad": (_I, [_I, _I, _I, _P, _D, _P, _P, _P, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
+    "panel_debug_wait_limit": (ctypes.c_int64, [ctypes.c_int64]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
 }
@@ -219,6 +220,12 @@ def panel_ga_step(B, P, k, p, pm, lo, hi, sigma, genome_in, fitness, rand, genom
 def panel_df_eval(op, count, a, b, out, stream=None):
     _check(load().panel_df_eval(int(op), int(count), _ptr(a), _ptr(b), _ptr(out),
                                 _stream(stream)), "panel_df_eval")
+
+
+def panel_debug_wait_limit(polls: int) -> int:
+    """Polls after which a pipeline wait of the large-airfoil tensor-core update
+    gives up (diagnostic; <= 0 restores the default).  Returns the previous value."""
+    return int(load().panel_debug_wait_limit(int(polls)))
 
 
 def panel_strerror(status: int) -> str:

@@ -48,6 +48,7 @@ constexpr size_t kMaxDynSmem = 232448;
 cudaError_t launch_adjoint_df(const Batch&, const double*, const double*, const double*,
                               const double*, const double*, const double*, double*,
                               const int32_t*, cudaStream_t, bool lam_weighted = false);
+long long set_wait_limit(long long polls);
 cudaError_t launch_ir_vjp(const Batch&, const float*, const float*, const float*,
                           const int32_t*, const double*, const double*, const double*,
                           const double*, const double*, const double*, double*, int, double,
@@ -101,6 +102,8 @@ const char* panel_strerror(int status) {
     default: return "unknown panel status";
   }
 }
+
+int64_t panel_debug_wait_limit(int64_t polls) { return panel::set_wait_limit(polls); }
 
 const char* panel_version(void) { return "panel-gb300 0.1 (sm_103a)"; }
 

@@ -182,7 +182,9 @@ __global__ void k_ga_step(int B, int P, int k, double p, double pm, const double
 // dL/dg_r = sum_i N_r(t_i) dL/dy_i.  One block per airfoil: the basis of every
 // node into shared memory, then thread r sums over the nodes in the support of
 // control point r in node order (deterministic).  With lr != 0 the genome also
-// takes the ascent step g_r <- min(max(g_r + lr dL/dg_r, lo_r), hi_r).
+// takes the ascent step g_r <- min(max(g_r + lr dL/dg_r, lo_r), hi_r) where
+// dL/dg_r is finite; a gene whose gradient is not (an airfoil whose solve
+// failed has NaN node gradients) keeps its value.
 constexpr int kGradThreads = 128;
 
 __global__ void __launch_bounds__(kGradThreads) k_ga_genome_grad(
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(kGradThreads) k_ga_genome_grad(
       if (q >= 0 && q < 4) acc = fma(Nb[4 * i + q], gy[i], acc);
     }
     if (grad_genome) grad_genome[(int64_t)b * P + r] = acc;
-    if (lr != 0.0) {
+    if (lr != 0.0 && isfinite(acc)) {
       double* g = genome + (int64_t)b * P + r;
       *g = fmin(fmax(*g + lr * acc, lo[r]), hi[r]);
     }

@@ -31,6 +31,8 @@
 // The finished factor has the layout of the one-block kernels: P A = L U in
 // the caller's LU buffer (ld = m), pivots as sequential exchanges, and the
 // 32 x 32 diagonal blocks of L and U replaced by their inverses.
+#include <atomic>
+
 #include "lu_mixed.cuh"
 
 namespace panel {
@@ -340,6 +342,17 @@ __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   invert_diagonal_blocks(a.LU + bt.mat_off[b], m, m);
 }
 
+// Polls of each pipeline wait in k_update_tc before it gives up (a wait that
+// runs out marks the airfoil PANEL_INFO_DEVICE_TIMEOUT instead of hanging).
+// The default is far above any wait of a working pipeline; panel_debug_wait_limit
+// lowers it to exercise that path.
+constexpr long long kDefaultWaitLimit = 1ll << 22;
+static std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
+
+long long set_wait_limit(long long polls) {
+  return g_wait_limit.exchange(polls > 0 ? polls : kDefaultWaitLimit);
+}
+
 // gridDim.y per airfoil: enough blocks for ~4 per SM over the whole batch.
 static int split_for(int B, int per_airfoil_max) {
   const int want = (4 * 152 + B - 1) / max(B, 1);
@@ -357,6 +370,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = ensure_smem(k_update_tc, update_tc_smem());
   if (e != cudaSuccess) return e;
+  const long long spin = g_wait_limit.load();
   k_large_init<<<dim3(B, split_for(B, 64)), 256, 0, s>>>(a);
   for (int k0 = 0; k0 < m_max; k0 += kBW) {
     k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, k0);
@@ -364,7 +378,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     if (rest <= 0) break;
     const int ns = (rest + 127) / 128;
     k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, k0);
-    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 288, update_tc_smem(), s>>>(a, k0);
+    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 288, update_tc_smem(), s>>>(a, k0, spin);
   }
   k_large_finish<<<B, 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -34,9 +34,14 @@
 // apart (stride byte offset).  A generic-to-async proxy fence orders the
 // stores before the MMAs that read them.
 //
-// Every wait is bounded and polls a shared failure flag: a block that gives up
-// sets info[b] = PANEL_INFO_DEVICE_TIMEOUT, stops issuing work, waits
-// (bounded) for its own MMAs, frees its tensor memory and returns.
+// Every pipeline wait is bounded (`spin` polls, a kernel argument) and polls a
+// shared failure flag: a block that gives up stops issuing work, and every
+// role leaves its loop.  The MMA lane commits a final arrival on done_bar on
+// every path, after the last MMA it issued; the block then waits for that
+// arrival with its own bound (kDoneLimit, independent of `spin` and of the
+// failure flag), so that no MMA is still reading shared memory or writing
+// tensor memory when the block sets info[b] = PANEL_INFO_DEVICE_TIMEOUT, frees
+// its tensor memory and returns.
 #include "lu_mixed.cuh"
 
 namespace panel {
@@ -54,7 +59,9 @@ constexpr int kBufBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
 constexpr int kSmemBytes = kStages * kBufBytes + 128;  // stages + barriers + flags
 constexpr uint32_t kTmemCols = 2 * kTN;            // two FP32 accumulators, 128 x 128 each
 constexpr int kThreadsTc = 288;                    // 4 epilogue + 4 producer + 1 MMA warps
-constexpr long long kSpinLimit = 1ll << 22;        // bounded waits (well under a second each)
+// bound of the final wait for the block's own MMAs (they finish in
+// microseconds; the bound only keeps the wait finite)
+constexpr long long kDoneLimit = 1ll << 24;
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22,
@@ -97,22 +104,35 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
       : "memory");
 }
 
-// Waits for the phase with the given parity; false if the bounded spin ran out
-// or another thread of the block has already given up (*fail).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for the phase with the given parity; false if `spin` polls ran out
+// (then sets *fail) or another thread of the block has already given up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* fail,
+                                          long long spin) {
+  for (long long it = 0; it < spin; ++it) {
+    if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 255 && *fail) return false;
   }
   *fail = 1;
+  return false;
+}
+
+// The final wait for the block's own MMAs: bounded, but it does not give up
+// when *fail is set (the MMAs issued before the failure are still running).
+__device__ __forceinline__ bool mbar_wait_done(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < kDoneLimit; ++it)
+    if (mbar_try(bar, parity)) return true;
   return false;
 }
 
@@ -160,7 +180,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0) {
+__global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0,
+                                                              long long spin) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
@@ -237,7 +258,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
     };
     auto store = [&](int q, const float (&ra)[kPer], const float (&rb)[kPer]) -> bool {
       const int st = q % kStages, u = q / kStages;
-      if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail)) return false;
+      if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail, spin)) return false;
       unsigned char* B = smraw + st * kBufBytes;
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
@@ -271,8 +292,8 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
       for (int q = 0; q < nq; ++q) {
         const int st = q % kStages, u = q / kStages;
         const int kc = q % kChunks, tau = q / kChunks, ac = tau & 1, v = tau >> 1;
-        if (kc == 0 && v >= 1 && !mbar_wait(tempty_bar(ac), (v - 1) & 1, fail)) break;
-        if (!mbar_wait(full_bar(st), u & 1, fail)) break;
+        if (kc == 0 && v >= 1 && !mbar_wait(tempty_bar(ac), (v - 1) & 1, fail, spin)) break;
+        if (!mbar_wait(full_bar(st), u & 1, fail, spin)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ac * kTN);
         const uint32_t ah = sbase + st * kBufBytes, al = ah + kOpBytes;
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
     // ---------------- epilogue: A22 -= D ----------------
     for (int tau = 0; tau < my_tiles; ++tau) {
       const int ac = tau & 1, v = tau >> 1;
-      if (!mbar_wait(tfull_bar(ac), v & 1, fail)) break;
+      if (!mbar_wait(tfull_bar(ac), v & 1, fail, spin)) break;
       tc_fence_after();
       int r0, c0;
       tile_rc(tau, r0, c0);
@@ -321,9 +342,11 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
     }
   }
 
-  // every MMA this block issued has completed once done_bar has flipped
+  // every MMA this block issued has completed once done_bar has flipped (the
+  // MMA lane commits it on every path, also after giving up)
   __syncthreads();
-  if (!mbar_wait(done_bar, 0, fail) || *fail) {
+  const bool drained = mbar_wait_done(done_bar, 0);
+  if (!drained || *fail) {
     if (tid == 0) a.info[b] = PANEL_INFO_DEVICE_TIMEOUT;
   }
   tc_fence_before();

@@ -137,3 +137,13 @@ def test_workspace_size_counts_the_work_arrays():
         bd.panel_workspace_size(offs, 0)
     with pytest.raises(ValueError):
         bd.panel_workspace_size(np.array([0, bd.PANEL_N_MAX + 1]), bd.PANEL_MIXED)
+
+
+def test_debug_wait_limit_is_host_state_with_a_default():
+    # the tensor-core update's wait bound is a host-side setting: set, read back
+    # through the previous value, restored by a non-positive argument
+    default = bd.panel_debug_wait_limit(0)
+    assert default == 1 << 22
+    assert bd.panel_debug_wait_limit(5) == default
+    assert bd.panel_debug_wait_limit(-1) == 5
+    assert bd.panel_debug_wait_limit(0) == default

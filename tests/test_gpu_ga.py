@@ -104,8 +104,35 @@ def test_genome_gradient_and_ascent_step(n, lr):
     bd.panel_ga_genome_grad(B, P, n, dev(w), lr, dev(lo), dev(hi), gd, out)
     torch.cuda.synchronize()
     assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-13 * np.max(np.abs(ref))
-    want = np.minimum(np.maximum(g + lr * ref, lo), hi) if lr else g
+    want = oga.ascent_step(g, ref, lr, lo, hi) if lr else g
     assert np.max(np.abs(gd.cpu().numpy() - want)) <= 1e-14
+
+
+def test_ascent_step_leaves_genomes_with_nan_gradients_unchanged():
+    # an airfoil whose solve failed has NaN node gradients: its genome keeps its
+    # values instead of being clamped to a bound, the others take the step
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300 import binding as bd
+    from paper_1511_02166_gb300.ga import default_bounds, default_control_x
+    cx = default_control_x()
+    lo, hi = default_bounds(cx)
+    rng = np.random.default_rng(3)
+    B, P, n, lr = 6, len(cx), 90, 2e-3
+    g = lo + rng.random((B, P)) * (hi - lo)
+    w = rng.normal(size=(B * n, 2)) * 20.0
+    w[2 * n:3 * n] = np.nan            # airfoil 2 failed
+    ref = oga.genome_grad(cx, w, n)
+    want = oga.ascent_step(g, ref, lr, lo, hi)
+    assert np.array_equal(want[2], g[2])
+    dev = lambda a: torch.tensor(a, device="cuda")
+    gd, out = dev(g), torch.empty(B, P, dtype=torch.float64, device="cuda")
+    bd.panel_ga_genome_grad(B, P, n, dev(w), lr, dev(lo), dev(hi), gd, out)
+    torch.cuda.synchronize()
+    got = gd.cpu().numpy()
+    assert np.array_equal(got[2], g[2])
+    assert np.array_equal(np.isnan(out.cpu().numpy()), np.isnan(ref))
+    assert np.max(np.abs(got - want)) <= 1e-14
 
 
 def test_gradient_refined_generation_raises_lift():

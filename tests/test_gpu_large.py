@@ -96,3 +96,34 @@ def test_large_gradient_matches_tangent_oracle():
     ref, info = oracle.cl_gradient(pop.nodes[s], pop.alpha[0])
     assert info == 0
     assert rel_inf(pb.grad.cpu().numpy()[s], ref) < 1e-9
+
+
+def test_update_wait_limit_reports_timeout_and_recovers():
+    # the tensor-core update's pipeline waits are bounded; with the bound cut to
+    # one poll the waits run out on a working pipeline: the call still returns,
+    # every airfoil is either finished correctly or flagged
+    # PANEL_INFO_DEVICE_TIMEOUT (no hang, no partial result passed on), and the
+    # next call with the default bound matches the oracle
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300 import binding as bd
+    pop = _ragged(14, [700, 900, 1100, 130])
+    prev = bd.panel_debug_wait_limit(1)
+    try:
+        pb = _run(pop)
+    finally:
+        bd.panel_debug_wait_limit(0)
+    info = pb.info.cpu().numpy()
+    assert set(info.tolist()) <= {0, bd.INFO_DEVICE_TIMEOUT}
+    assert info[3] == 0                               # no tensor-core update below 640 panels
+    assert np.sum(info == bd.INFO_DEVICE_TIMEOUT) >= 1
+    cl = pb.cl.cpu().numpy()
+    assert np.all(np.isnan(cl[info != 0]))
+    ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    ok = info == 0
+    assert cl_err(cl[ok], ref["cl"][ok]) < 1e-10
+    assert bd.panel_debug_wait_limit(0) == prev       # the default was restored
+    pb.run()
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == 0)
+    _check(pop, pb)

@@ -117,3 +117,30 @@ def test_genome_gradient_is_the_adjoint_of_the_sampler():
             gm[b, r] -= h
             assert abs((L(gp) - L(gm)) / (2 * h) - grad[b, r]) < 1e-8 * max(1.0, abs(grad[b, r]))
     assert np.allclose(grad.sum(axis=1), w[:, 1].reshape(B, n).sum(axis=1), rtol=1e-13, atol=1e-13)
+
+
+def test_ascent_step_moves_along_the_gradient_within_bounds_and_skips_non_finite():
+    # the step increases every unclamped gene by exactly lr times its gradient
+    # (first-order ascent), never leaves [lo, hi], and leaves a gene with a
+    # non-finite gradient untouched (a failed solve's NaN gradient must not snap
+    # the genome to a bound)
+    cx = default_control_x()
+    lo, hi = default_bounds(cx)
+    rng = np.random.default_rng(7)
+    B, P = 5, len(cx)
+    g = lo + rng.random((B, P)) * (hi - lo)
+    d = rng.normal(size=(B, P))
+    d[1, :] = np.nan
+    d[3, 2] = np.inf
+    lr = 1e-3
+    out = ga.ascent_step(g, d, lr, lo, hi)
+    assert np.array_equal(out[1], g[1])
+    assert out[3, 2] == g[3, 2]
+    assert np.all(out >= lo) and np.all(out <= hi)
+    inside = np.isfinite(d) & (g + lr * d > lo) & (g + lr * d < hi)
+    assert inside.sum() > 0.8 * np.isfinite(d).sum()
+    assert np.allclose(out[inside] - g[inside], lr * d[inside], rtol=0, atol=1e-15)
+    big = ga.ascent_step(g, np.where(np.isfinite(d), np.sign(d) * 1e9, d), 1.0, lo, hi)
+    fin = np.isfinite(d)
+    assert np.all(big[fin & (d > 0)] == np.broadcast_to(hi, (B, P))[fin & (d > 0)])
+    assert np.all(big[fin & (d < 0)] == np.broadcast_to(lo, (B, P))[fin & (d < 0)])
