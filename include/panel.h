@@ -69,7 +69,9 @@ typedef enum {
   PANEL_OK = 0,
   PANEL_EINVAL = 1,   /* bad argument: size, NULL pointer, flag combination  */
   PANEL_ENOTSUP = 2,  /* size beyond what the library supports (n_b > PANEL_N_MAX) */
-  PANEL_ECUDA = 3     /* a CUDA launch or device query failed                 */
+  PANEL_ECUDA = 3,    /* a CUDA launch or device query failed                 */
+  PANEL_ESCRATCH = 4  /* panel_solve_noalloc: the batch's factor and pivots do
+                         not fit PANEL_NOALLOC_SCRATCH_BYTES                   */
 } panel_status;
 
 #define PANEL_FP64 0x1
@@ -363,6 +365,55 @@ int panel_df_eval(int op, int count, const double* a, const double* b, double* o
  * on other host threads).  Not part of the paper's method.
  */
 int64_t panel_debug_wait_limit(int64_t polls);
+
+/*
+ * panel_solve_noalloc -- panel_solve for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a memory-management variant
+ * of panel_solve, not a step of the method.
+ *
+ * Who needs it.  panel_solve takes two work arrays from the caller, the factor
+ * buffer LU and the pivots piv.  A caller that cannot call cudaMalloc (or any
+ * allocator) -- a plug-in that runs inside a host application which owns every
+ * device allocation, a real-time loop that must not allocate once it runs, a
+ * binding from a language without a device allocator -- cannot provide them.
+ * This entry point keeps both in one fixed-size array of device memory that
+ * the library itself declares (file scope, static): the CUDA runtime sets it
+ * aside on each GPU when the library's device code is loaded there, and it
+ * stays reserved on that GPU until the process exits.  The call allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine) and runs
+ * the same kernels as panel_solve on the given stream.
+ *
+ * Arguments are those of panel_solve without LU and piv, plus
+ *   node_offsets_host [B+1] i64 in HOST memory, equal to the device array
+ *   node_offsets: the library sums the work array sizes on the host before
+ *   launching anything.  mat_offsets must be panel_plan's for the same offsets.
+ *   flags: PANEL_FP64 or PANEL_MIXED, optionally with PANEL_WITH_ADJOINT (and
+ *   PANEL_INVERSE in PANEL_MIXED mode); PANEL_FACTOR_ONLY and
+ *   PANEL_REUSE_FACTOR are rejected (the factor does not outlive the call).
+ *   n_max must bound every n_b (PANEL_EINVAL otherwise).
+ * Limit.  The factor (sum m_b^2 elements of 4 bytes in PANEL_MIXED mode, 8 in
+ *   PANEL_FP64 mode) and, 256-byte aligned after it, the pivots (sum m_b int32)
+ *   must fit PANEL_NOALLOC_SCRATCH_BYTES (32 MiB: e.g. about 200 airfoils of 200
+ *   panels in PANEL_MIXED mode, or one of 2048); a larger batch returns
+ *   PANEL_ESCRATCH before anything is launched.  Split larger populations into
+ *   several calls, or use panel_solve.
+ * Sharing.  Every call on a GPU uses the same array, which keeps the last
+ *   call's factor and pivots; each call writes all it reads, so nothing needs
+ *   to be cleared between calls.  Calls whose kernels overlap on the GPU (on
+ *   different streams, or from different host threads) race on the array and
+ *   give wrong results: order them on one stream, or synchronise between them.
+ * Set-up.  The first call on each device (the current device of the calling
+ *   thread) looks up the array's device address (cudaGetSymbolAddress) and
+ *   caches it; make that first call before any stream capture on that device.
+ *   A failed look-up returns PANEL_ECUDA.
+ */
+#define PANEL_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int panel_solve_noalloc(int B, int n_max, int flags, const int64_t* node_offsets_host,
+                        const double* nodes, const int64_t* node_offsets,
+                        const int64_t* mat_offsets, const int32_t* order, const double* A64,
+                        const float* A_hi, const float* A_lo, const double* rhs,
+                        const double* vinf, const double* chord, double* u, double* lambda,
+                        int max_iter, double tol, int32_t* info, int32_t* iters, void* stream);
 
 /* Human-readable name of a panel_status value (static string). */
 const char* panel_strerror(int status);

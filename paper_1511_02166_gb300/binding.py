@@ -19,7 +19,8 @@ from . import build as _build
 _lock = threading.Lock()
 _lib = None
 
-PANEL_OK, PANEL_EINVAL, PANEL_ENOTSUP, PANEL_ECUDA = 0, 1, 2, 3
+PANEL_OK, PANEL_EINVAL, PANEL_ENOTSUP, PANEL_ECUDA, PANEL_ESCRATCH = 0, 1, 2, 3, 4
+PANEL_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 PANEL_FP64 = 0x1
 PANEL_MIXED = 0x2
 PANEL_WITH_ADJOINT = 0x10
@@ -60,6 +61,8 @@ SIGNATURES = {
     "panel_ga_step": (_I, [_I, _I, _I, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P]),
     "panel_ga_genome_grad": (_I, [_I, _I, _I, _P, _D, _P, _P, _P, _P, _P]),
     "panel_df_eval": (_I, [_I, _I, _P, _P, _P, _P]),
+    "panel_solve_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                 _P, _I, _D, _P, _P, _P]),
     "panel_debug_wait_limit": (ctypes.c_int64, [ctypes.c_int64]),
     "panel_strerror": (ctypes.c_char_p, [_I]),
     "panel_version": (ctypes.c_char_p, []),
@@ -151,6 +154,20 @@ def panel_solve(B, n_max, flags, nodes, node_offsets, mat_offsets, order, A64, A
                               _ptr(LU), _ptr(piv), _ptr(rhs), _ptr(vinf), _ptr(chord), _ptr(u),
                               _ptr(lam), int(max_iter), float(tol), _ptr(info), _ptr(iters),
                               _stream(stream)), "panel_solve")
+
+
+def panel_solve_noalloc(B, n_max, flags, node_offsets_host, nodes, node_offsets, mat_offsets,
+                        order, A64, A_hi, A_lo, rhs, vinf, chord, u, lam, max_iter, tol, info,
+                        iters, stream=None):
+    """panel_solve with the factor and pivots in the library's static device array
+    (for callers that cannot allocate); node_offsets_host is a host int64 array."""
+    node_offsets_host = np.ascontiguousarray(node_offsets_host, dtype=np.int64)
+    _check(load().panel_solve_noalloc(B, n_max, flags, _ptr(node_offsets_host), _ptr(nodes),
+                                      _ptr(node_offsets), _ptr(mat_offsets), _ptr(order),
+                                      _ptr(A64), _ptr(A_hi), _ptr(A_lo), _ptr(rhs), _ptr(vinf),
+                                      _ptr(chord), _ptr(u), _ptr(lam), int(max_iter), float(tol),
+                                      _ptr(info), _ptr(iters), _stream(stream)),
+           "panel_solve_noalloc")
 
 
 def panel_forces(B, nodes, node_offsets, u, alpha, vinf, chord, info, cp, cl, cl_p, cd_p,

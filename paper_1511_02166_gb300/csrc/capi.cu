@@ -99,6 +99,9 @@ const char* panel_strerror(int status) {
     case PANEL_EINVAL: return "invalid argument";
     case PANEL_ENOTSUP: return "size or mode not supported";
     case PANEL_ECUDA: return "CUDA launch failed";
+    case PANEL_ESCRATCH:
+      return "batch too large for the static work array of panel_solve_noalloc "
+             "(PANEL_NOALLOC_SCRATCH_BYTES)";
     default: return "unknown panel status";
   }
 }
