@@ -6,10 +6,16 @@ panel_assemble (geometry + influence matrix + Kutta row), panel_solve (LU +
 refinement, with the transposed system for the adjoint), panel_forces
 (Cp, Cl) and panel_adjoint (dCl/d(nodes)).  Every airfoil of the batch gets
 Cl and its node gradient, so `value` counts airfoils (solve + gradient) per
-second over all ranks.
+second over all ranks; `solves_per_s` is the same batch without the gradient.
+
+The headline workload is the largest one, 1024 airfoils of 1024..2048 panels
+(`--config` picks another).  The other workloads are measured in the same run
+and reported under `configs`: 64 x 100 panels on the plain FP64 path and mixed,
+4096 x 200 mixed and plain FP64 (the mixed path against the plain FP64 path),
+10 000 airfoils of 64..512 panels, and 4096 x 256 panels.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
-                  [--mode mixed|fp64] [--impl ours|reference]
+                  [--mode mixed|fp64] [--impl ours|reference] [--no-extra-configs]
 
 --impl reference times the FP64 CPU oracle (the plain C restatement of the
 method) on a bounded sample of the same workload on the host cores.
@@ -32,7 +38,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "airfoil solves/sec and dCl/dx gradients/sec on 1 GB300 at <=1e-10 Cl error"
-DEFAULT_CONFIG = "naca_b4096_n200"
+DEFAULT_CONFIG = "large_b1024_n1024_2048"
+# measured besides the headline workload: (workload, precision mode)
+EXTRA_CONFIGS = [("naca_b64_n100", "fp64"), ("naca_b64_n100", "mixed"),
+                 ("naca_b4096_n200", "mixed"), ("naca_b4096_n200", "fp64"),
+                 ("uneven_b10000_n64_512", "mixed"), ("adjoint_b4096_n256", "mixed")]
+# workload whose measurement also times polars, vector-Jacobian products, the
+# viscous correction and GA generations
+EXTRAS_ON = "naca_b4096_n200"
 L2_BYTES = 135528448
 
 # Algorithmic work per unit:
@@ -56,6 +69,27 @@ ADJOINT_F64_FLOP_PER_PAIR = 110
 # FP32 peak from unit counts and the maximum clock: 152 SMs x 128 lanes x 2 x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+# nominal dense TF32 / bf16 tensor rates of the GB300 (1.1 and 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+# what `roofline.achieved` counts for each call (the method's work) ...
+ROOF_WORK = {
+    "mixed": {"assemble": "%d FP64-class flops per (control point, panel) pair"
+                          % ASSEMBLY_F64_FLOP_PER_PAIR,
+              "factor": "2/3 m^3 flops per airfoil (m = n + 1)",
+              "refine": "8 B per matrix entry + 16 B per entry and refinement step",
+              "forces": "40 B per node",
+              "adjoint": "%d FP64-class flops per pair" % ADJOINT_F64_FLOP_PER_PAIR},
+    "fp64": {"assemble": "%d FP64 flops per pair" % ASSEMBLY_F64_FLOP_PER_PAIR,
+             "solve": "2/3 m^3 FP64 flops per airfoil",
+             "forces": "40 B per node",
+             "adjoint": "%d FP64 flops per pair" % ADJOINT_F64_FLOP_PER_PAIR},
+}
+# ... and what `roofline.issue_frac` counts (the work the kernels execute)
+ROOF_IMPL_WORK = {
+    "assemble": "%d FP32 flops per pair of the double-float evaluation" % ASSEMBLY_FLOP_PER_PAIR,
+    "adjoint": "%d FP32 flops per pair of the double-float evaluation" % ADJOINT_FLOP_PER_PAIR,
+    "factor": "3 TF32 products per multiply-add (3xTF32) in the tensor-core update",
+}
 
 
 def _peaks():
@@ -225,6 +259,56 @@ def whole_job_rate(world, units_per_rank, ms):
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
+def gradient_stride(n_max):
+    """Node stride of the oracle's sampled gradient: 1 (the whole gradient) up to
+    640 panels; above, about 96 nodes per airfoil (the forward-tangent gradient
+    costs O(n^3) per airfoil, a minute and more at 1500-2000 panels)."""
+    return 1 if n_max <= 640 else max(2, int(n_max) // 96)
+
+
+def oracle_time(sub, stride):
+    """Wall seconds of the FP64 oracle on the airfoils of `sub` (OpenMP across
+    airfoils): the solve (oracle.evaluate_batch) and the forward-tangent dCl/dx.
+
+    With stride 1 both are timed as they are.  With stride s > 1 the gradient is
+    timed on the nodes k = 0, s, 2s, ... only, once with stride s and once with
+    2s: each node's two tangents cost the same and are independent, so the
+    gradient's time is F + G / s (F the assembly, LU and solve inside the
+    gradient call, G the tangents of all nodes), and the two timings give F and
+    G.  Returns (measured seconds, seconds of the solve + whole gradient)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
+    t_eval = time.perf_counter() - t0
+    if stride <= 1:
+        t0 = time.perf_counter()
+        oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
+        t_grad = time.perf_counter() - t0
+        return t_eval + t_grad, t_eval + t_grad
+    t0 = time.perf_counter()
+    oracle.cl_gradient_strided_batch(sub.nodes, sub.offsets, sub.alpha, stride)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.cl_gradient_strided_batch(sub.nodes, sub.offsets, sub.alpha, 2 * stride)
+    t2 = time.perf_counter() - t0
+    G = max(2.0 * stride * (t1 - t2), 0.0)
+    F = max(t1 - G / stride, 0.0)
+    return t_eval + t1 + t2, t_eval + F + G
+
+
+def _sample_text(sub, spec, config, stride, threads, measured, full):
+    what = ("%d of %d airfoils of %s (solve + forward-tangent dCl/dx), %d threads"
+            % (sub.batch, spec.batch, config, threads))
+    if stride > 1:
+        what += ("; the gradient timed on every %d-th and every %d-th node and extended "
+                 "linearly to all nodes (each node's tangents cost the same): %.1f s "
+                 "measured for an estimated %.1f s of whole-gradient work"
+                 % (stride, 2 * stride, measured, full))
+    else:
+        what += ", %.1f s" % measured
+    return what
+
+
 def cpu_baseline(config, seconds=15.0, max_airfoils=None):
     import oracle
     from paper_1511_02166_gb300 import inputs
@@ -232,23 +316,20 @@ def cpu_baseline(config, seconds=15.0, max_airfoils=None):
     spec = inputs.SPECS[config]
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = oracle.max_threads()
-    # grow the sample until it takes about `seconds`
-    k = 4 * threads
-    done, elapsed = 0, 0.0
+    stride = gradient_stride(spec.n_max)
+    # grow the sample until it takes about `seconds` (one airfoil per thread at
+    # least)
+    k = threads if stride > 1 else 4 * threads
     pop_all = inputs.make_population(spec, batch=min(spec.batch, max_airfoils or spec.batch))
     while True:
         sub = pop_all.subset(np.arange(min(k, pop_all.batch)))
-        t0 = time.perf_counter()
-        oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
-        oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
-        dt = time.perf_counter() - t0
-        done, elapsed = sub.batch, dt
-        if dt > seconds / 4 or sub.batch >= pop_all.batch:
+        measured, full = oracle_time(sub, stride)
+        if measured > seconds / 4 or sub.batch >= pop_all.batch:
             break
-        k = min(pop_all.batch, int(k * max(2.0, seconds / 4 / max(dt, 1e-3))))
+        k = min(pop_all.batch, int(k * max(2.0, seconds / 4 / max(measured, 1e-3))))
     # library-solve reference: LAPACK (numpy.linalg.solve) on the oracle's assembled
     # matrices of the first airfoils of the sample, the solve alone
-    ls = pop_all.subset(np.arange(min(64, pop_all.batch)))
+    ls = pop_all.subset(np.arange(min(64, sub.batch, pop_all.batch)))
     mats = []
     for b in range(ls.batch):
         s0, s1 = ls.offsets[b], ls.offsets[b + 1]
@@ -257,10 +338,9 @@ def cpu_baseline(config, seconds=15.0, max_airfoils=None):
     for M, rhs in mats:
         np.linalg.solve(M, rhs)
     lapack = ls.batch / (time.perf_counter() - t0)
-    return {"value": done / elapsed, "unit": "airfoils/s", "cores": int(threads),
+    return {"value": sub.batch / full, "unit": "airfoils/s", "cores": int(threads),
             "host_cores": int(cores), "kind": "oracle",
-            "sample": "%d of %d airfoils of %s (solve + forward-tangent gradient), %.1f s"
-                      % (done, spec.batch, config, elapsed),
+            "sample": _sample_text(sub, spec, config, stride, threads, measured, full),
             "lapack_solves_per_s": lapack,
             "lapack_sample": "numpy.linalg.solve of the oracle's assembled systems, first %d "
                              "airfoils" % ls.batch}
@@ -269,8 +349,11 @@ def cpu_baseline(config, seconds=15.0, max_airfoils=None):
 def run_reference(args):
     """The oracle as it stands on the host cores: W untimed and K timed steps,
     each the solve and forward-tangent gradient of the same bounded sample of
-    the workload (sized so that the whole run takes about args.ref_seconds).
-    Under torchrun only rank 0 runs; the other ranks exit without work."""
+    the workload (sized so that the whole run takes about args.ref_seconds;
+    above 640 panels the gradient is sampled by node and extended as
+    oracle_time describes).  `value` is airfoils per second of the whole work,
+    `ms_per_step` the measured wall time of a step.  Under torchrun only rank 0
+    runs; the other ranks exit without work."""
     world, rank, _ = _dist()
     if rank != 0:
         return
@@ -278,35 +361,33 @@ def run_reference(args):
     from paper_1511_02166_gb300 import inputs
     spec = inputs.SPECS[args.config]
     threads = oracle.max_threads()
+    stride = gradient_stride(spec.n_max)
     pop_all = inputs.make_population(spec)
     per_step = max(1.0, args.ref_seconds / max(args.steps + args.warmup, 1))
 
-    def one(sub):
-        t0 = time.perf_counter()
-        oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
-        oracle.cl_gradient_batch(sub.nodes, sub.offsets, sub.alpha)
-        return time.perf_counter() - t0
-
     # size the sample: grow it until one step takes about per_step seconds
-    k = 2 * threads
+    # (one airfoil per thread at least)
+    k = threads if stride > 1 else 2 * threads
     while True:
         sub = pop_all.subset(np.arange(min(k, pop_all.batch)))
-        dt = one(sub)
-        if dt > per_step / 2 or sub.batch >= pop_all.batch:
+        measured, _ = oracle_time(sub, stride)
+        if measured > per_step / 2 or sub.batch >= pop_all.batch:
             break
-        k = min(pop_all.batch, int(k * max(2.0, per_step / max(dt, 1e-3))))
+        k = min(pop_all.batch, int(k * max(2.0, per_step / max(measured, 1e-3))))
     for _ in range(args.warmup):
-        one(sub)
-    times = [one(sub) for _ in range(args.steps)]
-    sec = float(np.mean(times))
-    value = sub.batch / sec
-    sample = ("%d of %d airfoils of %s per step (solve + forward-tangent gradient), "
-              "%d threads" % (sub.batch, spec.batch, args.config, threads))
+        oracle_time(sub, stride)
+    runs = [oracle_time(sub, stride) for _ in range(args.steps)]
+    measured = float(np.mean([r[0] for r in runs]))
+    full = float(np.mean([r[1] for r in runs]))
+    value = sub.batch / full
+    sample = _sample_text(sub, spec, args.config, stride, threads, measured, full)
     out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "impl": "reference",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": measured * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.config, "batch_per_step": int(sub.batch)},
+           "config": {"workload": args.config, "batch_per_step": int(sub.batch),
+                      "gradient_node_stride": stride,
+                      "whole_work_s_per_step": full},
            "cpu_baseline": {"value": value, "unit": "airfoils/s", "cores": int(threads),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "airfoils/s", "h2d_bytes_per_step": 0,
@@ -317,53 +398,119 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_ours(args):
-    import torch
+def call_work(mode, sizes, iters_mean):
+    """Per library call: (bound, algorithmic work of the method, implementation
+    work or None, unit of the work) for one batch with panel counts `sizes`.
 
-    from paper_1511_02166_gb300 import binding as bd
-    from paper_1511_02166_gb300 import inputs
-    from paper_1511_02166_gb300.solver import PanelBatch
+    The method's work: the panel integral's pairs at the FP64-class flop count
+    of its formulas (ASSEMBLY_F64_FLOP_PER_PAIR, ADJOINT_F64_FLOP_PER_PAIR),
+    2/3 m^3 flops for the LU, the refinement's and the forces' bytes.  The
+    implementation's work (issue efficiency of the mixed path): the FP32 flops
+    the double-float kernels execute per pair, and three TF32 products per
+    multiply-add in the tensor-core update of airfoils above 640 panels."""
+    sizes = np.asarray(sizes, dtype=np.float64)
+    m = sizes + 1
+    pairs = float((sizes ** 2).sum())
+    m2 = float((m ** 2).sum())
+    m3_small = float((m[m <= 640] ** 3).sum())
+    m3_large = float((m[m > 640] ** 3).sum())
+    lu = 2.0 / 3.0 * (m3_small + m3_large)
+    if mode == "mixed":
+        factor_bound = "tensor" if m3_large > m3_small else "alu"
+        return {"assemble": ("alu", pairs * ASSEMBLY_F64_FLOP_PER_PAIR,
+                             pairs * ASSEMBLY_FLOP_PER_PAIR),
+                "factor": (factor_bound, lu,
+                           2.0 / 3.0 * (m3_small + 3.0 * m3_large)),
+                "refine": ("hbm", m2 * (8.0 + 16.0 * iters_mean), None),
+                "forces": ("hbm", float(sizes.sum()) * 40.0, None),
+                "adjoint": ("alu", pairs * ADJOINT_F64_FLOP_PER_PAIR,
+                            pairs * ADJOINT_FLOP_PER_PAIR)}
+    return {"assemble": ("alu", pairs * ASSEMBLY_F64_FLOP_PER_PAIR, None),
+            "solve": ("alu", lu, None),
+            "forces": ("hbm", float(sizes.sum()) * 40.0, None),
+            "adjoint": ("alu", pairs * ADJOINT_F64_FLOP_PER_PAIR, None)}
 
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
 
-    spec_r = rank_population_spec(inputs.SPECS[args.config], rank)
-    pop = inputs.make_population(spec_r, batch=args.batch)
-    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=args.mode, device=dev,
-                    max_iter=args.max_iter, tol=args.tol)
-    tuned = pb.autotune() if (args.autotune and args.mode == "mixed") else {}
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+def peaks_by_bound(mode):
+    """Roofline denominators: (value, unit, source) per bound."""
+    pk = _peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    bf16 = pk.get("bf16_tflops")
+    if bf16:
+        tf32 = float(bf16) * TF32_OVER_BF16
+        tsrc = ("TF32 dense = measured cuBLAS bf16 burst (MEASURED_PEAKS.json bf16_tflops "
+                "%.1f) x nominal TF32/bf16 ratio 1.1/2.25, of measured" % float(bf16))
+    else:
+        tf32 = 1900.0 * TF32_OVER_BF16
+        tsrc = "TF32 dense = fallback bf16 1.9 PFLOP/s x nominal 1.1/2.25, of fallback"
+    alu = (FP32_PEAK_TFLOPS, "TFLOP/s",
+           "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (from unit counts)")
+    if mode == "fp64":
+        alu = (FP64_PEAK_TFLOPS, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s")
+    return {"alu": alu, "tensor": (tf32, "TFLOP/s", tsrc),
+            "hbm": (hbm, "GB/s", "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")}
 
-    def timed_ms(fn, reps, warmup):
-        """Mean CUDA-event time of fn() on the launching stream over `reps` calls
-        after `warmup` untimed ones, with the L2 flushed before each call."""
+
+class Timer:
+    """CUDA-event timing on the launching stream, with the L2 flushed (a write
+    of twice its size) before every timed call, outside the events."""
+
+    def __init__(self, torch, dev, stream):
+        self.torch = torch
+        self.stream = stream
+        self.flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush(self):
+        self.flush_buf.zero_()
+
+    def times(self, fn, reps, warmup):
+        torch = self.torch
         ts = []
         for it in range(warmup + reps):
-            flush.zero_()
+            self.flush()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(self.stream)
             fn()
-            e1.record(stream)
+            e1.record(self.stream)
             e1.synchronize()
             if it >= warmup:
                 ts.append(e0.elapsed_time(e1))
-        return float(np.mean(ts)), len(ts)
+        return ts
 
-    if args.mode == "mixed":
+    def mean(self, fn, reps, warmup):
+        return float(np.mean(self.times(fn, reps, warmup)))
+
+
+def measure_workload(name, mode, args, ctx, headline=False, extras=False):
+    """Time one workload: the whole step (solve + dCl/dx) and the solve alone
+    (assemble, solve, forces), each replayed from a captured CUDA graph, plus a
+    per-call breakdown from eager steps with events around every library call.
+    The headline workload also gets the clock record and the end-to-end figure
+    through host buffers; `extras` adds the polar, vector-Jacobian, viscous and
+    GA timings."""
+    import torch
+
+    from paper_1511_02166_gb300 import inputs
+    from paper_1511_02166_gb300.solver import PanelBatch
+
+    world, rank, dev, timer = ctx["world"], ctx["rank"], ctx["dev"], ctx["timer"]
+    spec_r = rank_population_spec(inputs.SPECS[name], rank)
+    pop = inputs.make_population(spec_r, batch=args.batch if headline else None)
+    B = pop.batch
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode=mode, device=dev,
+                    max_iter=args.max_iter, tol=args.tol)
+    tuned = pb.autotune() if (args.autotune and mode == "mixed") else {}
+    if mode == "mixed":
         names = ["assemble", "factor", "refine", "forces", "adjoint"]
         fns = [pb.assemble, lambda: pb.solve(stage="factor"),
                lambda: pb.solve(with_adjoint=True, stage="refine"), pb.forces, pb.adjoint]
     else:
         names = ["assemble", "solve", "forces", "adjoint"]
         fns = [pb.assemble, lambda: pb.solve(with_adjoint=True), pb.forces, pb.adjoint]
+    stream = timer.stream
 
-    def step(evs=None):
+    def eager_step(evs=None):
         for k, fn in enumerate(fns):
             if evs is not None:
                 evs[k][0].record(stream)
@@ -372,10 +519,21 @@ def run_ours(args):
                 evs[k][1].record(stream)
 
     for _ in range(args.warmup):
-        step()
+        eager_step()
     torch.cuda.synchronize()
     info = pb.info.cpu().numpy()
     iters = pb.iters.cpu().numpy()
+
+    # per-call breakdown (events around every library call of eager steps)
+    kern = {nm: [] for nm in names}
+    for _ in range(max(2, args.steps // 2)):
+        timer.flush()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in names]
+        eager_step(evs)
+        torch.cuda.synchronize()
+        for k, nm in enumerate(names):
+            kern[nm].append(evs[k][0].elapsed_time(evs[k][1]))
 
     def barrier():
         if world > 1:
@@ -383,84 +541,131 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # per-call breakdown (CUDA events around every library call), untimed for `value`
-    kern = {nm: [] for nm in names}
-    for _ in range(max(2, args.steps // 2)):
-        flush.zero_()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in names]
-        step(evs)
-        torch.cuda.synchronize()
-        for k, nm in enumerate(names):
-            kern[nm].append(evs[k][0].elapsed_time(evs[k][1]))
+    # the solve alone (assemble + solve + forces), replayed from its own graph
+    if args.graph:
+        pb.capture(with_grad=False)
+        solve_step = pb.step
+    else:
+        def solve_step():
+            pb.run(with_grad=False)
+    barrier()
+    ms_solve = max_over_ranks(timer.mean(solve_step, args.steps, args.warmup), dev)
 
+    # the whole step (solve + dCl/dx)
     if args.graph:
         pb.capture(with_grad=True)
         run_step = pb.step
     else:
-        run_step = step
+        run_step = eager_step
     for _ in range(args.warmup):
         run_step()
     torch.cuda.synchronize()
-
-    clk = ClockSampler(local)
-    clk.start()
-    totals = []
+    clk = None
+    if headline:
+        clk = ClockSampler(ctx["local"])
+        clk.start()
     barrier()
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed events
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        run_step()
-        e1.record(stream)
-        e1.synchronize()
-        totals.append(e0.elapsed_time(e1))
+    totals = timer.times(run_step, args.steps, 0)
     barrier()
-    clocks = clk.stop()
+    clocks = clk.stop() if clk is not None else None
     ms = max_over_ranks(float(np.mean(totals)), dev)
+
+    out = {"workload": name, "mode": mode, "batch_per_gpu": B,
+           "n_min": int(pop.sizes.min()), "n_max": int(pop.sizes.max()),
+           "ms_per_step": ms, "solves_and_gradients_per_s": whole_job_rate(world, B, ms),
+           "ms_per_solve_step": ms_solve, "solves_per_s": whole_job_rate(world, B, ms_solve),
+           "size_buckets": len(pb.buckets), "inverse_buckets": int(sum(pb.inverse)),
+           "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())}
+           if mode == "mixed" else None,
+           "info_nonzero": int((info != 0).sum()),
+           "launches_per_step": pb.launches_per_step(with_grad=True)}
+
+    # rooflines of every call, on the method's work (and the implementation's
+    # issue efficiency where it differs)
+    kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
+    work = call_work(mode, pop.sizes, float(iters.mean()) if mode == "mixed" else 0.0)
+    pk = peaks_by_bound(mode)
+    kernels = {}
+    for nm in names:
+        bound, w, w_impl = work[nm]
+        sec = kms[nm] * 1e-3
+        peak, unit, _ = pk[bound]
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ent = {"ms": kms[nm], "bound": bound, "achieved": w / sec / scale, "peak": peak,
+               "unit": unit, "frac": w / sec / scale / peak}
+        if w_impl is not None and w_impl != w:
+            ent["issue_frac"] = w_impl / sec / scale / peak
+        kernels[nm] = ent
+    out["kernels"] = kernels
+    dom = max(kms, key=kms.get)
+    dk = kernels[dom]
+    digest = kernel_source_digest(dom, mode)
+    roof = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+            "unit": dk["unit"], "frac": dk["frac"],
+            "traffic": recorded_traffic(dom, name, mode, B, digest),
+            "traffic_unit": "bytes per launch", "kernel_digest": digest,
+            "work": ROOF_WORK[mode][dom], "peak_source": pk[dk["bound"]][2]}
+    if "issue_frac" in dk:
+        roof["issue_frac"] = dk["issue_frac"]
+        roof["issue_work"] = ROOF_IMPL_WORK[dom]
+    out["roofline"] = roof
+
+    if headline:
+        out["clocks"] = clocks
+        # ---- e2e through the public API with host buffers ----
+        nodes_h = torch.from_numpy(pop.nodes).pin_memory()
+        alpha_h = torch.from_numpy(pop.alpha).pin_memory()
+        cl_h = torch.empty(B, dtype=torch.float64).pin_memory()
+        grad_h = torch.empty(pop.nodes.shape, dtype=torch.float64).pin_memory()
+        h2d = nodes_h.numel() * 8 + alpha_h.numel() * 8
+        d2h = cl_h.numel() * 8 + grad_h.numel() * 8
+        e2e_ms = []
+        for it in range(args.warmup + args.steps):
+            timer.flush()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pb.nodes.copy_(nodes_h, non_blocking=True)
+            pb.alpha.copy_(alpha_h, non_blocking=True)
+            run_step()
+            cl_h.copy_(pb.cl, non_blocking=True)
+            grad_h.copy_(pb.grad, non_blocking=True)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = max_over_ranks(float(np.mean(e2e_ms)), dev)
+        out["e2e"] = {"value": whole_job_rate(world, B, e2e), "unit": "airfoils/s",
+                      "ms_per_step": e2e, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+        out["autotuned"] = tuned
+    if extras and mode == "mixed":
+        out.update(measure_extras(pb, pop, args, ctx))
+    del pb
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_extras(pb, pop, args, ctx):
+    """Polars, vector-Jacobian products, the viscous correction and GA
+    generations on a solved population (the calls of the library beyond the
+    solve and the Cl gradient)."""
+    import torch
+    world, rank, dev, timer = ctx["world"], ctx["rank"], ctx["dev"], ctx["timer"]
     B = pop.batch
-    value = whole_job_rate(world, B, ms)
-
-    # ---- e2e through the public API with host buffers ----
-    nodes_h = torch.from_numpy(pop.nodes).pin_memory()
-    alpha_h = torch.from_numpy(pop.alpha).pin_memory()
-    cl_h = torch.empty(B, dtype=torch.float64).pin_memory()
-    grad_h = torch.empty(pop.nodes.shape, dtype=torch.float64).pin_memory()
-    h2d = nodes_h.numel() * 8 + alpha_h.numel() * 8
-    d2h = cl_h.numel() * 8 + grad_h.numel() * 8
-    e2e_ms = []
-    for it in range(args.warmup + args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pb.nodes.copy_(nodes_h, non_blocking=True)
-        pb.alpha.copy_(alpha_h, non_blocking=True)
-        run_step()
-        cl_h.copy_(pb.cl, non_blocking=True)
-        grad_h.copy_(pb.grad, non_blocking=True)
-        torch.cuda.synchronize()
-        if it >= args.warmup:
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = max_over_ranks(float(np.mean(e2e_ms)), dev)
-
-    # ---- polar: Cl at POLAR_ANGLES angles per airfoil from one factorisation ----
-    polar = None
-    if args.mode == "mixed" and args.polar > 0:
+    reps = max(2, args.steps // 2)
+    res = {}
+    pb.graph = None
+    if args.polar > 0:
         K = int(args.polar)
         alphas = torch.linspace(math.radians(-4.0), math.radians(10.0), K, dtype=torch.float64,
                                 device=dev).repeat(B, 1).contiguous()
         pb.polar(alphas)
         torch.cuda.synchronize()
-        # assemble + factor + two basis refinements + combination
-        pm, _ = timed_ms(lambda: pb.polar(alphas), max(2, args.steps // 2), args.warmup)
-        polar = {"angles": K, "ms": pm, "cl_per_s": world * B * K / (pm * 1e-3),
-                 "airfoil_polars_per_s": world * B / (pm * 1e-3),
-                 "what": "panel_assemble + panel_solve(factor) + panel_polar per step"}
-
-    # ---- vector-Jacobian product of (Cl, u, Cp) on the solved population ----
-    vjp = None
-    if args.mode == "mixed" and args.vjp:
+        pm = timer.mean(lambda: pb.polar(alphas), reps, args.warmup)
+        res["polar"] = {"angles": K, "ms": pm, "cl_per_s": world * B * K / (pm * 1e-3),
+                        "airfoil_polars_per_s": world * B / (pm * 1e-3),
+                        "what": "panel_assemble + panel_solve(factor) + panel_polar per step"}
+    if args.vjp:
         gen = torch.Generator(device=dev)
         gen.manual_seed(1511)
         w_cl = torch.randn(B, dtype=torch.float64, device=dev, generator=gen)
@@ -469,34 +674,28 @@ def run_ours(args):
         pb.run()
         pb.vjp(w_cl, w_u, w_cp)
         torch.cuda.synchronize()
-        # transposed refinement + dM/dx contraction
-        vm, _ = timed_ms(lambda: pb.vjp(w_cl, w_u, w_cp), max(2, args.steps // 2), args.warmup)
-        vjp = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
-               "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
-
-    # ---- viscous correction (Thwaites boundary layer, drag, L/D) on the solved population ----
-    viscous = None
-    if args.mode == "mixed" and args.viscous:
+        vm = timer.mean(lambda: pb.vjp(w_cl, w_u, w_cp), reps, args.warmup)
+        res["vjp"] = {"ms": vm, "products_per_s": world * B / (vm * 1e-3),
+                      "what": "panel_vjp of w_cl.Cl + w_u.u + w_cp.Cp per airfoil, after a solve"}
+    if args.viscous:
         pb.run()
         pb.viscous(1.0e6)
         torch.cuda.synchronize()
-        vm_, _ = timed_ms(pb.viscous, max(2, args.steps // 2), args.warmup)
+        vm_ = timer.mean(pb.viscous, reps, args.warmup)
         vbytes = float(pop.sizes.sum()) * VISCOUS_BYTES_PER_NODE
         sep = pb.sep.cpu().numpy()
-        viscous = {"ms": vm_, "airfoils_per_s": world * B / (vm_ * 1e-3),
-                   "reynolds": 1.0e6, "bound": "hbm", "achieved_gbs": vbytes / (vm_ * 1e-3) / 1e9,
-                   "attached_surfaces": float((sep == -1).mean()),
-                   "what": "panel_viscous: Thwaites march, separation, Squire-Young and friction "
-                           "drag, L/D per airfoil, after a solve"}
-
-    # ---- genetic optimisation: sample -> evaluate -> select/crossover/mutate on the device ----
-    ga = None
-    if args.mode == "mixed" and args.ga > 0:
+        res["viscous"] = {"ms": vm_, "airfoils_per_s": world * B / (vm_ * 1e-3),
+                          "reynolds": 1.0e6, "bound": "hbm",
+                          "achieved_gbs": vbytes / (vm_ * 1e-3) / 1e9,
+                          "attached_surfaces": float((sep == -1).mean()),
+                          "what": "panel_viscous: Thwaites march, separation, Squire-Young and "
+                                  "friction drag, L/D per airfoil, after a solve"}
+    if args.ga > 0:
         from paper_1511_02166_gb300.ga import GeneticOptimizer
         n_ga = int(np.clip(int(pop.sizes.max()), 16, 1024))
         opt = GeneticOptimizer(B=B - (B % 2), n=n_ga, alpha=math.radians(4.0), seed=1511 + rank,
                                device=dev)
-        opt.evaluate()  # nodes of the first population, then pick each bucket's factorisation
+        opt.evaluate()
         if args.autotune:
             opt.pb.autotune()
         for _ in range(args.warmup):
@@ -508,85 +707,80 @@ def run_ours(args):
             opt.evaluate()  # panel_ga_sample + assemble + solve + forces + viscous
             opt.step()      # uniforms + panel_ga_step
 
-        gm, ngen = timed_ms(generation, int(args.ga), 0)
+        gts = timer.times(generation, int(args.ga), 0)
+        gm = float(np.mean(gts))
         best = float(torch.nan_to_num(opt.evaluate(), nan=-np.inf).max())
-        ga = {"population": opt.B, "nodes": n_ga, "control_points": opt.P, "generations": ngen,
-              "fitness": "lift over drag (Re 1e6, alpha 4 deg)", "best_fitness": best,
-              "ms_per_generation": gm, "generations_per_s": 1e3 / gm,
-              "airfoils_per_s": world * opt.B / (gm * 1e-3),
-              "what": "panel_ga_sample + assemble + solve + forces + panel_viscous + "
-                      "panel_ga_step per generation"}
+        res["ga"] = {"population": opt.B, "nodes": n_ga, "control_points": opt.P,
+                     "generations": len(gts), "fitness": "lift over drag (Re 1e6, alpha 4 deg)",
+                     "best_fitness": best, "ms_per_generation": gm,
+                     "generations_per_s": 1e3 / gm,
+                     "airfoils_per_s": world * opt.B / (gm * 1e-3),
+                     "what": "panel_ga_sample + assemble + solve + forces + panel_viscous + "
+                             "panel_ga_step per generation"}
+        del opt
+    return res
 
-    # ---- roofline of the dominant kernel ----
-    kms = {nm: float(np.mean(v)) for nm, v in kern.items()}
-    sizes = pop.sizes.astype(np.float64)
-    pairs = float((sizes ** 2).sum())
-    m2 = float(((sizes + 1) ** 2).sum())
-    m3 = float(((sizes + 1) ** 3).sum())
-    peaks = _peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    it_mean = float(iters.mean())
-    if args.mode == "mixed":
-        work = {"assemble": ("alu", pairs * ASSEMBLY_FLOP_PER_PAIR),
-                "factor": ("alu", 2.0 / 3.0 * m3),
-                "refine": ("hbm", m2 * (8.0 + 16.0 * it_mean)),
-                "forces": ("hbm", float(sizes.sum()) * 40.0),
-                "adjoint": ("alu", pairs * ADJOINT_FLOP_PER_PAIR)}
-        alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-    else:
-        work = {"assemble": ("alu", pairs * ASSEMBLY_F64_FLOP_PER_PAIR),
-                "solve": ("alu", 2.0 / 3.0 * m3),
-                "forces": ("hbm", float(sizes.sum()) * 40.0),
-                "adjoint": ("alu", pairs * ADJOINT_F64_FLOP_PER_PAIR)}
-        alu_peak, alu_src = FP64_PEAK_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
-    kernels = {}
-    for nm in names:
-        bound, w = work[nm]
-        sec = kms[nm] * 1e-3
-        if bound == "alu":
-            ach, peak, unit = w / sec / 1e12, alu_peak, "TFLOP/s"
-        else:
-            ach, peak, unit = w / sec / 1e9, hbm, "GB/s"
-        kernels[nm] = {"ms": kms[nm], "bound": bound, "achieved": ach, "peak": peak,
-                       "unit": unit, "frac": ach / peak}
-    dom = max(kms, key=kms.get)
-    dk = kernels[dom]
-    digest = kernel_source_digest(dom, args.mode)
-    traffic = recorded_traffic(dom, args.config, args.mode, B, digest)
-    roofline = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"],
-                "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"],
-                "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel_digest": digest,
-                "peak_source": alu_src if dk["bound"] == "alu"
-                else "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    launches_per_step = pb.launches_per_step(with_grad=True)
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = {"world": world, "rank": rank, "local": local, "dev": dev,
+           "timer": Timer(torch, dev, torch.cuda.current_stream())}
+
+    head = measure_workload(args.config, args.mode, args, ctx, headline=True,
+                            extras=args.extras_on == args.config)
+    configs = {}
+    if args.extra_configs:
+        for name, mode in EXTRA_CONFIGS:
+            if (name, mode) == (args.config, args.mode):
+                continue
+            configs["%s/%s" % (name, mode)] = measure_workload(
+                name, mode, args, ctx, extras=(args.extras_on == name and mode == "mixed"))
+        c2m, c2f = configs.get("naca_b4096_n200/mixed"), configs.get("naca_b4096_n200/fp64")
+        if c2m and c2f:
+            configs["naca_b4096_n200/mixed_over_fp64"] = {
+                "solves_and_gradients": c2m["solves_and_gradients_per_s"]
+                / c2f["solves_and_gradients_per_s"],
+                "solves": c2m["solves_per_s"] / c2f["solves_per_s"]}
+
+    B = head["batch_per_gpu"]
+    value = head["solves_and_gradients_per_s"]
     out = {"metric": METRIC, "value": value, "unit": "airfoils/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+df32" if args.mode == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": args.config, "batch_per_gpu": B, "mode": args.mode,
                       "subset": args.batch is not None,
-                      "n_min": int(sizes.min()), "n_max": int(sizes.max()),
+                      "n_min": head["n_min"], "n_max": head["n_max"],
                       "l2": "flushed before every timed step (%d MB write)"
-                            % (flush.numel() * 4 // 2**20),
+                            % (ctx["timer"].flush_buf.numel() * 4 // 2**20),
                       "max_iter": args.max_iter, "tol": args.tol,
-                      "graph": bool(args.graph), "size_buckets": len(pb.buckets),
-                      "inverse_buckets": int(sum(pb.inverse)),
+                      "graph": bool(args.graph), "size_buckets": head["size_buckets"],
+                      "inverse_buckets": head["inverse_buckets"],
                       "parallelism": "dp%d (independent airfoils)" % world},
+           "what": "value: airfoils per second with Cl and dCl/dx (assemble, LU, refinement of "
+                   "the forward and transposed systems, forces, adjoint contraction); "
+                   "solves_per_s: assemble, LU, refinement, forces only",
+           "solves_per_s": head["solves_per_s"],
            "gradients_per_s": value,
-           "polar": polar,
-           "vjp": vjp,
-           "ga": ga,
-           "viscous": viscous,
-           "kernels": kernels,
-           "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())},
-           "info_nonzero": int((info != 0).sum()),
-           "e2e": {"value": whole_job_rate(world, B, e2e), "unit": "airfoils/s",
-                   "ms_per_step": e2e, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)},
-           "roofline": roofline,
-           "gpu_launches": launches_per_step * args.steps,
-           "clocks": clocks}
+           "ms_per_solve_step": head["ms_per_solve_step"],
+           "kernels": head["kernels"],
+           "refinement_iters": head["refinement_iters"],
+           "info_nonzero": head["info_nonzero"],
+           "e2e": head["e2e"],
+           "roofline": head["roofline"],
+           "gpu_launches": head["launches_per_step"] * args.steps,
+           "clocks": head["clocks"],
+           "configs": configs}
+    for k in ("polar", "vjp", "viscous", "ga"):
+        if k in head:
+            out[k] = head[k]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.config, seconds=args.cpu_seconds)
     if rank == 0:
@@ -620,6 +814,11 @@ def main():
     ap.add_argument("--ga", type=int, default=5,
                     help="also time this many generations of the device genetic optimiser on a "
                          "population of the configured batch (0: skip)")
+    ap.add_argument("--no-extra-configs", dest="extra_configs", action="store_false",
+                    help="measure only the --config workload")
+    ap.add_argument("--extras-on", default=EXTRAS_ON,
+                    help="workload on which polars, vector-Jacobian products, the viscous "
+                         "correction and the GA are timed")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the calls one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")

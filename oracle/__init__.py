@@ -85,6 +85,9 @@ def _bind(lib):
     lib.oracle_cl_gradient_batch.restype = None
     lib.oracle_cl_gradient_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D, _D, _I32,
                                              ctypes.c_int]
+    lib.oracle_cl_gradient_strided_batch.restype = None
+    lib.oracle_cl_gradient_strided_batch.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _D,
+                                                     ctypes.c_int, _D, _I32, ctypes.c_int]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
     return lib
@@ -263,6 +266,24 @@ def cl_gradient_batch(nodes, offsets, alpha, vinf=None, chord=None, nthreads: in
     _load().oracle_cl_gradient_batch(B, _dp(nodes), offsets.ctypes.data_as(_I64), _dp(alpha),
                                      _dp(vinf), _dp(chord), _dp(grad),
                                      info.ctypes.data_as(_I32), int(nthreads))
+    return grad, info
+
+
+def cl_gradient_strided_batch(nodes, offsets, alpha, node_stride: int, vinf=None, chord=None,
+                              nthreads: int = 0):
+    """dCl/d(nodes) of the nodes k = 0, s, 2s, ... of every airfoil only (the
+    other rows of the result are 0): a bounded sample of the gradient's work."""
+    nodes = _f64(nodes)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    alpha = _f64(alpha)
+    B = len(offsets) - 1
+    grad = np.zeros_like(nodes)
+    info = np.zeros(B, dtype=np.int32)
+    vinf = _f64(vinf) if vinf is not None else None
+    chord = _f64(chord) if chord is not None else None
+    _load().oracle_cl_gradient_strided_batch(B, _dp(nodes), offsets.ctypes.data_as(_I64),
+                                             _dp(alpha), _dp(vinf), _dp(chord), int(node_stride),
+                                             _dp(grad), info.ctypes.data_as(_I32), int(nthreads))
     return grad, info
 
 

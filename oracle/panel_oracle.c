@@ -443,8 +443,22 @@ static void node_dual(const double *nodes, int n, int i, int k, int coord, dual 
  * derivative and are skipped.  grad[2k+c] = dL/d(x_k)_c.  Returns the LU info
  * (0 on success) or a negative geometry code.
  */
+static int vjp_nodes(int n, const double *nodes, double alpha, double vinf, double chord,
+                     double w_cl, const double *w_u, const double *w_cp, int node_stride,
+                     double *grad);
+
 int oracle_vjp(int n, const double *nodes, double alpha, double vinf, double chord, double w_cl,
                const double *w_u, const double *w_cp, double *grad) {
+  return vjp_nodes(n, nodes, alpha, vinf, chord, w_cl, w_u, w_cp, 1, grad);
+}
+
+/* The same product for the nodes k = 0, s, 2s, ... only (s = node_stride >= 1;
+ * the other entries of grad are left untouched).  Each node's two tangents are
+ * independent of the others', so the cost is the assembly, LU and solve of M
+ * plus a part proportional to the nodes computed. */
+static int vjp_nodes(int n, const double *nodes, double alpha, double vinf, double chord,
+                     double w_cl, const double *w_u, const double *w_cp, int node_stride,
+                     double *grad) {
   if (n < 3) return -1;
   if (!(oracle_signed_area(n, nodes) > 0.0)) return -2;
   int m = n + 1;
@@ -462,7 +476,7 @@ int oracle_vjp(int n, const double *nodes, double alpha, double vinf, double cho
     memcpy(u, b, sizeof(real) * (size_t)m);
     lu_solve(m, LU, piv, u);
     refine(m, M, LU, piv, b, u, 2);
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < n; k += node_stride) {
       for (int coord = 0; coord < 2; ++coord) {
         for (int j = 0; j < m; ++j) r[j] = 0.0;
         for (int j = 0; j < n; ++j) {
@@ -570,6 +584,27 @@ void oracle_cl_gradient_batch(int B, const double *nodes, const int64_t *offsets
     int n = (int)(offsets[b + 1] - off);
     double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
     info[b] = oracle_cl_gradient(n, nodes + 2 * off, alpha[b], v, c, grad + 2 * off);
+  }
+}
+
+/* dCl/d(nodes) of the nodes k = 0, s, 2s, ... of every airfoil (grad packed like
+ * the nodes; the other entries are left untouched): a bounded sample of the
+ * gradient's work for timing the oracle on large airfoils. */
+void oracle_cl_gradient_strided_batch(int B, const double *nodes, const int64_t *offsets,
+                                      const double *alpha, const double *vinf, const double *chord,
+                                      int node_stride, double *grad, int32_t *info, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int b = 0; b < B; ++b) {
+    int64_t off = offsets[b];
+    int n = (int)(offsets[b + 1] - off);
+    double v = vinf ? vinf[b] : 1.0, c = chord ? chord[b] : 1.0;
+    info[b] = vjp_nodes(n, nodes + 2 * off, alpha[b], v, c, 1.0, NULL, NULL,
+                        node_stride < 1 ? 1 : node_stride, grad + 2 * off);
   }
 }
 

@@ -584,3 +584,20 @@ def test_refined_solution_has_tiny_extended_residual():
     res = rhs.astype(np.longdouble) - Ml @ r["u"].astype(np.longdouble)
     scale = np.abs(Ml).sum(1).max() * np.abs(r["u"]).max()
     assert float(np.abs(res).max() / scale) < 4e-17
+
+
+def test_strided_gradient_is_the_full_gradient_on_its_nodes():
+    # the sampled gradient used to time the oracle on large airfoils computes
+    # exactly the full gradient's entries on every s-th node and nothing else
+    from paper_1511_02166_gb300 import inputs
+    pop = inputs.make_population("naca_b64_n100", batch=3)
+    g, info = oracle.cl_gradient_batch(pop.nodes, pop.offsets, pop.alpha)
+    assert np.all(info == 0)
+    for s in (1, 3, 7):
+        gs, info_s = oracle.cl_gradient_strided_batch(pop.nodes, pop.offsets, pop.alpha, s)
+        assert np.all(info_s == 0)
+        for b in range(pop.batch):
+            sl = slice(pop.offsets[b], pop.offsets[b + 1])
+            k = np.arange(pop.offsets[b + 1] - pop.offsets[b])
+            assert np.array_equal(gs[sl][k % s == 0], g[sl][k % s == 0])
+            assert np.all(gs[sl][k % s != 0] == 0)
