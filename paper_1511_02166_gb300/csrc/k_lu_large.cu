@@ -3,18 +3,28 @@
 // across the batch, so that each block column is spread over many blocks
 // instead of one block per airfoil.
 //
-// Per block column k0 (kBW = 128 wide) three launches:
-//   k_large_diag    one block per airfoil: LU of the kBW x kBW diagonal block D
-//                   in shared memory, with the pivot search restricted to the
-//                   rows of D; its row exchanges are applied to the rest of
-//                   those rows.
-//   k_large_trsm    U12 = L11^{-1} A12 and L21 = A21 U11^{-1}: the two
-//                   triangles of the diagonal block are inverted in shared
-//                   memory, then 128-wide slabs are multiplied by them.
-//   k_update_tc     A22 -= L21 U12 in 128 x 128 tiles on the tcgen05 tensor
-//                   cores (k_update_tc.cu).
-// Each of the three takes gridDim.y blocks per airfoil striding over its
-// slabs / tiles, so a batch of few airfoils still fills the GPU.
+// The factor is kept in the tiled layout of tl_layout.cuh while the steps run
+// (a ragged first block of e rows, then 128-row blocks), so that the tensor
+// memory access unit can move whole 128 x 32 chunks.  Launches:
+//   k_large_init      the scaled hi plane into the factor buffer, tiled;
+//   per block K = 0 .. T-1:
+//     k_large_diag    one block per airfoil: LU of the diagonal block in
+//                     shared memory, with the pivot search restricted to its
+//                     rows; its row exchanges are applied to the rest of
+//                     those rows;
+//     k_large_trsm    U12 = L11^{-1} A12 (stored transposed, the tensor cores'
+//                     K-major B operand) and L21 = A21 U11^{-1}: the two
+//                     triangles of the diagonal block are inverted in shared
+//                     memory, then 128-wide slabs are multiplied by them;
+//     k_update_tc     A22 -= L21 U12 on the tcgen05 tensor cores, operands
+//                     loaded by TMA, A22 updated by TMA reduce-add
+//                     (k_update_tc.cu);
+//   k_tl_to_rowmajor  the tiled layout back to row-major, one 8-block cluster
+//                     per 128-row block row (the block row's floats are staged
+//                     across the cluster's shared memory);
+//   k_large_finish    the 32 x 32 diagonal blocks of L and U inverted in place.
+// The per-airfoil kernels take gridDim.y blocks per airfoil striding over
+// slabs / tiles / rows, so a batch of few airfoils still fills the GPU.
 //
 // Pivoting.  The system is the collocation matrix of the logarithmic
 // single-layer kernel (Section 2) bordered by the Kutta row and the C column
@@ -33,11 +43,11 @@
 // 32 x 32 diagonal blocks of L and U replaced by their inverses.
 #include <atomic>
 
-#include "lu_mixed.cuh"
+#include "tl_layout.cuh"
 
 namespace panel {
 
-constexpr int kBW = 128;      // block column width
+constexpr int kBW = kTlB;     // block size
 constexpr int kLdD = kBW + 1;
 
 size_t lu_large_min_m() { return kLargeM + 1; }
@@ -48,8 +58,10 @@ __device__ __forceinline__ bool large_live(const SolveArgs& a, int b, int& n, in
   return m > kLargeM && n <= a.bt.n_max && a.info[b] == 0;
 }
 
-// Scaled copy A_hi -> LU (border row and column times s); rows strided over
-// gridDim.y blocks per airfoil.
+// Scaled copy A_hi -> LU (border row and column times s) into the tiled
+// layout.  Block y of gridDim.y takes block rows blockIdx.y, + gridDim.y, ...;
+// the writes run along the tiled order (consecutive threads, consecutive
+// floats) and the reads along rows of A_hi within 32-column chunks.
 __global__ void __launch_bounds__(256) k_large_init(SolveArgs a) {
   __shared__ double red[32];
   const Batch& bt = a.bt;
@@ -63,32 +75,55 @@ __global__ void __launch_bounds__(256) k_large_init(SolveArgs a) {
   const int64_t moff = bt.mat_off[b];
   const float* Ah = a.A_hi + moff;
   float* F = a.LU + moff;
+  TlGeom g;
+  g.init(m, moff);
   const float sf = (float)border_scale(Ah, n, m, red);
-  for (int r = blockIdx.y; r < m; r += gridDim.y) {
-    const float* src = Ah + r * m;
-    float* dst = F + r * m;
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-      const float v = src[c];
-      dst[c] = ((c == n && r < n) || r == n) ? v * sf : v;
+  auto scaled = [&](int r, int c) {
+    const float v = Ah[(int64_t)r * m + c];
+    return ((c == n && r < n) || r == n) ? v * sf : v;
+  };
+  for (int I = blockIdx.y; I < g.T; I += gridDim.y) {
+    const int r0 = g.start(I);
+    if (I == 0) {  // row-major rows 0..e-1
+      for (int p = threadIdx.x; p < g.e * m; p += blockDim.x) F[p] = scaled(p / m, p % m);
+      continue;
     }
+    for (int J = 1; J < g.T; ++J) {
+      float* Tt = F + g.tile(I, J);
+      const int c0 = g.start(J);
+      for (int p = threadIdx.x; p < kTlTile; p += blockDim.x) {
+        const int kc = p >> 12, r = (p & 4095) >> 5, c = (kc << 5) + (p & 31);
+        Tt[p] = scaled(r0 + r, c0 + c);
+      }
+    }
+    for (int p = threadIdx.x; p < kTlB * g.e; p += blockDim.x)
+      F[g.rag(I, p / g.e, p % g.e)] = scaled(r0 + p / g.e, p % g.e);
   }
 }
 
-// LU of the diagonal block with partial pivoting inside the block.
-__global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int k0) {
+// LU of the diagonal block K with partial pivoting inside the block.
+__global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* D = reinterpret_cast<float*>(smraw);          // kBW x kLdD
   int* sp = reinterpret_cast<int*>(D + kBW * kLdD);    // kBW
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   int n, m;
-  if (!large_live(a, b, n, m) || k0 >= m) return;
-  const int kb = min(kBW, m - k0);
+  if (!large_live(a, b, n, m)) return;
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
+  if (K >= g.T) return;
+  const int k0 = g.start(K), kb = g.size(K);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* F = a.LU + bt.mat_off[b];
+  // the diagonal block: rows of block row 0 (row-major), or the full tile (K, K)
+  float* Td = (K == 0) ? F : F + g.tile(K, K);
+  auto dpos = [&](int r, int c) {
+    return (K == 0) ? (int64_t)r * m + c : (int64_t)((c >> 5) << 12) + r * 32 + (c & 31);
+  };
   for (int e = tid; e < kBW * kBW; e += 256) {
-    const int r = e / kBW, c = e % kBW;
-    D[r * kLdD + c] = (r < kb && c < kb) ? F[(k0 + r) * m + k0 + c] : 0.0f;
+    const int r = e >> 7, c = e & 127;
+    D[r * kLdD + c] = (r < kb && c < kb) ? Td[dpos(r, c)] : 0.0f;
   }
   __syncthreads();
   for (int q = 0; q < kb; ++q) {
@@ -141,46 +176,62 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int k0) {
     }
     __syncthreads();
   }
-  for (int e = tid; e < kb * kb; e += 256) {
-    const int r = e / kb, c = e % kb;
-    F[(k0 + r) * m + k0 + c] = D[r * kLdD + c];
+  for (int e = tid; e < kBW * kBW; e += 256) {
+    const int r = e >> 7, c = e & 127;
+    if (r < kb && c < kb) Td[dpos(r, c)] = D[r * kLdD + c];
   }
   int32_t* gpiv = a.piv + vec_off(bt, b);
   if (tid < kb) gpiv[k0 + tid] = k0 + sp[tid];
-  // the same exchanges, in order, on the columns outside the block
+  // the exchanges made (usually a few), in order, as a list
+  int* ex = sp + kBW;  // 2 x kBW ints after the pivots
+  __shared__ int nex;
+  if (tid == 0) {
+    int k = 0;
+    for (int q = 0; q < kb; ++q)
+      if (sp[q] != q) {
+        ex[2 * k] = q;
+        ex[2 * k + 1] = sp[q];
+        ++k;
+      }
+    nex = k;
+  }
+  __syncthreads();
+  // ... applied to the columns outside the block (block row K: the finished L
+  // to the left, A12 to the right, both untransposed here)
   for (int c = tid; c < m; c += 256) {
     if (c >= k0 && c < k0 + kb) continue;
-    for (int q = 0; q < kb; ++q) {
-      const int p = sp[q];
-      if (p != q) {
-        float* x = F + (k0 + q) * m + c;
-        float* y = F + (k0 + p) * m + c;
-        const float t = *x;
-        *x = *y;
-        *y = t;
-      }
+    for (int x = 0; x < nex; ++x) {
+      float* u = F + g.off(k0 + ex[2 * x], c, false);
+      float* v = F + g.off(k0 + ex[2 * x + 1], c, false);
+      const float t = *u;
+      *u = *v;
+      *v = t;
     }
   }
 }
 
-size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + kBW * 4; }
+size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + 3 * kBW * 4; }
 
 // U12 = L11^{-1} A12 and L21 = A21 U11^{-1} as products with the explicit
-// inverses of the two triangles of the factored diagonal block.  Per block:
-//   1. the block D = L11 \ U11 is staged; thread j < 128 forms column j of
-//      L11^{-1} (forward substitution on e_j), thread 128 + i row i of
-//      U11^{-1} (from X U = I, so each row needs only its own earlier
-//      entries); four partial sums per dot product keep the chains short;
-//   2. tasks 0..ns-1 are 128-column slabs of A12, tasks ns..2ns-1 128-row
-//      slabs of A21: the slab is staged in shared memory and multiplied by the
-//      inverse, 8 x 8 outputs per thread, written straight back to the factor.
+// inverses of the two triangles of the factored diagonal block K.  Per block:
+//   1. the block D = L11 \ U11 is staged (a ragged block of e < 128 rows is
+//      completed by the identity, whose inverse it leaves alone); thread
+//      j < 128 forms column j of L11^{-1} (forward substitution on e_j), thread
+//      128 + i row i of U11^{-1} (from X U = I, so each row needs only its own
+//      earlier entries); four partial sums per dot product keep the chains
+//      short;
+//   2. tasks 0..ns-1 are the tiles (K, J > K) of A12, tasks ns..2ns-1 the tiles
+//      (I > K, K) of A21 (every block after the first is 128 wide): the tile is
+//      staged in shared memory and multiplied by the inverse, 8 x 8 outputs per
+//      thread, written straight back to the factor -- U12 transposed (K >= 1),
+//      L21 as it is.
 // Li holds L11^{-1} transposed (Li[k][t] = (L11^{-1})[t][k]) and Ui holds
 // U11^{-1} by rows, both with an odd row stride (conflict-free while they are
 // formed); the slab has 16-byte rows for vector reads.
 constexpr int kLdI = kBW + 1;
 constexpr int kLdX = kBW + 4;
 
-__global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
+__global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* X = reinterpret_cast<float*>(smraw);  // kBW x kLdX: D (stride kLdI), then the slab
   float* Li = X + kBW * kLdX;                  // kBW x kLdI
@@ -190,14 +241,17 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
   const int b = bt.order[blockIdx.x];
   int n, m;
   if (!large_live(a, b, n, m)) return;
-  const int k1 = k0 + kBW;  // a block column narrower than kBW is the last one
-  if (k1 >= m) return;
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
+  if (K >= g.T - 1) return;  // the last block has no trailing matrix
+  const int k0 = g.start(K), kb = g.size(K);
   const int tid = threadIdx.x;
   float* F = a.LU + bt.mat_off[b];
   float* D = X;
   for (int e = tid; e < kBW * kBW; e += 256) {
     const int r = e / kBW, c = e % kBW;
-    D[r * kLdI + c] = F[(k0 + r) * m + k0 + c];
+    D[r * kLdI + c] = (r < kb && c < kb) ? F[g.off(k0 + r, k0 + c, false)]
+                                         : (r == c ? 1.0f : 0.0f);
   }
   __syncthreads();
   if (tid < kBW) dinv[tid] = 1.0f / D[tid * kLdI + tid];
@@ -240,24 +294,33 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
       y[t] = -((s0 + s1) + (s2 + s3)) * dinv[t];
     }
   }
-  const int rest = m - k1, ns = (rest + 127) >> 7;
+  const int ns = g.T - 1 - K;
   const int tx = tid & 15, ty = tid >> 4;
   for (int task = blockIdx.y; task < 2 * ns; task += gridDim.y) {
     const bool cols = task < ns;
-    const int base = k1 + (cols ? task : task - ns) * 128;
-    const int cnt = min(128, m - base);
+    const int JI = K + 1 + (cols ? task : task - ns);  // the tile column J or row I
+    const int base = g.start(JI);
+    // the tile: (K, J) of A12 or (I, K) of A21; at K = 0 block row 0 (row-major)
+    // and the ragged tiles (I, 0)
+    float* Tt = (K == 0) ? nullptr : F + (cols ? g.tile(K, JI) : g.tile(JI, K));
     __syncthreads();
     if (cols) {
       // X[k][c] = A12[k0 + k][base + c]
       for (int e = tid; e < kBW * 128; e += 256) {
         const int k = e >> 7, c = e & 127;
-        X[k * kLdX + c] = (c < cnt) ? F[(k0 + k) * m + base + c] : 0.0f;
+        float v = 0.0f;
+        if (k < kb)
+          v = (K == 0) ? F[(int64_t)k * m + base + c] : Tt[((c >> 5) << 12) + k * 32 + (c & 31)];
+        X[k * kLdX + c] = v;
       }
     } else {
       // X[k][r] = A21[base + r][k0 + k]
       for (int e = tid; e < 128 * kBW; e += 256) {
-        const int r = e / kBW, k = e % kBW;
-        X[k * kLdX + r] = (r < cnt) ? F[(base + r) * m + k0 + k] : 0.0f;
+        const int r = e >> 7, k = e & 127;
+        float v = 0.0f;
+        if (k < kb)
+          v = (K == 0) ? F[g.rag(JI, r, k)] : Tt[((k >> 5) << 12) + r * 32 + (k & 31)];
+        X[k * kLdX + r] = v;
       }
     }
     __syncthreads();
@@ -286,14 +349,34 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
+      if (K == 0) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int t = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
-        float* row = F + (k0 + t) * m + base;
+        for (int i = 0; i < 8; ++i) {
+          const int t = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
+          if (t >= kb) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
-          if (c < cnt) row[c] = acc[i][j];
+          for (int j = 0; j < 8; ++j) {
+            const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
+            F[(int64_t)t * m + base + c] = acc[i][j];
+          }
+        }
+      } else {
+        // U12 of tile (K, J) goes back transposed (chunks of 32 rows of U12,
+        // column by column): staged as X[c][t], then written in storage order
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int t = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
+            X[c * kLdX + t] = acc[i][j];
+          }
+        }
+        __syncthreads();
+        for (int p = tid; p < kTlTile; p += 256) {
+          const int c = (p & 4095) >> 5, t = ((p >> 12) << 5) + (p & 31);
+          Tt[p] = X[c * kLdX + t];
         }
       }
     } else {
@@ -315,15 +398,27 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
+      // L21 staged as X[r][t], then written in storage order
+      __syncthreads();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + i - 4;
-        if (r >= cnt) continue;
-        float* row = F + (base + r) * m + k0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int t = (j < 4) ? 4 * tx + j : 64 + 4 * tx + j - 4;
-          row[t] = acc[i][j];
+          X[r * kLdX + t] = acc[i][j];
+        }
+      }
+      __syncthreads();
+      if (K == 0) {
+        for (int p = tid; p < kTlB * kb; p += 256) {
+          const int r = p / kb, t = p - r * kb;
+          F[g.rag(JI, r, t)] = X[r * kLdX + t];
+        }
+      } else {
+        for (int p = tid; p < kTlTile; p += 256) {
+          const int r = (p & 4095) >> 5, t = ((p >> 12) << 5) + (p & 31);
+          Tt[p] = X[r * kLdX + t];
         }
       }
     }
@@ -332,6 +427,124 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int k0) {
 
 size_t large_trsm_smem() {
   return ((size_t)kBW * kLdX + 2 * (size_t)kBW * kLdI + kBW) * 4;
+}
+
+// The tiled layout of block row I >= 1 back to row-major.  Both orders fill
+// the same 128 m floats (the block row's span), so the span is first staged
+// across the shared memory of an 8-block cluster (block c holds floats
+// [c part, (c + 1) part) of the tiled order), and after a cluster barrier the
+// blocks' warps write the row-major order in 32 x 32 pieces, reading every
+// value from whichever block holds it (distributed shared memory): lane l
+// takes column l of a piece, so each read and each write of a warp is 128
+// contiguous bytes; a piece of a transposed U tile is read column by column
+// into a per-warp buffer and written row by row.  Loads are issued eight at a
+// time.  A second barrier keeps every block's shared memory alive until all
+// reads are done.  Grid: x = the cluster's 8 blocks, y = I - 1, z = the launch
+// position of the airfoil.
+constexpr int kClusterTl = 8;
+constexpr int kConvThreads = 512;
+constexpr int kConvWarps = kConvThreads / 32;
+constexpr int kTbufLd = 33;
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+// float q of the staged span (block q / part of the cluster holds it)
+__device__ __forceinline__ float dsmem_ld(uint32_t local, int part, int q) {
+  const unsigned owner = (unsigned)(q / part);
+  const uint32_t addr = local + 4u * (uint32_t)(q - (int)owner * part);
+  uint32_t remote;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(owner));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote));
+  return v;
+}
+
+__global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, int part) {
+  extern __shared__ __align__(16) float stage[];
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.z];
+  const int I = 1 + blockIdx.y;
+  int n, m;
+  // uniform across the cluster: every block of it has the same (b, I)
+  if (!large_live(a, b, n, m)) return;
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
+  if (I >= g.T) return;
+  const int L = kTlB * m;
+  unsigned rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* S = a.LU + bt.mat_off[b] + g.span(I);
+  const int lo = (int)rank * part, hi = min(L, lo + part);
+  for (int i = lo + tid; i < hi; i += kConvThreads) stage[i - lo] = S[i];
+  cluster_sync_all();
+
+  const uint32_t local = (uint32_t)__cvta_generic_to_shared(stage);
+  float* tb = stage + part + warp * (32 * kTbufLd);
+  const int sp = (int)(g.tile(I, 1) - g.span(I));  // the full tiles start here (the head)
+  const int nbr = (g.e + 31) >> 5;                 // 32-column pieces of the ragged columns
+  const int ncb = nbr + 4 * (g.T - 1);
+  const int items = 4 * ncb;
+  for (int it = (int)rank * kConvWarps + warp; it < items; it += kClusterTl * kConvWarps) {
+    const int rg = it / ncb, cb = it - rg * ncb;
+    const int rr0 = 32 * rg;
+    if (cb < nbr) {
+      // ragged tile (I, 0): row-major 128 x e around the full tiles
+      const int c = 32 * cb + lane;
+      const bool ok = c < g.e;
+      for (int r8 = 0; r8 < 32; r8 += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int idx = (rr0 + r8 + j) * g.e + c;
+          const int q = idx < sp ? idx : sp + (g.T - 1) * kTlTile + (idx - sp);
+          v[j] = ok ? dsmem_ld(local, part, q) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (ok) S[(int64_t)(rr0 + r8 + j) * m + c] = v[j];
+      }
+    } else {
+      const int J = 1 + (cb - nbr) / 4, kc = (cb - nbr) & 3;
+      const int t0 = sp + (J - 1) * kTlTile;
+      const int col = g.start(J) + 32 * kc + lane;
+      if (J > I) {
+        // transposed U tile: rows rr0.. of this piece are chunk rg, column cc
+        // at t0 + rg 4096 + 32 cc + (rr % 32)
+        for (int j8 = 0; j8 < 32; j8 += 8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            v[j] = dsmem_ld(local, part, t0 + rg * kTlChunk + (32 * kc + j8 + j) * 32 + lane);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tb[lane * kTbufLd + j8 + j] = v[j];
+        }
+        __syncwarp();
+        for (int r = 0; r < 32; ++r) S[(int64_t)(rr0 + r) * m + col] = tb[r * kTbufLd + lane];
+        __syncwarp();
+      } else {
+        // row rr of chunk kc at t0 + kc 4096 + 32 rr + (column % 32)
+        for (int r8 = 0; r8 < 32; r8 += 8) {
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            v[j] = dsmem_ld(local, part, t0 + kc * kTlChunk + (rr0 + r8 + j) * 32 + lane);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) S[(int64_t)(rr0 + r8 + j) * m + col] = v[j];
+        }
+      }
+    }
+  }
+  cluster_sync_all();
+}
+
+// floats of a block row per cluster block (a multiple of 4), for size m
+static int tl_part(int m) { return ((kTlB * m + kClusterTl - 1) / kClusterTl + 3) & ~3; }
+static size_t tl_conv_smem(int part) {
+  return (size_t)part * 4 + (size_t)kConvWarps * 32 * kTbufLd * 4;
 }
 
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
@@ -353,9 +566,10 @@ long long set_wait_limit(long long polls) {
   return g_wait_limit.exchange(polls > 0 ? polls : kDefaultWaitLimit);
 }
 
-// gridDim.y per airfoil: enough blocks for ~4 per SM over the whole batch.
-static int split_for(int B, int per_airfoil_max) {
-  const int want = (4 * 152 + B - 1) / max(B, 1);
+// gridDim.y per airfoil: enough blocks for ~`per_sm` per SM over the whole batch.
+static int split_for(int B, int per_airfoil_max, int per_sm = 4) {
+  const int sms = sm_count() > 0 ? sm_count() : 152;
+  const int want = (per_sm * sms + B - 1) / max(B, 1);
   return max(1, min(want, per_airfoil_max));
 }
 
@@ -363,23 +577,45 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   const Batch& bt = a.bt;
   const int B = bt.B, m_max = bt.n_max + 1;
   if (B == 0 || m_max <= kLargeM) return cudaSuccess;
+  if (B > 65535) return cudaErrorInvalidValue;
+  const int T_max = (m_max + kTlB - 1) / kTlB;
   cudaError_t e;
+  UpdateMap tmap;
+  e = make_update_map(a.LU, (uint64_t)B * (uint64_t)m_max * (uint64_t)m_max, &tmap);
+  if (e != cudaSuccess) return e;
   e = ensure_smem(k_large_diag, large_diag_smem());
   if (e != cudaSuccess) return e;
   e = ensure_smem(k_large_trsm, large_trsm_smem());
   if (e != cudaSuccess) return e;
-  e = ensure_smem(k_update_tc, update_tc_smem());
+  e = ensure_update_smem();
+  if (e != cudaSuccess) return e;
+  const int part = tl_part(m_max);
+  e = ensure_smem(k_tl_to_rowmajor, tl_conv_smem(part));
   if (e != cudaSuccess) return e;
   const long long spin = g_wait_limit.load();
   k_large_init<<<dim3(B, split_for(B, 64)), 256, 0, s>>>(a);
-  for (int k0 = 0; k0 < m_max; k0 += kBW) {
-    k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, k0);
-    const int rest = m_max - (k0 + kBW);
-    if (rest <= 0) break;
-    const int ns = (rest + 127) / 128;
-    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, k0);
-    k_update_tc<<<dim3(B, split_for(B, ns * ns)), 288, update_tc_smem(), s>>>(a, k0, spin);
+  for (int K = 0; K < T_max; ++K) {
+    k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, K);
+    const int ns = T_max - 1 - K;  // blocks after K in the largest airfoil
+    if (ns <= 0) break;
+    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, K);
+    e = launch_update_tc(a, tmap, K, split_for(B, ns * ns, 1), spin, s);
+    if (e != cudaSuccess) return e;
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterTl, T_max - 1, B);
+  cfg.blockDim = dim3(kConvThreads);
+  cfg.dynamicSmemBytes = tl_conv_smem(part);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterTl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_tl_to_rowmajor, a, part);
+  if (e != cudaSuccess) return e;
   k_large_finish<<<B, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

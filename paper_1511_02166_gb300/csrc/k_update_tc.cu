@@ -1,66 +1,75 @@
 // k_update_tc.cu -- the trailing update A22 -= L21 U12 of the step-synchronous
 // blocked LU of large airfoils (k_lu_large.cu) on the 5th-generation tensor
-// cores: tcgen05.mma (kind::tf32) with the accumulator in tensor memory.
+// cores: tcgen05.mma (kind::tf32) with the accumulator in tensor memory, the
+// operands loaded by the tensor memory access (TMA) unit and the result added
+// into A22 by TMA reduce-add.
+//
+// The factor is in the tiled layout of tl_layout.cuh: every 128 x 32 chunk of
+// a full tile is 128 rows of 128 bytes on a 128-byte boundary of the factor
+// buffer, so one two-dimensional tensor map (the whole buffer as rows of 32
+// floats, 128-byte swizzle) describes every operand chunk of every airfoil.
+// At step K >= 1 the output tile (I, J) (I, J > K) takes A = L21 tile (I, K)
+// (rows x k: K-major) and B = U12 tile (K, J), which k_large_trsm stored
+// transposed (columns x k: K-major as well), four chunks of K = 32 each.  At
+// step 0 the inner dimension is the ragged first block (e <= 128 columns of
+// L, e rows of U, neither on a 16-byte grid): the converter warps load those
+// operands themselves, zero-padded to whole chunks.
 //
 // One block takes 128 x 128 output tiles of one airfoil (block y of gridDim.y
-// strides over the airfoil's tiles); K = 128 (the block column) is fed in
-// chunks of kKC = 16.  The block is warp-specialised (288 threads):
-//   warps 0-3  epilogue: wait for a finished accumulator, read it from tensor
-//              memory (warp w owns TMEM lanes 32w..32w+31 = tile rows) and
-//              subtract it from A22;
-//   warps 4-7  producers: load a chunk of L21 and U12 into registers (the
-//              next chunk is in flight while the current one is stored), split
-//              it into TF32 hi / lo parts and store them in shared memory;
-//   warp 8     one lane issues the MMAs.
-// Producers and the MMA lane pass kStages shared-memory stages through
-// full / empty mbarriers; the MMA lane and the epilogue pass two tensor-memory
-// accumulators (2 x 128 columns) through tfull / tempty mbarriers, so the
-// epilogue of one tile overlaps the MMAs of the next.
-//
-// Precision.  The factor is FP32; a TF32 product alone (11 significant bits)
-// would make the LU far less accurate than FP32 and the refinement would stall
-// on these ill-conditioned systems.  Each operand is split x = x_hi + x_lo with
-// x_hi = x rounded to TF32 and x_lo = x - x_hi (exact in FP32), and the
-// product is formed as A_hi B_hi + A_hi B_lo + A_lo B_hi (three MMAs per K
-// step, the dropped A_lo B_lo is ~2^-22 relative), accumulated in FP32 in
-// tensor memory.  The rank-128 product is accumulated on its own and
-// subtracted from A22 once, in the epilogue.
-//
-// Layout.  The airfoil's row stride m is arbitrary, so rows are not 16-byte
-// aligned and a tensor map cannot describe them; the producers write the
-// canonical K-major, non-swizzled layout themselves: 8-row x 16-byte core
-// matrices, 128 contiguous bytes each; core matrices adjacent in K are 128 B
-// apart (leading byte offset), those adjacent in M / N are kKC / 4 x 128 B
-// apart (stride byte offset).  A generic-to-async proxy fence orders the
-// stores before the MMAs that read them.
+// strides over the airfoil's tiles).  Warp-specialised, 320 threads:
+//   warp 8     one lane issues the TMA loads of a chunk of A and of B into a
+//              shared-memory stage (three stages, 64 KB each);
+//   warps 4-7  converters: split each operand value x = x_hi + x_lo, x_hi = x
+//              rounded to TF32 (in place), x_lo = x - x_hi (exact in FP32,
+//              into the stage's second half); at step 0 they first load it;
+//   warp 9     one lane issues the MMAs: A_hi B_hi + A_hi B_lo + A_lo B_hi
+//              ("3xTF32", the dropped A_lo B_lo is ~2^-22 relative; TF32 alone
+//              would make the factor far less accurate than FP32 and the
+//              refinement would stall on these ill-conditioned systems),
+//              M = N = 128, K = 8 per instruction, into one of two FP32
+//              accumulators in tensor memory (2 x 128 columns);
+//   warps 0-3  epilogue: read a finished accumulator (warp w owns TMEM lanes
+//              = tile rows 32w..32w+31), write -D in 128 x 32 chunks into a
+//              swizzled staging buffer, and let the TMA add it to A22
+//              (cp.reduce.async.bulk.tensor .add: the read-modify-write of
+//              A22 happens in L2, not in the block).
+// Full (TMA bytes) / converted / empty (MMA commit) mbarriers connect the
+// stages, full / empty mbarriers the accumulators; the epilogue of one tile
+// overlaps the MMAs of the next.
 //
 // Every pipeline wait is bounded (`spin` polls, a kernel argument) and polls a
 // shared failure flag: a block that gives up stops issuing work, and every
-// role leaves its loop.  The MMA lane commits a final arrival on done_bar on
-// every path, after the last MMA it issued; the block then waits for that
-// arrival with its own bound (kDoneLimit, independent of `spin` and of the
-// failure flag), so that no MMA is still reading shared memory or writing
-// tensor memory when the block sets info[b] = PANEL_INFO_DEVICE_TIMEOUT, frees
-// its tensor memory and returns.
-#include "lu_mixed.cuh"
+// role leaves its loop.  Before the block ends, the TMA lane waits for the
+// loads it has issued, the epilogue for its reduce-adds, and the block for a
+// final arrival that the MMA lane commits on every path after the last MMA it
+// issued; these waits have their own bound (kDoneLimit) and ignore the flag,
+// so that nothing still writes shared or tensor memory when the block sets
+// info[b] = PANEL_INFO_DEVICE_TIMEOUT, frees its tensor memory and returns.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tl_layout.cuh"
 
 namespace panel {
 
 namespace {
 
-constexpr int kTM = 128;               // tile rows (MMA M)
-constexpr int kTN = 128;               // tile columns (MMA N)
-constexpr int kKC = 16;                // K per chunk
-constexpr int kBWc = 128;              // block column width (K of the update)
-constexpr int kChunks = kBWc / kKC;    // 8
-constexpr int kStages = 3;             // shared-memory stages
-constexpr int kOpBytes = kTM * kKC * 4;            // one operand plane of a chunk: 8 KB
-constexpr int kBufBytes = 4 * kOpBytes;            // A_hi, A_lo, B_hi, B_lo
-constexpr int kSmemBytes = kStages * kBufBytes + 128;  // stages + barriers + flags
-constexpr uint32_t kTmemCols = 2 * kTN;            // two FP32 accumulators, 128 x 128 each
-constexpr int kThreadsTc = 288;                    // 4 epilogue + 4 producer + 1 MMA warps
-// bound of the final wait for the block's own MMAs (they finish in
-// microseconds; the bound only keeps the wait finite)
+constexpr int kTM = 128;                                // tile rows (MMA M)
+constexpr int kTN = 128;                                // tile columns (MMA N)
+constexpr int kKC = kTlC;                               // K per chunk (32)
+constexpr int kStages = 3;
+constexpr uint32_t kOpBytes = kTM * kKC * 4;            // one operand chunk: 16 KB
+constexpr uint32_t kStageBytes = 4 * kOpBytes;          // A (-> A_hi), A_lo, B (-> B_hi), B_lo
+constexpr uint32_t kEpiBytes = kOpBytes;                // a 128 x 32 chunk of -D
+constexpr int kEpiBufs = 2;
+constexpr uint32_t kBarOff = kStages * kStageBytes + kEpiBufs * kEpiBytes;
+constexpr uint32_t kSmemBytes = kBarOff + 256 + 1024;   // barriers, then 1 KB alignment slack
+constexpr uint32_t kTmemCols = 2 * kTN;                 // two FP32 accumulators, 128 x 128 each
+constexpr int kThreadsTc = 320;
+constexpr int kWarpTma = 8, kWarpMma = 9;
+// bound of the final waits for the block's own asynchronous operations (they
+// finish in microseconds; the bound only keeps the wait finite)
 constexpr long long kDoneLimit = 1ll << 24;
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -69,19 +78,21 @@ constexpr long long kDoneLimit = 1ll << 24;
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
                             ((uint32_t)(kTM >> 4) << 24);
 
-// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
-// byte offset >> 4 (16-29), stride byte offset >> 4 (32-45), descriptor
-// version 1 (bit 46), no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  constexpr uint64_t lbo = 128 >> 4;
-  constexpr uint64_t sbo = ((kKC / 4) * 128) >> 4;
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand with the 128-byte
+// swizzle (the layout the TMA writes with CU_TENSOR_MAP_SWIZZLE_128B): rows of
+// 128 bytes, 8-row atoms of 1 KB (stride byte offset 1024), leading byte
+// offset unused (1); start address >> 4 in bits 0-13, descriptor version 1
+// (bit 46), layout type 2 = 128-byte swizzle (bits 61-63).  Stepping K by 8
+// TF32 values inside the atom adds 32 bytes to the start address.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
 }
 
-// Byte offset of element (row, k) of a kTM x kKC operand plane in the
-// canonical layout.
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((((row >> 3) * (kKC / 4) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+// Byte offset of element (row, k) of a 128 x 32 operand chunk in the 128-byte
+// swizzled layout: 16-byte units of a row XOR the row's position in its atom.
+__device__ __forceinline__ uint32_t sw_off(int row, int k) {
+  return (uint32_t)(row * 128 + ((((k >> 2) ^ (row & 7)) & 7) << 4) + ((k & 3) << 2));
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -101,6 +112,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile(
       "{\n\t.reg .b64 st;\n\t"
       "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+      "r"(bytes)
       : "memory");
 }
 
@@ -128,12 +147,55 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
-// The final wait for the block's own MMAs: bounded, but it does not give up
-// when *fail is set (the MMAs issued before the failure are still running).
+// A final wait for the block's own asynchronous operations: bounded, but it
+// does not give up when *fail is set (what was issued before is still running).
 __device__ __forceinline__ bool mbar_wait_done(uint32_t bar, uint32_t parity) {
   for (long long it = 0; it < kDoneLimit; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
+}
+
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int y,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_reduce_add(const CUtensorMap* map, int y, uint32_t src) {
+  asm volatile(
+      "cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group "
+      "[%0, {%1, %2}], [%3];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(0), "r"(y), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// True on every epilogue thread iff `ok` holds on all 128 of them (named
+// barrier 1 with an AND reduction): the epilogue leaves its loop together.
+__device__ __forceinline__ bool epi_all(bool ok) {
+  uint32_t all;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(all)
+      : "r"((uint32_t)ok)
+      : "memory");
+  return all != 0;
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -180,31 +242,37 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0,
-                                                              long long spin) {
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    k_update_tc(SolveArgs a, const __grid_constant__ CUtensorMap tmap, int K, long long spin) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   const int n = airfoil_n(bt, b), m = n + 1;
   if (!(m > kLargeM && n <= bt.n_max && a.info[b] == 0)) return;
-  const int k1 = k0 + kBWc;
-  if (k1 >= m) return;
-  const int rest = m - k1, nt = (rest + kTN - 1) / kTN, tiles = nt * nt;
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
+  if (K >= g.T - 1) return;
+  const int nt = g.T - 1 - K, tiles = nt * nt;
   if ((int)blockIdx.y >= tiles) return;
+  const int nkc = (K == 0) ? (g.e + kKC - 1) / kKC : kTlB / kKC;
+  const int my_tiles = (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int nq = my_tiles * nkc;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float* F = a.LU + bt.mat_off[b];
-  unsigned char* misc = smraw + kStages * kBufBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(misc);  // full[3] empty[3] tfull[2] tempty[2] done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(misc + 96);
-  volatile int* fail = reinterpret_cast<volatile int*>(misc + 100);
-  const uint32_t sbase = smem_u32(smraw);
-  const uint32_t bar_base = smem_u32(bars);
+  const uint32_t sraw = smem_u32(smraw);
+  const uint32_t sbase = (sraw + 1023u) & ~1023u;
+  unsigned char* gbase = smraw + (sbase - sraw);
+  const uint32_t ebase = sbase + kStages * kStageBytes;
+  const uint32_t bar_base = sbase + kBarOff;
+  // full[3] conv[3] empty[3] tfull[2] tempty[2] done
   auto full_bar = [&](int st) { return bar_base + 8u * st; };
-  auto empty_bar = [&](int st) { return bar_base + 8u * (kStages + st); };
-  auto tfull_bar = [&](int ac) { return bar_base + 8u * (2 * kStages + ac); };
-  auto tempty_bar = [&](int ac) { return bar_base + 8u * (2 * kStages + 2 + ac); };
-  const uint32_t done_bar = bar_base + 8u * (2 * kStages + 4);
+  auto conv_bar = [&](int st) { return bar_base + 8u * (kStages + st); };
+  auto empty_bar = [&](int st) { return bar_base + 8u * (2 * kStages + st); };
+  auto tfull_bar = [&](int ac) { return bar_base + 8u * (3 * kStages + ac); };
+  auto tempty_bar = [&](int ac) { return bar_base + 8u * (3 * kStages + 2 + ac); };
+  const uint32_t done_bar = bar_base + 8u * (3 * kStages + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + kBarOff + 128);
+  volatile int* fail = reinterpret_cast<volatile int*>(gbase + kBarOff + 132);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -213,9 +281,10 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
+  if (tid == 32) {
     for (int st = 0; st < kStages; ++st) {
-      mbar_init(full_bar(st), 4);   // one arrival per producer warp
+      mbar_init(full_bar(st), 1);   // the TMA lane's arrival (+ the bytes of two chunks)
+      mbar_init(conv_bar(st), 4);   // one arrival per converter warp
       mbar_init(empty_bar(st), 1);  // tcgen05.commit
     }
     for (int ac = 0; ac < 2; ++ac) {
@@ -230,116 +299,156 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const float* F = a.LU + bt.mat_off[b];
 
-  const int my_tiles = (tiles - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;
-  const int nq = my_tiles * kChunks;
-  auto tile_rc = [&](int tau, int& r0, int& c0) {
+  auto tile_ij = [&](int tau, int& I, int& J) {
     const int t = (int)blockIdx.y + tau * (int)gridDim.y;
-    r0 = k1 + (t / nt) * kTM;
-    c0 = k1 + (t % nt) * kTN;
+    I = K + 1 + t / nt;
+    J = K + 1 + t % nt;
+  };
+  // row of the tensor map (rows of 32 floats) where chunk kc of tile (I, J) starts
+  auto map_row = [&](int I, int J, int kc) {
+    return (int)((g.base + g.tile(I, J) + (int64_t)kc * kTlChunk) >> 5);
   };
 
-  if (warp >= 4 && warp < 8) {
-    // ---------------- producers ----------------
-    const int pt = tid - 128;
-    constexpr int kPer = kTM * kKC / 128;  // 16 values of A and 16 of B^T per thread
-    auto load = [&](int q, float (&ra)[kPer], float (&rb)[kPer]) {
-      int r0, c0;
-      tile_rc(q / kChunks, r0, c0);
-      const int kg = k0 + (q % kChunks) * kKC;
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) {
-        const int e = pt + 128 * j;
-        const int r = r0 + (e >> 4);          // A[row][k], k fastest
-        ra[j] = (r < m) ? F[r * m + kg + (e & 15)] : 0.0f;
-        const int c = c0 + (e & 127);         // U12[k][col], col fastest
-        rb[j] = (c < m) ? F[(kg + (e >> 7)) * m + c] : 0.0f;
+  if (warp == kWarpTma) {
+    // ---------------- TMA loads (one lane) ----------------
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int st = q % kStages, u = q / kStages;
+        if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail, spin)) break;
+        if (K == 0) {  // the converters load the ragged operands themselves
+          mbar_arrive(full_bar(st));
+          continue;
+        }
+        int I, J;
+        tile_ij(q / nkc, I, J);
+        const int kc = q % nkc;
+        const uint32_t sA = sbase + st * kStageBytes;
+        mbar_arrive_tx(full_bar(st), 2 * kOpBytes);
+        tma_load(sA, &tmap, map_row(I, K, kc), full_bar(st));
+        tma_load(sA + 2 * kOpBytes, &tmap, map_row(K, J, kc), full_bar(st));
+        issued = q + 1;
       }
-    };
-    auto store = [&](int q, const float (&ra)[kPer], const float (&rb)[kPer]) -> bool {
+      // the loads still in flight land before the block may end
+      for (int q = max(0, issued - kStages); q < issued; ++q)
+        mbar_wait_done(full_bar(q % kStages), (q / kStages) & 1);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- converters: x -> (x_hi in place, x_lo) ----------------
+    const int ct = tid - 128;
+    for (int q = 0; q < nq; ++q) {
       const int st = q % kStages, u = q / kStages;
-      if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail, spin)) return false;
-      unsigned char* B = smraw + st * kBufBytes;
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) {
-        const int e = pt + 128 * j;
-        const uint32_t oa = core_off(e >> 4, e & 15);
-        const float ha = tf32_hi(ra[j]);
-        *reinterpret_cast<float*>(B + oa) = ha;
-        *reinterpret_cast<float*>(B + kOpBytes + oa) = ra[j] - ha;
-        const uint32_t ob = core_off(e & 127, e >> 7);
-        const float hb = tf32_hi(rb[j]);
-        *reinterpret_cast<float*>(B + 2 * kOpBytes + ob) = hb;
-        *reinterpret_cast<float*>(B + 3 * kOpBytes + ob) = rb[j] - hb;
+      // every lane waits (acquiring the TMA's bytes), and the warp leaves together
+      const bool ok = mbar_wait(full_bar(st), u & 1, fail, spin);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      unsigned char* S = gbase + st * kStageBytes;
+      if (K == 0) {
+        int I, J;
+        tile_ij(q / nkc, I, J);
+        const int k0 = (q % nkc) * kKC, c0 = g.start(J);
+#pragma unroll 4
+        for (int j = 0; j < kTM * kKC / 128; ++j) {
+          const int e = ct + 128 * j;
+          // A: row e / 32 of the ragged tile (I, 0), column k0 + e % 32
+          const int ar = e >> 5, ak = e & 31;
+          const float va = (k0 + ak < g.e) ? F[g.rag(I, ar, k0 + ak)] : 0.0f;
+          const uint32_t oa = sw_off(ar, ak);
+          const float ha = tf32_hi(va);
+          *reinterpret_cast<float*>(S + oa) = ha;
+          *reinterpret_cast<float*>(S + kOpBytes + oa) = va - ha;
+          // B: row k0 + e / 128 of block row 0 (row-major), column c0 + e % 128
+          const int bk = e >> 7, bn = e & 127;
+          const float vb = (k0 + bk < g.e) ? F[(int64_t)(k0 + bk) * m + c0 + bn] : 0.0f;
+          const uint32_t ob = sw_off(bn, bk);
+          const float hb = tf32_hi(vb);
+          *reinterpret_cast<float*>(S + 2 * kOpBytes + ob) = hb;
+          *reinterpret_cast<float*>(S + 3 * kOpBytes + ob) = vb - hb;
+        }
+      } else {
+        float4* A4 = reinterpret_cast<float4*>(S);
+        float4* B4 = reinterpret_cast<float4*>(S + 2 * kOpBytes);
+        constexpr int kVec = kOpBytes / 16;  // float4 per chunk
+#pragma unroll 4
+        for (int j = 0; j < kVec / 128; ++j) {
+          const int i = ct + 128 * j;
+          const float4 va = A4[i], vb = B4[i];
+          const float4 ha = make_float4(tf32_hi(va.x), tf32_hi(va.y), tf32_hi(va.z),
+                                        tf32_hi(va.w));
+          const float4 hb = make_float4(tf32_hi(vb.x), tf32_hi(vb.y), tf32_hi(vb.z),
+                                        tf32_hi(vb.w));
+          A4[i] = ha;
+          A4[kVec + i] = make_float4(va.x - ha.x, va.y - ha.y, va.z - ha.z, va.w - ha.w);
+          B4[i] = hb;
+          B4[kVec + i] = make_float4(vb.x - hb.x, vb.y - hb.y, vb.z - hb.z, vb.w - hb.w);
+        }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(full_bar(st));
-      return true;
-    };
-    float a0[kPer], b0[kPer], a1[kPer], b1[kPer];
-    load(0, a0, b0);
-    for (int q = 0; q < nq; q += 2) {
-      if (q + 1 < nq) load(q + 1, a1, b1);
-      if (!store(q, a0, b0)) break;
-      if (q + 1 >= nq) break;
-      if (q + 2 < nq) load(q + 2, a0, b0);
-      if (!store(q + 1, a1, b1)) break;
+      if (lane == 0) mbar_arrive(conv_bar(st));
     }
-  } else if (warp == 8) {
+  } else if (warp == kWarpMma) {
     // ---------------- MMA issue (one lane) ----------------
     if (lane == 0) {
       for (int q = 0; q < nq; ++q) {
         const int st = q % kStages, u = q / kStages;
-        const int kc = q % kChunks, tau = q / kChunks, ac = tau & 1, v = tau >> 1;
+        const int kc = q % nkc, tau = q / nkc, ac = tau & 1, v = tau >> 1;
         if (kc == 0 && v >= 1 && !mbar_wait(tempty_bar(ac), (v - 1) & 1, fail, spin)) break;
-        if (!mbar_wait(full_bar(st), u & 1, fail, spin)) break;
+        if (!mbar_wait(conv_bar(st), u & 1, fail, spin)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ac * kTN);
-        const uint32_t ah = sbase + st * kBufBytes, al = ah + kOpBytes;
+        const uint32_t ah = sbase + st * kStageBytes, al = ah + kOpBytes;
         const uint32_t bh = ah + 2 * kOpBytes, bl = ah + 3 * kOpBytes;
 #pragma unroll
-        for (int s = 0; s < kKC / 8; ++s) {  // K = 8 per MMA: two core matrices
-          const uint32_t ko = s * 2 * 128;
+        for (int s = 0; s < kKC / 8; ++s) {  // K = 8 per MMA: 32 bytes of each row
+          const uint32_t ko = 32u * s;
           const uint32_t acc0 = (kc > 0 || s > 0) ? 1u : 0u;
-          tc_mma(d, smem_desc(ah + ko), smem_desc(bh + ko), acc0);
-          tc_mma(d, smem_desc(ah + ko), smem_desc(bl + ko), 1u);
-          tc_mma(d, smem_desc(al + ko), smem_desc(bh + ko), 1u);
+          tc_mma(d, desc_sw128(ah + ko), desc_sw128(bh + ko), acc0);
+          tc_mma(d, desc_sw128(ah + ko), desc_sw128(bl + ko), 1u);
+          tc_mma(d, desc_sw128(al + ko), desc_sw128(bh + ko), 1u);
         }
         tc_commit(empty_bar(st));
-        if (kc == kChunks - 1) tc_commit(tfull_bar(ac));
+        if (kc == nkc - 1) tc_commit(tfull_bar(ac));
       }
       tc_commit(done_bar);  // arrives once every MMA issued above has completed
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: A22 -= D ----------------
+    // ---------------- epilogue: A22 += -D by TMA reduce-add ----------------
+    const int r = 32 * warp + lane;  // tile row = TMEM lane
+    int cnt = 0;
     for (int tau = 0; tau < my_tiles; ++tau) {
       const int ac = tau & 1, v = tau >> 1;
-      if (!mbar_wait(tfull_bar(ac), v & 1, fail, spin)) break;
+      if (!epi_all(mbar_wait(tfull_bar(ac), v & 1, fail, spin))) break;
       tc_fence_after();
-      int r0, c0;
-      tile_rc(tau, r0, c0);
-      const int r = r0 + 32 * warp + lane;
+      int I, J;
+      tile_ij(tau, I, J);
 #pragma unroll 1
-      for (int s = 0; s < kTN / 32; ++s) {
+      for (int s = 0; s < kTN / kKC; ++s) {
         float v32[32];
-        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * kTN + 32 * s), v32);
-        if (r < m) {
-          float* row = F + r * m + c0 + 32 * s;
-          const int cn = min(32, m - (c0 + 32 * s));
-          float c[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) c[i] = (i < cn) ? row[i] : 0.0f;
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (i < cn) row[i] = c[i] - v32[i];
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * kTN + kKC * s), v32);
+        if (s == kTN / kKC - 1) {  // the accumulator is free once its last columns are read
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty_bar(ac));
         }
+        const uint32_t buf = (uint32_t)(cnt & 1) * kEpiBytes;
+        if (tid == 0 && cnt >= 2) bulk_wait_read_1();  // this buffer's previous reduce has read it
+        epi_bar();
+        unsigned char* E = gbase + kStages * kStageBytes + buf;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<float4*>(E + r * 128 + (((j ^ (r & 7)) & 7) << 4)) =
+              make_float4(-v32[4 * j], -v32[4 * j + 1], -v32[4 * j + 2], -v32[4 * j + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_bar();
+        if (tid == 0) tma_reduce_add(&tmap, map_row(I, J, s), ebase + buf);
+        ++cnt;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(ac));
     }
+    if (tid == 0) bulk_wait_all();  // every reduce-add has completed
   }
 
   // every MMA this block issued has completed once done_bar has flipped (the
@@ -359,6 +468,41 @@ __global__ void __launch_bounds__(kThreadsTc, 2) k_update_tc(SolveArgs a, int k0
   }
 }
 
-size_t update_tc_smem() { return (size_t)kSmemBytes; }
+// The tensor map of the factor buffer as rows of 32 floats (128 bytes), boxes
+// of 128 rows (one chunk), 128-byte swizzle.  `floats` bounds the buffer's
+// size from above; only chunks inside the caller's buffer are ever addressed.
+cudaError_t make_update_map(float* base, uint64_t floats, UpdateMap* out) {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0) return cudaErrorMisalignedAddress;
+  uint64_t rows = (floats + kTlC - 1) / kTlC;
+  if (rows > 0xFFFFFFFFull) rows = 0xFFFFFFFFull;
+  if (rows < (uint64_t)kTM) rows = kTM;
+  const cuuint64_t dims[2] = {(cuuint64_t)kTlC, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kTlC * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kTlC, (cuuint32_t)kTM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&out->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t ensure_update_smem() { return ensure_smem(k_update_tc, (size_t)kSmemBytes); }
+
+cudaError_t launch_update_tc(const SolveArgs& a, const UpdateMap& map, int K, int split,
+                             long long spin, cudaStream_t s) {
+  k_update_tc<<<dim3(a.bt.B, split), kThreadsTc, kSmemBytes, s>>>(a, map.map, K, spin);
+  return cudaGetLastError();
+}
 
 }  // namespace panel

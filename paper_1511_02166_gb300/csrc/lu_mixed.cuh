@@ -110,9 +110,7 @@ __device__ inline void invert_diagonal_blocks(float* F, int ld, int m) {
 
 cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s);
 cudaError_t launch_gj_mixed(const SolveArgs& a, cudaStream_t s);
-__global__ void k_update_tc(SolveArgs a, int k0, long long spin);
 long long set_wait_limit(long long polls);
-size_t update_tc_smem();
 size_t lu_large_min_m();
 
 }  // namespace panel
