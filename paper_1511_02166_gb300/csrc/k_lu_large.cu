@@ -62,7 +62,8 @@ __device__ __forceinline__ bool large_live(const SolveArgs& a, int b, int& n, in
 // layout.  Block y of gridDim.y takes block rows blockIdx.y, + gridDim.y, ...;
 // the writes run along the tiled order (consecutive threads, consecutive
 // floats) and the reads along rows of A_hi within 32-column chunks.
-__global__ void __launch_bounds__(256) k_large_init(SolveArgs a) {
+constexpr int kInitThreads = 256;
+__global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
   __shared__ double red[32];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
@@ -82,21 +83,29 @@ __global__ void __launch_bounds__(256) k_large_init(SolveArgs a) {
     const float v = Ah[(int64_t)r * m + c];
     return ((c == n && r < n) || r == n) ? v * sf : v;
   };
+  constexpr int kU = 8;  // loads in flight per thread
   for (int I = blockIdx.y; I < g.T; I += gridDim.y) {
     const int r0 = g.start(I);
     if (I == 0) {  // row-major rows 0..e-1
-      for (int p = threadIdx.x; p < g.e * m; p += blockDim.x) F[p] = scaled(p / m, p % m);
+      for (int p = threadIdx.x; p < g.e * m; p += kInitThreads) F[p] = scaled(p / m, p % m);
       continue;
     }
     for (int J = 1; J < g.T; ++J) {
       float* Tt = F + g.tile(I, J);
       const int c0 = g.start(J);
-      for (int p = threadIdx.x; p < kTlTile; p += blockDim.x) {
-        const int kc = p >> 12, r = (p & 4095) >> 5, c = (kc << 5) + (p & 31);
-        Tt[p] = scaled(r0 + r, c0 + c);
+      for (int p0 = 0; p0 < kTlTile; p0 += kU * kInitThreads) {
+        float v[kU];
+#pragma unroll
+        for (int i = 0; i < kU; ++i) {
+          const int p = p0 + i * kInitThreads + threadIdx.x;
+          const int kc = p >> 12, r = (p & 4095) >> 5, c = (kc << 5) + (p & 31);
+          v[i] = scaled(r0 + r, c0 + c);
+        }
+#pragma unroll
+        for (int i = 0; i < kU; ++i) Tt[p0 + i * kInitThreads + threadIdx.x] = v[i];
       }
     }
-    for (int p = threadIdx.x; p < kTlB * g.e; p += blockDim.x)
+    for (int p = threadIdx.x; p < kTlB * g.e; p += kInitThreads)
       F[g.rag(I, p / g.e, p % g.e)] = scaled(r0 + p / g.e, p % g.e);
   }
 }
@@ -126,53 +135,129 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
     D[r * kLdD + c] = (r < kb && c < kb) ? Td[dpos(r, c)] : 0.0f;
   }
   __syncthreads();
-  for (int q = 0; q < kb; ++q) {
+  // Blocked in panels of 32 columns.  Per panel: warp 0 factors the panel
+  // (rows c0..kb-1) column by column with partial pivoting over those rows,
+  // lane l holding column c0 + l for the exchanges and the rank-1 updates and
+  // rows q + l, q + l + 32, ... for the pivot search (warp barriers only); then
+  // the whole block applies the panel's exchanges to the other columns, solves
+  // U12 = L11^{-1} A12 (a thread per column) and updates the trailing block in
+  // 4 x 4 register tiles.
+  __shared__ int zero_pivot;
+  if (tid == 0) zero_pivot = -1;
+  __syncthreads();
+  for (int c0 = 0; c0 < kb; c0 += 32) {
+    const int w = min(32, kb - c0);
     if (warp == 0) {
-      // argmax |D[r][q]| over the rows q..kb-1, lowest row on ties
-      float bv = -1.0f;
-      int br = kBW;
-#pragma unroll
-      for (int t = 0; t < kBW / 32; ++t) {
-        const int r = lane + 32 * t;
-        const float v = (r >= q && r < kb) ? fabsf(D[r * kLdD + q]) : -1.0f;
-        if (v > bv) {
-          bv = v;
-          br = r;
+      for (int q = c0; q < c0 + w; ++q) {
+        // argmax |D[r][q]| over the rows q..kb-1, lowest row on ties
+        float bv = -1.0f;
+        int br = kBW;
+        for (int r = q + lane; r < kb; r += 32) {
+          const float v = fabsf(D[r * kLdD + q]);
+          if (v > bv) {
+            bv = v;
+            br = r;
+          }
         }
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-        if (ov > bv || (ov == bv && orr < br)) {
-          bv = ov;
-          br = orr;
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+          if (ov > bv || (ov == bv && orr < br)) {
+            bv = ov;
+            br = orr;
+          }
         }
+        const int p = (br < kb) ? br : q;
+        if (lane == 0) sp[q] = p;
+        if (!(fabsf(D[p * kLdD + q]) > 0.0f)) {  // exact zero (or NaN) pivot
+          if (lane == 0) zero_pivot = q;
+          break;
+        }
+        if (p != q && lane < w) {
+          const float t = D[q * kLdD + c0 + lane];
+          D[q * kLdD + c0 + lane] = D[p * kLdD + c0 + lane];
+          D[p * kLdD + c0 + lane] = t;
+        }
+        __syncwarp();
+        // multipliers and the rank-1 update of the panel's later columns: lane
+        // l takes the rows q + 1 + l, + 32, ... (independent across rows)
+        const float inv = 1.0f / D[q * kLdD + q];
+        float lr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = q + 1 + lane + 32 * i;
+          lr[i] = (r < kb) ? D[r * kLdD + q] * inv : 0.0f;
+          if (r < kb) D[r * kLdD + q] = lr[i];
+        }
+        for (int j = q + 1; j < c0 + w; ++j) {
+          const float uqj = D[q * kLdD + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = q + 1 + lane + 32 * i;
+            if (r < kb) D[r * kLdD + j] = fmaf(-lr[i], uqj, D[r * kLdD + j]);
+          }
+        }
+        __syncwarp();
       }
-      if (lane == 0) sp[q] = (br < kb) ? br : q;
     }
     __syncthreads();
-    const int p = sp[q];
-    if (!(fabsf(D[p * kLdD + q]) > 0.0f)) {  // exact zero (or NaN) pivot: uniform exit
+    if (zero_pivot >= 0) {  // uniform exit
       if (tid == 0) {
-        a.info[b] = k0 + q + 1;
+        a.info[b] = k0 + zero_pivot + 1;
         if (a.iters) a.iters[b] = 0;
       }
       return;
     }
-    if (p != q && tid < kBW) {
-      const float t = D[q * kLdD + tid];
-      D[q * kLdD + tid] = D[p * kLdD + tid];
-      D[p * kLdD + tid] = t;
+    // the panel's exchanges, in order, on the block's other columns
+    for (int c = tid; c < kb; c += 256) {
+      if (c >= c0 && c < c0 + w) continue;
+      for (int q = c0; q < c0 + w; ++q) {
+        const int p = sp[q];
+        if (p != q) {
+          const float t = D[q * kLdD + c];
+          D[q * kLdD + c] = D[p * kLdD + c];
+          D[p * kLdD + c] = t;
+        }
+      }
     }
     __syncthreads();
-    const float inv = 1.0f / D[q * kLdD + q];
-    for (int r = q + 1 + warp; r < kb; r += 8) {
-      const float l = D[r * kLdD + q] * inv;
-      for (int c = q + 1 + lane; c < kb; c += 32)
-        D[r * kLdD + c] = fmaf(-l, D[q * kLdD + c], D[r * kLdD + c]);
-      __syncwarp();
-      if (lane == 0) D[r * kLdD + q] = l;
+    const int c1 = c0 + w;
+    if (c1 >= kb) break;
+    // U12 = L11^{-1} A12 on rows c0..c1-1, columns c1..kb-1 (unit lower L11)
+    for (int c = c1 + tid; c < kb; c += 256) {
+      for (int i = 1; i < w; ++i) {
+        float s = D[(c0 + i) * kLdD + c];
+        for (int t = 0; t < i; ++t) s = fmaf(-D[(c0 + i) * kLdD + c0 + t], D[(c0 + t) * kLdD + c], s);
+        D[(c0 + i) * kLdD + c] = s;
+      }
+    }
+    __syncthreads();
+    // trailing block: rows and columns c1..kb-1, D -= L21 U12, 4 x 4 per task
+    const int nr = kb - c1, nb4 = (nr + 3) >> 2;
+    for (int task = tid; task < nb4 * nb4; task += 256) {
+      const int r0 = c1 + 4 * (task / nb4), cc0 = c1 + 4 * (task % nb4);
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.0f;
+      for (int t = 0; t < w; ++t) {
+        float av[4], bw[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = (r0 + i < kb) ? D[(r0 + i) * kLdD + c0 + t] : 0.0f;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) bw[jj] = (cc0 + jj < kb) ? D[(c0 + t) * kLdD + cc0 + jj] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(av[i], bw[jj], acc[i][jj]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (r0 + i < kb && cc0 + jj < kb) D[(r0 + i) * kLdD + cc0 + jj] -= acc[i][jj];
     }
     __syncthreads();
   }
@@ -296,6 +381,32 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
   }
   const int ns = g.T - 1 - K;
   const int tx = tid & 15, ty = tid >> 4;
+  // The task's tile is read into registers one task ahead (64 values per
+  // thread; element e = tid + 256 i is (k, c) = (e / 128, e % 128) of A12 or
+  // (r, k) of A21), so that its loads overlap the previous task's products.
+  constexpr int kPre = kBW * 128 / 256;
+  float pre[kPre];
+  auto fetch = [&](int task) {
+    const bool cols = task < ns;
+    const int JI = K + 1 + (cols ? task : task - ns);
+    const int base = g.start(JI);
+    const float* Tt = (K == 0) ? nullptr : F + (cols ? g.tile(K, JI) : g.tile(JI, K));
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      const int e = tid + 256 * i, hi7 = e >> 7, lo7 = e & 127;
+      float v = 0.0f;
+      if (cols) {  // A12[k0 + k][base + c], k = hi7, c = lo7
+        if (hi7 < kb)
+          v = (K == 0) ? F[(int64_t)hi7 * m + base + lo7]
+                       : Tt[((lo7 >> 5) << 12) + hi7 * 32 + (lo7 & 31)];
+      } else {     // A21[base + r][k0 + k], r = hi7, k = lo7
+        if (lo7 < kb)
+          v = (K == 0) ? F[g.rag(JI, hi7, lo7)] : Tt[((lo7 >> 5) << 12) + hi7 * 32 + (lo7 & 31)];
+      }
+      pre[i] = v;
+    }
+  };
+  if ((int)blockIdx.y < 2 * ns) fetch(blockIdx.y);
   for (int task = blockIdx.y; task < 2 * ns; task += gridDim.y) {
     const bool cols = task < ns;
     const int JI = K + 1 + (cols ? task : task - ns);  // the tile column J or row I
@@ -304,26 +415,17 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
     // and the ragged tiles (I, 0)
     float* Tt = (K == 0) ? nullptr : F + (cols ? g.tile(K, JI) : g.tile(JI, K));
     __syncthreads();
-    if (cols) {
-      // X[k][c] = A12[k0 + k][base + c]
-      for (int e = tid; e < kBW * 128; e += 256) {
-        const int k = e >> 7, c = e & 127;
-        float v = 0.0f;
-        if (k < kb)
-          v = (K == 0) ? F[(int64_t)k * m + base + c] : Tt[((c >> 5) << 12) + k * 32 + (c & 31)];
-        X[k * kLdX + c] = v;
-      }
-    } else {
-      // X[k][r] = A21[base + r][k0 + k]
-      for (int e = tid; e < 128 * kBW; e += 256) {
-        const int r = e >> 7, k = e & 127;
-        float v = 0.0f;
-        if (k < kb)
-          v = (K == 0) ? F[g.rag(JI, r, k)] : Tt[((k >> 5) << 12) + r * 32 + (k & 31)];
-        X[k * kLdX + r] = v;
-      }
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      const int e = tid + 256 * i, hi7 = e >> 7, lo7 = e & 127;
+      // X[k][c] = A12[k0 + k][base + c], or X[k][r] = A21[base + r][k0 + k]
+      if (cols)
+        X[hi7 * kLdX + lo7] = pre[i];
+      else
+        X[lo7 * kLdX + hi7] = pre[i];
     }
     __syncthreads();
+    if (task + (int)gridDim.y < 2 * ns) fetch(task + gridDim.y);
     float acc[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -479,7 +581,19 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* S = a.LU + bt.mat_off[b] + g.span(I);
   const int lo = (int)rank * part, hi = min(L, lo + part);
-  for (int i = lo + tid; i < hi; i += kConvThreads) stage[i - lo] = S[i];
+  for (int i0 = lo; i0 < hi; i0 += 8 * kConvThreads) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * kConvThreads + tid;
+      v[j] = (i < hi) ? S[i] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * kConvThreads + tid;
+      if (i < hi) stage[i - lo] = v[j];
+    }
+  }
   cluster_sync_all();
 
   const uint32_t local = (uint32_t)__cvta_generic_to_shared(stage);
@@ -593,7 +707,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   e = ensure_smem(k_tl_to_rowmajor, tl_conv_smem(part));
   if (e != cudaSuccess) return e;
   const long long spin = g_wait_limit.load();
-  k_large_init<<<dim3(B, split_for(B, 64)), 256, 0, s>>>(a);
+  k_large_init<<<dim3(B, split_for(B, 64, 8)), kInitThreads, 0, s>>>(a);
   for (int K = 0; K < T_max; ++K) {
     k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, K);
     const int ns = T_max - 1 - K;  // blocks after K in the largest airfoil

@@ -339,33 +339,41 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   } else if (warp >= 4 && warp < 8) {
     // ---------------- converters: x -> (x_hi in place, x_lo) ----------------
     const int ct = tid - 128;
+    constexpr int kPer = kTM * kKC / 128;  // operand values of a chunk per converter thread
     for (int q = 0; q < nq; ++q) {
       const int st = q % kStages, u = q / kStages;
+      // step 0: this thread's values of the chunk, all loads in flight before
+      // the stage is waited for.  A: rows ct / 32 + 4 j of the ragged tile
+      // (I, 0), column k0 + ct % 32; B: row k0 + j of block row 0 (row-major),
+      // column c0 + ct.  A warp reads 128 contiguous bytes per load.
+      float va[kPer], vb[kPer];
+      if (K == 0) {
+        int I, J;
+        tile_ij(q / nkc, I, J);
+        const int k0 = (q % nkc) * kKC, c0 = g.start(J);
+        const int ak = ct & 31, ar0 = ct >> 5;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          va[j] = (k0 + ak < g.e) ? F[g.rag(I, ar0 + 4 * j, k0 + ak)] : 0.0f;
+          vb[j] = (k0 + j < g.e) ? F[(int64_t)(k0 + j) * m + c0 + ct] : 0.0f;
+        }
+      }
       // every lane waits (acquiring the TMA's bytes), and the warp leaves together
       const bool ok = mbar_wait(full_bar(st), u & 1, fail, spin);
       if (!__all_sync(0xffffffffu, ok)) break;
       unsigned char* S = gbase + st * kStageBytes;
       if (K == 0) {
-        int I, J;
-        tile_ij(q / nkc, I, J);
-        const int k0 = (q % nkc) * kKC, c0 = g.start(J);
-#pragma unroll 4
-        for (int j = 0; j < kTM * kKC / 128; ++j) {
-          const int e = ct + 128 * j;
-          // A: row e / 32 of the ragged tile (I, 0), column k0 + e % 32
-          const int ar = e >> 5, ak = e & 31;
-          const float va = (k0 + ak < g.e) ? F[g.rag(I, ar, k0 + ak)] : 0.0f;
-          const uint32_t oa = sw_off(ar, ak);
-          const float ha = tf32_hi(va);
+        const int ak = ct & 31, ar0 = ct >> 5;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          const uint32_t oa = sw_off(ar0 + 4 * j, ak);
+          const float ha = tf32_hi(va[j]);
           *reinterpret_cast<float*>(S + oa) = ha;
-          *reinterpret_cast<float*>(S + kOpBytes + oa) = va - ha;
-          // B: row k0 + e / 128 of block row 0 (row-major), column c0 + e % 128
-          const int bk = e >> 7, bn = e & 127;
-          const float vb = (k0 + bk < g.e) ? F[(int64_t)(k0 + bk) * m + c0 + bn] : 0.0f;
-          const uint32_t ob = sw_off(bn, bk);
-          const float hb = tf32_hi(vb);
+          *reinterpret_cast<float*>(S + kOpBytes + oa) = va[j] - ha;
+          const uint32_t ob = sw_off(ct, j);
+          const float hb = tf32_hi(vb[j]);
           *reinterpret_cast<float*>(S + 2 * kOpBytes + ob) = hb;
-          *reinterpret_cast<float*>(S + 3 * kOpBytes + ob) = vb - hb;
+          *reinterpret_cast<float*>(S + 3 * kOpBytes + ob) = vb[j] - hb;
         }
       } else {
         float4* A4 = reinterpret_cast<float4*>(S);
