@@ -712,7 +712,12 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, K);
     const int ns = T_max - 1 - K;  // blocks after K in the largest airfoil
     if (ns <= 0) break;
-    k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, K);
+    if (K == 0) {
+      k_large_trsm<<<dim3(B, split_for(B, 2 * ns)), 256, large_trsm_smem(), s>>>(a, K);
+    } else {
+      e = launch_trsm_tc(a, tmap, K, split_for(B, ns, 1), spin, s);
+      if (e != cudaSuccess) return e;
+    }
     e = launch_update_tc(a, tmap, K, split_for(B, ns * ns, 1), spin, s);
     if (e != cudaSuccess) return e;
   }

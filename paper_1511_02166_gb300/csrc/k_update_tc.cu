@@ -476,10 +476,315 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_trsm_tc -- the triangular solves of step K >= 1 on the tensor cores:
+//   L21 = A21 U11^{-1}  for the tiles (I, K), I > K   (blocks with y odd);
+//   U12 = L11^{-1} A12  for the tiles (K, J), J > K   (blocks with y even),
+// written back in place, U12 transposed (the update's K-major B operand).
+// In MMA terms D[M][N] = sum_k A[M][k] B[N][k] with M = 128 rows of the tile
+// (r of A21, or c of A12^T), N = t, B[t][k] = X[k][t] for X = U11^{-1} (L21)
+// or B[t][k] = L11^{-1}[t][k] (U12^T).  Per block:
+//   1. the diagonal tile (K, K) is staged and the one triangular inverse this
+//      block needs is formed by substitution (a thread per column of the
+//      inverse); it is split into TF32 hi / lo and kept in shared memory as the
+//      B operand of all the block's tiles (128 KB);
+//   2. the tiles stream through two stages: warp 8 loads a K-chunk by TMA (a
+//      128 x 32 chunk of A21, or four 32 x 32 boxes of A12 that the converters
+//      transpose to A12^T), warps 4-7 split it into hi / lo, warp 9 issues the
+//      3xTF32 MMAs into one of two TMEM accumulators, warps 0-3 store the result
+//      over the tile (the tile's loads have all completed by then).
+// Waits are bounded as in k_update_tc.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint32_t kTsBhi = 0;                        // B hi: 4 chunks [t][32 k], 128-byte swizzle
+constexpr uint32_t kTsBlo = 4 * kOpBytes;             // B lo
+constexpr uint32_t kTsA = 8 * kOpBytes;               // A stages: raw, hi, lo (16 KB each)
+constexpr uint32_t kTsStage = 3 * kOpBytes;
+constexpr int kTsStages = 2;
+constexpr uint32_t kTsBar = kTsA + kTsStages * kTsStage;
+constexpr uint32_t kTsSmem = kTsBar + 1024 + 1024;    // barriers, then alignment slack
+constexpr int kTsLdD = 129;                           // row stride of the staged diagonal tile
+}  // namespace
+
+__global__ void __launch_bounds__(kThreadsTc, 1)
+    k_trsm_tc(SolveArgs a, const __grid_constant__ CUtensorMap tmap,
+              const __grid_constant__ CUtensorMap tmap32, int K, long long spin) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b), m = n + 1;
+  if (!(m > kLargeM && n <= bt.n_max && a.info[b] == 0)) return;
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
+  if (K < 1 || K >= g.T - 1) return;
+  const int ns = g.T - 1 - K;
+  const int kind = blockIdx.y & 1;  // 0: U12 tiles, 1: L21 tiles
+  const int gy = (int)gridDim.y >> 1, y0 = (int)blockIdx.y >> 1;
+  if (y0 >= ns) return;
+  const int my_tiles = (ns - y0 + gy - 1) / gy;
+  constexpr int nkc = kTlB / kKC;  // 4
+  const int nq = my_tiles * nkc;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t sraw = smem_u32(smraw);
+  const uint32_t sbase = (sraw + 1023u) & ~1023u;
+  unsigned char* gbase = smraw + (sbase - sraw);
+  const uint32_t bar_base = sbase + kTsBar;
+  // full[2] conv[2] empty[2] tfull[2] tempty[2] done
+  auto full_bar = [&](int st) { return bar_base + 8u * st; };
+  auto conv_bar = [&](int st) { return bar_base + 8u * (2 + st); };
+  auto empty_bar = [&](int st) { return bar_base + 8u * (4 + st); };
+  auto tfull_bar = [&](int ac) { return bar_base + 8u * (6 + ac); };
+  auto tempty_bar = [&](int ac) { return bar_base + 8u * (8 + ac); };
+  const uint32_t done_bar = bar_base + 8u * 10;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + kTsBar + 128);
+  volatile int* fail = reinterpret_cast<volatile int*>(gbase + kTsBar + 132);
+  float* F = a.LU + bt.mat_off[b];
+
+  // ---- 1. the inverse, as the B operand ----
+  // Thread j < 128 forms column j of the inverse, all threads walking the same
+  // rows t and terms q together (the staged tile is read by broadcast, the
+  // inverse by consecutive columns: no bank conflicts); entries that are zero
+  // by triangularity are computed as zeros rather than skipped.
+  {
+    float* D = reinterpret_cast<float*>(gbase + kTsA);  // 128 x kTsLdD
+    float* X = reinterpret_cast<float*>(gbase);         // 128 x 128, X[t][j]
+    const float* Td = F + g.tile(K, K);
+    for (int e = tid; e < kTlTile; e += kThreadsTc) {
+      const int r = e >> 7, c = e & 127;
+      D[r * kTsLdD + c] = Td[((c >> 5) << 12) + r * 32 + (c & 31)];
+    }
+    __syncthreads();
+    if (tid < kTlB) {
+      const int j = tid;
+      if (kind == 0) {
+        // L X = I (unit lower): X[t][j] = [t == j] - sum_{q < t} L[t][q] X[q][j]
+        for (int t = 0; t < kTlB; ++t) {
+          const float* Lt = D + t * kTsLdD;
+          float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+          int q = 0;
+          for (; q + 3 < t; q += 4) {
+            s0 = fmaf(Lt[q], X[q * 128 + j], s0);
+            s1 = fmaf(Lt[q + 1], X[(q + 1) * 128 + j], s1);
+            s2 = fmaf(Lt[q + 2], X[(q + 2) * 128 + j], s2);
+            s3 = fmaf(Lt[q + 3], X[(q + 3) * 128 + j], s3);
+          }
+          for (; q < t; ++q) s0 = fmaf(Lt[q], X[q * 128 + j], s0);
+          X[t * 128 + j] = (t == j ? 1.0f : 0.0f) - ((s0 + s1) + (s2 + s3));
+        }
+      } else {
+        // U Y = I: Y[t][j] = ([t == j] - sum_{q > t} U[t][q] Y[q][j]) / U[t][t]
+        for (int t = kTlB - 1; t >= 0; --t) {
+          const float* Ut = D + t * kTsLdD;
+          float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+          int q = t + 1;
+          for (; q + 3 < kTlB; q += 4) {
+            s0 = fmaf(Ut[q], X[q * 128 + j], s0);
+            s1 = fmaf(Ut[q + 1], X[(q + 1) * 128 + j], s1);
+            s2 = fmaf(Ut[q + 2], X[(q + 2) * 128 + j], s2);
+            s3 = fmaf(Ut[q + 3], X[(q + 3) * 128 + j], s3);
+          }
+          for (; q < kTlB; ++q) s0 = fmaf(Ut[q], X[q * 128 + j], s0);
+          X[t * 128 + j] = ((t == j ? 1.0f : 0.0f) - ((s0 + s1) + (s2 + s3))) / Ut[t];
+        }
+      }
+    }
+    __syncthreads();
+    // X -> the A region (D is no longer needed), then the B operand from it:
+    // U12^T = A12^T (L11^{-1})^T needs B[t][k] = L11^{-1}[t][k] = X[t][k];
+    // L21 = A21 U11^{-1} needs B[t][k] = U11^{-1}[k][t] = X[k][t]
+    float* Xc = D;
+    for (int e = tid; e < kTlTile; e += kThreadsTc) Xc[e] = X[e];
+    __syncthreads();
+    for (int e = tid; e < kTlTile; e += kThreadsTc) {
+      const int k = e >> 7, t = e & 127;
+      const float v = (kind == 0) ? Xc[t * 128 + k] : Xc[k * 128 + t];
+      const float h = tf32_hi(v);
+      const uint32_t o = (uint32_t)(k >> 5) * kOpBytes + sw_off(t, k & 31);
+      *reinterpret_cast<float*>(gbase + kTsBhi + o) = h;
+      *reinterpret_cast<float*>(gbase + kTsBlo + o) = v - h;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int st = 0; st < kTsStages; ++st) {
+      mbar_init(full_bar(st), 1);
+      mbar_init(conv_bar(st), 4);
+      mbar_init(empty_bar(st), 1);
+    }
+    for (int ac = 0; ac < 2; ++ac) {
+      mbar_init(tfull_bar(ac), 1);
+      mbar_init(tempty_bar(ac), 4);
+    }
+    mbar_init(done_bar, 1);
+    *fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  // the task's tile: (K, J) of A12 (kind 0) or (I, K) of A21 (kind 1)
+  auto tile_of = [&](int tau) {
+    const int j = y0 + tau * gy;
+    return (kind == 0) ? g.tile(K, K + 1 + j) : g.tile(K + 1 + j, K);
+  };
+  auto row_of = [&](int64_t tile_off, int kc) {
+    return (int)((g.base + tile_off + (int64_t)kc * kTlChunk) >> 5);
+  };
+
+  if (warp == kWarpTma) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nq; ++q) {
+        const int st = q % kTsStages, u = q / kTsStages;
+        if (u >= 1 && !mbar_wait(empty_bar(st), (u - 1) & 1, fail, spin)) break;
+        const int64_t t0 = tile_of(q / nkc);
+        const int kk = q % nkc;
+        const uint32_t raw = sbase + kTsA + st * kTsStage;
+        mbar_arrive_tx(full_bar(st), kOpBytes);
+        if (kind == 1) {
+          tma_load(raw, &tmap, row_of(t0, kk), full_bar(st));
+        } else {
+          // rows k in [32 kk, 32 kk + 32) of each 32-column chunk of A12
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            tma_load(raw + c4 * (kOpBytes / 4), &tmap32, row_of(t0, c4) + kKC * kk, full_bar(st));
+        }
+        issued = q + 1;
+      }
+      for (int q = max(0, issued - kTsStages); q < issued; ++q)
+        mbar_wait_done(full_bar(q % kTsStages), (q / kTsStages) & 1);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    const int ct = tid - 128;
+    for (int q = 0; q < nq; ++q) {
+      const int st = q % kTsStages, u = q / kTsStages;
+      const bool ok = mbar_wait(full_bar(st), u & 1, fail, spin);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      unsigned char* S = gbase + kTsA + st * kTsStage;  // raw, hi, lo
+      if (kind == 1) {
+        // raw is already in the MMA's swizzled layout: split element by element
+        const float4* R4 = reinterpret_cast<const float4*>(S);
+        float4* H4 = reinterpret_cast<float4*>(S + kOpBytes);
+        float4* L4 = reinterpret_cast<float4*>(S + 2 * kOpBytes);
+#pragma unroll 4
+        for (int j = 0; j < (int)(kOpBytes / 16) / 128; ++j) {
+          const int i = ct + 128 * j;
+          const float4 v = R4[i];
+          const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+          H4[i] = h;
+          L4[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+      } else {
+        // raw [c / 32][k][c % 32] -> A^T element (row c, column k), swizzled
+        const float* R = reinterpret_cast<const float*>(S);
+#pragma unroll 4
+        for (int j = 0; j < kTM * kKC / 128; ++j) {
+          const int e = ct + 128 * j;
+          const int k = e >> 7, c = e & 127;
+          const float v = R[(c >> 5) * (kTM * kKC / 4) + k * 32 + (c & 31)];
+          const float h = tf32_hi(v);
+          const uint32_t o = sw_off(c, k);
+          *reinterpret_cast<float*>(S + kOpBytes + o) = h;
+          *reinterpret_cast<float*>(S + 2 * kOpBytes + o) = v - h;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(conv_bar(st));
+    }
+  } else if (warp == kWarpMma) {
+    if (lane == 0) {
+      for (int q = 0; q < nq; ++q) {
+        const int st = q % kTsStages, u = q / kTsStages;
+        const int kk = q % nkc, tau = q / nkc, ac = tau & 1, v = tau >> 1;
+        if (kk == 0 && v >= 1 && !mbar_wait(tempty_bar(ac), (v - 1) & 1, fail, spin)) break;
+        if (!mbar_wait(conv_bar(st), u & 1, fail, spin)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ac * kTN);
+        const uint32_t ah = sbase + kTsA + st * kTsStage + kOpBytes, al = ah + kOpBytes;
+        const uint32_t bh = sbase + kTsBhi + kk * kOpBytes, bl = sbase + kTsBlo + kk * kOpBytes;
+#pragma unroll
+        for (int s = 0; s < kKC / 8; ++s) {
+          const uint32_t ko = 32u * s;
+          const uint32_t acc0 = (kk > 0 || s > 0) ? 1u : 0u;
+          tc_mma(d, desc_sw128(ah + ko), desc_sw128(bh + ko), acc0);
+          tc_mma(d, desc_sw128(ah + ko), desc_sw128(bl + ko), 1u);
+          tc_mma(d, desc_sw128(al + ko), desc_sw128(bh + ko), 1u);
+        }
+        tc_commit(empty_bar(st));
+        if (kk == nkc - 1) tc_commit(tfull_bar(ac));
+      }
+      tc_commit(done_bar);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: D over the tile (U12 transposed): row = M index ----
+    const int r = 32 * warp + lane;
+    for (int tau = 0; tau < my_tiles; ++tau) {
+      const int ac = tau & 1, v = tau >> 1;
+      if (!epi_all(mbar_wait(tfull_bar(ac), v & 1, fail, spin))) break;
+      tc_fence_after();
+      float* out = F + tile_of(tau);
+#pragma unroll 1
+      for (int s = 0; s < kTN / kKC; ++s) {
+        float v32[32];
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ac * kTN + kKC * s), v32);
+        if (s == kTN / kKC - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty_bar(ac));
+        }
+        float4* o4 = reinterpret_cast<float4*>(out + (int64_t)s * kTlChunk + r * 32);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          o4[j] = make_float4(v32[4 * j], v32[4 * j + 1], v32[4 * j + 2], v32[4 * j + 3]);
+      }
+    }
+  }
+
+  __syncthreads();
+  const bool drained = mbar_wait_done(done_bar, 0);
+  if (!drained || *fail) {
+    if (tid == 0) a.info[b] = PANEL_INFO_DEVICE_TIMEOUT;
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
 // The tensor map of the factor buffer as rows of 32 floats (128 bytes), boxes
 // of 128 rows (one chunk), 128-byte swizzle.  `floats` bounds the buffer's
 // size from above; only chunks inside the caller's buffer are ever addressed.
+static cudaError_t encode_map(float* base, uint64_t floats, uint32_t box_rows, bool swizzle,
+                              CUtensorMap* out);
+
 cudaError_t make_update_map(float* base, uint64_t floats, UpdateMap* out) {
+  cudaError_t e = encode_map(base, floats, kTM, true, &out->map);
+  if (e == cudaSuccess) e = encode_map(base, floats, kKC, false, &out->map32);
+  return e;
+}
+
+// rows of 32 floats, boxes of `box_rows` rows; 128-byte swizzle or none
+static cudaError_t encode_map(float* base, uint64_t floats, uint32_t box_rows, bool swizzle,
+                              CUtensorMap* out) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   std::call_once(once, [] {
@@ -497,15 +802,25 @@ cudaError_t make_update_map(float* base, uint64_t floats, UpdateMap* out) {
   if (rows < (uint64_t)kTM) rows = kTM;
   const cuuint64_t dims[2] = {(cuuint64_t)kTlC, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)kTlC * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)kTlC, (cuuint32_t)kTM};
+  const cuuint32_t box[2] = {(cuuint32_t)kTlC, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(&out->map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides,
-                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUresult r = encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t ensure_update_smem() { return ensure_smem(k_update_tc, (size_t)kSmemBytes); }
+cudaError_t ensure_update_smem() {
+  const cudaError_t e = ensure_smem(k_update_tc, (size_t)kSmemBytes);
+  return e != cudaSuccess ? e : ensure_smem(k_trsm_tc, (size_t)kTsSmem);
+}
+
+cudaError_t launch_trsm_tc(const SolveArgs& a, const UpdateMap& map, int K, int split,
+                           long long spin, cudaStream_t s) {
+  k_trsm_tc<<<dim3(a.bt.B, 2 * split), kThreadsTc, kTsSmem, s>>>(a, map.map, map.map32, K, spin);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_update_tc(const SolveArgs& a, const UpdateMap& map, int K, int split,
                              long long spin, cudaStream_t s) {

@@ -85,11 +85,14 @@ struct TlGeom {
 
 // The factor buffer as one tensor map (k_update_tc.cu).
 struct UpdateMap {
-  CUtensorMap map;
+  CUtensorMap map;    // boxes of 128 rows, 128-byte swizzle (a chunk)
+  CUtensorMap map32;  // boxes of 32 rows, no swizzle (a quarter of a chunk)
 };
 cudaError_t make_update_map(float* base, uint64_t floats, UpdateMap* out);
 cudaError_t ensure_update_smem();
 cudaError_t launch_update_tc(const SolveArgs& a, const UpdateMap& map, int K, int split,
                              long long spin, cudaStream_t s);
+cudaError_t launch_trsm_tc(const SolveArgs& a, const UpdateMap& map, int K, int split,
+                           long long spin, cudaStream_t s);
 
 }  // namespace panel
