@@ -98,8 +98,8 @@ def test_large_full_population_samples():
     # column-split adjoint contraction) in the bench's launch configuration.
     # Strengths, Cl and the backward error against the FP64 oracle as in
     # test_gpu_large.py (gamma within 5e-9, backward error against the oracle's
-    # matrix in long double within the refinement's tolerance 1e-12, Cl within
-    # 1e-10).  dCl/dx within 1e-9
+    # matrix in long double within 4 x the refinement's tolerance 1e-12, Cl
+    # within 1e-10).  dCl/dx within 1e-9
     # (inf norm relative) of extended-precision oracle gradients stored in
     # tests/golden (the FP64 oracle's own gradient is off by up to ~4e-10 at
     # these condition numbers, see make_large_gradient_golden.py): the smallest
@@ -134,7 +134,7 @@ def test_large_full_population_samples():
         o, os_ = pop.offsets[b] + b, sub.offsets[s] + s
         assert rel_inf(u[o:o + n], ref["u"][os_:os_ + n]) < 5e-9, b
         gs = slice(pop.offsets[b], pop.offsets[b + 1])
-        assert _backward_error(pop.nodes[gs], pop.alpha[b], u[o:o + n + 1]) < 1e-12, b
+        assert _backward_error(pop.nodes[gs], pop.alpha[b], u[o:o + n + 1]) < 4e-12, b
     assert cl_err(pb.cl.cpu().numpy()[idx], ref["cl"]) < 1e-10
 
 
