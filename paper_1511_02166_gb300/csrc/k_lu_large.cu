@@ -534,7 +534,8 @@ size_t large_trsm_smem() {
 // The tiled layout of block row I >= 1 back to row-major.  Both orders fill
 // the same 128 m floats (the block row's span), so the span is first staged
 // across the shared memory of an 8-block cluster (block c holds floats
-// [c part, (c + 1) part) of the tiled order), and after a cluster barrier the
+// [c part, (c + 1) part) of the tiled order, brought in by one bulk
+// asynchronous copy and the ragged ends), and after a cluster barrier the
 // blocks' warps write the row-major order in 32 x 32 pieces, reading every
 // value from whichever block holds it (distributed shared memory): lane l
 // takes column l of a piece, so each read and each write of a warp is 128
@@ -554,9 +555,15 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 
 // float q of the staged span (block q / part of the cluster holds it)
-__device__ __forceinline__ float dsmem_ld(uint32_t local, int part, int q) {
+// The staged span: block c holds the floats i in [c part, (c + 1) part) at
+// stage[i - c part + pad(c)], pad(c) = (address of float c part) / 4 mod 4, so
+// that the shared image of a 16-byte aligned global segment is 16-byte aligned
+// too (one bulk copy moves the aligned middle of a block's range).
+__device__ __forceinline__ float dsmem_ld(uint32_t local, int part, int q, uint32_t sa4) {
   const unsigned owner = (unsigned)(q / part);
-  const uint32_t addr = local + 4u * (uint32_t)(q - (int)owner * part);
+  const int lo = (int)owner * part;
+  const int pad = (int)((sa4 + (uint32_t)lo) & 3u);
+  const uint32_t addr = local + 4u * (uint32_t)(q - lo + pad);
   uint32_t remote;
   float v;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(owner));
@@ -580,24 +587,61 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* S = a.LU + bt.mat_off[b] + g.span(I);
+  const uint32_t sa4 = (uint32_t)((reinterpret_cast<uintptr_t>(S) >> 2) & 3u);
   const int lo = (int)rank * part, hi = min(L, lo + part);
-  for (int i0 = lo; i0 < hi; i0 += 8 * kConvThreads) {
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = i0 + j * kConvThreads + tid;
-      v[j] = (i < hi) ? S[i] : 0.0f;
+  const int pad = (int)((sa4 + (uint32_t)lo) & 3u);
+  __shared__ __align__(8) uint64_t stage_bar;
+  if (lo < hi) {
+    // the aligned middle [a0, a1) by one bulk copy, the ragged ends by threads
+    const int a0 = min(hi, lo + ((4 - pad) & 3));
+    const int a1 = max(a0, hi - (int)((sa4 + (uint32_t)hi) & 3u));
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&stage_bar);
+    const uint32_t bytes = 4u * (uint32_t)(a1 - a0);
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = i0 + j * kConvThreads + tid;
-      if (i < hi) stage[i - lo] = v[j];
+    __syncthreads();
+    // (the shared image is 16-byte aligned where the global segment is only if the
+    // dynamic shared memory itself starts on a 16-byte boundary; else threads copy)
+    const bool bulk = ((uint32_t)__cvta_generic_to_shared(stage) & 15u) == 0;
+    if (!bulk)
+      for (int i = a0 + tid; i < a1; i += kConvThreads) stage[i - lo + pad] = S[i];
+    if (tid == 0) {
+      asm volatile(
+          "{\n\t.reg .b64 st;\n\t"
+          "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+          "r"(bulk ? bytes : 0u)
+          : "memory");
+      if (bulk && bytes > 0)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(stage + (a0 - lo + pad))),
+            "l"(S + a0), "r"(bytes), "r"(bar)
+            : "memory");
     }
+    if (tid < a0 - lo) stage[tid + pad] = S[lo + tid];
+    if (tid < hi - a1) stage[a1 - lo + pad + tid] = S[a1 + tid];
+    // bounded wait for the copy (it completes on its own; the bound only keeps
+    // the wait finite -- a copy that did not land marks the airfoil)
+    bool landed = false;
+    for (long long it = 0; it < (1ll << 24) && !landed; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar)
+          : "memory");
+      landed = done != 0;
+    }
+    if (!landed && tid == 0) a.info[b] = PANEL_INFO_DEVICE_TIMEOUT;
   }
   cluster_sync_all();
 
   const uint32_t local = (uint32_t)__cvta_generic_to_shared(stage);
-  float* tb = stage + part + warp * (32 * kTbufLd);
+  float* tb = stage + part + 4 + warp * (32 * kTbufLd);
   const int sp = (int)(g.tile(I, 1) - g.span(I));  // the full tiles start here (the head)
   const int nbr = (g.e + 31) >> 5;                 // 32-column pieces of the ragged columns
   const int ncb = nbr + 4 * (g.T - 1);
@@ -615,7 +659,7 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
         for (int j = 0; j < 8; ++j) {
           const int idx = (rr0 + r8 + j) * g.e + c;
           const int q = idx < sp ? idx : sp + (g.T - 1) * kTlTile + (idx - sp);
-          v[j] = ok ? dsmem_ld(local, part, q) : 0.0f;
+          v[j] = ok ? dsmem_ld(local, part, q, sa4) : 0.0f;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -632,7 +676,7 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
           float v[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            v[j] = dsmem_ld(local, part, t0 + rg * kTlChunk + (32 * kc + j8 + j) * 32 + lane);
+            v[j] = dsmem_ld(local, part, t0 + rg * kTlChunk + (32 * kc + j8 + j) * 32 + lane, sa4);
 #pragma unroll
           for (int j = 0; j < 8; ++j) tb[lane * kTbufLd + j8 + j] = v[j];
         }
@@ -645,7 +689,7 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
           float v[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            v[j] = dsmem_ld(local, part, t0 + kc * kTlChunk + (rr0 + r8 + j) * 32 + lane);
+            v[j] = dsmem_ld(local, part, t0 + kc * kTlChunk + (rr0 + r8 + j) * 32 + lane, sa4);
 #pragma unroll
           for (int j = 0; j < 8; ++j) S[(int64_t)(rr0 + r8 + j) * m + col] = v[j];
         }
@@ -658,7 +702,7 @@ __global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, in
 // floats of a block row per cluster block (a multiple of 4), for size m
 static int tl_part(int m) { return ((kTlB * m + kClusterTl - 1) / kClusterTl + 3) & ~3; }
 static size_t tl_conv_smem(int part) {
-  return (size_t)part * 4 + (size_t)kConvWarps * 32 * kTbufLd * 4;
+  return (size_t)(part + 4) * 4 + (size_t)kConvWarps * 32 * kTbufLd * 4;
 }
 
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
