@@ -575,6 +575,7 @@ def measure_workload(name, mode, args, ctx, headline=False, extras=False):
            "ms_per_step": ms, "solves_and_gradients_per_s": whole_job_rate(world, B, ms),
            "ms_per_solve_step": ms_solve, "solves_per_s": whole_job_rate(world, B, ms_solve),
            "size_buckets": len(pb.buckets), "inverse_buckets": int(sum(pb.inverse)),
+           "tuning": pb.tuning(),
            "refinement_iters": {"mean": float(iters.mean()), "max": int(iters.max())}
            if mode == "mixed" else None,
            "info_nonzero": int((info != 0).sum()),
@@ -763,6 +764,7 @@ def run_ours(args):
                       "max_iter": args.max_iter, "tol": args.tol,
                       "graph": bool(args.graph), "size_buckets": head["size_buckets"],
                       "inverse_buckets": head["inverse_buckets"],
+                      "tuning": head["tuning"],
                       "parallelism": "dp%d (independent airfoils)" % world},
            "what": "value: airfoils per second with Cl and dCl/dx (assemble, LU, refinement of "
                    "the forward and transposed systems, forces, adjoint contraction); "

@@ -27,6 +27,20 @@ PANEL_WITH_ADJOINT = 0x10
 PANEL_FACTOR_ONLY = 0x20
 PANEL_REUSE_FACTOR = 0x40
 PANEL_INVERSE = 0x80
+PANEL_TUNE_IR_SHIFT = 8
+PANEL_TUNE_ROUNDS_SHIFT = 12
+
+
+def PANEL_TUNE_IR(shape: int) -> int:
+    """Refinement block shape field of the flags: 0 by size, 1..4 = 128, 256, 512,
+    1024 threads per block."""
+    return int(shape) << PANEL_TUNE_IR_SHIFT
+
+
+def PANEL_TUNE_ROUNDS(sel: int) -> int:
+    """Assembly near-field queue field of the flags: 0 by size, 1 inline, 2..5 =
+    after 4, 8, 16, 32 pairs per thread."""
+    return int(sel) << PANEL_TUNE_ROUNDS_SHIFT
 PANEL_N_MAX = 2048
 
 INFO_FEW_NODES = -1

@@ -22,13 +22,13 @@ cudaError_t launch_forces(const Batch&, const double*, const double*, const doub
                           const double*, const int32_t*, double*, double*, double*, double*,
                           cudaStream_t);
 cudaError_t launch_assemble_df(const Batch&, const double*, const double*, float*, float*,
-                               double*, int32_t*, cudaStream_t);
+                               double*, int32_t*, cudaStream_t, int rounds_sel = 0);
 cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_t*, int32_t*,
                             bool, cudaStream_t);
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t,
-                            int rhs_kind = 0);
+                            int rhs_kind = 0, int ir_shape = 0);
 cudaError_t launch_ga_sample(int, int, int, const double*, const double*, double*, cudaStream_t);
 cudaError_t launch_ga_step(int, int, int, double, double, const double*, const double*,
                            const double*, const double*, const double*, const double*, double*,
@@ -65,9 +65,14 @@ int mode_of(int flags) {
   return 0;
 }
 
+int tune_ir(int flags) { return (flags >> PANEL_TUNE_IR_SHIFT) & 7; }
+int tune_rounds(int flags) { return (flags >> PANEL_TUNE_ROUNDS_SHIFT) & 7; }
+
 bool flags_ok(int flags) {
   const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
-                    PANEL_REUSE_FACTOR | PANEL_INVERSE;
+                    PANEL_REUSE_FACTOR | PANEL_INVERSE | (7 << PANEL_TUNE_IR_SHIFT) |
+                    (7 << PANEL_TUNE_ROUNDS_SHIFT);
+  if (tune_ir(flags) > 4 || tune_rounds(flags) > 5) return false;
   if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
   const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
   if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;
@@ -165,7 +170,8 @@ int panel_assemble(int B, int n_max, int flags, const double* nodes, const int64
     return status_of(panel::launch_assemble_f64(bt, alpha, vinf, A64, rhs, info, s));
   }
   if (!A_hi || !A_lo) return PANEL_EINVAL;
-  return status_of(panel::launch_assemble_df(bt, alpha, vinf, A_hi, A_lo, rhs, info, s));
+  return status_of(
+      panel::launch_assemble_df(bt, alpha, vinf, A_hi, A_lo, rhs, info, s, tune_rounds(flags)));
 }
 
 int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t* node_offsets,
@@ -196,7 +202,8 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
                                (flags & PANEL_INVERSE) != 0, s);
   if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
-                               adj ? lambda : nullptr, max_iter, tol, info, iters, s);
+                               adj ? lambda : nullptr, max_iter, tol, info, iters, s, 0,
+                               tune_ir(flags));
   return status_of(e);
 }
 

@@ -25,7 +25,7 @@ cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t,
-                            int rhs_kind);
+                            int rhs_kind, int ir_shape);
 }  // namespace panel
 
 namespace {
@@ -124,7 +124,7 @@ int panel_solve_noalloc(int B, int n_max, int flags, const int64_t* node_offsets
     if (e == cudaSuccess)
       e = panel::launch_ir_mixed(bt, A_hi, A_lo, static_cast<const float*>(LU), piv, rhs, vinf,
                                  chord, u, adj ? lambda : nullptr, max_iter, tol, info, iters, s,
-                                 0);
+                                 0, 0);
   }
   return e == cudaSuccess ? PANEL_OK : PANEL_ECUDA;
 }

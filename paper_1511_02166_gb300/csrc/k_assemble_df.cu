@@ -138,21 +138,29 @@ __global__ void __launch_bounds__(256) k_assemble_df(Batch bt, const double* __r
 // pair indices, 16 KB); 0 above 1024 panels: there the panel constants take
 // most of the shared memory, one block fits an SM, and the barriers of the
 // deferred pass cost more than the mixed branches (C5 assembly 36 -> 49 ms).
-static int assemble_rounds(int n_max) { return n_max <= 1024 ? 16 : 0; }
+// `sel` (the PANEL_TUNE_ROUNDS field of the flags) overrides it: 1 inline, 2..5
+// rounds of 4, 8, 16 or 32 pairs; 0 keeps the default.
+static int assemble_rounds(int n_max, int sel) {
+  static const int kSel[6] = {-1, 0, 4, 8, 16, 32};
+  if (sel >= 1 && sel <= 5) return kSel[sel];
+  return n_max <= 1024 ? 16 : 0;
+}
 
-size_t assemble_df_smem(int n_max) {
+static size_t assemble_df_smem(int n_max, int rounds) {
   return 257 * 16 + 34 * 8 + (size_t)(2 * n_max + 32) * 8 + (size_t)kPanelFields * n_max * 4 +
-         ((size_t)256 * assemble_rounds(n_max) + 1) * 4;
+         ((size_t)256 * rounds + 1) * 4;
 }
 
 cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const double* vinf,
                                float* A_hi, float* A_lo, double* rhs, int32_t* info,
-                               cudaStream_t s) {
-  const size_t smem = assemble_df_smem(bt.n_max);
+                               cudaStream_t s, int rounds_sel) {
+  int rounds = assemble_rounds(bt.n_max, rounds_sel);
+  // a requested queue that does not fit the shared memory falls back to the default
+  if (assemble_df_smem(bt.n_max, rounds) > 232448) rounds = assemble_rounds(bt.n_max, 0);
+  const size_t smem = assemble_df_smem(bt.n_max, rounds);
   cudaError_t e = ensure_smem(k_assemble_df, smem);
   if (e != cudaSuccess) return e;
-  k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info,
-                                        assemble_rounds(bt.n_max));
+  k_assemble_df<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info, rounds);
   return cudaGetLastError();
 }
 

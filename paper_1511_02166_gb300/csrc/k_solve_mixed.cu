@@ -880,6 +880,7 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.inverse = 0;
   a.n_cap = bt.n_max;
   a.rhs_kind = 0;
+  a.ir_shape = 0;
   a.vjp = 0;
   a.w_cl = a.w_u = a.w_cp = a.u_in = nullptr;
   return a;
@@ -936,6 +937,23 @@ static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
   auto fits = [&](int nt, int blocks) {
     return (size_t)blocks * (ir_mixed_smem(n_max, nt) + 1024) <= 233472;
   };
+  // an explicit shape (autotuning), when one block of it fits the shared memory
+  switch (a.ir_shape) {
+    case 1:
+      if (fits(128, 1) && n_max + 1 <= 7 * 32) return launch_ir_shape<128, 8, 7>(a, s);
+      break;
+    case 2:
+      if (fits(kThreads, 1)) return launch_ir_shape<kThreads, 4>(a, s);
+      break;
+    case 3:
+      if (fits(512, 1)) return launch_ir_shape<512, 2>(a, s);
+      break;
+    case 4:
+      if (fits(1024, 1)) return launch_ir_shape<1024, 1>(a, s);
+      break;
+    default:
+      break;
+  }
   if (fits(128, 8) && n_max + 1 <= 7 * 32 && a.bt.B >= 8 * sm_count())
     return launch_ir_shape<128, 8, 7>(a, s);
   if (n_max + 1 <= kFuseM || fits(kThreads, 4)) return launch_ir_shape<kThreads, 4>(a, s);
@@ -963,10 +981,11 @@ cudaError_t launch_ir_mixed(const Batch& bt, const float* A_hi, const float* A_l
                             const float* LU, const int32_t* piv, const double* rhs,
                             const double* vinf, const double* chord, double* u, double* lam,
                             int max_iter, double tol, int32_t* info, int32_t* iters,
-                            cudaStream_t s, int rhs_kind) {
+                            cudaStream_t s, int rhs_kind, int ir_shape) {
   SolveArgs a = make_args(bt, A_hi, A_lo, const_cast<float*>(LU), const_cast<int32_t*>(piv),
                           rhs, vinf, chord, u, lam, max_iter, tol, info, iters);
   a.rhs_kind = rhs_kind;
+  a.ir_shape = ir_shape;
   return launch_ir_kernel(a, s);
 }
 

@@ -31,6 +31,7 @@ struct SolveArgs {
   int inverse;       // m <= kGjM: Gauss-Jordan inverse (k_gj_mixed.cu) instead of the LU
   int n_cap;         // the caller's n_max (bt.n_max may be lowered to size a kernel)
   int rhs_kind;      // forward right-hand side: 0 rhs, 1 v m_y, 2 -v m_x (polar basis)
+  int ir_shape;      // refinement block shape: 0 by size, 1..4 = 128x8, 256x4, 512x2, 1024x1
   // Transposed right-hand side of a vector-Jacobian product (vjp != 0):
   // w_cl[b] dCl/du + w_u + w_cp dCp/du (each may be NULL = 0), with the
   // strengths u_in of the forward solution; vjp == 0 is dCl/du alone.

@@ -5,9 +5,10 @@ matrices, factors, solutions, forces and gradients) and runs the four library
 calls on the current torch stream.  A ragged population is cut into size
 buckets (contiguous runs of the size-sorted launch order), each launched with
 its own size bound so that small airfoils get small shared-memory footprints;
-``autotune()`` times the two factorisations (LU, or the Gauss-Jordan inverse)
-per bucket and remembers the faster one, and ``capture()`` records a whole
-step into a CUDA graph.  ``PanelCl`` is
+``autotune()`` times the bucket width, and per bucket the assembly's near-field
+rounds, the factorisation (LU, or the Gauss-Jordan inverse) and the
+refinement's block shape, and remembers the fastest; ``capture()`` records a
+whole step into a CUDA graph.  ``PanelCl`` is
 a ``torch.autograd.Function`` mapping node coordinates to Cl whose backward is
 ``panel_adjoint``.  Everything numerical happens in the CUDA library.
 """
@@ -158,23 +159,52 @@ class PanelBatch:
         self.have_lambda = False
         sizes = np.diff(offsets_h)
         sorted_sizes = sizes[order_h] if self.B else sizes
+        self.bucket_min = int(bucket_min)
+        self.bucket_width = bucket_width
         if bucket_width is None or self.B == 0:
             self.buckets = [(0, self.B, self.n_max)] if self.B else []
         else:
             self.buckets = size_buckets(sorted_sizes, int(bucket_width), int(bucket_min))
+        self._reset_tuning()
+        self.graph = None
+
+    def _reset_tuning(self):
+        """Per bucket: the factorisation (Gauss-Jordan inverse or LU), the
+        refinement's block shape and the assembly's near-field rounds (0 = the
+        library's choice by size)."""
         self.inverse = [False] * len(self.buckets)
+        self.ir_shape = [0] * len(self.buckets)
+        self.rounds = [0] * len(self.buckets)
+
+    def set_bucket_width(self, width):
+        """Cut the population into buckets of `width` panels (None: one bucket)
+        and forget the per-bucket tuning."""
+        sizes = np.diff(self.offsets_h)
+        order_h = self.order.cpu().numpy()
+        if width is None or self.B == 0:
+            self.buckets = [(0, self.B, self.n_max)] if self.B else []
+        else:
+            self.buckets = size_buckets(sizes[order_h], int(width), self.bucket_min)
+        self.bucket_width = width
+        self._reset_tuning()
         self.graph = None
 
     # -- the four library calls (per size bucket) --------------------------------
     def assemble(self):
-        for start, cnt, nmax in self.buckets:
-            bd.panel_assemble(cnt, nmax, self.flags, self.nodes, self.node_offsets,
-                              self.mat_offsets, self.order[start:], self.alpha, self.vinf,
-                              self.A64, self.A_hi, self.A_lo, self.rhs, self.info)
+        for k, (start, cnt, nmax) in enumerate(self.buckets):
+            bd.panel_assemble(cnt, nmax, self.flags | self._asm_tune(k), self.nodes,
+                              self.node_offsets, self.mat_offsets, self.order[start:],
+                              self.alpha, self.vinf, self.A64, self.A_hi, self.A_lo, self.rhs,
+                              self.info)
+
+    def _asm_tune(self, k):
+        return bd.PANEL_TUNE_ROUNDS(self.rounds[k]) if self.flags == bd.PANEL_MIXED else 0
 
     def _solve_bucket(self, k, start, cnt, nmax, with_adjoint, stage, stream=None):
         f = self.flags | (bd.PANEL_WITH_ADJOINT if with_adjoint else 0)
         f |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
+        if self.flags == bd.PANEL_MIXED:
+            f |= bd.PANEL_TUNE_IR(self.ir_shape[k])
         if self.inverse[k] and stage != "refine":
             f |= bd.PANEL_INVERSE
         bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
@@ -312,52 +342,93 @@ class PanelBatch:
         return n
 
     # -- autotuning and graph capture -------------------------------------------
-    def autotune(self, reps: int = 3, use_cache: bool = True):
-        """Pick, per size bucket, the faster factorisation for a whole solve
-        (factor + refinement of both systems, mixed mode): the default LU, or
-        the Gauss-Jordan inverse (PANEL_INVERSE, m <= 288: three times the
-        factor's flops, one matrix-vector product per correction instead of
-        two triangular sweeps).  Buckets of larger airfoils have only the LU.
-        Results are cached by device, bucket size bound and batch size."""
+    BUCKET_WIDTHS = (96, 128, 192, 256, None)
+
+    def _time(self, fn, reps):
+        fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def autotune(self, reps: int = 3, use_cache: bool = True, widths=BUCKET_WIDTHS):
+        """Pick the launch configuration by timing it (mixed mode):
+          1. the bucket width, when the population's sizes differ: each width of
+             `widths` (None = one bucket) times a whole step (assemble, solve with
+             the transposed system, forces, adjoint);
+          2. per bucket, the assembly's near-field rounds (PANEL_TUNE_ROUNDS 0..5);
+          3. per bucket, the solve (factor + refinement of both systems): the LU or
+             the Gauss-Jordan inverse (m <= 288) with each refinement block shape
+             (PANEL_TUNE_IR 0..4).
+        Choices are cached by device, size bound and batch class
+        ($PANEL_AUTOTUNE_CACHE).  Returns {key: choice}."""
         if self.flags != bd.PANEL_MIXED or not self.buckets:
             return dict()
         dev = torch.cuda.get_device_name(self.device)
         with _tune_lock:
             cache = _load_tune_cache() if use_cache else {}
+        chosen = {}
+        bclass = lambda cnt: min(cnt, 1024) // 152 * 152
+        sizes = np.diff(self.offsets_h)
+        # 1. bucket width
+        if len(set(sizes.tolist())) > 1 and widths:
+            sig = "%s|width|B%d|n%d-%d|w%s" % (dev, self.B, int(sizes.min()), int(sizes.max()),
+                                               ",".join(str(w) for w in widths))
+            if sig in cache:
+                best = cache[sig]
+            else:
+                times = {}
+                for w in widths:
+                    self.set_bucket_width(w)
+                    times[str(w)] = self._time(lambda: self.run(with_grad=True), reps)
+                best = min(times, key=times.get)
+                cache[sig] = best
+            self.set_bucket_width(None if best == "None" else int(best))
+            chosen[sig] = best
         self.assemble()
         torch.cuda.synchronize(self.device)
-        chosen = {}
         for k, (start, cnt, nmax) in enumerate(self.buckets):
-            if nmax + 1 > GJ_MAX_M:
-                self.inverse[k] = False  # the LU is the only factorisation here
-                continue
-            key = "%s|gj-lu|n%d|b%d" % (dev, nmax, min(cnt, 1024) // 152 * 152)
-            if key in cache:
-                self.inverse[k] = bool(cache[key])
-                chosen[key] = cache[key]
-                continue
-            times = []
-            for variant in (False, True):
-                f = bd.PANEL_MIXED | bd.PANEL_WITH_ADJOINT | (bd.PANEL_INVERSE if variant else 0)
+            # 2. assembly rounds
+            key = "%s|asm-rounds|n%d|b%d" % (dev, nmax, bclass(cnt))
+            if key not in cache:
+                times = []
+                for r in range(6):
+                    f = bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(r)
 
-                def call(f=f, start=start, cnt=cnt, nmax=nmax):
-                    bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets,
-                                   self.mat_offsets, self.order[start:], None, self.A_hi,
-                                   self.A_lo, self.LU, self.piv, self.rhs, self.vinf,
-                                   self.chord, self.u, self.lam, self.max_iter, self.tol,
-                                   self.info, self.iters)
-                call()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(reps):
-                    call()
-                e1.record()
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            self.inverse[k] = times[1] < times[0]
-            chosen[key] = self.inverse[k]
-            cache[key] = self.inverse[k]
+                    def call(f=f, start=start, cnt=cnt, nmax=nmax):
+                        bd.panel_assemble(cnt, nmax, f, self.nodes, self.node_offsets,
+                                          self.mat_offsets, self.order[start:], self.alpha,
+                                          self.vinf, None, self.A_hi, self.A_lo, self.rhs,
+                                          self.info)
+                    times.append(self._time(call, reps))
+                cache[key] = int(np.argmin(times))
+            self.rounds[k] = int(cache[key])
+            chosen[key] = self.rounds[k]
+            # 3. factorisation and refinement shape
+            key = "%s|solve|n%d|b%d" % (dev, nmax, bclass(cnt))
+            if key not in cache:
+                best, best_t = None, None
+                for inverse in ((False, True) if nmax + 1 <= GJ_MAX_M else (False,)):
+                    for shape in range(5):
+                        f = (bd.PANEL_MIXED | bd.PANEL_WITH_ADJOINT | bd.PANEL_TUNE_IR(shape) |
+                             (bd.PANEL_INVERSE if inverse else 0))
+
+                        def call(f=f, start=start, cnt=cnt, nmax=nmax):
+                            bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets,
+                                           self.mat_offsets, self.order[start:], None,
+                                           self.A_hi, self.A_lo, self.LU, self.piv, self.rhs,
+                                           self.vinf, self.chord, self.u, self.lam,
+                                           self.max_iter, self.tol, self.info, self.iters)
+                        t = self._time(call, reps)
+                        if best_t is None or t < best_t:
+                            best, best_t = [bool(inverse), shape], t
+                cache[key] = best
+            self.inverse[k], self.ir_shape[k] = bool(cache[key][0]), int(cache[key][1])
+            chosen[key] = [self.inverse[k], self.ir_shape[k]]
         if use_cache:
             with _tune_lock:
                 merged = _load_tune_cache()
@@ -365,6 +436,18 @@ class PanelBatch:
                 _store_tune_cache(merged)
         self.info.zero_()
         return chosen
+
+    def tuning(self):
+        """The launch configuration in use: bucket width and, per bucket, its
+        size bound and count, factorisation, refinement shape and assembly rounds."""
+        return {"bucket_width": self.bucket_width,
+                "buckets": [{"n_max": int(nmax), "count": int(cnt),
+                             "factor": "gauss-jordan" if self.inverse[k] else "lu",
+                             "refine_shape": ["by size", "128x8", "256x4", "512x2",
+                                              "1024x1"][self.ir_shape[k]],
+                             "assembly_rounds": ["by size", "inline", 4, 8, 16,
+                                                 32][self.rounds[k]]}
+                            for k, (start, cnt, nmax) in enumerate(self.buckets)]}
 
     def capture(self, with_grad: bool = True):
         """Record one step into a CUDA graph (after a warm-up step outside it)."""

@@ -147,3 +147,17 @@ def test_debug_wait_limit_is_host_state_with_a_default():
     assert bd.panel_debug_wait_limit(5) == default
     assert bd.panel_debug_wait_limit(-1) == 5
     assert bd.panel_debug_wait_limit(0) == default
+
+
+def test_tuning_fields_of_the_flags_are_validated():
+    # the launch-shape fields are accepted in range and rejected out of range, on
+    # the host, before anything is launched (null device pointers: nothing runs)
+    lib = bd.load()
+    offs = np.array([0, 10], dtype=np.int64)
+    mat, order, nmax = bd.panel_plan(offs)
+    p = ctypes.c_void_p(1)  # never dereferenced: validation fails or B = 0 returns first
+    for f, want in [(bd.PANEL_MIXED | bd.PANEL_TUNE_IR(5), bd.PANEL_EINVAL),
+                    (bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(6), bd.PANEL_EINVAL),
+                    (bd.PANEL_MIXED | bd.PANEL_TUNE_IR(4) | bd.PANEL_TUNE_ROUNDS(5), bd.PANEL_OK)]:
+        st = lib.panel_assemble(0, 10, f, p, p, p, p, p, None, None, p, p, p, p, None)
+        assert st == want, (f, st)

@@ -125,3 +125,55 @@ def test_empty_batch_is_a_no_op():
     pb.viscous(1.0e6)
     assert pb.cl.numel() == 0 and pb.grad.numel() == 0 and pb.cd.numel() == 0
     torch.cuda.synchronize()
+
+
+def test_every_launch_shape_gives_the_oracle_result():
+    # the autotuner's search space: every refinement block shape, every assembly
+    # near-field setting, both factorisations, with buckets of several widths;
+    # each combination is a layout of the same computation and matches the
+    # oracle (long double) to 1e-10
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = _ragged(31, [300, 257, 200, 130, 64, 3])
+    with oracle.extended():
+        ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
+    for width in (None, 128):
+        for inverse in (False, True):
+            for shape in range(5):
+                for rounds in (0, 1, 2, 5):
+                    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed",
+                                    bucket_width=width, bucket_min=1)
+                    pb.inverse = [inverse] * len(pb.buckets)
+                    pb.ir_shape = [shape] * len(pb.buckets)
+                    pb.rounds = [rounds] * len(pb.buckets)
+                    pb.run()
+                    torch.cuda.synchronize()
+                    assert np.all(pb.info.cpu().numpy() == 0), (width, inverse, shape, rounds)
+                    u = pb.u.cpu().numpy()
+                    for b in range(pop.batch):
+                        o = pop.offsets[b] + b
+                        n = pop.offsets[b + 1] - pop.offsets[b]
+                        assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 1e-10, (b, shape)
+                    assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < 1e-10
+
+
+def test_autotuner_records_a_configuration_per_bucket(tmp_path, monkeypatch):
+    # the broadened search picks a bucket width for a ragged population and,
+    # per bucket, rounds, factorisation and refinement shape; a second batch of
+    # the same population reads the same choices from the cache
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    monkeypatch.setenv("PANEL_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    pop = inputs.make_population("uneven_b10000_n64_512", batch=1216)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    chosen = pb.autotune(reps=1)
+    t = pb.tuning()
+    assert len(t["buckets"]) == len(pb.buckets) >= 1
+    assert any("|width|" in k for k in chosen)
+    pb.run(with_grad=True)
+    torch.cuda.synchronize()
+    assert np.all(pb.info.cpu().numpy() == 0)
+    pb2 = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+    assert pb2.autotune(reps=1) == chosen and pb2.tuning() == t
