@@ -97,20 +97,27 @@ typedef enum {
  * values an autotuner searches; 0 keeps the library's choice by size).  They
  * change how the work is laid out on the GPU, not what is computed: results
  * agree to rounding.
- *   PANEL_TUNE_IR(s), s = 1..4: the refinement (panel_solve, PANEL_MIXED) runs
+ *   PANEL_TUNE_IR(s), s = 1..5: the refinement (panel_solve, PANEL_MIXED) runs
  *     blocks of 128 threads (8 per SM; airfoils of at most 223 panels), 256
- *     (4 per SM), 512 (2 per SM) or 1024 threads (1 per SM); a shape whose
- *     shared memory does not fit the airfoils' size falls back to the choice by
- *     size.
+ *     (4 per SM), 512 (2 per SM), 1024 (1 per SM) or 256 threads (3 per SM); a
+ *     shape whose shared memory does not fit the airfoils' size falls back to
+ *     the choice by size.
  *   PANEL_TUNE_ROUNDS(r), r = 1..5: the double-float assembly (panel_assemble,
  *     PANEL_MIXED) evaluates near-field pairs inline with the far-field ones
  *     (1) or queues them and evaluates them together after every 4, 8, 16 or
  *     32 pairs per thread (2..5).
+ *   PANEL_TUNE_LU(k), k = 1..2: the FP32 LU (panel_solve, PANEL_MIXED, without
+ *     PANEL_INVERSE) of airfoils with n_b < 224 keeps the trailing matrix in
+ *     the LU buffer through L2, several airfoils per SM (1), or the whole
+ *     matrix in shared memory, one airfoil per SM (2, the choice by size).
+ *     The two compute the same factor (the same operations in the same order).
  * Other values are rejected (PANEL_EINVAL). */
 #define PANEL_TUNE_IR_SHIFT 8
 #define PANEL_TUNE_ROUNDS_SHIFT 12
+#define PANEL_TUNE_LU_SHIFT 16
 #define PANEL_TUNE_IR(s) ((s) << PANEL_TUNE_IR_SHIFT)
 #define PANEL_TUNE_ROUNDS(r) ((r) << PANEL_TUNE_ROUNDS_SHIFT)
+#define PANEL_TUNE_LU(k) ((k) << PANEL_TUNE_LU_SHIFT)
 
 /* Largest panel count per airfoil the library accepts. */
 #define PANEL_N_MAX 2048

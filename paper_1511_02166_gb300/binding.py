@@ -29,11 +29,12 @@ PANEL_REUSE_FACTOR = 0x40
 PANEL_INVERSE = 0x80
 PANEL_TUNE_IR_SHIFT = 8
 PANEL_TUNE_ROUNDS_SHIFT = 12
+PANEL_TUNE_LU_SHIFT = 16
 
 
 def PANEL_TUNE_IR(shape: int) -> int:
-    """Refinement block shape field of the flags: 0 by size, 1..4 = 128, 256, 512,
-    1024 threads per block."""
+    """Refinement block shape field of the flags: 0 by size, 1..5 = 128 x 8, 256 x 4,
+    512 x 2, 1024 x 1, 256 x 3 (threads per block x blocks per SM)."""
     return int(shape) << PANEL_TUNE_IR_SHIFT
 
 
@@ -41,6 +42,12 @@ def PANEL_TUNE_ROUNDS(sel: int) -> int:
     """Assembly near-field queue field of the flags: 0 by size, 1 inline, 2..5 =
     after 4, 8, 16, 32 pairs per thread."""
     return int(sel) << PANEL_TUNE_ROUNDS_SHIFT
+
+
+def PANEL_TUNE_LU(kind: int) -> int:
+    """FP32 LU field of the flags (n_b < 224): 0 by size, 1 trailing matrix
+    through L2, 2 whole matrix in shared memory."""
+    return int(kind) << PANEL_TUNE_LU_SHIFT
 PANEL_N_MAX = 2048
 
 INFO_FEW_NODES = -1

@@ -24,7 +24,7 @@ cudaError_t launch_forces(const Batch&, const double*, const double*, const doub
 cudaError_t launch_assemble_df(const Batch&, const double*, const double*, float*, float*,
                                double*, int32_t*, cudaStream_t, int rounds_sel = 0);
 cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_t*, int32_t*,
-                            bool, cudaStream_t);
+                            bool, cudaStream_t, int lu_kind = 0);
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t,
@@ -67,12 +67,13 @@ int mode_of(int flags) {
 
 int tune_ir(int flags) { return (flags >> PANEL_TUNE_IR_SHIFT) & 7; }
 int tune_rounds(int flags) { return (flags >> PANEL_TUNE_ROUNDS_SHIFT) & 7; }
+int tune_lu(int flags) { return (flags >> PANEL_TUNE_LU_SHIFT) & 3; }
 
 bool flags_ok(int flags) {
   const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
                     PANEL_REUSE_FACTOR | PANEL_INVERSE | (7 << PANEL_TUNE_IR_SHIFT) |
-                    (7 << PANEL_TUNE_ROUNDS_SHIFT);
-  if (tune_ir(flags) > 4 || tune_rounds(flags) > 5) return false;
+                    (7 << PANEL_TUNE_ROUNDS_SHIFT) | (3 << PANEL_TUNE_LU_SHIFT);
+  if (tune_ir(flags) > 5 || tune_rounds(flags) > 5 || tune_lu(flags) > 2) return false;
   if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
   const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
   if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;
@@ -199,7 +200,7 @@ int panel_solve(int B, int n_max, int flags, const double* nodes, const int64_t*
   cudaError_t e = cudaSuccess;
   if (!reuse)
     e = panel::launch_lu_mixed(bt, A_hi, (float*)LU, piv, info, iters,
-                               (flags & PANEL_INVERSE) != 0, s);
+                               (flags & PANEL_INVERSE) != 0, s, tune_lu(flags));
   if (e == cudaSuccess && !factor_only)
     e = panel::launch_ir_mixed(bt, A_hi, A_lo, (const float*)LU, piv, rhs, vinf, chord, u,
                                adj ? lambda : nullptr, max_iter, tol, info, iters, s, 0,

@@ -21,7 +21,7 @@ cudaError_t launch_solve_f64(const Batch&, const double*, double*, int32_t*, con
                              const double*, const double*, double*, double*, int32_t*, int32_t*,
                              cudaStream_t);
 cudaError_t launch_lu_mixed(const Batch&, const float*, float*, int32_t*, int32_t*, int32_t*,
-                            bool, cudaStream_t);
+                            bool, cudaStream_t, int lu_kind = 0);
 cudaError_t launch_ir_mixed(const Batch&, const float*, const float*, const float*,
                             const int32_t*, const double*, const double*, const double*, double*,
                             double*, int, double, int32_t*, int32_t*, cudaStream_t,

@@ -14,6 +14,9 @@
 // The FP32 factor depends on the size m = n + 1:
 //   m <= kGjM (288)        explicit inverse by blocked Gauss-Jordan
 //                          (k_gj_mixed.cu); a correction is one GEMV;
+//                          without the inverse, for m <= kSmemLuM (224):
+//                          k_lu_smem below, the same LU with the whole
+//                          matrix in shared memory;
 //   kGjM < m <= kLargeM    k_lu_global below: one block per airfoil, blocked
 //                          right-looking LU with partial pivoting, the factor
 //                          in the caller's LU buffer through L2;
@@ -25,10 +28,69 @@
 //  k_ir_mixed  one block per airfoil: the corrections with the stored factor
 //    (read through L1/L2) and the refinement residuals (one pass over the rows
 //    for M u, one over the columns for M^T lambda).
+#include <type_traits>
+
 #include "df.cuh"
 #include "lu_mixed.cuh"
 
 namespace panel {
+
+// ---------------------------------------------------------------------------
+// LU with partial pivoting of one kb x kb diagonal block (kb <= 32) by one
+// warp, register-resident: lane r holds row r (x = its NB columns); rows keep
+// their lanes and `pos` tracks their current position, so an exchange of
+// positions q and p is bookkeeping plus one ipiv entry.  The pivot of column
+// q is the largest |x_q| among the rows not yet pivotal (the lowest position
+// among equal maxima).  The loop is not unrolled (the single warp would run
+// thousands of straight-line instructions once each, fetched from beyond the
+// instruction cache); instead the columns rotate through the registers: at
+// step q the current column is x[0], the later ones x[1 .. NB-1-q], and the
+// finished entries of the earlier columns x[NB-q ..]; each step retires x[0]
+// (the multiplier, or the U entry of a pivotal row) to x[NB-1] and shifts the
+// rest down, so every register index is a constant and after NB steps the
+// columns are back in order.  The reciprocal of the pivot is the correctly
+// rounded one (the same value as 1 / p).  ipiv[q] receives base + the position of column
+// q's pivot row.  On return `fz` is 0, or q + 1 for the first exactly zero (or
+// NaN) pivot column q, after which the block is left as it stands.
+// ---------------------------------------------------------------------------
+template <int NB>
+__device__ __forceinline__ void warp_block_lu(float (&x)[NB], int& pos, bool& done, int& fz,
+                                              int kb, int* ipiv, int base) {
+  const int lane = threadIdx.x & 31;
+  // every step is straight-line code: the warp-uniform conditions (the step is
+  // inside the block, no zero pivot so far) act as predicates, not branches
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) {
+    const bool act = q < kb && fz == 0;
+    const float v = (act && !done) ? fabsf(x[0]) : -1.0f;
+    const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;  // |x| bits are monotone
+    const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+    const bool ok = act && mx > 1u;  // a nonzero pivot (mx <= 1: zero or NaN column)
+    if (act && !ok) fz = q + 1;
+    // the lowest current position among the maxima
+    const unsigned pm = __reduce_min_sync(0xffffffffu, (ok && key == mx) ? (unsigned)pos : 0xffu);
+    const int pl = (__ffs(__ballot_sync(0xffffffffu, ok && key == mx && pos == (int)pm)) - 1) & 31;
+    const int ql = __ffs(__ballot_sync(0xffffffffu, ok && pos == q)) - 1;  // the row now at q
+    if (ok && lane == 0) ipiv[q] = base + (int)pm;
+    if (ok && lane == ql) pos = (int)pm;
+    if (ok && lane == pl) {
+      pos = q;
+      done = true;
+    }
+    const float inv = __frcp_rn(__shfl_sync(0xffffffffu, x[0], pl));
+    const float l = x[0] * inv;
+    const bool elim = ok && !done;
+#pragma unroll
+    for (int t = 1; t < NB; ++t) {
+      const float uc = __shfl_sync(0xffffffffu, x[t], pl);
+      x[t] = (elim && t < NB - q) ? fmaf(-l, uc, x[t]) : x[t];  // a later column
+    }
+    const float out = elim ? l : x[0];
+#pragma unroll
+    for (int t = 0; t < NB - 1; ++t) x[t] = x[t + 1];
+    x[NB - 1] = out;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // The LU kernel, factor in global memory (kGjM < m <= kLargeM): blocked right-looking
@@ -78,7 +140,7 @@ __device__ __forceinline__ void update_tiles(float* __restrict__ F, const float*
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LDP = NB + 1;
   constexpr int CW = 128;  // GEMM column slab
@@ -93,6 +155,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
     return;
   }
   if (m > kLargeM) return;  // taken by the blocked factor (k_lu_large.cu)
+  if (m <= kSmemLuM && a.lu_kind != 1) return;  // taken by k_lu_smem
   const int mv = bt.n_max + 1;
   float* P = reinterpret_cast<float*>(smraw);           // mv x LDP panel
   float* U = P + mv * LDP;                              // NB x CW slab of U12
@@ -134,37 +197,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
       int pos = lane;
       bool done = lane >= kb;  // already a pivot row (or outside the block)
       int fz = 0;
-#pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q < kb && fz == 0) {
-          const float v = done ? -1.0f : fabsf(x[q]);
-          const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;  // |x| bits are monotone
-          const unsigned mx = __reduce_max_sync(0xffffffffu, key);
-          if (mx <= 1u) {  // exactly zero (or NaN) pivot column
-            fz = q + 1;
-          } else {
-            // the lowest current position among the maxima
-            const unsigned pm = __reduce_min_sync(0xffffffffu, key == mx ? (unsigned)pos : 0xffu);
-            const int pl = __ffs(__ballot_sync(0xffffffffu, key == mx && pos == (int)pm)) - 1;
-            const int ql = __ffs(__ballot_sync(0xffffffffu, pos == q)) - 1;  // the row now at q
-            if (lane == 0) ipiv[k0 + q] = k0 + (int)pm;
-            if (lane == ql) pos = (int)pm;
-            if (lane == pl) {
-              pos = q;
-              done = true;
-            }
-            const float inv = 1.0f / __shfl_sync(0xffffffffu, x[q], pl);
-            const float l = x[q] * inv;
-            const bool elim = !done;
-#pragma unroll
-            for (int c = q + 1; c < NB; ++c) {
-              const float uc = __shfl_sync(0xffffffffu, x[c], pl);
-              if (elim) x[c] = fmaf(-l, uc, x[c]);
-            }
-            if (elim) x[q] = l;
-          }
-        }
-      }
+      warp_block_lu<NB>(x, pos, done, fz, kb, ipiv + k0, k0);
       __syncwarp();
       if (lane < kb) {
 #pragma unroll
@@ -189,12 +222,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
         float x[NB];
 #pragma unroll
         for (int t = 0; t < NB; ++t) x[t] = P[r * LDP + t];
+        // right-looking: once x_q is final it goes into every later column
+        // (the same terms in the same order as the row's dot products)
 #pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          float acc = x[t];
+        for (int q = 0; q < NB; ++q) {
+          x[q] *= (float)red[q];
 #pragma unroll
-          for (int q = 0; q < t; ++q) acc = fmaf(-x[q], P[q * LDP + t], acc);
-          x[t] = acc * (float)red[t];
+          for (int t = q + 1; t < NB; ++t) x[t] = fmaf(-x[q], P[q * LDP + t], x[t]);
         }
 #pragma unroll
         for (int t = 0; t < NB; ++t) P[r * LDP + t] = x[t];
@@ -277,6 +311,273 @@ __global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
   __syncthreads();
   int32_t* gpiv = a.piv + vec_off(bt, b);
   for (int k = tid; k < m; k += kThreads) gpiv[k] = ipiv[k];
+}
+
+// ---------------------------------------------------------------------------
+// The LU kernel with the whole matrix in shared memory (3 <= m <= kSmemLuM):
+// one block of 512 threads per airfoil and per SM.  The algorithm and the
+// factor's layout are those of k_lu_global (32-column panels, the pivot search
+// inside the diagonal block, register LU of the diagonal block by one warp, L21
+// by a thread per row, the block's exchanges composed, U12 by a thread per
+// column, the rank-32 update in 8 x 32J register tiles accumulated in the same
+// order, the 32 x 32 diagonal blocks inverted at the end), so the two kernels
+// store the same factor bit for bit.  Here every step works on the scaled
+// matrix staged once in shared memory (odd row stride: conflict-free columns)
+// and the factor goes to the caller's buffer once: one read of the hi plane and
+// one write of the factor per airfoil.  Since one airfoil has the SM to itself,
+// the steps are arranged to keep its warps busy:
+//   A  L21 (threads 0..255, one row each, also kept transposed in LT so that the
+//      update reads eight rows' multipliers with two broadcast vector loads)
+//      and U12 (threads 256..511, one column each) at once, then the exchanges
+//      on the columns left of the panel;
+//   B  the update of the next panel's 32 columns;
+//   C  warp 0 factors the next diagonal block (look-ahead) while warps 1..15
+//      update the remaining columns.
+// ---------------------------------------------------------------------------
+constexpr int kSmemLuThreads = 512;
+constexpr int kSmemLuWarps = kSmemLuThreads / 32;
+static_assert(kSmemLuM <= 256, "k_lu_smem moves rows of at most 8 x 32 columns");
+static_assert(kSmemLuM - 32 <= kSmemLuThreads / 2, "a thread per row / column in phase A");
+
+// A22 -= L21 U12 on rows [r0, r0 + 8) x columns cc + lane + 32 j (j < J): the
+// multipliers of the 8 rows from LT (panel column q at LT[q ldt + r - k1]),
+// U12 from the matrix rows k0..k0 + kb.
+template <int J>
+__device__ __forceinline__ void smem_update_tile(float* __restrict__ F, int ld,
+                                                 const float* __restrict__ LT, int ldt, int m,
+                                                 int k0, int k1, int kb, int r0, int cc) {
+  const int lane = threadIdx.x & 31;
+  float acc[8][J];
+#pragma unroll
+  for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int r = r0 + aa, c = cc + lane + 32 * j;
+      acc[aa][j] = (r < m && c < m) ? F[r * ld + c] : 0.0f;
+    }
+  const float* lt = LT + (r0 - k1);
+#pragma unroll 4
+  for (int q = 0; q < kb; ++q) {
+    const float4 la = *reinterpret_cast<const float4*>(lt + q * ldt);
+    const float4 lb = *reinterpret_cast<const float4*>(lt + q * ldt + 4);
+    const float lv[8] = {la.x, la.y, la.z, la.w, lb.x, lb.y, lb.z, lb.w};
+    float uv[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int c = cc + lane + 32 * j;
+      uv[j] = (c < m) ? F[(k0 + q) * ld + c] : 0.0f;
+    }
+#pragma unroll
+    for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+      for (int j = 0; j < J; ++j) acc[aa][j] = fmaf(-lv[aa], uv[j], acc[aa][j]);
+  }
+#pragma unroll
+  for (int aa = 0; aa < 8; ++aa)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int r = r0 + aa, c = cc + lane + 32 * j;
+      if (r < m && c < m) F[r * ld + c] = acc[aa][j];
+    }
+}
+
+// Update tasks of 8 rows x 32 J columns over the columns [c0, c1) of the rows
+// [k1, m), distributed over the warps w0 .. kSmemLuWarps - 1.
+__device__ __forceinline__ void smem_update(float* F, int ld, const float* LT, int ldt, int m,
+                                            int k0, int k1, int kb, int c0, int c1, int w0,
+                                            int cw) {
+  const int warp = threadIdx.x >> 5;
+  if (warp < w0 || c1 <= c0) return;
+  const int nrt = (m - k1 + 7) >> 3, ncs = (c1 - c0 + cw - 1) / cw;
+  for (int task = warp - w0; task < nrt * ncs; task += kSmemLuWarps - w0) {
+    const int r0 = k1 + 8 * (task / ncs), cc = c0 + cw * (task % ncs);
+    const int J = min(cw / 32, (min(c1, m) - cc + 31) >> 5);
+    if (J >= 4)
+      smem_update_tile<4>(F, ld, LT, ldt, m, k0, k1, kb, r0, cc);
+    else if (J == 3)
+      smem_update_tile<3>(F, ld, LT, ldt, m, k0, k1, kb, r0, cc);
+    else if (J == 2)
+      smem_update_tile<2>(F, ld, LT, ldt, m, k0, k1, kb, r0, cc);
+    else
+      smem_update_tile<1>(F, ld, LT, ldt, m, k0, k1, kb, r0, cc);
+  }
+}
+
+// LU of the diagonal block at (k0, k0), kb x kb, by the calling warp: the block
+// rows in their final order, the pivots in ipiv[k0 ..], the composed exchanges
+// in bperm, 1 / U_tt in red, and in *fz 0 or the first zero pivot column + 1.
+__device__ __forceinline__ void smem_diag_lu(float* F, int ld, int k0, int kb, int* ipiv,
+                                             int* bperm, double* red,
+                                             unsigned long long* fzp) {
+  constexpr int NB = 32;
+  const int lane = threadIdx.x & 31;
+  float* P = F + k0 * ld + k0;
+  float x[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) x[t] = (lane < kb && t < kb) ? P[lane * ld + t] : 0.0f;
+  int pos = lane;
+  bool done = lane >= kb;
+  int fz = 0;
+  warp_block_lu<NB>(x, pos, done, fz, kb, ipiv + k0, k0);
+  __syncwarp();
+  if (lane < kb) {
+#pragma unroll
+    for (int t = 0; t < NB; ++t)
+      if (t < kb) P[pos * ld + t] = x[t];
+    bperm[pos] = lane;
+  }
+  __syncwarp();
+  if (lane == 0) *fzp = (unsigned long long)fz;
+  if (lane < kb && fz == 0) red[lane] = (double)(1.0f / P[lane * ld + lane]);
+}
+
+__global__ void __launch_bounds__(kSmemLuThreads, 1) k_lu_smem(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NB = 32;
+  const Batch& bt = a.bt;
+  const int b = bt.order[blockIdx.x];
+  const int n = airfoil_n(bt, b);
+  const int m = n + 1;
+  if (a.info[b] != 0) return;
+  if (m <= kGjM && a.inverse) return;  // taken by k_gj_mixed
+  if (n > a.n_cap) {
+    if (threadIdx.x == 0) a.info[b] = PANEL_INFO_TOO_LARGE;
+    return;
+  }
+  if (m > kSmemLuM || a.lu_kind == 1) return;  // taken by k_lu_global or the blocked factor
+  const int ld = m | 1;
+  const int mv = bt.n_max + 1;
+  const int ldv = mv | 1;
+  const int ldt = (mv + 7) & ~7;
+  float* F = reinterpret_cast<float*>(smraw);  // m x ld
+  float* LT = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(F + (size_t)mv * ldv) + 15) & ~(uintptr_t)15);  // NB x ldt
+  double* red = reinterpret_cast<double*>(LT + NB * ldt);                          // 32
+  unsigned long long* cand = reinterpret_cast<unsigned long long*>(red + 32);      // 1
+  int* ipiv = reinterpret_cast<int*>(cand + 2);                                    // mv
+  int* bperm = ipiv + mv;                                                          // NB
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t moff = bt.mat_off[b];
+  const float* Ah = a.A_hi + moff;
+  // the hi plane in by asynchronous copies (every element of the thread in
+  // flight at once; rows of stride m are only 4-byte aligned), a warp per row
+  for (int rr = warp; rr < m; rr += kSmemLuWarps)
+    for (int cc = lane; cc < m; cc += 32) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(F + rr * ld + cc);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(Ah + rr * m + cc)
+                   : "memory");
+    }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  const float sf = (float)border_scale(Ah, n, m, red);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  // the C column and the Kutta row scaled by sf
+  for (int k = tid; k < m; k += kSmemLuThreads) {
+    F[n * ld + k] *= sf;
+    if (k < n) F[k * ld + n] *= sf;
+  }
+  __syncthreads();
+  if (warp == 0) smem_diag_lu(F, ld, 0, min(NB, m), ipiv, bperm, red, cand);
+  __syncthreads();
+
+  for (int k0 = 0;; k0 += NB) {
+    if (cand[0] != 0ull) {
+      if (tid == 0) {
+        a.info[b] = k0 + (int)cand[0];
+        if (a.iters) a.iters[b] = 0;
+      }
+      return;
+    }
+    const int kb = min(NB, m - k0);
+    const int k1 = k0 + kb;
+    const float* P = F + k0 * ld + k0;
+    // ---- A: L21 = A21 U11^{-1} (also into LT), then the exchanges on the
+    // columns left of the panel (threads 0..255); U12 = L11^{-1} A12 with the
+    // rows read through the exchanges (threads 256..511) ----
+    if (tid < kSmemLuThreads / 2) {
+      const int r = k1 + tid;
+      if (r < m) {  // then kb == NB
+        float x[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) x[t] = F[r * ld + k0 + t];
+        // right-looking: once x_q is final it goes into every later column
+        // (the same terms in the same order as the row's dot products)
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          x[q] *= (float)red[q];
+#pragma unroll
+          for (int t = q + 1; t < NB; ++t) x[t] = fmaf(-x[q], P[q * ld + t], x[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          F[r * ld + k0 + t] = x[t];
+          LT[t * ldt + tid] = x[t];
+        }
+      }
+      for (int c = tid; c < k0; c += kSmemLuThreads / 2) {
+        float v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q] = (q < kb) ? F[(k0 + bperm[q]) * ld + c] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q < kb) F[(k0 + q) * ld + c] = v[q];
+      }
+    } else {
+      const int c = k1 + tid - kSmemLuThreads / 2;
+      if (c < m) {  // then kb == NB
+        float col[NB];
+#pragma unroll
+        for (int t = 0; t < NB; ++t) col[t] = F[(k0 + bperm[t]) * ld + c];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const float x = col[q];
+          F[(k0 + q) * ld + c] = x;
+#pragma unroll
+          for (int t = q + 1; t < NB; ++t) col[t] = fmaf(-P[t * ld + q], x, col[t]);
+        }
+      }
+    }
+    __syncthreads();
+    if (k1 >= m) break;
+    const int kb2 = min(NB, m - k1);
+    // ---- B: the next panel's columns [k1, k1 + kb2) ----
+    smem_update(F, ld, LT, ldt, m, k0, k1, kb, k1, k1 + kb2, 0, 32);
+    __syncthreads();
+    // ---- C: the next diagonal block (warp 0) | the remaining columns ----
+    if (warp == 0)
+      smem_diag_lu(F, ld, k1, kb2, ipiv, bperm, red, cand);
+    else
+      smem_update(F, ld, LT, ldt, m, k0, k1, kb, k1 + kb2, m, 1, 128);
+    __syncthreads();
+  }
+  // the 32 x 32 diagonal blocks inverted in place, a warp per triangle
+  {
+    const int nb = (m + NB - 1) / NB;
+    for (int t = warp; t < 2 * nb; t += kSmemLuWarps) {
+      const int d0 = NB * (t >> 1), kbd = min(NB, m - d0);
+      if (t & 1)
+        invert_upper(F + d0 * ld + d0, ld, kbd);
+      else
+        invert_lower_unit(F + d0 * ld + d0, ld, kbd);
+    }
+  }
+  __syncthreads();
+  float* G = a.LU + moff;
+  for (int rr = warp; rr < m; rr += kSmemLuWarps)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int cc = lane + 32 * u;
+      if (cc < m) G[rr * m + cc] = F[rr * ld + cc];
+    }
+  int32_t* gpiv = a.piv + vec_off(bt, b);
+  for (int k = tid; k < m; k += kSmemLuThreads) gpiv[k] = ipiv[k];
+}
+
+size_t lu_smem_smem(int n_max) {
+  const size_t mv = (size_t)n_max + 1, ldv = mv | 1, ldt = (mv + 7) & ~(size_t)7;
+  const size_t bytes = (mv * ldv * 4 + 15) & ~(size_t)15;
+  return bytes + 32 * ldt * 4 + 32 * 8 + 16 + mv * 4 + 32 * 4;
 }
 
 template <int NB>
@@ -523,9 +824,9 @@ __device__ __forceinline__ double resacc_sub_from(double c, const LiteAcc& a) {
 // r_j = b_j - sum_i M_ji x_i for all rows j; x given as float pairs (xh, xl).
 // A warp takes two rows at a time and issues all loads of a 256-column chunk
 // before accumulating.
-template <class Acc>
+template <class Acc, class Rhs, class RT>
 __device__ void residual_rows(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
-                              const float* xh, const float* xl, const double* b, double* r) {
+                              const float* xh, const float* xl, const Rhs& b, RT* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j0 = 2 * warp; j0 < m; j0 += 2 * (int)(blockDim.x >> 5)) {
     Acc acc0, acc1;
@@ -556,17 +857,17 @@ __device__ void residual_rows(const float* __restrict__ Ah, const float* __restr
     acc0 = warp_sum_res(acc0);
     acc1 = warp_sum_res(acc1);
     if (lane == 0) {
-      r[j0] = resacc_sub_from(b[j0], acc0);
-      if (two) r[j0 + 1] = resacc_sub_from(b[j0 + 1], acc1);
+      b.store(r, j0, resacc_sub_from(b(j0), acc0));
+      if (two) b.store(r, j0 + 1, resacc_sub_from(b(j0 + 1), acc1));
     }
   }
 }
 
 // r_i = g_i - sum_j M_ji x_j for all columns i: each warp owns 32 consecutive
 // columns (one per lane) and walks all rows, 8 rows of loads in flight.
-template <class Acc>
+template <class Acc, class Rhs, class RT>
 __device__ void residual_cols(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
-                              const float* xh, const float* xl, const double* g, double* r) {
+                              const float* xh, const float* xl, const Rhs& g, RT* r) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = 32 * warp; cb < m; cb += (int)blockDim.x) {
     const int c = cb + lane;
@@ -585,7 +886,7 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
       for (int q = 0; q < 8; ++q)
         if (jb + q < m) resacc_add(acc, h[q], l[q], xh[jb + q], xl[jb + q]);
     }
-    if (ok) r[c] = resacc_sub_from(g[c], acc);
+    if (ok) g.store(r, c, resacc_sub_from(g(c), acc));
   }
 }
 
@@ -596,11 +897,10 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
 // accumulators and are merged across the warps through `part` ((int)(blockDim.x >> 5) x m).
 constexpr int kFuseM = 288;
 constexpr int kFuseT = (kFuseM + 31) / 32;
-template <class Acc, int FT = kFuseT>
+template <class Acc, int FT = kFuseT, class Rhs, class RT>
 __device__ void residual_both(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const float* yh, const float* yl,
-                              const double* b, const double* g, double* rf, double* rt,
-                              Acc* part) {
+                              const Rhs& b, const Rhs& g, RT* rf, RT* rt, Acc* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Acc cacc[FT];
 #pragma unroll
@@ -626,7 +926,7 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
       }
     }
     racc = warp_sum_res(racc);
-    if (lane == 0) rf[j] = resacc_sub_from(b[j], racc);
+    if (lane == 0) b.store(rf, j, resacc_sub_from(b(j), racc));
   }
 #pragma unroll
   for (int t = 0; t < FT; ++t) {
@@ -637,27 +937,87 @@ __device__ void residual_both(const float* __restrict__ Ah, const float* __restr
   for (int c = threadIdx.x; c < m; c += (int)blockDim.x) {
     Acc acc = part[c];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) resacc_merge(acc, part[w * m + c]);
-    rt[c] = resacc_sub_from(g[c], acc);
+    g.store(rt, c, resacc_sub_from(g(c), acc));
   }
 }
 
 // ---------------------------------------------------------------------------
 // The refinement kernel: forward and/or transposed system of one airfoil
 // ---------------------------------------------------------------------------
+// Where the refinement keeps its vectors.  Launches of small airfoils
+// (n_max + 1 <= kFuseM, KEEP) hold x, the residual r and the right-hand side
+// in shared memory as doubles.  The others, whose shared memory bounds the
+// airfoils per SM, keep x in the caller's output array, the residual as the
+// float the correction solve takes (component n already times s) and evaluate
+// the right-hand side where it is needed, once per row or column of a
+// residual pass.
+template <class RT>
 struct IrSystem {
   double* x;   // m  current solution
-  double* r;   // m  residual
-  double* bb;  // m  right-hand side
-  float* xh;   // m
+  RT* r;       // m  residual
+  float* xh;   // m  x as float pairs for the residual
   float* xl;   // m
 };
+
+// A stored right-hand side (KEEP): the residual is kept as is.
+struct SmemRhs {
+  const double* bb;
+  __device__ double operator()(int k) const { return bb[k]; }
+  __device__ void store(double* r, int k, double v) const { r[k] = v; }
+};
+
+// Right-hand side of system q (0: M u = b, 1: M^T lambda = g), evaluated; the
+// residual is stored as the correction solve's float input.
+struct IrRhs {
+  const double* rhs;   // forward right-hand side (rhs_kind 0), at the airfoil's offset
+  const double* nd;    // the airfoil's nodes
+  const double* w_u;   // vector-Jacobian weights at the airfoil's offsets (or NULL)
+  const double* w_cp;
+  const double* u_in;
+  double w_cl;
+  int n, q, rhs_kind, vjp;
+  double v, cc, s;
+  __device__ double operator()(int k) const { return eval(k); }
+  __device__ double eval(int k) const {
+    if (q == 0) {
+      if (rhs_kind == 0) return rhs[k];
+      // the basis right-hand sides of a polar: b(alpha) = cos(alpha) b_y +
+      // sin(alpha) b_x with b_y = v m_y, b_x = -v m_x (m the control point)
+      if (k >= n) return 0.0;
+      const int k1 = (k + 1 == n) ? 0 : k + 1;
+      return (rhs_kind == 1) ? 0.5 * v * (nd[2 * k + 1] + nd[2 * k1 + 1])
+                                : -0.5 * v * (nd[2 * k] + nd[2 * k1]);
+    }
+    double g = 0.0;
+    if (k < n) {
+      const int k1 = (k + 1 == n) ? 0 : k + 1;
+      const double hx = nd[2 * k1] - nd[2 * k], hy = nd[2 * k1 + 1] - nd[2 * k + 1];
+      g = 2.0 * sqrt(hx * hx + hy * hy) / (v * cc);  // dCl/dgamma_k
+    }
+    if (vjp) {
+      // dL/du for L = w_cl Cl + w_u . u + w_cp . Cp, Cp_k = 1 - (gamma_k / v)^2
+      g *= w_cl;
+      if (w_u) g += w_u[k];
+      if (w_cp && k < n) g += w_cp[k] * (-2.0 * u_in[k] / (v * v));
+    }
+    return g;
+  }
+  __device__ float scaled(int k, double r) const { return (float)((k == n) ? r * s : r); }
+  __device__ void store(float* r, int k, double v) const { r[k] = scaled(k, v); }
+};
+
+// The float input of the correction solve from a residual component.
+__device__ __forceinline__ float solve_input(double r, int k, int n, double s) {
+  return (float)((k == n) ? r * s : r);
+}
+__device__ __forceinline__ float solve_input(float r, int, int, double) { return r; }
 
 __device__ __forceinline__ int gpiv_first(const SolveArgs& a, int b) {
   return a.piv[vec_off(a.bt, b)];
 }
 
 // NT threads, MINB blocks per SM (see launch_ir_kernel).
-template <int NT, int MINB, int FT>
+template <int NT, int MINB, int FT, bool KEEP>
 __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const Batch& bt = a.bt;
@@ -666,14 +1026,19 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   const int m = n + 1;
   if (a.info[b] != 0 || n > bt.n_max) return;
   const int mv = bt.n_max + 1;
+  using RT = typename std::conditional<KEEP, double, float>::type;
   double* red = reinterpret_cast<double*>(smraw);  // 32
-  IrSystem sys[2];
+  IrSystem<RT> sys[2];
   double* dp = red + 32;
-  for (int q = 0; q < 2; ++q) {
-    sys[q].x = dp;
-    sys[q].r = dp + mv;
-    sys[q].bb = dp + 2 * mv;
-    dp += 3 * mv;
+  double* bbs = dp;  // KEEP: x, r, bb of both systems (6 m doubles)
+  if (KEEP) {
+    for (int q = 0; q < 2; ++q) {
+      sys[q].x = dp;
+      sys[q].r = reinterpret_cast<RT*>(dp + mv);
+      dp += 2 * mv;
+    }
+    bbs = dp;
+    dp += 2 * mv;
   }
   float* y = reinterpret_cast<float*>(dp);  // m
   float* fp = y + mv;
@@ -681,6 +1046,10 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
     sys[q].xh = fp;
     sys[q].xl = fp + mv;
     fp += 2 * mv;
+    if (!KEEP) {
+      sys[q].r = reinterpret_cast<RT*>(fp);
+      fp += mv;
+    }
   }
   int* perm = reinterpret_cast<int*>(fp);  // m
   float* t32 = reinterpret_cast<float*>(perm + mv);  // 32
@@ -701,44 +1070,42 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   // the fused residual pass needs `part`, allocated when the launch's n_max fits
   const bool fuse = bt.n_max + 1 <= kFuseM;
 
-  // right-hand sides: b, and g = dCl/du = 2 |h_k| / (v c) (0 for C)
-  const double* nd = bt.nodes + 2 * bt.node_off[b];
-  const double v = a.vinf ? a.vinf[b] : 1.0, cc = a.chord ? a.chord[b] : 1.0;
+  // right-hand sides: b, and g = dCl/du = 2 |h_k| / (v c) (0 for C); x = 0, r = b
+  IrRhs rhs[2];
+  for (int q = 0; q < 2; ++q) {
+    const int64_t vo = vec_off(bt, b);
+    rhs[q].rhs = (a.rhs_kind == 0 && a.rhs) ? a.rhs + vo : nullptr;
+    rhs[q].nd = bt.nodes + 2 * bt.node_off[b];
+    rhs[q].w_u = a.w_u ? a.w_u + vo : nullptr;
+    rhs[q].w_cp = a.w_cp ? a.w_cp + bt.node_off[b] : nullptr;
+    rhs[q].u_in = a.u_in ? a.u_in + vo : nullptr;
+    rhs[q].w_cl = a.w_cl ? a.w_cl[b] : 0.0;
+    rhs[q].n = n;
+    rhs[q].q = q;
+    rhs[q].rhs_kind = a.rhs_kind;
+    rhs[q].vjp = a.vjp;
+    rhs[q].v = a.vinf ? a.vinf[b] : 1.0;
+    rhs[q].cc = a.chord ? a.chord[b] : 1.0;
+    rhs[q].s = s;
+  }
+  SmemRhs srhs[2];
+  srhs[0].bb = bbs;
+  srhs[1].bb = bbs + mv;
+  if (!KEEP) {
+    sys[0].x = act0 ? a.u + vec_off(bt, b) : nullptr;
+    sys[1].x = act1 ? a.lam + vec_off(bt, b) : nullptr;
+  }
   for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
-    if (act0) {
-      if (a.rhs_kind == 0) {
-        sys[0].bb[k] = a.rhs[vec_off(bt, b) + k];
-      } else {
-        // the basis right-hand sides of a polar: b(alpha) = cos(alpha) b_y +
-        // sin(alpha) b_x with b_y = v m_y, b_x = -v m_x (m the control point)
-        double bk = 0.0;
-        if (k < n) {
-          const int k1 = (k + 1 == n) ? 0 : k + 1;
-          bk = (a.rhs_kind == 1) ? 0.5 * v * (nd[2 * k + 1] + nd[2 * k1 + 1])
-                                 : -0.5 * v * (nd[2 * k] + nd[2 * k1]);
-        }
-        sys[0].bb[k] = bk;
-      }
-    }
-    if (act1) {
-      double g = 0.0;
-      if (k < n) {
-        const int k1 = (k + 1 == n) ? 0 : k + 1;
-        const double hx = nd[2 * k1] - nd[2 * k], hy = nd[2 * k1 + 1] - nd[2 * k + 1];
-        g = 2.0 * sqrt(hx * hx + hy * hy) / (v * cc);  // dCl/dgamma_k
-      }
-      if (a.vjp) {
-        // dL/du for L = w_cl Cl + w_u . u + w_cp . Cp, Cp_k = 1 - (gamma_k / v)^2
-        g *= a.w_cl ? a.w_cl[b] : 0.0;
-        if (a.w_u) g += a.w_u[vec_off(bt, b) + k];
-        if (a.w_cp && k < n)
-          g += a.w_cp[bt.node_off[b] + k] * (-2.0 * a.u_in[vec_off(bt, b) + k] / (v * v));
-      }
-      sys[1].bb[k] = g;
-    }
     for (int q = 0; q < 2; ++q) {
+      if (!(q == 0 ? act0 : act1)) continue;
+      const double bk = rhs[q].eval(k);
       sys[q].x[k] = 0.0;
-      sys[q].r[k] = sys[q].bb[k];
+      if constexpr (KEEP) {
+        bbs[q * mv + k] = bk;
+        sys[q].r[k] = bk;
+      } else {
+        sys[q].r[k] = rhs[q].scaled(k, bk);
+      }
     }
   }
   // row permutation of the factor: P y = y[perm]
@@ -760,12 +1127,12 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   for (;; ++it) {
     for (int q = 0; q < 2; ++q) {
       if (!active[q] || conv[q]) continue;
-      IrSystem& S = sys[q];
+      IrSystem<RT>& S = sys[q];
       if (q == 0) {
         // y = P S_r r;  solve;  dx = S_c y
         for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
           const int src = perm[k];
-          y[k] = (float)((src == n) ? S.r[src] * s : S.r[src]);
+          y[k] = solve_input(S.r[src], src, n, s);
         }
         __syncthreads();
         if (gj)
@@ -775,7 +1142,7 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
       } else {
         // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
         for (int k = threadIdx.x; k < m; k += (int)blockDim.x)
-          y[k] = (float)((k == n) ? S.r[k] * s : S.r[k]);
+          y[k] = solve_input(S.r[k], k, n, s);
         __syncthreads();
         if (gj)
           gj_apply_transposed(F, m, y, part);
@@ -816,30 +1183,38 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
     }
     __syncthreads();
     const bool both = active[0] && !conv[0] && active[1] && !conv[1];
-    if (it == 0) {
-      if (both && fuse) {
-        residual_both<LiteAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
-                               sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<LiteAcc*>(part));
+    auto residuals = [&](const auto& R0, const auto& R1) {
+      if (it == 0) {
+        if (both && fuse) {
+          residual_both<LiteAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, R0,
+                                     R1, sys[0].r, sys[1].r, reinterpret_cast<LiteAcc*>(part));
+        } else {
+          if (active[0] && !conv[0])
+            residual_rows<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, R0, sys[0].r);
+          if (active[1] && !conv[1])
+            residual_cols<LiteAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, R1, sys[1].r);
+        }
+      } else if (both && fuse) {
+        residual_both<ResAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, R0, R1,
+                                  sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
       } else {
         if (active[0] && !conv[0])
-          residual_rows<LiteAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
+          residual_rows<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, R0, sys[0].r);
         if (active[1] && !conv[1])
-          residual_cols<LiteAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
+          residual_cols<ResAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, R1, sys[1].r);
       }
-    } else if (both && fuse) {
-      residual_both<ResAcc, FT>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[1].xh, sys[1].xl, sys[0].bb,
-                            sys[1].bb, sys[0].r, sys[1].r, reinterpret_cast<ResAcc*>(part));
-    } else {
-      if (active[0] && !conv[0])
-        residual_rows<ResAcc>(Ah, Al, m, sys[0].xh, sys[0].xl, sys[0].bb, sys[0].r);
-      if (active[1] && !conv[1])
-        residual_cols<ResAcc>(Ah, Al, m, sys[1].xh, sys[1].xl, sys[1].bb, sys[1].r);
-    }
+    };
+    if constexpr (KEEP)
+      residuals(srhs[0], srhs[1]);
+    else
+      residuals(rhs[0], rhs[1]);
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
-    if (act0) a.u[vec_off(bt, b) + k] = sys[0].x[k];
-    if (act1) a.lam[vec_off(bt, b) + k] = sys[1].x[k];
+  if (KEEP) {
+    for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
+      if (act0) a.u[vec_off(bt, b) + k] = sys[0].x[k];
+      if (act1) a.lam[vec_off(bt, b) + k] = sys[1].x[k];
+    }
   }
   if (threadIdx.x == 0) {
     if (a.iters && act0) a.iters[b] = it;
@@ -855,7 +1230,9 @@ size_t ir_mixed_smem(int n_max, int nt) {
   const size_t mv = (size_t)n_max + 1;
   const size_t part = (mv <= (size_t)kFuseM) ? (size_t)(nt / 32) * mv * sizeof(ResAcc)
                                              : (size_t)(nt / 32) * kGjM * sizeof(float);
-  return 32 * 8 + 6 * mv * 8 + 5 * mv * 4 + mv * 4 + 32 * 4 + 32 + part;
+  // x, r and the right-hand side of both systems as doubles (KEEP), or r as floats
+  const size_t vecs = (mv <= (size_t)kFuseM) ? 6 * mv * 8 + 5 * mv * 4 : 7 * mv * 4;
+  return 32 * 8 + vecs + mv * 4 + 32 * 4 + 32 + part;
 }
 
 static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo, float* LU,
@@ -881,25 +1258,40 @@ static SolveArgs make_args(const Batch& bt, const float* A_hi, const float* A_lo
   a.n_cap = bt.n_max;
   a.rhs_kind = 0;
   a.ir_shape = 0;
+  a.lu_kind = 0;
   a.vjp = 0;
   a.w_cl = a.w_u = a.w_cp = a.u_in = nullptr;
   return a;
 }
 
-// Factor every airfoil: one-block LU in global memory up to kLargeM (or, with
-// `inverse`, the Gauss-Jordan inverse for m <= kGjM), the step-synchronous
-// blocked LU beyond.
+// Factor every airfoil: with `inverse` the Gauss-Jordan inverse for m <= kGjM;
+// otherwise the one-block LU with the whole matrix in shared memory for m <=
+// kSmemLuM (lu_kind 0 or 2) or in the LU buffer through L2 (lu_kind 1, and
+// every m up to kLargeM); the step-synchronous blocked LU beyond.
 cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32_t* piv,
-                            int32_t* info, int32_t* iters, bool inverse, cudaStream_t s) {
+                            int32_t* info, int32_t* iters, bool inverse, cudaStream_t s,
+                            int lu_kind) {
   SolveArgs a = make_args(bt, A_hi, nullptr, LU, piv, nullptr, nullptr, nullptr, nullptr,
                           nullptr, 0, 0.0, info, iters);
   a.inverse = inverse ? 1 : 0;
+  a.lu_kind = lu_kind;
   cudaError_t e;
   if (bt.n_max + 1 > kLargeM) {
     e = launch_lu_large(a, s);
     if (e != cudaSuccess) return e;
   }
-  if (bt.n_max + 1 > kGjM || !inverse) {
+  if (!inverse && lu_kind != 1) {
+    // airfoils up to kSmemLuM unknowns with the whole matrix in shared memory
+    SolveArgs h = a;
+    h.bt.n_max = min(bt.n_max, kSmemLuM - 1);
+    const size_t hs = lu_smem_smem(h.bt.n_max);
+    e = ensure_smem(k_lu_smem, hs);
+    if (e != cudaSuccess) return e;
+    k_lu_smem<<<bt.B, kSmemLuThreads, hs, s>>>(h);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if ((bt.n_max + 1 > kSmemLuM || lu_kind == 1) && (bt.n_max + 1 > kGjM || !inverse)) {
     SolveArgs g = a;
     g.bt.n_max = min(bt.n_max, kLargeM - 1);
     const size_t smem = lu_global_smem<32>(g.bt.n_max);
@@ -920,15 +1312,21 @@ cudaError_t launch_lu_mixed(const Batch& bt, const float* A_hi, float* LU, int32
 // sweeps (a smaller batch is better served by more warps per airfoil).  Then 256
 // threads, 4 per SM up to kFuseM unknowns (a few spilled registers), and above
 // it the most warps per airfoil that shared memory allows: 4 x 256, 2 x 512 or
-// 1 x 1024 threads.
+// 1 x 1024 threads (3 x 256 is the autotuner's fifth shape).
 // FT: columns per lane of the fused residual pass (ceil(n_max + 1 / 32) at most;
 // fewer registers for the smaller airfoils of the 128-thread shape, m <= 204).
 template <int NT, int MINB, int FT = kFuseT>
 static cudaError_t launch_ir_shape(const SolveArgs& a, cudaStream_t s) {
   const size_t smem = ir_mixed_smem(a.bt.n_max, NT);
-  const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB, FT>, smem);
-  if (e != cudaSuccess) return e;
-  k_ir_mixed<NT, MINB, FT><<<a.bt.B, NT, smem, s>>>(a);
+  if (a.bt.n_max + 1 <= kFuseM) {
+    const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB, FT, true>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<NT, MINB, FT, true><<<a.bt.B, NT, smem, s>>>(a);
+  } else {
+    const cudaError_t e = ensure_smem(k_ir_mixed<NT, MINB, FT, false>, smem);
+    if (e != cudaSuccess) return e;
+    k_ir_mixed<NT, MINB, FT, false><<<a.bt.B, NT, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -950,6 +1348,9 @@ static cudaError_t launch_ir_kernel(const SolveArgs& a, cudaStream_t s) {
       break;
     case 4:
       if (fits(1024, 1)) return launch_ir_shape<1024, 1>(a, s);
+      break;
+    case 5:
+      if (fits(kThreads, 1)) return launch_ir_shape<kThreads, 3>(a, s);
       break;
     default:
       break;

@@ -9,6 +9,7 @@ namespace panel {
 constexpr int kSmemM = 230;  // largest m = n + 1 factored in shared memory
 constexpr int kGjM = 288;    // m up to this: Gauss-Jordan inverse (k_gj_mixed.cu)
 constexpr int kLargeM = 640; // m above this takes the step-synchronous blocked factor
+constexpr int kSmemLuM = 224; // m up to this: LU with the whole matrix in shared memory
 constexpr int kNB = 32;      // panel width
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -32,6 +33,7 @@ struct SolveArgs {
   int n_cap;         // the caller's n_max (bt.n_max may be lowered to size a kernel)
   int rhs_kind;      // forward right-hand side: 0 rhs, 1 v m_y, 2 -v m_x (polar basis)
   int ir_shape;      // refinement block shape: 0 by size, 1..4 = 128x8, 256x4, 512x2, 1024x1
+  int lu_kind;       // LU of m <= kSmemLuM: 0/2 whole matrix in shared memory, 1 through L2
   // Transposed right-hand side of a vector-Jacobian product (vjp != 0):
   // w_cl[b] dCl/du + w_u + w_cp dCp/du (each may be NULL = 0), with the
   // strengths u_in of the forward solution; vjp == 0 is dCl/du alone.
@@ -63,41 +65,63 @@ __device__ __forceinline__ double border_scale(const float* Ah, int n, int m, do
 }
 
 // ---------------------------------------------------------------------------
-// Inverted diagonal blocks, in place, one warp per 32 x 32 block (lane j =
-// column j of the inverse).  X = L_dd^{-1} (unit lower) replaces the part
-// below the diagonal row by row (row i is written after every lane has read
-// it); Y = U_dd^{-1} (upper) replaces the rest row by row from the bottom.
-// invert_block takes one kb x kb block (kb <= 32) at B with row stride ld,
-// called by all lanes of one warp.
+// Inverted diagonal blocks, in place: X = L_dd^{-1} (unit lower) replaces the
+// part below the diagonal, Y = U_dd^{-1} (upper) the rest.  Each is one warp's
+// work, lane j computing column j of the inverse in registers by substitution
+// against the unit vector e_j, right-looking: once entry k of the column is
+// final, it is multiplied into every later entry (L: rows below k, U: rows
+// above k) at once, so each step is 31 independent FMAs on broadcast loads
+// instead of a dependent dot product.  The two parts read and write disjoint
+// entries (strictly below / on and above the diagonal): two warps may do them
+// at the same time.  Every index into the register column is a compile-time
+// constant (fully unrolled loops); kb <= 32 is the block size, B its first
+// element, ld the row stride, all lanes of the warp call.
 // ---------------------------------------------------------------------------
-__device__ inline void invert_block(float* B, int ld, int kb) {
+__device__ inline void invert_lower_unit(float* B, int ld, int kb) {
   const int j = threadIdx.x & 31;
-  // X[i][j] = -(L[i][j] + sum_{j<k<i} L[i][k] X[k][j]),  i > j
-  for (int i = 1; i < kb; ++i) {
-    float x = 0.0f;
-    if (j < i) {
-      x = -B[i * ld + j];
-      for (int k = j + 1; k < i; ++k) x = fmaf(-B[i * ld + k], B[k * ld + j], x);
+  float acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = (i == j) ? 1.0f : 0.0f;
+#pragma unroll
+  for (int k = 0; k < 31; ++k) {
+    if (k < kb) {
+      const float xk = acc[k];  // X[k][j], final
+#pragma unroll
+      for (int i = k + 1; i < 32; ++i)
+        if (i < kb) acc[i] = fmaf(-B[i * ld + k], xk, acc[i]);
     }
-    __syncwarp();
-    if (j < i) B[i * ld + j] = x;
-    __syncwarp();
   }
-  // Y[i][j] = -(sum_{i<k<=j} U[i][k] Y[k][j]) / U[i][i] (i < j), Y[j][j] = 1/U[j][j]
-  for (int i = kb - 1; i >= 0; --i) {
-    float y = 0.0f;
-    const float uii = B[i * ld + i];
-    if (j == i) {
-      y = 1.0f / uii;
-    } else if (j > i && j < kb) {
-      float acc = 0.0f;
-      for (int k = i + 1; k <= j; ++k) acc = fmaf(B[i * ld + k], B[k * ld + j], acc);
-      y = -acc / uii;
+  __syncwarp();
+#pragma unroll
+  for (int i = 1; i < 32; ++i)
+    if (i < kb && j < i) B[i * ld + j] = acc[i];
+  __syncwarp();
+}
+
+__device__ inline void invert_upper(float* B, int ld, int kb) {
+  const int j = threadIdx.x & 31;
+  float acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = (i == j) ? 1.0f : 0.0f;
+#pragma unroll
+  for (int k = 31; k >= 0; --k) {
+    if (k < kb) {
+      const float yk = acc[k] / B[k * ld + k];  // Y[k][j], final
+      acc[k] = yk;
+#pragma unroll
+      for (int i = 0; i < k; ++i) acc[i] = fmaf(-B[i * ld + k], yk, acc[i]);
     }
-    __syncwarp();
-    if (j >= i && j < kb) B[i * ld + j] = y;
-    __syncwarp();
   }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < kb && j >= i && j < kb) B[i * ld + j] = acc[i];
+  __syncwarp();
+}
+
+__device__ inline void invert_block(float* B, int ld, int kb) {
+  invert_lower_unit(B, ld, kb);
+  invert_upper(B, ld, kb);
 }
 
 __device__ inline void invert_diagonal_blocks(float* F, int ld, int m) {

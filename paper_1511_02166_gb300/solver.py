@@ -81,6 +81,7 @@ def size_buckets(sorted_sizes, width, min_count=1):
 
 MODES = {"fp64": bd.PANEL_FP64, "mixed": bd.PANEL_MIXED}
 GJ_MAX_M = 288  # largest m = n + 1 that the library factors by Gauss-Jordan
+LU_SMEM_MAX_M = 224  # largest m whose LU the library can run in shared memory
 
 
 def _require_cuda(device):
@@ -169,10 +170,11 @@ class PanelBatch:
         self.graph = None
 
     def _reset_tuning(self):
-        """Per bucket: the factorisation (Gauss-Jordan inverse or LU), the
-        refinement's block shape and the assembly's near-field rounds (0 = the
-        library's choice by size)."""
+        """Per bucket: the factorisation (Gauss-Jordan inverse or LU, and the
+        LU's kernel), the refinement's block shape and the assembly's near-field
+        rounds (0 = the library's choice by size)."""
         self.inverse = [False] * len(self.buckets)
+        self.lu_kind = [0] * len(self.buckets)
         self.ir_shape = [0] * len(self.buckets)
         self.rounds = [0] * len(self.buckets)
 
@@ -205,6 +207,8 @@ class PanelBatch:
         f |= {"all": 0, "factor": bd.PANEL_FACTOR_ONLY, "refine": bd.PANEL_REUSE_FACTOR}[stage]
         if self.flags == bd.PANEL_MIXED:
             f |= bd.PANEL_TUNE_IR(self.ir_shape[k])
+            if not self.inverse[k]:
+                f |= bd.PANEL_TUNE_LU(self.lu_kind[k])
         if self.inverse[k] and stage != "refine":
             f |= bd.PANEL_INVERSE
         bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets, self.mat_offsets,
@@ -330,7 +334,7 @@ class PanelBatch:
                 if self.inverse[k]:
                     n += 1 + (m > 230) + (m > GJ_MAX_M)
                 else:
-                    n += 1
+                    n += (self.lu_kind[k] != 1) + (m > LU_SMEM_MAX_M or self.lu_kind[k] == 1)
                 if m > 640:
                     blocks = -(-m // 128)
                     n += 2 + blocks + 2 * (blocks - 1)
@@ -361,9 +365,10 @@ class PanelBatch:
              `widths` (None = one bucket) times a whole step (assemble, solve with
              the transposed system, forces, adjoint);
           2. per bucket, the assembly's near-field rounds (PANEL_TUNE_ROUNDS 0..5);
-          3. per bucket, the solve (factor + refinement of both systems): the LU or
-             the Gauss-Jordan inverse (m <= 288) with each refinement block shape
-             (PANEL_TUNE_IR 0..4).
+          3. per bucket, the solve (factor + refinement of both systems): the LU
+             (for m <= 224 with the matrix in shared memory or through L2,
+             PANEL_TUNE_LU 2 / 1) or the Gauss-Jordan inverse (m <= 288), each
+             with each refinement block shape (PANEL_TUNE_IR 0..5).
         Choices are cached by device, size bound and batch class
         ($PANEL_AUTOTUNE_CACHE).  Returns {key: choice}."""
         if self.flags != bd.PANEL_MIXED or not self.buckets:
@@ -409,13 +414,16 @@ class PanelBatch:
             self.rounds[k] = int(cache[key])
             chosen[key] = self.rounds[k]
             # 3. factorisation and refinement shape
-            key = "%s|solve|n%d|b%d" % (dev, nmax, bclass(cnt))
+            key = "%s|solve-lu|n%d|b%d" % (dev, nmax, bclass(cnt))
             if key not in cache:
                 best, best_t = None, None
-                for inverse in ((False, True) if nmax + 1 <= GJ_MAX_M else (False,)):
-                    for shape in range(5):
+                factors = [(False, 2), (False, 1)] if nmax + 1 <= LU_SMEM_MAX_M else [(False, 0)]
+                if nmax + 1 <= GJ_MAX_M:
+                    factors.append((True, 0))
+                for inverse, lu in factors:
+                    for shape in range(6):
                         f = (bd.PANEL_MIXED | bd.PANEL_WITH_ADJOINT | bd.PANEL_TUNE_IR(shape) |
-                             (bd.PANEL_INVERSE if inverse else 0))
+                             (bd.PANEL_INVERSE if inverse else bd.PANEL_TUNE_LU(lu)))
 
                         def call(f=f, start=start, cnt=cnt, nmax=nmax):
                             bd.panel_solve(cnt, nmax, f, self.nodes, self.node_offsets,
@@ -425,10 +433,12 @@ class PanelBatch:
                                            self.max_iter, self.tol, self.info, self.iters)
                         t = self._time(call, reps)
                         if best_t is None or t < best_t:
-                            best, best_t = [bool(inverse), shape], t
+                            best, best_t = [bool(inverse), shape, lu], t
                 cache[key] = best
-            self.inverse[k], self.ir_shape[k] = bool(cache[key][0]), int(cache[key][1])
-            chosen[key] = [self.inverse[k], self.ir_shape[k]]
+            c = cache[key]
+            self.inverse[k], self.ir_shape[k] = bool(c[0]), int(c[1])
+            self.lu_kind[k] = int(c[2]) if len(c) > 2 else 0
+            chosen[key] = [self.inverse[k], self.ir_shape[k], self.lu_kind[k]]
         if use_cache:
             with _tune_lock:
                 merged = _load_tune_cache()
@@ -442,9 +452,10 @@ class PanelBatch:
         size bound and count, factorisation, refinement shape and assembly rounds."""
         return {"bucket_width": self.bucket_width,
                 "buckets": [{"n_max": int(nmax), "count": int(cnt),
-                             "factor": "gauss-jordan" if self.inverse[k] else "lu",
+                             "factor": "gauss-jordan" if self.inverse[k] else
+                             ["lu", "lu (L2)", "lu (shared memory)"][self.lu_kind[k]],
                              "refine_shape": ["by size", "128x8", "256x4", "512x2",
-                                              "1024x1"][self.ir_shape[k]],
+                                              "1024x1", "256x3"][self.ir_shape[k]],
                              "assembly_rounds": ["by size", "inline", 4, 8, 16,
                                                  32][self.rounds[k]]}
                             for k, (start, cnt, nmax) in enumerate(self.buckets)]}

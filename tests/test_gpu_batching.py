@@ -129,7 +129,8 @@ def test_empty_batch_is_a_no_op():
 
 def test_every_launch_shape_gives_the_oracle_result():
     # the autotuner's search space: every refinement block shape, every assembly
-    # near-field setting, both factorisations, with buckets of several widths;
+    # near-field setting, the three factorisations (LU through L2, LU in shared
+    # memory, Gauss-Jordan inverse), with buckets of several widths;
     # each combination is a layout of the same computation and matches the
     # oracle (long double) to 1e-10
     need_gpu()
@@ -139,12 +140,13 @@ def test_every_launch_shape_gives_the_oracle_result():
     with oracle.extended():
         ref = oracle.evaluate_batch(pop.nodes, pop.offsets, pop.alpha)
     for width in (None, 128):
-        for inverse in (False, True):
-            for shape in range(5):
+        for inverse, lu in ((False, 1), (False, 2), (True, 0)):
+            for shape in range(6):
                 for rounds in (0, 1, 2, 5):
                     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed",
                                     bucket_width=width, bucket_min=1)
                     pb.inverse = [inverse] * len(pb.buckets)
+                    pb.lu_kind = [lu] * len(pb.buckets)
                     pb.ir_shape = [shape] * len(pb.buckets)
                     pb.rounds = [rounds] * len(pb.buckets)
                     pb.run()
@@ -156,6 +158,28 @@ def test_every_launch_shape_gives_the_oracle_result():
                         n = pop.offsets[b + 1] - pop.offsets[b]
                         assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 1e-10, (b, shape)
                     assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < 1e-10
+
+
+def test_lu_kernels_give_the_same_factor():
+    # the LU with the trailing matrix through L2 and the LU with the whole matrix
+    # in shared memory perform the same operations in the same order: the stored
+    # factors and pivots agree bit for bit (sizes across the 32-column panels and
+    # up to the largest shared-memory size, 223 panels, and one above it)
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = _ragged(32, [230, 223, 222, 200, 131, 96, 64, 33, 32, 31, 3])
+    out = []
+    for lu in (1, 2):
+        pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed")
+        pb.lu_kind = [lu] * len(pb.buckets)
+        pb.assemble()
+        pb.solve(stage="factor")
+        torch.cuda.synchronize()
+        assert np.all(pb.info.cpu().numpy() == 0)
+        out.append((pb.LU.cpu().numpy().copy(), pb.piv.cpu().numpy().copy()))
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][0].view(np.uint32), out[1][0].view(np.uint32))
 
 
 def test_autotuner_records_a_configuration_per_bucket(tmp_path, monkeypatch):

@@ -92,14 +92,23 @@ def _large_golden():
     return np.load(path)
 
 
+def _large_solution_golden():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "large_solution_extended.npz")
+    return np.load(path)
+
+
 def test_large_full_population_samples():
     # all 1024 airfoils of 1024..2048 panels (the step-synchronous factor with
     # the tcgen05 update, the 1024-thread refinement of both systems, the
     # column-split adjoint contraction) in the bench's launch configuration.
-    # Strengths, Cl and the backward error against the FP64 oracle as in
-    # test_gpu_large.py (gamma within 5e-9, backward error against the oracle's
-    # matrix in long double within 4 x the refinement's tolerance 1e-12, Cl
-    # within 1e-10).  dCl/dx within 1e-9
+    # Strengths, Cl and the backward error as in test_gpu_large.py: gamma of the
+    # three stored airfoils within 1e-10 of the extended-precision oracle
+    # (tests/golden/large_solution_extended.npz), of the other samples within
+    # 5e-9 of the FP64 oracle (itself off by up to ~2e-9 at these condition
+    # numbers), backward error against the oracle's matrix in long double
+    # within 4 x the refinement's tolerance 1e-12, Cl within 1e-10.  dCl/dx within 1e-9
     # (inf norm relative) of extended-precision oracle gradients stored in
     # tests/golden (the FP64 oracle's own gradient is off by up to ~4e-10 at
     # these condition numbers, see make_large_gradient_golden.py): the smallest
@@ -129,6 +138,14 @@ def test_large_full_population_samples():
     sub = pop.subset(idx)
     ref = oracle.evaluate_batch(sub.nodes, sub.offsets, sub.alpha)
     u = pb.u.cpu().numpy()
+    sol = _large_solution_golden()
+    assert [int(i) for i in sol["c5_index"]] == gidx
+    for s, b in enumerate(gidx):
+        n = pop.offsets[b + 1] - pop.offsets[b]
+        o, oe = pop.offsets[b] + b, sol["c5_offsets"][s] + s
+        dev = rel_inf(u[o:o + n], sol["c5_u"][oe:oe + n])
+        print("large airfoil %d n=%d: gamma deviation from the extended oracle %.2e" % (b, n, dev))
+        assert dev < 1e-10, (b, dev)
     for s, b in enumerate(idx):
         n = pop.offsets[b + 1] - pop.offsets[b]
         o, os_ = pop.offsets[b] + b, sub.offsets[s] + s
