@@ -27,6 +27,12 @@
 //     2pi dG/dp = (l1 - l2)/2 t + theta n,
 //     2pi dG/db = l2/2 t + ((l1 - l2)/2 eta - theta xi)/L n.
 //  On the own panel theta (+-pi) cancels between the terms and is set to 0.
+//  In every branch 2pi dG/db = R_t K - (2pi dG/dp)/2 with K = (K_r, K_i) in the
+//  panel frame (R_t K = K_r t + K_i n): far field K = log|P| + Re log(1 - u)/2 +
+//  i Im F1, near field K = (l2 + (l1 - l2)/2, ((l1 - l2)/2 eta - theta xi)/L +
+//  theta/2).  So B_i = sum_j lambda_j dG_ji/db needs per pair only the two
+//  scalars lambda_j K (t_i is the lane's own panel): B_i = R_t (sum lambda K) -
+//  S_i / 2, rotated once per panel in FP64.
 //
 // Layout: one block per airfoil; each warp owns 32 consecutive columns (panels
 // i, one per lane) and sweeps all rows j: S_i = sum_j lambda_j dG_ji/dp and B_i
@@ -42,11 +48,12 @@
 
 namespace panel {
 
-// 2pi dG/dp and 2pi dG/db for the pair (p; panel i).
+// 2pi dG/dp and the panel-frame K of 2pi dG/db = R_t K - pi dG/dp for the pair
+// (p; panel i).
 __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __restrict__ s, int ld,
                                             int i, bool self, const float4* __restrict__ tlog,
                                             const float2* __restrict__ tatan, df2& gpx, df2& gpy,
-                                            df2& gbx, df2& gby) {
+                                            df2& kr, df2& ki) {
   const df2 px = split_diff(p.xh, p.xm, p.xl, s[kCx * ld + i], s[(kCx + 1) * ld + i],
                             s[(kCx + 2) * ld + i]);
   const df2 py = split_diff(p.yh, p.ym, p.yl, s[kCy * ld + i], s[(kCy + 1) * ld + i],
@@ -54,7 +61,6 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
   const df2 px2 = df_sqr(px), py2 = df_sqr(py);
   const df2 rho2 = df_add(px2, py2);
   const float Lh = s[kL * ld + i];
-  const df2 tx = pf(s, ld, kTx, i), ty = pf(s, ld, kTy, i);
   const df2 L = pf(s, ld, kL, i);
   if (__all_sync(0xffffffffu, rho2.hi >= 1024.0f * Lh * Lh)) {
     // every lane of the warp at |P| >= 32 L (warp-uniform branch): |u| <= 1/4096,
@@ -85,10 +91,8 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
     const float Lif = Li.hi;
     gpx = df_add_f(gpx, Lif * (Fr * pxh + Fi * pyh));
     gpy = df_add_f(gpy, Lif * (Fr * pyh - Fi * pxh));
-    const float dK = -0.5f * rl;
-    const float txh = tx.hi, tyh = ty.hi;
-    gbx = df_add_f(df_sub(df_mul(tx, lg), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo)), txh * dK - tyh * Fi);
-    gby = df_add_f(df_sub(df_mul(ty, lg), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo)), tyh * dK + txh * Fi);
+    kr = df_add_f(lg, -0.5f * rl);
+    ki = mkdf(Fi);
     return;
   }
   // A warp with a lane in the near field (|P| < 4 L) and every lane within 64 L
@@ -130,17 +134,17 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
     const df2 Li = df_mul(L, inv);
     gpx = df_mul(Li, df_add(df_mul(fr, px), df_mul(Fim, py)));
     gpy = df_mul(Li, df_sub(df_mul(fr, py), df_mul(Fim, px)));
-    // K = log|P| + Re log(1 - u)/2 + i Im F1;  2pi dG/db = t K - gp / 2
+    // K = log|P| + Re log(1 - u)/2 + i Im F1
     df2 lg = df_log(rho2, tlog);
     lg.hi *= 0.5f;
     lg.lo *= 0.5f;
     const df2 rl = df_add_f(ure, hL);  // -Re log(1 - u)
-    const df2 Kr = df_sub(lg, mkdf(0.5f * rl.hi, 0.5f * rl.lo));
-    gbx = df_sub(df_sub(df_mul(tx, Kr), df_mul(ty, Fim)), mkdf(0.5f * gpx.hi, 0.5f * gpx.lo));
-    gby = df_sub(df_add(df_mul(ty, Kr), df_mul(tx, Fim)), mkdf(0.5f * gpy.hi, 0.5f * gpy.lo));
+    kr = df_sub(lg, mkdf(0.5f * rl.hi, 0.5f * rl.lo));
+    ki = Fim;
     return;
   }
   // near field, panel frame (n = t rotated by +90 degrees)
+  const df2 tx = pf(s, ld, kTx, i), ty = pf(s, ld, kTy, i);
   const df2 zeta = df_add(df_mul(px, tx), df_mul(py, ty));
   const df2 eta = df_sub(df_mul(py, tx), df_mul(px, ty));
   const df2 half = mkdf(0.5f * L.hi, 0.5f * L.lo);
@@ -160,10 +164,23 @@ __device__ __forceinline__ void panel_dG_df(const point3& p, const float* __rest
   gpx = df_sub(df_mul(hd, tx), df_mul(th, ty));
   gpy = df_add(df_mul(hd, ty), df_mul(th, tx));
   const df2 cn = df_div(df_sub(df_mul(hd, eta), df_mul(th, xi)), L);
-  const df2 hl2 = mkdf(0.5f * l2.hi, 0.5f * l2.lo);
-  gbx = df_sub(df_mul(hl2, tx), df_mul(cn, ty));
-  gby = df_add(df_mul(hl2, ty), df_mul(cn, tx));
+  // K = (l2/2, cn) + (hd, theta)/2: 2pi dG/dp is R_t (hd, theta)
+  kr = df_add(mkdf(0.5f * l2.hi, 0.5f * l2.lo), mkdf(0.5f * hd.hi, 0.5f * hd.lo));
+  ki = df_add(cn, mkdf(0.5f * th.hi, 0.5f * th.lo));
 }
+
+// acc += a b with the product's two parts added to an unnormalised pair (the
+// low word collects the rounding errors of a window of terms; acc_norm
+// renormalises it at the end of the window).
+__device__ __forceinline__ void acc_add_prod(df2& acc, df2 a, df2 b) {
+  df2 p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  const df2 t = two_sum(acc.hi, p.hi);
+  acc.hi = t.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(t.lo, p.lo));
+}
+__device__ __forceinline__ void acc_norm(df2& acc) { acc = two_sum(acc.hi, acc.lo); }
 
 __device__ __forceinline__ df2 shfl_xor_df(df2 a, int o) {
   return mkdf(__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o));
@@ -249,7 +266,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
     const bool ok = i < n;
     const int ii = ok ? i : n - 1;
     const df2 ui = ok ? df_from_double(ub[ii]) : mkdf(0.0f);
-    df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+    df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sKr = mkdf(0.0f), sKi = mkdf(0.0f);
     // rows in windows of 4: the lane's u_i dG/dp terms are shifted into rx/ry
     // (static register indices with a rolled loop) and reduced per window
     df2 rx[4], ry[4];
@@ -260,14 +277,14 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
         df2 vx = mkdf(0.0f), vy = mkdf(0.0f);
         if (j < n) {
           const point3 pj = load_point(pc, ld, j);
-          df2 gpx, gpy, gbx, gby;
-          panel_dG_df(pj, pc, ld, ii, ii == j, tlog, tatan, gpx, gpy, gbx, gby);
+          df2 gpx, gpy, kr, ki;
+          panel_dG_df(pj, pc, ld, ii, ii == j, tlog, tatan, gpx, gpy, kr, ki);
           const df2 lj = mkdf(lamh[j], laml[j]);
-          // S_i += lambda_j gp, B_i += lambda_j gb  (A_i = -S_i - B_i)
-          sBx = df_add(sBx, df_mul(lj, gbx));
-          sBy = df_add(sBy, df_mul(lj, gby));
-          sSx = df_add(sSx, df_mul(lj, gpx));
-          sSy = df_add(sSy, df_mul(lj, gpy));
+          // S_i += lambda_j gp, sum lambda_j K (B_i = R_t sum lambda K - S_i / 2)
+          acc_add_prod(sSx, lj, gpx);
+          acc_add_prod(sSy, lj, gpy);
+          acc_add_prod(sKr, lj, kr);
+          acc_add_prod(sKi, lj, ki);
           if (ok) {
             vx = df_mul(ui, gpx);
             vy = df_mul(ui, gpy);
@@ -276,6 +293,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
         rx[0] = rx[1]; rx[1] = rx[2]; rx[2] = rx[3]; rx[3] = vx;
         ry[0] = ry[1]; ry[1] = ry[2]; ry[2] = ry[3]; ry[3] = vy;
       }
+      acc_norm(sSx);
+      acc_norm(sSy);
+      acc_norm(sKr);
+      acc_norm(sKi);
       const df2 sx = warp_rowsum4(rx, lane), sy = warp_rowsum4(ry, lane);
       const int jr = j0 + (lane >> 3);
       if ((lane & 7) == 0 && jr < n) {
@@ -285,9 +306,15 @@ __global__ void __launch_bounds__(256) k_adjoint_df(
       }
     }
     if (ok) {
-      const double bx = df_to_double(sBx), by = df_to_double(sBy);
-      Ac[2 * i] = -(df_to_double(sSx) + bx);
-      Ac[2 * i + 1] = -(df_to_double(sSy) + by);
+      // B_i = R_t K - S_i / 2 with the panel's FP64 unit tangent; A_i = -S_i - B_i
+      const int i1 = (i + 1 == n) ? 0 : i + 1;
+      const double hx = xs[i1] - xs[i], hy = ys[i1] - ys[i];
+      const double Li = sqrt(hx * hx + hy * hy), tx = hx / Li, ty = hy / Li;
+      const double Sx = df_to_double(sSx), Sy = df_to_double(sSy);
+      const double Kr = df_to_double(sKr), Ki = df_to_double(sKi);
+      const double bx = tx * Kr - ty * Ki - 0.5 * Sx, by = ty * Kr + tx * Ki - 0.5 * Sy;
+      Ac[2 * i] = -(Sx + bx);
+      Ac[2 * i + 1] = -(Sy + by);
       Bc[2 * i] = bx;
       Bc[2 * i + 1] = by;
     }
@@ -412,7 +439,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
   const bool warp_on = 32 * warp < nc;
   const int ic = ok ? il : 0;
   const df2 ui = ok ? df_from_double(ub[i]) : mkdf(0.0f);
-  df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sBx = mkdf(0.0f), sBy = mkdf(0.0f);
+  df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sKr = mkdf(0.0f), sKi = mkdf(0.0f);
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
     if (warp_on) {
@@ -424,13 +451,13 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
           df2 vx = mkdf(0.0f), vy = mkdf(0.0f);
           if (t < jn) {
             const point3 pj = load_point(rp, ld, j);
-            df2 gpx, gpy, gbx, gby;
-            panel_dG_df(pj, cpc, kSplitChunk, ic, ok && i == j, tlog, tatan, gpx, gpy, gbx, gby);
+            df2 gpx, gpy, kr, ki;
+            panel_dG_df(pj, cpc, kSplitChunk, ic, ok && i == j, tlog, tatan, gpx, gpy, kr, ki);
             const df2 lj = mkdf(lamh[j], laml[j]);
-            sBx = df_add(sBx, df_mul(lj, gbx));
-            sBy = df_add(sBy, df_mul(lj, gby));
-            sSx = df_add(sSx, df_mul(lj, gpx));
-            sSy = df_add(sSy, df_mul(lj, gpy));
+            acc_add_prod(sSx, lj, gpx);
+            acc_add_prod(sSy, lj, gpy);
+            acc_add_prod(sKr, lj, kr);
+            acc_add_prod(sKi, lj, ki);
             if (ok) {
               vx = df_mul(ui, gpx);
               vy = df_mul(ui, gpy);
@@ -439,6 +466,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
           rx[0] = rx[1]; rx[1] = rx[2]; rx[2] = rx[3]; rx[3] = vx;
           ry[0] = ry[1]; ry[1] = ry[2]; ry[2] = ry[3]; ry[3] = vy;
         }
+        acc_norm(sSx);
+        acc_norm(sSy);
+        acc_norm(sKr);
+        acc_norm(sKi);
         const df2 sx = warp_rowsum4(rx, lane), sy = warp_rowsum4(ry, lane);
         const int tr = t0 + (lane >> 3);
         if ((lane & 7) == 0 && tr < jn) win[warp * 32 + tr] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
@@ -470,9 +501,14 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
     // u_i A_i belongs to node i (start of panel i), u_i B_i to node i + 1
     const int i1 = (i + 1 == n) ? 0 : i + 1;
     const double f = w2pi * ub[i];
-    const double bx = df_to_double(sBx), by = df_to_double(sBy);
-    atomicAdd(&gout[2 * i], -f * (df_to_double(sSx) + bx));
-    atomicAdd(&gout[2 * i + 1], -f * (df_to_double(sSy) + by));
+    // B_i = R_t K - S_i / 2 with the panel's FP64 unit tangent; A_i = -S_i - B_i
+    const double hx = nodes[2 * i1] - nodes[2 * i], hy = nodes[2 * i1 + 1] - nodes[2 * i + 1];
+    const double Li = sqrt(hx * hx + hy * hy), tx = hx / Li, ty = hy / Li;
+    const double Sx = df_to_double(sSx), Sy = df_to_double(sSy);
+    const double Kr = df_to_double(sKr), Ki = df_to_double(sKi);
+    const double bx = tx * Kr - ty * Ki - 0.5 * Sx, by = ty * Kr + tx * Ki - 0.5 * Sy;
+    atomicAdd(&gout[2 * i], -f * (Sx + bx));
+    atomicAdd(&gout[2 * i + 1], -f * (Sy + by));
     atomicAdd(&gout[2 * i1], f * bx);
     atomicAdd(&gout[2 * i1 + 1], f * by);
   }

@@ -140,7 +140,7 @@ __device__ __forceinline__ void update_tiles(float* __restrict__ F, const float*
 }
 
 template <int NB>
-__global__ void __launch_bounds__(kThreads, 2) k_lu_global(SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_lu_global(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LDP = NB + 1;
   constexpr int CW = 128;  // GEMM column slab
