@@ -485,9 +485,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 // (r of A21, or c of A12^T), N = t, B[t][k] = X[k][t] for X = U11^{-1} (L21)
 // or B[t][k] = L11^{-1}[t][k] (U12^T).  Per block:
 //   1. the diagonal tile (K, K) is staged and the one triangular inverse this
-//      block needs is formed by substitution (a thread per column of the
-//      inverse); it is split into TF32 hi / lo and kept in shared memory as the
-//      B operand of all the block's tiles (128 KB);
+//      block needs is formed by 32 x 32 blocks (the diagonal blocks by
+//      substitution in registers, then the blocks below them as small products,
+//      operands read as broadcast vector loads); it is split into TF32 hi / lo
+//      and kept in shared memory as the B operand of all the block's tiles
+//      (128 KB);
 //   2. the tiles stream through two stages: warp 8 loads a K-chunk by TMA (a
 //      128 x 32 chunk of A21, or four 32 x 32 boxes of A12 that the converters
 //      transpose to A12^T), warps 4-7 split it into hi / lo, warp 9 issues the
@@ -503,7 +505,7 @@ constexpr uint32_t kTsStage = 3 * kOpBytes;
 constexpr int kTsStages = 2;
 constexpr uint32_t kTsBar = kTsA + kTsStages * kTsStage;
 constexpr uint32_t kTsSmem = kTsBar + 1024 + 1024;    // barriers, then alignment slack
-constexpr int kTsLdD = 129;                           // row stride of the staged diagonal tile
+constexpr int kTsLdW = 132;                           // column stride of the staged triangle
 }  // namespace
 
 __global__ void __launch_bounds__(kThreadsTc, 1)
@@ -542,63 +544,115 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   float* F = a.LU + bt.mat_off[b];
 
   // ---- 1. the inverse, as the B operand ----
-  // Thread j < 128 forms column j of the inverse, all threads walking the same
-  // rows t and terms q together (the staged tile is read by broadcast, the
-  // inverse by consecutive columns: no bank conflicts); entries that are zero
-  // by triangularity are computed as zeros rather than skipped.
+  // Both solves need the inverse X of a lower triangular matrix W: W = L11
+  // (unit diagonal) for U12, W = U11^T for L21 (then X = (U11^{-1})^T).  W is
+  // staged column-major (WT[c][r] = W[r][c], columns 16-byte aligned, so a
+  // piece of a column is a broadcast vector load) and inverted by 32 x 32
+  // blocks: the four diagonal blocks X_ii = W_ii^{-1} (warps 0-3, lane j the
+  // column j of X_ii in registers, right-looking substitution), then the blocks
+  // at distance d = 1, 2, 3 below the diagonal, X_ij = -X_ii sum_{j<=k<i} W_ik
+  // X_kj (one warp per block, lane c the column c of the block in registers).
   {
-    float* D = reinterpret_cast<float*>(gbase + kTsA);  // 128 x kTsLdD
-    float* X = reinterpret_cast<float*>(gbase);         // 128 x 128, X[t][j]
+    float* WT = reinterpret_cast<float*>(gbase + kTsA);       // 128 x kTsLdW, column-major
+    float* X = reinterpret_cast<float*>(gbase);               // 128 x 128, row-major
+    float* XD = reinterpret_cast<float*>(gbase + kTsBlo);     // 4 x 32 x 32, X_ii column-major
     const float* Td = F + g.tile(K, K);
+    const bool unit = (kind == 0);
     for (int e = tid; e < kTlTile; e += kThreadsTc) {
       const int r = e >> 7, c = e & 127;
-      D[r * kTsLdD + c] = Td[((c >> 5) << 12) + r * 32 + (c & 31)];
+      const float v = Td[((c >> 5) << 12) + r * 32 + (c & 31)];  // tile element (r, c)
+      // kind 0: W = L (W[r][c] = tile(r, c)); kind 1: W = U^T (W[c][r] = tile(r, c))
+      if (kind == 0)
+        WT[c * kTsLdW + r] = v;
+      else
+        WT[r * kTsLdW + c] = v;
     }
     __syncthreads();
-    if (tid < kTlB) {
-      const int j = tid;
-      if (kind == 0) {
-        // L X = I (unit lower): X[t][j] = [t == j] - sum_{q < t} L[t][q] X[q][j]
-        for (int t = 0; t < kTlB; ++t) {
-          const float* Lt = D + t * kTsLdD;
-          float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-          int q = 0;
-          for (; q + 3 < t; q += 4) {
-            s0 = fmaf(Lt[q], X[q * 128 + j], s0);
-            s1 = fmaf(Lt[q + 1], X[(q + 1) * 128 + j], s1);
-            s2 = fmaf(Lt[q + 2], X[(q + 2) * 128 + j], s2);
-            s3 = fmaf(Lt[q + 3], X[(q + 3) * 128 + j], s3);
+    if (warp < 4) {
+      // X_ii, i = warp: W_ii x = e_j for the lane's column j
+      const int i0 = 32 * warp;
+      float acc[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] = (t == lane) ? 1.0f : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float* wk = WT + (i0 + k) * kTsLdW + i0;  // column k of W_ii
+        const float xk = unit ? acc[k] : acc[k] / wk[k];
+        acc[k] = xk;
+#pragma unroll
+        for (int t4 = 0; t4 < 32; t4 += 4) {
+          if (t4 + 3 > k) {
+            const float4 w = *reinterpret_cast<const float4*>(wk + t4);
+            if (t4 > k) acc[t4] = fmaf(-w.x, xk, acc[t4]);
+            if (t4 + 1 > k) acc[t4 + 1] = fmaf(-w.y, xk, acc[t4 + 1]);
+            if (t4 + 2 > k) acc[t4 + 2] = fmaf(-w.z, xk, acc[t4 + 2]);
+            acc[t4 + 3] = fmaf(-w.w, xk, acc[t4 + 3]);
           }
-          for (; q < t; ++q) s0 = fmaf(Lt[q], X[q * 128 + j], s0);
-          X[t * 128 + j] = (t == j ? 1.0f : 0.0f) - ((s0 + s1) + (s2 + s3));
-        }
-      } else {
-        // U Y = I: Y[t][j] = ([t == j] - sum_{q > t} U[t][q] Y[q][j]) / U[t][t]
-        for (int t = kTlB - 1; t >= 0; --t) {
-          const float* Ut = D + t * kTsLdD;
-          float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-          int q = t + 1;
-          for (; q + 3 < kTlB; q += 4) {
-            s0 = fmaf(Ut[q], X[q * 128 + j], s0);
-            s1 = fmaf(Ut[q + 1], X[(q + 1) * 128 + j], s1);
-            s2 = fmaf(Ut[q + 2], X[(q + 2) * 128 + j], s2);
-            s3 = fmaf(Ut[q + 3], X[(q + 3) * 128 + j], s3);
-          }
-          for (; q < kTlB; ++q) s0 = fmaf(Ut[q], X[q * 128 + j], s0);
-          X[t * 128 + j] = ((t == j ? 1.0f : 0.0f) - ((s0 + s1) + (s2 + s3))) / Ut[t];
         }
       }
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const float v = (t >= lane) ? acc[t] : 0.0f;
+        X[(i0 + t) * 128 + i0 + lane] = v;
+        XD[warp * 1024 + lane * 32 + t] = v;  // column lane of X_ii
+      }
+    }
+    // the strictly lower blocks are zero above the diagonal blocks
+    for (int e = tid; e < kTlTile; e += kThreadsTc) {
+      const int r = e >> 7, c = e & 127;
+      if ((c >> 5) > (r >> 5)) X[e] = 0.0f;
     }
     __syncthreads();
-    // X -> the A region (D is no longer needed), then the B operand from it:
+    for (int d = 1; d < 4; ++d) {
+      if (warp < 4 - d) {
+        const int j = warp, i = warp + d;
+        // T = sum_{j<=k<i} W_ik X_kj (rows of the block in registers, column c)
+        float acc[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc[t] = 0.0f;
+        for (int kk = 32 * j; kk < 32 * i; ++kk) {
+          const float xv = X[kk * 128 + 32 * j + lane];
+          const float* wc = WT + kk * kTsLdW + 32 * i;  // W[32 i + t][kk], t = 0..31
+#pragma unroll
+          for (int t4 = 0; t4 < 32; t4 += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(wc + t4);
+            acc[t4] = fmaf(w.x, xv, acc[t4]);
+            acc[t4 + 1] = fmaf(w.y, xv, acc[t4 + 1]);
+            acc[t4 + 2] = fmaf(w.z, xv, acc[t4 + 2]);
+            acc[t4 + 3] = fmaf(w.w, xv, acc[t4 + 3]);
+          }
+        }
+        // X_ij = -X_ii T: column c of the result from the lane's T column
+        float out[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) out[t] = 0.0f;
+        const float* xd = XD + i * 1024;
+#pragma unroll
+        for (int kk = 0; kk < 32; ++kk) {
+          const float tv = acc[kk];
+#pragma unroll
+          for (int t4 = 0; t4 < 32; t4 += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(xd + kk * 32 + t4);  // X_ii[t][kk]
+            out[t4] = fmaf(-w.x, tv, out[t4]);
+            out[t4 + 1] = fmaf(-w.y, tv, out[t4 + 1]);
+            out[t4 + 2] = fmaf(-w.z, tv, out[t4 + 2]);
+            out[t4 + 3] = fmaf(-w.w, tv, out[t4 + 3]);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < 32; ++t) X[(32 * i + t) * 128 + 32 * j + lane] = out[t];
+      }
+      __syncthreads();
+    }
+    // X -> the A region (W is no longer needed), then the B operand from it:
     // U12^T = A12^T (L11^{-1})^T needs B[t][k] = L11^{-1}[t][k] = X[t][k];
-    // L21 = A21 U11^{-1} needs B[t][k] = U11^{-1}[k][t] = X[k][t]
-    float* Xc = D;
+    // L21 = A21 U11^{-1} needs B[t][k] = U11^{-1}[k][t] = X[t][k] as well
+    float* Xc = WT;
     for (int e = tid; e < kTlTile; e += kThreadsTc) Xc[e] = X[e];
     __syncthreads();
     for (int e = tid; e < kTlTile; e += kThreadsTc) {
       const int k = e >> 7, t = e & 127;
-      const float v = (kind == 0) ? Xc[t * 128 + k] : Xc[k * 128 + t];
+      const float v = Xc[t * 128 + k];
       const float h = tf32_hi(v);
       const uint32_t o = (uint32_t)(k >> 5) * kOpBytes + sw_off(t, k & 31);
       *reinterpret_cast<float*>(gbase + kTsBhi + o) = h;
