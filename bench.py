@@ -160,7 +160,9 @@ TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 
 CALL_SOURCES = {
     "mixed": {"assemble": ["k_assemble_df.cu"],
-              "factor": ["k_solve_mixed.cu", "k_gj_mixed.cu", "k_lu_large.cu", "k_update_tc.cu"],
+              "factor": ["k_solve_mixed.cu", "k_gj_mixed.cu"],
+              "factor-large": ["k_solve_mixed.cu", "k_gj_mixed.cu", "k_lu_large.cu",
+                               "k_update_tc.cu"],
               "refine": ["k_solve_mixed.cu"],
               "forces": ["k_forces.cu"],
               "adjoint": ["k_adjoint_df.cu"]},
@@ -169,11 +171,12 @@ CALL_SOURCES = {
 }
 
 
-def kernel_source_digest(call=None, mode="mixed") -> str:
+def kernel_source_digest(call=None, mode="mixed", large=False) -> str:
     """sha256 over the CUDA sources of the kernels one library call launches
-    (the .cu files and the csrc headers they include, transitively), or over
-    every source when `call` is None: a DRAM-traffic figure recorded with
-    another digest was taken on different kernels."""
+    (the .cu files and the csrc headers they include, transitively; the mixed
+    factor of airfoils above 639 panels, `large`, adds the step-synchronous
+    LU's), or over every source when `call` is None: a DRAM-traffic figure
+    recorded with another digest was taken on different kernels."""
     import hashlib
     import glob
     import re
@@ -182,7 +185,8 @@ def kernel_source_digest(call=None, mode="mixed") -> str:
         files = sorted(os.path.basename(f) for f in
                        glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
     else:
-        todo, seen = list(CALL_SOURCES[mode][call]), set()
+        key = "factor-large" if (call == "factor" and large and mode == "mixed") else call
+        todo, seen = list(CALL_SOURCES[mode][key]), set()
         while todo:
             f = todo.pop()
             if f in seen:
@@ -600,10 +604,17 @@ def measure_workload(name, mode, args, ctx, headline=False, extras=False):
     out["kernels"] = kernels
     dom = max(kms, key=kms.get)
     dk = kernels[dom]
-    digest = kernel_source_digest(dom, mode)
+    digest = kernel_source_digest(dom, mode, large=int(pop.sizes.max()) + 1 > 640)
+    # the traffic row of the kernels in use: the factor's LU kernel as tuned
+    tkey = dom
+    if dom == "factor" and mode == "mixed":
+        kinds = {"lu" if bk["factor"] == "lu (shared memory)" else bk["factor"]
+                 for bk in pb.tuning()["buckets"]}
+        if len(kinds) == 1 and kinds != {"lu"}:
+            tkey = "factor:" + kinds.pop()
     roof = {"kernel": dom, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
             "unit": dk["unit"], "frac": dk["frac"],
-            "traffic": recorded_traffic(dom, name, mode, B, digest),
+            "traffic": recorded_traffic(tkey, name, mode, B, digest),
             "traffic_unit": "bytes per launch", "kernel_digest": digest,
             "work": ROOF_WORK[mode][dom], "peak_source": pk[dk["bound"]][2]}
     if "issue_frac" in dk:
@@ -644,6 +655,29 @@ def measure_workload(name, mode, args, ctx, headline=False, extras=False):
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return out
+
+
+def profile_step(args):
+    """One eager mixed step of a workload prefix, nothing timed: the command
+    that per-kernel ncu captures (profiles/dram_traffic.txt) run."""
+    import torch
+
+    from paper_1511_02166_gb300 import inputs
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = inputs.make_population(args.config, batch=args.batch)
+    pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", max_iter=args.max_iter,
+                    tol=args.tol)
+    pb.lu_kind = [args.lu_kind] * len(pb.buckets)
+    pb.assemble()
+    pb.solve(with_adjoint=True)
+    pb.forces()
+    pb.adjoint()
+    torch.cuda.synchronize()
+    bad = int((pb.info != 0).sum())
+    print(json.dumps({"profile_step": args.config, "batch": pop.batch, "lu_kind": args.lu_kind,
+                      "info_nonzero": bad, "tuning": pb.tuning()}))
+    if bad:
+        sys.exit(1)
 
 
 def measure_extras(pb, pop, args, ctx):
@@ -824,10 +858,18 @@ def main():
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="launch the calls one by one instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one eager mixed step (assemble, solve with the transposed "
+                         "system, forces, adjoint) of --config/--batch with the library's "
+                         "launch choices and exit: the driver of per-kernel ncu captures")
+    ap.add_argument("--lu-kind", type=int, default=0,
+                    help="with --profile-step: PANEL_TUNE_LU of every bucket (0 by size)")
     ap.add_argument("--batch", type=int, default=None,
                     help="evaluate only the first BATCH airfoils of the workload (profiling)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_step:
+        profile_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -111,10 +111,12 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
 }
 
 // LU of the diagonal block K with partial pivoting inside the block.
-__global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
+__global__ void __launch_bounds__(256, 3) k_large_diag(SolveArgs a, int K) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* D = reinterpret_cast<float*>(smraw);          // kBW x kLdD
-  int* sp = reinterpret_cast<int*>(D + kBW * kLdD);    // kBW
+  float* rows4 = D + kBW * kLdD;                       // 2 x 4 x 32: the warps' candidate rows
+  unsigned* red = reinterpret_cast<unsigned*>(rows4 + 256);  // 2 x 4 x 2: their keys, positions
+  int* sp = reinterpret_cast<int*>(red + 16);          // kBW
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   int n, m;
@@ -135,70 +137,107 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
     D[r * kLdD + c] = (r < kb && c < kb) ? Td[dpos(r, c)] : 0.0f;
   }
   __syncthreads();
-  // Blocked in panels of 32 columns.  Per panel: warp 0 factors the panel
+  // Blocked in panels of 32 columns.  Per panel: warps 0-3 factor the panel
   // (rows c0..kb-1) column by column with partial pivoting over those rows,
-  // lane l holding column c0 + l for the exchanges and the rank-1 updates and
-  // rows q + l, q + l + 32, ... for the pivot search (warp barriers only); then
-  // the whole block applies the panel's exchanges to the other columns, solves
-  // U12 = L11^{-1} A12 (a thread per column) and updates the trailing block in
-  // 4 x 4 register tiles.
+  // thread t holding row c0 + t of the panel in registers; rows keep their
+  // threads and `pos` tracks their current position, so an exchange is
+  // bookkeeping plus one sp entry.  Per column, one 128-thread barrier: each
+  // warp finds its candidate (largest |x|, the lowest position among equal
+  // maxima) and puts its key, position and whole row in shared memory (two
+  // buffers, alternating by column); after the barrier every thread picks the
+  // pivot among the four and reads its row; the rank-1 update in registers.  The step loop is rolled, the columns
+  // rotating through the registers (x[0] is the current one) so that every
+  // register index is a constant; each finished entry goes to the row's own
+  // place in D (by original row), and the rows are written back in their final
+  // order at the end.  Then the whole block applies the panel's exchanges to
+  // the other columns, solves U12 = L11^{-1} A12 (a thread per column) and
+  // updates the trailing block in 4 x 4 register tiles.
   __shared__ int zero_pivot;
   if (tid == 0) zero_pivot = -1;
   __syncthreads();
   for (int c0 = 0; c0 < kb; c0 += 32) {
     const int w = min(32, kb - c0);
-    if (warp == 0) {
-      for (int q = c0; q < c0 + w; ++q) {
-        // argmax |D[r][q]| over the rows q..kb-1, lowest row on ties
-        float bv = -1.0f;
-        int br = kBW;
-        for (int r = q + lane; r < kb; r += 32) {
-          const float v = fabsf(D[r * kLdD + q]);
-          if (v > bv) {
-            bv = v;
-            br = r;
+    if (warp < 4) {
+      const int nrow = kb - c0;  // rows taking part: c0 .. kb-1
+      float x[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        x[t] = (tid < nrow && t < w) ? D[(c0 + tid) * kLdD + c0 + t] : 0.0f;
+      int pos = tid;
+      bool done = tid >= nrow;
+      int fz = -1;
+#pragma unroll 1
+      for (int q = 0; q < 32; ++q) {
+        const bool act = q < w && fz < 0;  // uniform over the 128 threads
+        const float v = (act && !done) ? fabsf(x[0]) : -1.0f;
+        const unsigned key = (v >= 0.0f) ? __float_as_uint(v) + 1u : 0u;
+        const unsigned wm = __reduce_max_sync(0xffffffffu, key);
+        const unsigned wp = __reduce_min_sync(0xffffffffu, key == wm ? (unsigned)pos : 0xffffu);
+        float* slot = rows4 + (q & 1) * 128;
+        unsigned* rk = red + (q & 1) * 8;
+        if (key == wm && pos == (int)wp) {  // the warp's candidate (one lane)
+#pragma unroll
+          for (int t = 0; t < 32; t += 4)
+            *reinterpret_cast<float4*>(slot + warp * 32 + t) =
+                make_float4(x[t], x[t + 1], x[t + 2], x[t + 3]);
+        }
+        if (lane == 0) {
+          rk[warp] = wm;
+          rk[4 + warp] = wp;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        unsigned mx = rk[0], pm = rk[4];
+        int ww = 0;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+          const unsigned kk = rk[k], pk = rk[4 + k];
+          if (kk > mx || (kk == mx && pk < pm)) {
+            mx = kk;
+            pm = pk;
+            ww = k;
           }
         }
+        const bool ok = act && mx > 1u;  // mx <= 1: exactly zero (or NaN) column
+        if (act && !ok) fz = q;
+        const bool piv = ok && key == mx && pos == (int)pm;
+        if (ok && tid == 0) sp[c0 + q] = c0 + (int)pm;
+        if (ok && pos == q && !piv) pos = (int)pm;
+        if (piv) {
+          pos = q;
+          done = true;
+        }
+        // the pivot row, four columns at a time straight into the update
+        const float* prow = slot + ww * 32;
+        const float4 f0 = *reinterpret_cast<const float4*>(prow);
+        const bool elim = ok && !done;
+        const float l = x[0] * __frcp_rn(f0.x);
+        const float le = elim ? l : 0.0f;
+        x[1] = fmaf(-le, f0.y, x[1]);
+        x[2] = fmaf(-le, f0.z, x[2]);
+        x[3] = fmaf(-le, f0.w, x[3]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-          const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-          if (ov > bv || (ov == bv && orr < br)) {
-            bv = ov;
-            br = orr;
-          }
+        for (int t = 4; t < 32; t += 4) {
+          const float4 r4 = *reinterpret_cast<const float4*>(prow + t);
+          x[t] = fmaf(-le, r4.x, x[t]);
+          x[t + 1] = fmaf(-le, r4.y, x[t + 1]);
+          x[t + 2] = fmaf(-le, r4.z, x[t + 2]);
+          x[t + 3] = fmaf(-le, r4.w, x[t + 3]);
         }
-        const int p = (br < kb) ? br : q;
-        if (lane == 0) sp[q] = p;
-        if (!(fabsf(D[p * kLdD + q]) > 0.0f)) {  // exact zero (or NaN) pivot
-          if (lane == 0) zero_pivot = q;
-          break;
-        }
-        if (p != q && lane < w) {
-          const float t = D[q * kLdD + c0 + lane];
-          D[q * kLdD + c0 + lane] = D[p * kLdD + c0 + lane];
-          D[p * kLdD + c0 + lane] = t;
-        }
-        __syncwarp();
-        // multipliers and the rank-1 update of the panel's later columns: lane
-        // l takes the rows q + 1 + l, + 32, ... (independent across rows)
-        const float inv = 1.0f / D[q * kLdD + q];
-        float lr[4];
+        if (tid < nrow && q < w) D[(c0 + tid) * kLdD + c0 + q] = elim ? l : x[0];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = q + 1 + lane + 32 * i;
-          lr[i] = (r < kb) ? D[r * kLdD + q] * inv : 0.0f;
-          if (r < kb) D[r * kLdD + q] = lr[i];
-        }
-        for (int j = q + 1; j < c0 + w; ++j) {
-          const float uqj = D[q * kLdD + j];
+        for (int t = 0; t < 31; ++t) x[t] = x[t + 1];
+        x[31] = 0.0f;
+      }
+      if (fz >= 0 && tid == 0) zero_pivot = c0 + fz;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // the panel's rows in their final order
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = q + 1 + lane + 32 * i;
-            if (r < kb) D[r * kLdD + j] = fmaf(-lr[i], uqj, D[r * kLdD + j]);
-          }
-        }
-        __syncwarp();
+      for (int t = 0; t < 32; ++t) x[t] = (tid < nrow && t < w) ? D[(c0 + tid) * kLdD + c0 + t] : 0.0f;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (tid < nrow) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (t < w) D[(c0 + pos) * kLdD + c0 + t] = x[t];
       }
     }
     __syncthreads();
@@ -224,13 +263,18 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
     __syncthreads();
     const int c1 = c0 + w;
     if (c1 >= kb) break;
-    // U12 = L11^{-1} A12 on rows c0..c1-1, columns c1..kb-1 (unit lower L11)
+    // U12 = L11^{-1} A12 on rows c0..c1-1, columns c1..kb-1 (unit lower L11;
+    // here w == 32): a thread per column in registers, right-looking
     for (int c = c1 + tid; c < kb; c += 256) {
-      for (int i = 1; i < w; ++i) {
-        float s = D[(c0 + i) * kLdD + c];
-        for (int t = 0; t < i; ++t) s = fmaf(-D[(c0 + i) * kLdD + c0 + t], D[(c0 + t) * kLdD + c], s);
-        D[(c0 + i) * kLdD + c] = s;
-      }
+      float col[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) col[t] = D[(c0 + t) * kLdD + c];
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+#pragma unroll
+        for (int t = q + 1; t < 32; ++t) col[t] = fmaf(-D[(c0 + t) * kLdD + c0 + q], col[q], col[t]);
+#pragma unroll
+      for (int t = 1; t < 32; ++t) D[(c0 + t) * kLdD + c] = col[t];
     }
     __syncthreads();
     // trailing block: rows and columns c1..kb-1, D -= L21 U12, 4 x 4 per task
@@ -283,19 +327,31 @@ __global__ void __launch_bounds__(256) k_large_diag(SolveArgs a, int K) {
   __syncthreads();
   // ... applied to the columns outside the block (block row K: the finished L
   // to the left, A12 to the right, both untransposed here)
-  for (int c = tid; c < m; c += 256) {
-    if (c >= k0 && c < k0 + kb) continue;
-    for (int x = 0; x < nex; ++x) {
-      float* u = F + g.off(k0 + ex[2 * x], c, false);
-      float* v = F + g.off(k0 + ex[2 * x + 1], c, false);
-      const float t = *u;
-      *u = *v;
-      *v = t;
+  // exchange by exchange, each thread's columns (at most 9: m <= 2049) all in
+  // flight at once
+  constexpr int kXc = (PANEL_N_MAX + 1 + 255) / 256;
+  for (int x = 0; x < nex; ++x) {
+    const int ra = k0 + ex[2 * x], rb = k0 + ex[2 * x + 1];
+    float va[kXc], vb[kXc];
+#pragma unroll
+    for (int j = 0; j < kXc; ++j) {
+      const int c = tid + 256 * j;
+      const bool on = c < m && (c < k0 || c >= k0 + kb);
+      va[j] = on ? F[g.off(ra, c, false)] : 0.0f;
+      vb[j] = on ? F[g.off(rb, c, false)] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < kXc; ++j) {
+      const int c = tid + 256 * j;
+      if (c < m && (c < k0 || c >= k0 + kb)) {
+        F[g.off(ra, c, false)] = vb[j];
+        F[g.off(rb, c, false)] = va[j];
+      }
     }
   }
 }
 
-size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + 3 * kBW * 4; }
+size_t large_diag_smem() { return (size_t)kBW * kLdD * 4 + 256 * 4 + 16 * 4 + 3 * kBW * 4; }
 
 // U12 = L11^{-1} A12 and L21 = A21 U11^{-1} as products with the explicit
 // inverses of the two triangles of the factored diagonal block K.  Per block:

@@ -322,10 +322,12 @@ class PanelBatch:
     def launches_per_step(self, with_grad: bool = True) -> int:
         """Kernel launches of one step: per bucket assemble, factor, refine and
         adjoint, plus one forces launch.  The mixed factor launches one kernel
-        per size class the bucket may hold (Gauss-Jordan in shared memory,
-        Gauss-Jordan in global memory, one-block LU) and, for m > 640, the
-        step-synchronous LU (2 + 3 per 128-column block); the adjoint of
-        n > 512 adds a zeroing launch."""
+        per size class the bucket may hold (Gauss-Jordan in shared memory and in
+        global memory, or the one-block LU in shared memory and through L2) and,
+        for m > 640 with T 128-column blocks, the step-synchronous LU: the tiled
+        copy, T diagonal LUs, one CUDA-core and T - 1 tensor-core triangular
+        solves, T - 1 updates, the conversion back and the inversion of the
+        diagonal blocks; the adjoint of n > 512 adds a zeroing launch."""
         n = 1  # forces
         for k, (start, cnt, nmax) in enumerate(self.buckets):
             m = nmax + 1
@@ -337,7 +339,7 @@ class PanelBatch:
                     n += (self.lu_kind[k] != 1) + (m > LU_SMEM_MAX_M or self.lu_kind[k] == 1)
                 if m > 640:
                     blocks = -(-m // 128)
-                    n += 2 + blocks + 2 * (blocks - 1)
+                    n += 3 + blocks + 2 * (blocks - 1)
                 n += 1  # refine
             else:
                 n += 1
