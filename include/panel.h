@@ -102,10 +102,13 @@ typedef enum {
  *     (4 per SM), 512 (2 per SM), 1024 (1 per SM) or 256 threads (3 per SM); a
  *     shape whose shared memory does not fit the airfoils' size falls back to
  *     the choice by size.
- *   PANEL_TUNE_ROUNDS(r), r = 1..5: the double-float assembly (panel_assemble,
+ *   PANEL_TUNE_ROUNDS(r), r = 1..6: the double-float assembly (panel_assemble,
  *     PANEL_MIXED) evaluates near-field pairs inline with the far-field ones
  *     (1) or queues them and evaluates them together after every 4, 8, 16 or
- *     32 pairs per thread (2..5).
+ *     32 pairs per thread (2..5), or (6, the choice by size above 1024 panels)
+ *     evaluates each pair of control points once for both of its entries,
+ *     sharing the far field's orientation-free terms.  All give the same
+ *     matrix.
  *   PANEL_TUNE_LU(k), k = 1..2: the FP32 LU (panel_solve, PANEL_MIXED, without
  *     PANEL_INVERSE) of airfoils with n_b < 224 keeps the trailing matrix in
  *     the LU buffer through L2, several airfoils per SM (1), or the whole

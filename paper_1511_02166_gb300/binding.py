@@ -39,8 +39,9 @@ def PANEL_TUNE_IR(shape: int) -> int:
 
 
 def PANEL_TUNE_ROUNDS(sel: int) -> int:
-    """Assembly near-field queue field of the flags: 0 by size, 1 inline, 2..5 =
-    after 4, 8, 16, 32 pairs per thread."""
+    """Assembly field of the flags: 0 by size, 1 near-field pairs inline, 2..5 =
+    queued after 4, 8, 16, 32 pairs per thread, 6 = both entries of a pair of
+    control points at once."""
     return int(sel) << PANEL_TUNE_ROUNDS_SHIFT
 
 

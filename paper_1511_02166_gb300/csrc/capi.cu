@@ -73,7 +73,7 @@ bool flags_ok(int flags) {
   const int known = PANEL_FP64 | PANEL_MIXED | PANEL_WITH_ADJOINT | PANEL_FACTOR_ONLY |
                     PANEL_REUSE_FACTOR | PANEL_INVERSE | (7 << PANEL_TUNE_IR_SHIFT) |
                     (7 << PANEL_TUNE_ROUNDS_SHIFT) | (3 << PANEL_TUNE_LU_SHIFT);
-  if (tune_ir(flags) > 5 || tune_rounds(flags) > 5 || tune_lu(flags) > 2) return false;
+  if (tune_ir(flags) > 5 || tune_rounds(flags) > 6 || tune_lu(flags) > 2) return false;
   if (mode_of(flags) == 0 || (flags & ~known) != 0) return false;
   const int stage = flags & (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR);
   if (stage == (PANEL_FACTOR_ONLY | PANEL_REUSE_FACTOR)) return false;

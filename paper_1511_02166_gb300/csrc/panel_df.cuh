@@ -139,6 +139,41 @@ __device__ __forceinline__ PairGeom pair_geom(const point3& p, const float* __re
   return g;
 }
 
+// The far-field series of G(p; panel i) from the quantities of the pair that
+// do not depend on the panel's orientation or length (they are the same for
+// the pair seen from either end: P -> -P leaves them unchanged exactly):
+// X + iY = P^2 (X = px^2 - py^2, Y = 2 px py), inv = 1/|P|^2, inv2 = inv^2,
+// lgh = log|P|.  Terms n = 1, 2 in double-float, n >= 3 in float32.
+__device__ __forceinline__ df2 panel_G_far(const df2 X, const df2 Y, const df2 inv,
+                                           const df2 inv2, const df2 lgh,
+                                           const float* __restrict__ s, int ld, int i, float Lh) {
+  const df2 Z = df_add(df_mul(pf(s, ld, kC2, i), X), df_mul(pf(s, ld, kS2, i), Y));
+  const df2 cc = df_mul(Z, inv);  // cos 2phi
+  const df2 t1 = df_mul(df_mul(pf(s, ld, kQ6, i), inv), cc);       // q c / 6
+  df2 T2 = df_sqr(cc);
+  T2.hi *= 2.0f;
+  T2.lo *= 2.0f;
+  T2 = df_add_f(T2, -1.0f);                                        // 2c^2 - 1
+  const df2 t2 = df_mul(df_mul(pf(s, ld, kQ20, i), inv2), T2);     // q^2 T2 / 20
+  // n >= 3 in float32: q^3 (T3/42 + q (T4/72 + q (T5/110 + q (T6/156 + q T7/210))))
+  const float q = __fmul_rn(__fmul_rn(0.25f * Lh, Lh), inv.hi);
+  const float c = cc.hi;
+  const float c2 = __fmul_rn(2.0f, c);
+  const float T3 = __fmul_rn(c, __fsub_rn(__fmul_rn(__fmul_rn(4.0f, c), c), 3.0f));
+  const float T4 = __fsub_rn(__fmul_rn(c2, T3), T2.hi);
+  const float T5 = __fsub_rn(__fmul_rn(c2, T4), T3);
+  const float T6 = __fsub_rn(__fmul_rn(c2, T5), T4);
+  const float T7 = __fsub_rn(__fmul_rn(c2, T6), T5);
+  float tail = __fadd_rn(__fmul_rn(T6, 1.0f / 156.0f), __fmul_rn(__fmul_rn(q, T7), 1.0f / 210.0f));
+  tail = __fadd_rn(__fmul_rn(T5, 1.0f / 110.0f), __fmul_rn(q, tail));
+  tail = __fadd_rn(__fmul_rn(T4, 1.0f / 72.0f), __fmul_rn(q, tail));
+  tail = __fadd_rn(__fmul_rn(T3, 1.0f / 42.0f), __fmul_rn(q, tail));
+  tail = __fmul_rn(tail, __fmul_rn(__fmul_rn(q, q), q));
+  df2 S = df_add(t1, t2);
+  S = fast_two_sum(S.hi, __fadd_rn(S.lo, tail));
+  return df_mul(pf(s, ld, kLg, i), df_sub(lgh, S));
+}
+
 // G(p; panel i) in double-float for the control point p.  WHICH = 0: the far or
 // the near form by |P| >= 4 L; 1: the far form; 2: the near form (the caller has
 // made the choice with PairGeom::far).
@@ -154,35 +189,11 @@ __device__ __forceinline__ df2 panel_G_df(const PairGeom& gm, const float* __res
     df2 Y = df_mul(px, py);
     Y.hi *= 2.0f;
     Y.lo *= 2.0f;
-    const df2 Z = df_add(df_mul(pf(s, ld, kC2, i), X), df_mul(pf(s, ld, kS2, i), Y));
     const df2 inv = df_rcp(rho2);
-    const df2 cc = df_mul(Z, inv);  // cos 2phi
-    const df2 t1 = df_mul(df_mul(pf(s, ld, kQ6, i), inv), cc);       // q c / 6
-    df2 T2 = df_sqr(cc);
-    T2.hi *= 2.0f;
-    T2.lo *= 2.0f;
-    T2 = df_add_f(T2, -1.0f);                                        // 2c^2 - 1
-    const df2 t2 = df_mul(df_mul(pf(s, ld, kQ20, i), df_sqr(inv)), T2);  // q^2 T2 / 20
-    // n >= 3 in float32: q^3 (T3/42 + q (T4/72 + q (T5/110 + q (T6/156 + q T7/210))))
-    const float q = __fmul_rn(__fmul_rn(0.25f * Lh, Lh), inv.hi);
-    const float c = cc.hi;
-    const float c2 = 2.0f * c;
-    const float T3 = c * (4.0f * c * c - 3.0f);
-    const float T4 = c2 * T3 - T2.hi;
-    const float T5 = c2 * T4 - T3;
-    const float T6 = c2 * T5 - T4;
-    const float T7 = c2 * T6 - T5;
-    float tail = T6 * (1.0f / 156.0f) + q * T7 * (1.0f / 210.0f);
-    tail = T5 * (1.0f / 110.0f) + q * tail;
-    tail = T4 * (1.0f / 72.0f) + q * tail;
-    tail = T3 * (1.0f / 42.0f) + q * tail;
-    tail *= q * q * q;
-    df2 S = df_add(t1, t2);
-    S = fast_two_sum(S.hi, __fadd_rn(S.lo, tail));
     df2 lg = df_log(rho2, tlog);
     lg.hi *= 0.5f;
     lg.lo *= 0.5f;
-    return df_mul(pf(s, ld, kLg, i), df_sub(lg, S));
+    return panel_G_far(X, Y, inv, df_sqr(inv), lg, s, ld, i, Lh);
   }
   if (WHICH == 1) return mkdf(0.0f);
   // ---- near field: exact closed form in the panel frame ----

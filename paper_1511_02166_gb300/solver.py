@@ -366,7 +366,8 @@ class PanelBatch:
           1. the bucket width, when the population's sizes differ: each width of
              `widths` (None = one bucket) times a whole step (assemble, solve with
              the transposed system, forces, adjoint);
-          2. per bucket, the assembly's near-field rounds (PANEL_TUNE_ROUNDS 0..5);
+          2. per bucket, the assembly (PANEL_TUNE_ROUNDS 0..6: near-field rounds, or
+             both entries of a pair at once);
           3. per bucket, the solve (factor + refinement of both systems): the LU
              (for m <= 224 with the matrix in shared memory or through L2,
              PANEL_TUNE_LU 2 / 1) or the Gauss-Jordan inverse (m <= 288), each
@@ -403,7 +404,7 @@ class PanelBatch:
             key = "%s|asm-rounds|n%d|b%d" % (dev, nmax, bclass(cnt))
             if key not in cache:
                 times = []
-                for r in range(6):
+                for r in range(7):
                     f = bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(r)
 
                     def call(f=f, start=start, cnt=cnt, nmax=nmax):
@@ -414,7 +415,7 @@ class PanelBatch:
                     times.append(self._time(call, reps))
                 # the library's choice (0) unless another is at least 1 % faster
                 best = 0
-                for r in range(1, 6):
+                for r in range(1, 7):
                     if times[r] < 0.99 * times[best]:
                         best = r
                 cache[key] = best
@@ -466,8 +467,8 @@ class PanelBatch:
                              ["lu", "lu (L2)", "lu (shared memory)"][self.lu_kind[k]],
                              "refine_shape": ["by size", "128x8", "256x4", "512x2",
                                               "1024x1", "256x3"][self.ir_shape[k]],
-                             "assembly_rounds": ["by size", "inline", 4, 8, 16,
-                                                 32][self.rounds[k]]}
+                             "assembly_rounds": ["by size", "inline", 4, 8, 16, 32,
+                                                 "pairs"][self.rounds[k]]}
                             for k, (start, cnt, nmax) in enumerate(self.buckets)]}
 
     def capture(self, with_grad: bool = True):

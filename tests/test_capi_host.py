@@ -158,7 +158,8 @@ def test_tuning_fields_of_the_flags_are_validated():
     p = ctypes.c_void_p(1)  # never dereferenced: validation fails or B = 0 returns first
     for f, want in [(bd.PANEL_MIXED | bd.PANEL_TUNE_IR(6), bd.PANEL_EINVAL),
                     (bd.PANEL_MIXED | bd.PANEL_TUNE_IR(5), bd.PANEL_OK),
-                    (bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(6), bd.PANEL_EINVAL),
+                    (bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(7), bd.PANEL_EINVAL),
+                    (bd.PANEL_MIXED | bd.PANEL_TUNE_ROUNDS(6), bd.PANEL_OK),
                     (bd.PANEL_MIXED | bd.PANEL_TUNE_LU(3), bd.PANEL_EINVAL),
                     (bd.PANEL_MIXED | bd.PANEL_TUNE_LU(2) | bd.PANEL_TUNE_IR(1), bd.PANEL_OK),
                     (bd.PANEL_MIXED | bd.PANEL_TUNE_IR(4) | bd.PANEL_TUNE_ROUNDS(5), bd.PANEL_OK)]:

@@ -142,7 +142,7 @@ def test_every_launch_shape_gives_the_oracle_result():
     for width in (None, 128):
         for inverse, lu in ((False, 1), (False, 2), (True, 0)):
             for shape in range(6):
-                for rounds in (0, 1, 2, 5):
+                for rounds in (0, 1, 2, 5, 6):
                     pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed",
                                     bucket_width=width, bucket_min=1)
                     pb.inverse = [inverse] * len(pb.buckets)
@@ -158,6 +158,30 @@ def test_every_launch_shape_gives_the_oracle_result():
                         n = pop.offsets[b + 1] - pop.offsets[b]
                         assert rel_inf(u[o:o + n], ref["u"][o:o + n]) < 1e-10, (b, shape)
                     assert cl_err(pb.cl.cpu().numpy(), ref["cl"]) < 1e-10
+
+
+def test_assembly_kernels_give_the_same_matrix():
+    # the pair-at-once assembly (both entries of a pair of control points from
+    # one evaluation of |P|^2, 1/|P|^2, log|P| and P^2) performs the same
+    # operations for every entry as the row-by-row assembly, inline or with the
+    # near-field queue: the planes agree bit for bit, across 32 x 32 tile edges
+    need_gpu()
+    import torch
+    from paper_1511_02166_gb300.solver import PanelBatch
+    pop = _ragged(33, [1100, 700, 200, 100, 64, 33, 32, 31, 3])
+    planes = []
+    for rounds in (1, 4, 6):
+        pb = PanelBatch(pop.nodes, pop.offsets, pop.alpha, mode="mixed", bucket_width=None)
+        pb.rounds = [rounds] * len(pb.buckets)
+        pb.assemble()
+        torch.cuda.synchronize()
+        assert np.all(pb.info.cpu().numpy() == 0)
+        planes.append((pb.A_hi.cpu().numpy().view(np.uint32).copy(),
+                       pb.A_lo.cpu().numpy().view(np.uint32).copy(), pb.rhs.cpu().numpy().copy()))
+    for k in (1, 2):
+        assert np.array_equal(planes[0][0], planes[k][0]), k
+        assert np.array_equal(planes[0][1], planes[k][1]), k
+        assert np.array_equal(planes[0][2], planes[k][2]), k
 
 
 def test_lu_kernels_give_the_same_factor():
