@@ -86,8 +86,22 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
   constexpr int kU = 8;  // loads in flight per thread
   for (int I = blockIdx.y; I < g.T; I += gridDim.y) {
     const int r0 = g.start(I);
-    if (I == 0) {  // row-major rows 0..e-1
-      for (int p = threadIdx.x; p < g.e * m; p += kInitThreads) F[p] = scaled(p / m, p % m);
+    if (I == 0) {  // row-major rows 0..e-1, kU loads in flight per thread
+      for (int r = 0; r < g.e; ++r) {
+        for (int c0 = threadIdx.x; c0 < m; c0 += kU * kInitThreads) {
+          float v[kU];
+#pragma unroll
+          for (int i = 0; i < kU; ++i) {
+            const int c = c0 + i * kInitThreads;
+            v[i] = (c < m) ? scaled(r, c) : 0.0f;
+          }
+#pragma unroll
+          for (int i = 0; i < kU; ++i) {
+            const int c = c0 + i * kInitThreads;
+            if (c < m) F[(int64_t)r * m + c] = v[i];
+          }
+        }
+      }
       continue;
     }
     for (int J = 1; J < g.T; ++J) {
@@ -105,8 +119,20 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
         for (int i = 0; i < kU; ++i) Tt[p0 + i * kInitThreads + threadIdx.x] = v[i];
       }
     }
-    for (int p = threadIdx.x; p < kTlB * g.e; p += kInitThreads)
-      F[g.rag(I, p / g.e, p % g.e)] = scaled(r0 + p / g.e, p % g.e);
+    // the ragged tile (I, 0), kU loads in flight per thread
+    for (int p0 = 0; p0 < kTlB * g.e; p0 += kU * kInitThreads) {
+      float v[kU];
+#pragma unroll
+      for (int i = 0; i < kU; ++i) {
+        const int p = p0 + i * kInitThreads + threadIdx.x;
+        v[i] = (p < kTlB * g.e) ? scaled(r0 + p / g.e, p % g.e) : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < kU; ++i) {
+        const int p = p0 + i * kInitThreads + threadIdx.x;
+        if (p < kTlB * g.e) F[g.rag(I, p / g.e, p % g.e)] = v[i];
+      }
+    }
   }
 }
 
@@ -761,12 +787,28 @@ static size_t tl_conv_smem(int part) {
   return (size_t)(part + 4) * 4 + (size_t)kConvWarps * 32 * kTbufLd * 4;
 }
 
+// Each warp stages a diagonal block in shared memory (32 coalesced row loads),
+// inverts both triangles there and writes the block back.
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
+  __shared__ float S[8][32 * 33];
   const Batch& bt = a.bt;
   const int b = bt.order[blockIdx.x];
   int n, m;
   if (!large_live(a, b, n, m)) return;
-  invert_diagonal_blocks(a.LU + bt.mat_off[b], m, m);
+  float* F = a.LU + bt.mat_off[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb = (m + 31) >> 5;
+  float* W = S[warp];
+  for (int d = blockIdx.y * 8 + warp; d < nb; d += 8 * (int)gridDim.y) {
+    const int k0 = 32 * d, kb = min(32, m - k0);
+    for (int r = 0; r < kb; ++r)
+      if (lane < kb) W[r * 33 + lane] = F[(int64_t)(k0 + r) * m + k0 + lane];
+    __syncwarp();
+    invert_block(W, 33, kb);
+    for (int r = 0; r < kb; ++r)
+      if (lane < kb) F[(int64_t)(k0 + r) * m + k0 + lane] = W[r * 33 + lane];
+    __syncwarp();
+  }
 }
 
 // Polls of each pipeline wait in k_update_tc before it gives up (a wait that
@@ -835,7 +877,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, k_tl_to_rowmajor, a, part);
   if (e != cudaSuccess) return e;
-  k_large_finish<<<B, 256, 0, s>>>(a);
+  k_large_finish<<<dim3(B, split_for(B, 8, 8)), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

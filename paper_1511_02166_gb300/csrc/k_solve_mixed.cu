@@ -600,6 +600,24 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// sum_{k in [k0, k1)} row[k] y[k] over the lanes (k = lane + 32 t), with eight
+// independent partial sums so that eight loads of the row are in flight per
+// lane (a long row is otherwise a chain of dependent round trips to L2).
+__device__ __forceinline__ float row_dot(const float* __restrict__ row, const float* y, int k0,
+                                         int k1, int lane) {
+  float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  int k = k0 + lane;
+  for (; k + 7 * 32 < k1; k += 8 * 32) {
+    float r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = __ldg(row + k + 32 * u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fmaf(r[u], y[k + 32 * u], a[u]);
+  }
+  for (; k < k1; k += 32) a[0] = fmaf(__ldg(row + k), y[k], a[0]);
+  return warp_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+}
+
 // y <- L^{-1} y then U^{-1} y, left-looking: the rows of block d read their
 // own contiguous segments L[i][0..k0) (coalesced across the lanes).
 __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, float* t32) {
@@ -608,10 +626,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
     const int kb = min(32, m - k0);
     for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
-      const float* row = F + i * m;
-      float acc = 0.0f;
-      for (int k = lane; k < k0; k += 32) acc = fmaf(__ldg(row + k), y[k], acc);
-      acc = warp_sum_f(acc);
+      const float acc = row_dot(F + i * m, y, 0, k0, lane);
       if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
@@ -628,10 +643,7 @@ __device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, f
     const int kb = min(32, m - k0);
     for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
       const int i = k0 + q;
-      const float* row = F + i * m;
-      float acc = 0.0f;
-      for (int k = k0 + kb + lane; k < m; k += 32) acc = fmaf(__ldg(row + k), y[k], acc);
-      acc = warp_sum_f(acc);
+      const float acc = row_dot(F + i * m, y, k0 + kb, m, lane);
       if (lane == 0) t32[q] = y[i] - acc;
     }
     __syncthreads();
