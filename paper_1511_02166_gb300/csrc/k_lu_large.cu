@@ -849,7 +849,9 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   e = ensure_smem(k_tl_to_rowmajor, tl_conv_smem(part));
   if (e != cudaSuccess) return e;
   const long long spin = g_wait_limit.load();
-  k_large_init<<<dim3(B, split_for(B, 64, 8)), kInitThreads, 0, s>>>(a);
+  // a block per block row: the work of one block is at most 128 rows of the
+  // largest airfoil, so the batch's last wave stays short
+  k_large_init<<<dim3(B, T_max), kInitThreads, 0, s>>>(a);
   for (int K = 0; K < T_max; ++K) {
     k_large_diag<<<B, 256, large_diag_smem(), s>>>(a, K);
     const int ns = T_max - 1 - K;  // blocks after K in the largest airfoil
