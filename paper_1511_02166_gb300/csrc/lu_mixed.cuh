@@ -6,7 +6,7 @@
 
 namespace panel {
 
-constexpr int kSmemM = 230;  // largest m = n + 1 factored in shared memory
+constexpr int kSmemM = 230;  // largest m = n + 1 of a Gauss-Jordan inverse in shared memory
 constexpr int kGjM = 288;    // m up to this: Gauss-Jordan inverse (k_gj_mixed.cu)
 constexpr int kLargeM = 640; // m above this takes the step-synchronous blocked factor
 constexpr int kSmemLuM = 224; // m up to this: LU with the whole matrix in shared memory
@@ -122,15 +122,6 @@ __device__ inline void invert_upper(float* B, int ld, int kb) {
 __device__ inline void invert_block(float* B, int ld, int kb) {
   invert_lower_unit(B, ld, kb);
   invert_upper(B, ld, kb);
-}
-
-__device__ inline void invert_diagonal_blocks(float* F, int ld, int m) {
-  const int warp = threadIdx.x >> 5;
-  const int nb = (m + 31) >> 5;
-  for (int d = warp; d < nb; d += kWarps) {
-    const int k0 = 32 * d;
-    invert_block(F + k0 * ld + k0, ld, min(32, m - k0));
-  }
 }
 
 cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s);
