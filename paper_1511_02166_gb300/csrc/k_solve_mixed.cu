@@ -11,23 +11,26 @@
 //   corrections predicts the next one below that.  The transposed system
 //   M^T lambda = g (g = dCl/du) is refined in the same kernel.
 //
-// The FP32 factor depends on the size m = n + 1:
-//   m <= kGjM (288)        explicit inverse by blocked Gauss-Jordan
-//                          (k_gj_mixed.cu); a correction is one GEMV;
-//                          without the inverse, for m <= kSmemLuM (224):
-//                          k_lu_smem below, the same LU with the whole
-//                          matrix in shared memory;
-//   kGjM < m <= kLargeM    k_lu_global below: one block per airfoil, blocked
-//                          right-looking LU with partial pivoting, the factor
-//                          in the caller's LU buffer through L2;
-//   m > kLargeM (640)      the step-synchronous blocked LU (k_lu_large.cu).
-// The LU variants replace the 32 x 32 diagonal blocks of L and U by their
-// inverses, so that the triangular solves below are sequences of
-// matrix-vector products.  The LU buffer therefore holds a library-internal
-// layout (an inverse, or an LU with inverted diagonal blocks, chosen by m).
+// The FP32 factor depends on the size m = n + 1 and the launch's choices:
+//   PANEL_INVERSE, m <= kGjM (288)   explicit inverse by blocked Gauss-Jordan
+//                                    (k_gj_mixed.cu); a correction is one GEMV;
+//   m <= kSmemLuM (224)              k_lu_smem below: LU with the whole matrix in
+//                                    shared memory (by size, PANEL_TUNE_LU(2)),
+//                                    or k_lu_global (PANEL_TUNE_LU(1));
+//   m <= kLargeM (640)               k_lu_global below: one block per airfoil,
+//                                    blocked right-looking LU, the trailing
+//                                    matrix in the caller's LU buffer through L2;
+//   m > kLargeM                      the step-synchronous blocked LU
+//                                    (k_lu_large.cu, k_update_tc.cu).
+// All LU variants pivot inside the current diagonal block and replace the
+// 32 x 32 diagonal blocks of L and U by their inverses, so that the triangular
+// solves below are sequences of matrix-vector products.  The LU buffer
+// therefore holds a library-internal layout (an inverse, or an LU with
+// inverted diagonal blocks).
 //  k_ir_mixed  one block per airfoil: the corrections with the stored factor
-//    (read through L1/L2) and the refinement residuals (one pass over the rows
-//    for M u, one over the columns for M^T lambda).
+//    (read through L1/L2) and the refinement residuals (for m <= kFuseM one
+//    pass over the matrix for both systems, else one over the rows for M u and
+//    one over the columns for M^T lambda).
 #include <type_traits>
 
 #include "df.cuh"
@@ -93,7 +96,8 @@ __device__ __forceinline__ void warp_block_lu(float (&x)[NB], int& pos, bool& do
 }
 
 // ---------------------------------------------------------------------------
-// The LU kernel, factor in global memory (kGjM < m <= kLargeM): blocked right-looking
+// The LU kernel, factor in global memory (kSmemLuM < m <= kLargeM, or every
+// m <= kLargeM with PANEL_TUNE_LU(1)): blocked right-looking
 // with the current panel of NB columns staged in shared memory (rows spread
 // over the threads), the row exchanges, U12 and the rank-NB update applied to
 // the factor in the caller's LU buffer through L2.  Shared memory stays small
