@@ -391,10 +391,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
   float4* tlog = reinterpret_cast<float4*>(smraw);        // 257
   float2* tatan = reinterpret_cast<float2*>(tlog + 257);  // 34
   float4* win = reinterpret_cast<float4*>(tatan + 34);    // 8 warps x 32 rows
-  float* lamh = reinterpret_cast<float*>(win + 8 * 32);   // n_max
-  float* laml = lamh + ld;                                // n_max
-  float* rp = laml + ld;                                  // 6 * n_max control points
-  float* cpc = rp + 6 * ld;                               // kPanelFields * kSplitChunk
+  // the current window's 32 rows, two buffers: control points (6 split
+  // coordinates, stride 32) and lambda as a float pair
+  float* wrow = reinterpret_cast<float*>(win + 8 * 32);   // 2 x 8 x 32
+  float* cpc = wrow + 2 * 8 * 32;                         // kPanelFields * kSplitChunk
 
   const int b = bt.order[blockIdx.x];
   const int n = airfoil_n(bt, b);
@@ -406,20 +406,25 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
   double* gout = grad + 2 * bt.node_off[b];
   const int nc = min(kSplitChunk, n - i0);
   df_stage_tables(tlog, tatan);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const int k1 = (k + 1 == n) ? 0 : k + 1;
-    const point3 c = make_point(0.5 * (nodes[2 * k] + nodes[2 * k1]),
-                                0.5 * (nodes[2 * k + 1] + nodes[2 * k1 + 1]));
-    rp[kCx * ld + k] = c.xh;
-    rp[(kCx + 1) * ld + k] = c.xm;
-    rp[(kCx + 2) * ld + k] = c.xl;
-    rp[kCy * ld + k] = c.yh;
-    rp[(kCy + 1) * ld + k] = c.ym;
-    rp[(kCy + 2) * ld + k] = c.yl;
-    const df2 l = df_from_double(lb[k]);
-    lamh[k] = l.hi;
-    laml[k] = l.lo;
-  }
+  // the rows of window j0 into buffer (j0 / 32) & 1, a thread per row
+  auto stage_rows = [&](int j0) {
+    const int t = threadIdx.x, k = j0 + t;
+    if (t < 32 && k < n) {
+      float* w = wrow + ((j0 >> 5) & 1) * 256;
+      const int k1 = (k + 1 == n) ? 0 : k + 1;
+      const point3 c = make_point(0.5 * (nodes[2 * k] + nodes[2 * k1]),
+                                  0.5 * (nodes[2 * k + 1] + nodes[2 * k1 + 1]));
+      w[kCx * 32 + t] = c.xh;
+      w[(kCx + 1) * 32 + t] = c.xm;
+      w[(kCx + 2) * 32 + t] = c.xl;
+      w[kCy * 32 + t] = c.yh;
+      w[(kCy + 1) * 32 + t] = c.ym;
+      w[(kCy + 2) * 32 + t] = c.yl;
+      const df2 l = df_from_double(lb[k]);
+      w[6 * 32 + t] = l.hi;
+      w[7 * 32 + t] = l.lo;
+    }
+  };
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const int i = i0 + k, i1 = (i + 1 == n) ? 0 : i + 1;
     panel_constants(cpc, kSplitChunk, k, nodes[2 * i], nodes[2 * i + 1], nodes[2 * i1],
@@ -442,6 +447,9 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
   df2 sSx = mkdf(0.0f), sSy = mkdf(0.0f), sKr = mkdf(0.0f), sKi = mkdf(0.0f);
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int jn = min(32, n - j0);
+    stage_rows(j0);
+    __syncthreads();
+    const float* wr = wrow + ((j0 >> 5) & 1) * 256;
     if (warp_on) {
       df2 rx[4], ry[4];
       for (int t0 = 0; t0 < jn; t0 += 4) {
@@ -450,10 +458,10 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
           const int j = j0 + t;
           df2 vx = mkdf(0.0f), vy = mkdf(0.0f);
           if (t < jn) {
-            const point3 pj = load_point(rp, ld, j);
+            const point3 pj = load_point(wr, 32, t);
             df2 gpx, gpy, kr, ki;
             panel_dG_df(pj, cpc, kSplitChunk, ic, ok && i == j, tlog, tatan, gpx, gpy, kr, ki);
-            const df2 lj = mkdf(lamh[j], laml[j]);
+            const df2 lj = mkdf(wr[6 * 32 + t], wr[7 * 32 + t]);
             acc_add_prod(sSx, lj, gpx);
             acc_add_prod(sSy, lj, gpy);
             acc_add_prod(sKr, lj, kr);
@@ -533,7 +541,7 @@ __global__ void __launch_bounds__(256) k_adjoint_df_split(
 
 size_t adjoint_df_smem(int n_max) {
   if (n_max > kPartialsN)
-    return 257 * 16 + 34 * 8 + 8 * 32 * 16 + (size_t)n_max * 8 * 4 +
+    return 257 * 16 + 34 * 8 + 8 * 32 * 16 + 2 * 8 * 32 * 4 +
            (size_t)kPanelFields * kSplitChunk * 4;
   return 257 * 16 + 34 * 8 + (size_t)n_max * 8 * 8 + (size_t)n_max * 4 * 2 +
          (size_t)kPanelFields * n_max * 4 + (size_t)8 * n_max * 16;
