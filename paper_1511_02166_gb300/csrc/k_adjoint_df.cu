@@ -212,7 +212,7 @@ __device__ __forceinline__ df2 warp_sum_df2(df2 a) {
   return a;
 }
 
-constexpr int kPartialsN = 512;
+constexpr int kPartialsN = 256;
 
 __global__ void __launch_bounds__(256) k_adjoint_df(
     Batch bt, const double* __restrict__ u, const double* __restrict__ lambda,

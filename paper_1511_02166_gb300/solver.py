@@ -327,7 +327,7 @@ class PanelBatch:
         for m > 640 with T 128-column blocks, the step-synchronous LU: the tiled
         copy, T diagonal LUs, one CUDA-core and T - 1 tensor-core triangular
         solves, T - 1 updates, the conversion back and the inversion of the
-        diagonal blocks; the adjoint of n > 512 adds a zeroing launch."""
+        diagonal blocks; the adjoint of n > 256 adds a zeroing launch."""
         n = 1  # forces
         for k, (start, cnt, nmax) in enumerate(self.buckets):
             m = nmax + 1
@@ -344,7 +344,7 @@ class PanelBatch:
             else:
                 n += 1
             if with_grad:
-                n += 1 + (nmax > 512 and self.flags == bd.PANEL_MIXED)
+                n += 1 + (nmax > 256 and self.flags == bd.PANEL_MIXED)
         return n
 
     # -- autotuning and graph capture -------------------------------------------
