@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) k_assemble_df(Batch bt, const double* __r
 // panel_G_df.  Every entry is computed by the same operations as in
 // k_assemble_df, so the two kernels give the same matrix bit for bit.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_assemble_df_sym(Batch bt, const double* __restrict__ alpha,
+__global__ void __launch_bounds__(512) k_assemble_df_sym(Batch bt, const double* __restrict__ alpha,
                                                          const double* __restrict__ vinf,
                                                          float* __restrict__ A_hi,
                                                          float* __restrict__ A_lo,
@@ -284,7 +284,8 @@ cudaError_t launch_assemble_df(const Batch& bt, const double* alpha, const doubl
     const size_t smem = assemble_df_smem(bt.n_max, 0);
     cudaError_t e = ensure_smem(k_assemble_df_sym, smem);
     if (e != cudaSuccess) return e;
-    k_assemble_df_sym<<<bt.B, 256, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info);
+    // 16 warps: one block fills an SM's shared memory above 1024 panels
+    k_assemble_df_sym<<<bt.B, 512, smem, s>>>(bt, alpha, vinf, A_hi, A_lo, rhs, info);
     return cudaGetLastError();
   }
   int rounds = assemble_rounds(bt.n_max, rounds_sel);
