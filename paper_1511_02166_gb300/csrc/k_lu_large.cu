@@ -19,9 +19,8 @@
 //     k_update_tc     A22 -= L21 U12 on the tcgen05 tensor cores, operands
 //                     loaded by TMA, A22 updated by TMA reduce-add
 //                     (k_update_tc.cu);
-//   k_tl_to_rowmajor  the tiled layout back to row-major, one 8-block cluster
-//                     per 128-row block row (the block row's floats are staged
-//                     across the cluster's shared memory);
+//   k_tl_untranspose  the U tiles back from their transposed order to row
+//                     chunks, one block per tile, in place;
 //   k_large_finish    the 32 x 32 diagonal blocks of L and U inverted in place.
 // The per-airfoil kernels take gridDim.y blocks per airfoil striding over
 // slabs / tiles / rows, so a batch of few airfoils still fills the GPU.
@@ -38,9 +37,11 @@
 // in as few steps as with full partial pivoting).  An exactly zero pivot still
 // sets info[b] = its index + 1.
 //
-// The finished factor has the layout of the one-block kernels: P A = L U in
-// the caller's LU buffer (ld = m), pivots as sequential exchanges, and the
-// 32 x 32 diagonal blocks of L and U replaced by their inverses.
+// The finished factor: P A = L U in the caller's LU buffer in the tiled layout
+// with every full tile in row chunks (tl_layout.cuh), pivots as sequential
+// exchanges, and the 32 x 32 diagonal blocks of L and U that follow the tiles
+// replaced by their inverses; the refinement (k_solve_mixed.cu) reads it in
+// that layout.
 #include <atomic>
 
 #include "tl_layout.cuh"
@@ -613,182 +614,59 @@ size_t large_trsm_smem() {
   return ((size_t)kBW * kLdX + 2 * (size_t)kBW * kLdI + kBW) * 4;
 }
 
-// The tiled layout of block row I >= 1 back to row-major.  Both orders fill
-// the same 128 m floats (the block row's span), so the span is first staged
-// across the shared memory of an 8-block cluster (block c holds floats
-// [c part, (c + 1) part) of the tiled order, brought in by one bulk
-// asynchronous copy and the ragged ends), and after a cluster barrier the
-// blocks' warps write the row-major order in 32 x 32 pieces, reading every
-// value from whichever block holds it (distributed shared memory): lane l
-// takes column l of a piece, so each read and each write of a warp is 128
-// contiguous bytes; a piece of a transposed U tile is read column by column
-// into a per-warp buffer and written row by row.  Loads are issued eight at a
-// time.  A second barrier keeps every block's shared memory alive until all
-// reads are done.  Grid: x = the cluster's 8 blocks, y = I - 1, z = the launch
-// position of the airfoil.
-constexpr int kClusterTl = 8;
-constexpr int kConvThreads = 512;
-constexpr int kConvWarps = kConvThreads / 32;
-constexpr int kTbufLd = 33;
+// The U tiles (I, J > I) back from their transposed order to row chunks, in
+// place, so that every full tile of the finished factor has the same order.
+// The 32 x 32 block (R, C) of a transposed tile (U rows 32 R .., columns
+// 32 C ..) is stored column by column at R 4096 + C 1024; in row chunks it is
+// stored row by row at C 4096 + R 1024.  A block takes one tile: it stages the
+// 64 KB in shared memory (the 32-float columns padded to 33 floats against bank
+// conflicts) and writes them back in the new order.  Grid: x = the launch
+// position of the airfoil, y = the tile, counted by J then I (tile (I, J) is
+// number (J - 1)(J - 2) / 2 + I - 1).
+constexpr int kUtThreads = 256;
+constexpr size_t kUtSmem = (size_t)16 * 32 * 33 * sizeof(float);
 
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
-// float q of the staged span (block q / part of the cluster holds it)
-// The staged span: block c holds the floats i in [c part, (c + 1) part) at
-// stage[i - c part + pad(c)], pad(c) = (address of float c part) / 4 mod 4, so
-// that the shared image of a 16-byte aligned global segment is 16-byte aligned
-// too (one bulk copy moves the aligned middle of a block's range).
-__device__ __forceinline__ float dsmem_ld(uint32_t local, int part, int q, uint32_t sa4) {
-  const unsigned owner = (unsigned)(q / part);
-  const int lo = (int)owner * part;
-  const int pad = (int)((sa4 + (uint32_t)lo) & 3u);
-  const uint32_t addr = local + 4u * (uint32_t)(q - lo + pad);
-  uint32_t remote;
-  float v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(addr), "r"(owner));
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote));
-  return v;
-}
-
-__global__ void __launch_bounds__(kConvThreads) k_tl_to_rowmajor(SolveArgs a, int part) {
-  extern __shared__ __align__(16) float stage[];
+__global__ void __launch_bounds__(kUtThreads, 3) k_tl_untranspose(SolveArgs a) {
+  extern __shared__ __align__(16) float S[];
   const Batch& bt = a.bt;
-  const int b = bt.order[blockIdx.z];
-  const int I = 1 + blockIdx.y;
+  const int b = bt.order[blockIdx.x];
   int n, m;
-  // uniform across the cluster: every block of it has the same (b, I)
   if (!large_live(a, b, n, m)) return;
   TlGeom g;
   g.init(m, bt.mat_off[b]);
-  if (I >= g.T) return;
-  const int L = kTlB * m;
-  unsigned rank;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* S = a.LU + bt.mat_off[b] + g.span(I);
-  const uint32_t sa4 = (uint32_t)((reinterpret_cast<uintptr_t>(S) >> 2) & 3u);
-  const int lo = (int)rank * part, hi = min(L, lo + part);
-  const int pad = (int)((sa4 + (uint32_t)lo) & 3u);
-  __shared__ __align__(8) uint64_t stage_bar;
-  if (lo < hi) {
-    // the aligned middle [a0, a1) by one bulk copy, the ragged ends by threads
-    const int a0 = min(hi, lo + ((4 - pad) & 3));
-    const int a1 = max(a0, hi - (int)((sa4 + (uint32_t)hi) & 3u));
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&stage_bar);
-    const uint32_t bytes = 4u * (uint32_t)(a1 - a0);
-    if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // (the shared image is 16-byte aligned where the global segment is only if the
-    // dynamic shared memory itself starts on a 16-byte boundary; else threads copy)
-    const bool bulk = ((uint32_t)__cvta_generic_to_shared(stage) & 15u) == 0;
-    if (!bulk)
-      for (int i = a0 + tid; i < a1; i += kConvThreads) stage[i - lo + pad] = S[i];
-    if (tid == 0) {
-      asm volatile(
-          "{\n\t.reg .b64 st;\n\t"
-          "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-          "r"(bulk ? bytes : 0u)
-          : "memory");
-      if (bulk && bytes > 0)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-            "[%3];" ::"r"((uint32_t)__cvta_generic_to_shared(stage + (a0 - lo + pad))),
-            "l"(S + a0), "r"(bytes), "r"(bar)
-            : "memory");
-    }
-    if (tid < a0 - lo) stage[tid + pad] = S[lo + tid];
-    if (tid < hi - a1) stage[a1 - lo + pad + tid] = S[a1 + tid];
-    // bounded wait for the copy (it completes on its own; the bound only keeps
-    // the wait finite -- a copy that did not land marks the airfoil)
-    bool landed = false;
-    for (long long it = 0; it < (1ll << 24) && !landed; ++it) {
-      uint32_t done;
-      asm volatile(
-          "{\n\t.reg .pred p;\n\t"
-          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(bar)
-          : "memory");
-      landed = done != 0;
-    }
-    if (!landed && tid == 0) a.info[b] = PANEL_INFO_DEVICE_TIMEOUT;
+  int k = blockIdx.y, J = 2;
+  while (J < g.T && k >= J - 1) {
+    k -= J - 1;
+    ++J;
   }
-  cluster_sync_all();
-
-  const uint32_t local = (uint32_t)__cvta_generic_to_shared(stage);
-  float* tb = stage + part + 4 + warp * (32 * kTbufLd);
-  const int sp = (int)(g.tile(I, 1) - g.span(I));  // the full tiles start here (the head)
-  const int nbr = (g.e + 31) >> 5;                 // 32-column pieces of the ragged columns
-  const int ncb = nbr + 4 * (g.T - 1);
-  const int items = 4 * ncb;
-  for (int it = (int)rank * kConvWarps + warp; it < items; it += kClusterTl * kConvWarps) {
-    const int rg = it / ncb, cb = it - rg * ncb;
-    const int rr0 = 32 * rg;
-    if (cb < nbr) {
-      // ragged tile (I, 0): row-major 128 x e around the full tiles
-      const int c = 32 * cb + lane;
-      const bool ok = c < g.e;
-      for (int r8 = 0; r8 < 32; r8 += 8) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int idx = (rr0 + r8 + j) * g.e + c;
-          const int q = idx < sp ? idx : sp + (g.T - 1) * kTlTile + (idx - sp);
-          v[j] = ok ? dsmem_ld(local, part, q, sa4) : 0.0f;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (ok) S[(int64_t)(rr0 + r8 + j) * m + c] = v[j];
-      }
-    } else {
-      const int J = 1 + (cb - nbr) / 4, kc = (cb - nbr) & 3;
-      const int t0 = sp + (J - 1) * kTlTile;
-      const int col = g.start(J) + 32 * kc + lane;
-      if (J > I) {
-        // transposed U tile: rows rr0.. of this piece are chunk rg, column cc
-        // at t0 + rg 4096 + 32 cc + (rr % 32)
-        for (int j8 = 0; j8 < 32; j8 += 8) {
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            v[j] = dsmem_ld(local, part, t0 + rg * kTlChunk + (32 * kc + j8 + j) * 32 + lane, sa4);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) tb[lane * kTbufLd + j8 + j] = v[j];
-        }
-        __syncwarp();
-        for (int r = 0; r < 32; ++r) S[(int64_t)(rr0 + r) * m + col] = tb[r * kTbufLd + lane];
-        __syncwarp();
-      } else {
-        // row rr of chunk kc at t0 + kc 4096 + 32 rr + (column % 32)
-        for (int r8 = 0; r8 < 32; r8 += 8) {
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            v[j] = dsmem_ld(local, part, t0 + kc * kTlChunk + (rr0 + r8 + j) * 32 + lane, sa4);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) S[(int64_t)(rr0 + r8 + j) * m + col] = v[j];
-        }
-      }
-    }
+  if (J >= g.T) return;
+  float* t = a.LU + bt.mat_off[b] + g.tile(1 + k, J);
+  const float4* t4 = reinterpret_cast<const float4*>(t);
+#pragma unroll 8
+  for (int p4 = threadIdx.x; p4 < kTlTile / 4; p4 += kUtThreads) {
+    const float4 v = t4[p4];
+    // floats 4 p4 .. 4 p4 + 3: rows (4 p4) % 32 .. of column (4 p4) / 32
+    float* d = S + ((4 * p4) >> 5) * 33 + ((4 * p4) & 31);
+    d[0] = v.x;
+    d[1] = v.y;
+    d[2] = v.z;
+    d[3] = v.w;
   }
-  cluster_sync_all();
+  __syncthreads();
+#pragma unroll 8
+  for (int p = threadIdx.x; p < kTlTile; p += kUtThreads) {
+    const int C = p >> 12, r = (p >> 5) & 127, c = p & 31;
+    t[p] = S[(((r >> 5) * 4 + C) * 32 + c) * 33 + (r & 31)];
+  }
 }
 
-// floats of a block row per cluster block (a multiple of 4), for size m
-static int tl_part(int m) { return ((kTlB * m + kClusterTl - 1) / kClusterTl + 3) & ~3; }
-static size_t tl_conv_smem(int part) {
-  return (size_t)(part + 4) * 4 + (size_t)kConvWarps * 32 * kTbufLd * 4;
-}
-
-// Each warp stages a diagonal block in shared memory (32 coalesced row loads),
-// inverts both triangles there and writes the block back.
+// The 32 x 32 diagonal blocks of L and U inverted in place, the form the
+// refinement's triangular sweeps take.  The blocks follow the tiles:
+// ceil(e / 32) blocks in the first block row (row-major, row stride m; the
+// last one e - 32 floor((e - 1) / 32) wide), then four per full diagonal tile,
+// each the diagonal 32 x 32 block of one of its row chunks (contiguous, row
+// stride 32).  Each warp stages a block in shared memory, inverts both
+// triangles there and writes the block back.
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   __shared__ float S[8][32 * 33];
   const Batch& bt = a.bt;
@@ -796,17 +674,33 @@ __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   int n, m;
   if (!large_live(a, b, n, m)) return;
   float* F = a.LU + bt.mat_off[b];
+  TlGeom g;
+  g.init(m, bt.mat_off[b]);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb = (m + 31) >> 5;
+  const int G0 = (g.e + 31) >> 5, G = G0 + 4 * (g.T - 1);
   float* W = S[warp];
-  for (int d = blockIdx.y * 8 + warp; d < nb; d += 8 * (int)gridDim.y) {
-    const int k0 = 32 * d, kb = min(32, m - k0);
-    for (int r = 0; r < kb; ++r)
-      if (lane < kb) W[r * 33 + lane] = F[(int64_t)(k0 + r) * m + k0 + lane];
+  for (int d = blockIdx.y * 8 + warp; d < G; d += 8 * (int)gridDim.y) {
+    float* B;
+    int ld, kb;
+    if (d < G0) {
+      B = F + (int64_t)(32 * d) * m + 32 * d;
+      ld = m;
+      kb = min(32, g.e - 32 * d);
+    } else {
+      const int h = d - G0;  // chunk 4 (I - 1) + q of block row I = 1 + h / 4
+      B = F + g.tile(1 + (h >> 2), 1) + (int64_t)h * kTlChunk + (h & 3) * 32 * kTlC;
+      ld = kTlC;
+      kb = 32;
+    }
+    float v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = (r < kb && lane < kb) ? B[(int64_t)r * ld + lane] : 0.0f;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) W[r * 33 + lane] = v[r];
     __syncwarp();
     invert_block(W, 33, kb);
     for (int r = 0; r < kb; ++r)
-      if (lane < kb) F[(int64_t)(k0 + r) * m + k0 + lane] = W[r * 33 + lane];
+      if (lane < kb) B[(int64_t)r * ld + lane] = W[r * 33 + lane];
     __syncwarp();
   }
 }
@@ -845,8 +739,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = ensure_update_smem();
   if (e != cudaSuccess) return e;
-  const int part = tl_part(m_max);
-  e = ensure_smem(k_tl_to_rowmajor, tl_conv_smem(part));
+  e = ensure_smem(k_tl_untranspose, kUtSmem);
   if (e != cudaSuccess) return e;
   const long long spin = g_wait_limit.load();
   // a block per block row: the work of one block is at most 128 rows of the
@@ -865,20 +758,8 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
     e = launch_update_tc(a, tmap, K, split_for(B, ns * ns, 1), spin, s);
     if (e != cudaSuccess) return e;
   }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kClusterTl, T_max - 1, B);
-  cfg.blockDim = dim3(kConvThreads);
-  cfg.dynamicSmemBytes = tl_conv_smem(part);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kClusterTl;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_tl_to_rowmajor, a, part);
-  if (e != cudaSuccess) return e;
+  const int tiles = (T_max - 1) * (T_max - 2) / 2;  // U tiles of the largest airfoil
+  if (tiles > 0) k_tl_untranspose<<<dim3(B, tiles), kUtThreads, kUtSmem, s>>>(a);
   k_large_finish<<<dim3(B, split_for(B, 8, 8)), 256, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -26,7 +26,8 @@
 // 32 x 32 diagonal blocks of L and U by their inverses, so that the triangular
 // solves below are sequences of matrix-vector products.  The LU buffer
 // therefore holds a library-internal layout (an inverse, or an LU with
-// inverted diagonal blocks).
+// inverted diagonal blocks: row-major up to kLargeM, above it the tiled layout
+// of the blocked factor, tl_layout.cuh).
 //  k_ir_mixed  one block per airfoil: the corrections with the stored factor
 //    (read through L1/L2) and the refinement residuals (for m <= kFuseM one
 //    pass over the matrix for both systems, else one over the rows for M u and
@@ -34,7 +35,7 @@
 #include <type_traits>
 
 #include "df.cuh"
-#include "lu_mixed.cuh"
+#include "tl_layout.cuh"
 
 namespace panel {
 
@@ -710,6 +711,228 @@ __device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, 
 }
 
 // ---------------------------------------------------------------------------
+// The same solves with the factor of an airfoil above kLargeM - 1 panels in
+// the layout the blocked LU (k_lu_large.cu) leaves: the tiled layout of
+// tl_layout.cuh with every full tile in row chunks.  Block row 0 (the first e
+// rows) is row-major (ld m); in block row I >= 1 the columns below e sit in the
+// ragged tile (I, 0) (row-major, ld e, split at the head) and column e + 32 ch
+// + c of row rr at tile(I, 1) + 4096 ch + 32 rr + c: a row is a run of 32-float
+// chunks 4096 floats apart.  The 32-row groups of the sweeps follow the tiles:
+// ceil(e / 32) groups in block row 0, then four per full block row, and the
+// diagonal blocks inverted are those of these groups.
+// ---------------------------------------------------------------------------
+struct CrFactor {
+  const float* F;  // the airfoil's matrix
+  TlGeom g;
+  int G0;          // groups of block row 0
+  int nch;         // chunks of a full block row: 4 (T - 1)
+  __device__ void init(const float* F_, int m, int64_t moff) {
+    F = F_;
+    g.init(m, moff);
+    G0 = (g.e + 31) >> 5;
+    nch = 4 * (g.T - 1);
+  }
+  __device__ int groups() const { return G0 + nch; }
+  __device__ int k0(int d) const { return d < G0 ? 32 * d : g.e + 32 * (d - G0); }
+  __device__ int kb(int d) const { return d < G0 ? min(32, g.e - 32 * d) : 32; }
+  // row rr of block row I (I >= 1): its chunk 0 (add 4096 ch + the column in the chunk)
+  __device__ const float* chunk_row(int I, int rr) const {
+    return F + g.tile(I, 1) + (int64_t)rr * kTlC;
+  }
+};
+
+// The ragged tile (I, 0) of block row I >= 1: element (rr, c), c < e, is float
+// rr e + c of the tile, which sits at span(I) up to the head and after the full
+// tiles beyond it.
+struct CrRag {
+  const float* p;  // the block row's span
+  int hh, e;
+  int64_t jump;    // the full tiles' floats
+  __device__ CrRag(const CrFactor& f, int I)
+      : p(f.F + f.g.span(I)), hh(f.g.head(I)), e(f.g.e),
+        jump((int64_t)(f.g.T - 1) * kTlTile) {}
+  __device__ float operator()(int rr, int c) const {
+    const int idx = rr * e + c;
+    return __ldg(p + (idx < hh ? (int64_t)idx : idx + jump));
+  }
+};
+
+// sum_{ch in [c0, c1)} p[4096 ch] yy[32 ch] (one lane's share of a chunked row:
+// p and yy already offset by the lane), eight loads in flight.
+__device__ __forceinline__ float chunk_dot(const float* __restrict__ p, const float* yy, int c0,
+                                           int c1) {
+  float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  int ch = c0;
+  for (; ch + 7 < c1; ch += 8) {
+    float r[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) r[u] = __ldg(p + (int64_t)(ch + u) * kTlChunk);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fmaf(r[u], yy[32 * (ch + u)], a[u]);
+  }
+  for (; ch < c1; ++ch) a[0] = fmaf(__ldg(p + (int64_t)ch * kTlChunk), yy[32 * ch], a[0]);
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+// One lane's share of sum_{c < e} L[row][c] y[c] for row rr of block row I.
+__device__ __forceinline__ float rag_dot(const CrFactor& f, int I, int rr, const float* y,
+                                         int lane) {
+  const CrRag rag(f, I);
+  float v = 0.0f;
+#pragma unroll
+  for (int t = 0; t < kTlB / 32; ++t) {
+    const int c = lane + 32 * t;
+    if (c < f.g.e) v = fmaf(rag(rr, c), y[c], v);
+  }
+  return v;
+}
+
+// Row i's 32 entries in the columns of group d (i in the group, or i < e).
+__device__ __forceinline__ const float* cr_diag_row(const CrFactor& f, int m, int d, int i) {
+  if (d < f.G0) return f.F + (int64_t)i * m + 32 * d;
+  const int h = d - f.G0, rr = (i - f.g.e) & (kTlB - 1);
+  return f.chunk_row(1 + (h >> 2), rr) + (int64_t)h * kTlChunk;
+}
+
+// y <- L^{-1} y then U^{-1} y (left-looking, a warp per row, as lu_apply_inverse).
+__device__ void lu_apply_inverse_cr(const CrFactor& f, int m, float* y, float* t32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int e = f.g.e, G = f.groups();
+  for (int d = 0; d < G; ++d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    for (int q = warp; q < kb; q += nw) {
+      const int i = k0 + q;
+      float acc;
+      if (d < f.G0) {
+        acc = row_dot(f.F + (int64_t)i * m, y, 0, k0, lane);
+      } else {
+        const int I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
+        acc = rag_dot(f, I, rr, y, lane) +
+              chunk_dot(f.chunk_row(I, rr) + lane, y + e + lane, 0, d - f.G0);
+        acc = warp_sum_f(acc);
+      }
+      if (lane == 0) t32[q] = y[i] - acc;
+    }
+    __syncthreads();
+    for (int q = warp; q < kb; q += nw) {
+      const int i = k0 + q;
+      float v = (lane < q) ? __ldg(cr_diag_row(f, m, d, i) + lane) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = t32[q] + v;
+    }
+    __syncthreads();
+  }
+  for (int d = G - 1; d >= 0; --d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    for (int q = warp; q < kb; q += nw) {
+      const int i = k0 + q;
+      float acc;
+      if (d < f.G0) {
+        acc = row_dot(f.F + (int64_t)i * m, y, k0 + kb, m, lane);
+      } else {
+        const int I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
+        acc = warp_sum_f(
+            chunk_dot(f.chunk_row(I, rr) + lane, y + e + lane, d - f.G0 + 1, f.nch));
+      }
+      if (lane == 0) t32[q] = y[i] - acc;
+    }
+    __syncthreads();
+    for (int q = warp; q < kb; q += nw) {
+      const int i = k0 + q;
+      float v = (lane >= q && lane < kb) ? __ldg(cr_diag_row(f, m, d, i) + lane) * t32[lane]
+                                         : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// y <- U^{-T} y then L^{-T} y (right-looking, a thread per column, as
+// lu_apply_inverse_transposed); in block row I >= 1 the threads of a warp take
+// the 32 columns of one chunk.
+__device__ void lu_apply_inverse_transposed_cr(const CrFactor& f, int m, float* y, float* t32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int nt = (int)blockDim.x, e = f.g.e, G = f.groups();
+  for (int d = 0; d < G; ++d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
+    __syncthreads();
+    for (int q = warp; q < kb; q += nw) {
+      // z_i = sum_{k<=i} Y[k][i] t_k
+      const int i = k0 + q;
+      float v = (lane <= q) ? __ldg(cr_diag_row(f, m, d, k0 + lane) + q) * t32[lane] : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = v;
+    }
+    __syncthreads();
+    if (d < f.G0) {
+      for (int r = k0 + kb + threadIdx.x; r < m; r += nt) {
+        float acc = y[r];
+#pragma unroll 8
+        for (int t = 0; t < kb; ++t)
+          acc = fmaf(-__ldg(f.F + (int64_t)(k0 + t) * m + r), y[k0 + t], acc);
+        y[r] = acc;
+      }
+    } else {
+      const int h = d - f.G0;
+      const float* p = f.chunk_row(1 + (h >> 2), 32 * (h & 3));  // row k0 of the group
+      for (int c = 32 * (h + 1) + threadIdx.x; c < 32 * f.nch; c += nt) {
+        const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
+        float acc = y[e + c];
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), y[k0 + t], acc);
+        y[e + c] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  for (int d = G - 1; d >= 0; --d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
+    __syncthreads();
+    for (int q = warp; q < kb; q += nw) {
+      // z_i = t_i + sum_{k>i} X[k][i] t_k
+      const int i = k0 + q;
+      float v = (lane > q && lane < kb) ? __ldg(cr_diag_row(f, m, d, k0 + lane) + q) * t32[lane]
+                                        : 0.0f;
+      v = warp_sum_f(v);
+      if (lane == 0) y[i] = t32[q] + v;
+    }
+    __syncthreads();
+    if (d < f.G0) {
+      for (int r = threadIdx.x; r < k0; r += nt) {
+        float acc = y[r];
+#pragma unroll 8
+        for (int t = 0; t < kb; ++t)
+          acc = fmaf(-__ldg(f.F + (int64_t)(k0 + t) * m + r), y[k0 + t], acc);
+        y[r] = acc;
+      }
+    } else {
+      const int h = d - f.G0, I = 1 + (h >> 2), rr0 = 32 * (h & 3);
+      // columns below e: the ragged tile (I, 0)
+      const CrRag rag(f, I);
+      for (int r = threadIdx.x; r < e; r += nt) {
+        float acc = y[r];
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) acc = fmaf(-rag(rr0 + t, r), y[k0 + t], acc);
+        y[r] = acc;
+      }
+      // columns e .. k0 - 1: the chunks before the group's
+      const float* p = f.chunk_row(I, rr0);
+      for (int c = threadIdx.x; c < 32 * h; c += nt) {
+        const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
+        float acc = y[e + c];
+#pragma unroll 8
+        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), y[k0 + t], acc);
+        y[e + c] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Double-float residuals against the stored planes
 // ---------------------------------------------------------------------------
 // Accumulator for sum_k (h_k + l_k)(xh_k + xl_k) with error ~2^-70 sum|p|:
@@ -1080,6 +1303,10 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   const float* Ah = a.A_hi + moff;
   const float* Al = a.A_lo + moff;
   const float* F = a.LU + moff;
+  // above kLargeM - 1 panels: the blocked factor's tiled layout
+  const bool cr = !gj && m > kLargeM;
+  CrFactor crf;
+  if (cr) crf.init(F, m, moff);
   const int32_t* gpiv = a.piv + vec_off(bt, b);
   const double s = border_scale(Ah, n, m, red);
   const bool act0 = a.u != nullptr, act1 = a.lam != nullptr;
@@ -1153,6 +1380,8 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
         __syncthreads();
         if (gj)
           gj_apply(F, m, y, part);
+        else if (cr)
+          lu_apply_inverse_cr(crf, m, y, t32);
         else
           lu_apply_inverse(F, m, y, t32);
       } else {
@@ -1162,6 +1391,8 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
         __syncthreads();
         if (gj)
           gj_apply_transposed(F, m, y, part);
+        else if (cr)
+          lu_apply_inverse_transposed_cr(crf, m, y, t32);
         else
           lu_apply_inverse_transposed(F, m, y, t32);
       }

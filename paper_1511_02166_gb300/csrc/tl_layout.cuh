@@ -28,9 +28,11 @@
 //
 // Viewed as rows of 32 floats, every chunk of every full tile starts on a row
 // boundary of one two-dimensional array (the whole factor buffer, 128-byte
-// rows), so one tensor map describes every chunk of every airfoil.  The
-// refinement reads the row-major factor: after the last step the layout is
-// turned back (k_tl_to_rowmajor).
+// rows), so one tensor map describes every chunk of every airfoil.  After the
+// last step the transposed U tiles are turned back to row chunks
+// (k_tl_untranspose), and the refinement reads the factor in this layout: a
+// row of block row I >= 1 is its ragged part, then 32-float chunks 4096 floats
+// apart.
 #pragma once
 #include <cuda.h>
 

@@ -326,8 +326,8 @@ class PanelBatch:
         global memory, or the one-block LU in shared memory and through L2) and,
         for m > 640 with T 128-column blocks, the step-synchronous LU: the tiled
         copy, T diagonal LUs, one CUDA-core and T - 1 tensor-core triangular
-        solves, T - 1 updates, the conversion back and the inversion of the
-        diagonal blocks; the adjoint of n > 256 adds a zeroing launch."""
+        solves, T - 1 updates, the untranspose of the U tiles and the inversion
+        of the diagonal blocks; the adjoint of n > 256 adds a zeroing launch."""
         n = 1  # forces
         for k, (start, cnt, nmax) in enumerate(self.buckets):
             m = nmax + 1
