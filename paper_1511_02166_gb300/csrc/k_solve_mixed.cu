@@ -594,10 +594,23 @@ size_t lu_global_smem(int n_max) {
 }
 
 // ---------------------------------------------------------------------------
-// Triangular solves with the stored factor (global memory, ld = m, diagonal
-// blocks inverted), on a float vector y in shared memory; `t32` is a 32-float
-// shared scratch.  Every 32-row block takes two block barriers and all eight
-// warps: a warp owns 4 rows of the block and reduces across its lanes.
+// Triangular solves with the stored factor (global memory, the 32 x 32
+// diagonal blocks inverted) on float vectors in shared memory: the forward
+// system y <- U^{-1} L^{-1} y and the transposed system z <- L^{-T} U^{-T} z,
+// one of them or both at once.  Both go over the 32-row groups of the factor
+// top-down (L, U^T) and then bottom-up (U, L^T), two block barriers per group:
+//   phase A  forward: t_i = y_i - (row i of L or U outside the group) . y, a
+//            warp per row, lanes along the row (left-looking, coalesced);
+//            transposed: the previous group's columns of U^T (rows of U), or
+//            of L^T, applied to the rest of z, a thread per column
+//            (right-looking, coalesced across the threads); the group's own
+//            entries go to its 32-float scratch instead of z;
+//   phase B  the group's diagonal block: y_i = sum X_iq t_q (a warp per row),
+//            z_i = sum X_qi t_q (a warp per column).
+// Solving both systems, every warp takes its share of both in each phase (the
+// two share the barriers, and a warp done with its forward rows goes on to its
+// transposed columns while others are still loading); each system's
+// arithmetic is the same as when it is solved alone.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -605,9 +618,9 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// sum_{k in [k0, k1)} row[k] y[k] over the lanes (k = lane + 32 t), with eight
-// independent partial sums so that eight loads of the row are in flight per
-// lane (a long row is otherwise a chain of dependent round trips to L2).
+// One lane's share of sum_{k in [k0, k1)} row[k] y[k] (k = lane + 32 t), with
+// eight independent partial sums so that eight loads of the row are in flight
+// per lane (a long row is otherwise a chain of dependent round trips to L2).
 __device__ __forceinline__ float row_dot(const float* __restrict__ row, const float* y, int k0,
                                          int k1, int lane) {
   float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -620,127 +633,66 @@ __device__ __forceinline__ float row_dot(const float* __restrict__ row, const fl
     for (int u = 0; u < 8; ++u) a[u] = fmaf(r[u], y[k + 32 * u], a[u]);
   }
   for (; k < k1; k += 32) a[0] = fmaf(__ldg(row + k), y[k], a[0]);
-  return warp_sum_f(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-// y <- L^{-1} y then U^{-1} y, left-looking: the rows of block d read their
-// own contiguous segments L[i][0..k0) (coalesced across the lanes).
-__device__ void lu_apply_inverse(const float* __restrict__ F, int m, float* y, float* t32) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < m; k0 += 32) {
-    const int kb = min(32, m - k0);
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      const int i = k0 + q;
-      const float acc = row_dot(F + i * m, y, 0, k0, lane);
-      if (lane == 0) t32[q] = y[i] - acc;
-    }
-    __syncthreads();
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      const int i = k0 + q;
-      // z_i = t_i + sum_{k<i} X[i][k] t_k  (X unit lower, stored below the diagonal)
-      float v = (lane < q) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = t32[q] + v;
-    }
-    __syncthreads();
+// The factor of an airfoil of at most kLargeM - 1 panels: row-major, ld m,
+// groups of 32 rows from row 0.
+struct RmFactor {
+  const float* F;
+  int m;
+  __device__ int groups() const { return (m + 31) >> 5; }
+  __device__ int k0(int d) const { return 32 * d; }
+  __device__ int kb(int d) const { return min(32, m - 32 * d); }
+  // lane shares of row i . y over the columns before / after group d
+  __device__ float dot_left(int i, int d, const float* y, int lane) const {
+    return row_dot(F + (int64_t)i * m, y, 0, 32 * d, lane);
   }
-  for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
-    const int kb = min(32, m - k0);
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      const int i = k0 + q;
-      const float acc = row_dot(F + i * m, y, k0 + kb, m, lane);
-      if (lane == 0) t32[q] = y[i] - acc;
-    }
-    __syncthreads();
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      const int i = k0 + q;
-      // x_i = sum_{k>=i} Y[i][k] t_k  (Y upper with diagonal)
-      float v = (lane >= q && lane < kb) ? __ldg(F + i * m + k0 + lane) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = v;
-    }
-    __syncthreads();
+  __device__ float dot_right(int i, int d, const float* y, int lane) const {
+    return row_dot(F + (int64_t)i * m, y, 32 * d + kb(d), m, lane);
   }
-}
-
-// y <- U^{-T} y then L^{-T} y.  Right-looking updates (a thread per row r reads
-// U[k][r], coalesced across r); the diagonal products are split over the warps.
-__device__ void lu_apply_inverse_transposed(const float* __restrict__ F, int m, float* y,
-                                            float* t32) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < m; k0 += 32) {
-    const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
-    __syncthreads();
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      // z_i = sum_{k<=i} Y[k][i] t_k
-      const int i = k0 + q;
-      float v = (lane <= q) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = v;
-    }
-    __syncthreads();
-    for (int r = k0 + kb + threadIdx.x; r < m; r += (int)blockDim.x) {
-      float acc = y[r];
+  // row i's entries in the columns of group d
+  __device__ const float* diag_row(int d, int i) const { return F + (int64_t)i * m + 32 * d; }
+  // z_r -= sum_t M[k0 + t][r] z_{k0 + t} (group d's rows) for the columns r after
+  // group d; those of group d + 1 go to nx.  Thread tid of nth.
+  __device__ void update_right(int d, float* z, float* nx, int tid, int nth) const {
+    const int k0 = 32 * d, kb = this->kb(d), c0 = k0 + kb;
+    for (int r = c0 + tid; r < m; r += nth) {
+      float acc = z[r];
 #pragma unroll 8
-      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
-      y[r] = acc;
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
+      if (r < c0 + 32)
+        nx[r - c0] = acc;
+      else
+        z[r] = acc;
     }
-    __syncthreads();
   }
-  for (int k0 = ((m - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
-    const int kb = min(32, m - k0);
-    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
-    __syncthreads();
-    for (int q = warp; q < kb; q += (int)(blockDim.x >> 5)) {
-      // z_i = t_i + sum_{k>i} X[k][i] t_k
-      const int i = k0 + q;
-      float v = (lane > q && lane < kb) ? __ldg(F + (k0 + lane) * m + i) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = t32[q] + v;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < k0; r += (int)blockDim.x) {
-      float acc = y[r];
+  // the same for the columns before group d; those of group d - 1 go to nx
+  __device__ void update_left(int d, float* z, float* nx, int tid, int nth) const {
+    const int k0 = 32 * d, kb = this->kb(d);
+    for (int r = tid; r < k0; r += nth) {
+      float acc = z[r];
 #pragma unroll 8
-      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (k0 + t) * m + r), y[k0 + t], acc);
-      y[r] = acc;
+      for (int t = 0; t < kb; ++t) acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
+      if (r >= k0 - 32)
+        nx[r - (k0 - 32)] = acc;
+      else
+        z[r] = acc;
     }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The same solves with the factor of an airfoil above kLargeM - 1 panels in
-// the layout the blocked LU (k_lu_large.cu) leaves: the tiled layout of
-// tl_layout.cuh with every full tile in row chunks.  Block row 0 (the first e
-// rows) is row-major (ld m); in block row I >= 1 the columns below e sit in the
-// ragged tile (I, 0) (row-major, ld e, split at the head) and column e + 32 ch
-// + c of row rr at tile(I, 1) + 4096 ch + 32 rr + c: a row is a run of 32-float
-// chunks 4096 floats apart.  The 32-row groups of the sweeps follow the tiles:
-// ceil(e / 32) groups in block row 0, then four per full block row, and the
-// diagonal blocks inverted are those of these groups.
-// ---------------------------------------------------------------------------
-struct CrFactor {
-  const float* F;  // the airfoil's matrix
-  TlGeom g;
-  int G0;          // groups of block row 0
-  int nch;         // chunks of a full block row: 4 (T - 1)
-  __device__ void init(const float* F_, int m, int64_t moff) {
-    F = F_;
-    g.init(m, moff);
-    G0 = (g.e + 31) >> 5;
-    nch = 4 * (g.T - 1);
-  }
-  __device__ int groups() const { return G0 + nch; }
-  __device__ int k0(int d) const { return d < G0 ? 32 * d : g.e + 32 * (d - G0); }
-  __device__ int kb(int d) const { return d < G0 ? min(32, g.e - 32 * d) : 32; }
-  // row rr of block row I (I >= 1): its chunk 0 (add 4096 ch + the column in the chunk)
-  __device__ const float* chunk_row(int I, int rr) const {
-    return F + g.tile(I, 1) + (int64_t)rr * kTlC;
   }
 };
 
+// The factor of an airfoil of more than kLargeM - 1 panels, in the layout the
+// blocked LU (k_lu_large.cu) leaves: the tiled layout of tl_layout.cuh with
+// every full tile in row chunks.  Block row 0 (the first e rows) is row-major
+// (ld m); in block row I >= 1 the columns below e sit in the ragged tile (I, 0)
+// (row-major, ld e, split at the head) and column e + 32 ch + c of row rr at
+// tile(I, 1) + 4096 ch + 32 rr + c: a row is a run of 32-float chunks 4096
+// floats apart.  The 32-row groups follow the tiles: ceil(e / 32) groups in
+// block row 0, then four per full block row, and the diagonal blocks inverted
+// are those of these groups.  In the transposed updates of block row I >= 1
+// the threads of a warp take the 32 columns of one chunk.
+struct CrFactor;
 // The ragged tile (I, 0) of block row I >= 1: element (rr, c), c < e, is float
 // rr e + c of the tile, which sits at span(I) up to the head and after the full
 // tiles beyond it.
@@ -748,9 +700,8 @@ struct CrRag {
   const float* p;  // the block row's span
   int hh, e;
   int64_t jump;    // the full tiles' floats
-  __device__ CrRag(const CrFactor& f, int I)
-      : p(f.F + f.g.span(I)), hh(f.g.head(I)), e(f.g.e),
-        jump((int64_t)(f.g.T - 1) * kTlTile) {}
+  __device__ CrRag(const float* F, const TlGeom& g, int I)
+      : p(F + g.span(I)), hh(g.head(I)), e(g.e), jump((int64_t)(g.T - 1) * kTlTile) {}
   __device__ float operator()(int rr, int c) const {
     const int idx = rr * e + c;
     return __ldg(p + (idx < hh ? (int64_t)idx : idx + jump));
@@ -774,162 +725,214 @@ __device__ __forceinline__ float chunk_dot(const float* __restrict__ p, const fl
   return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 }
 
-// One lane's share of sum_{c < e} L[row][c] y[c] for row rr of block row I.
-__device__ __forceinline__ float rag_dot(const CrFactor& f, int I, int rr, const float* y,
-                                         int lane) {
-  const CrRag rag(f, I);
-  float v = 0.0f;
+struct CrFactor {
+  const float* F;  // the airfoil's matrix
+  TlGeom g;
+  int m;
+  int G0;          // groups of block row 0
+  int nch;         // chunks of a full block row: 4 (T - 1)
+  __device__ void init(const float* F_, int m_, int64_t moff) {
+    F = F_;
+    m = m_;
+    g.init(m_, moff);
+    G0 = (g.e + 31) >> 5;
+    nch = 4 * (g.T - 1);
+  }
+  __device__ int groups() const { return G0 + nch; }
+  __device__ int k0(int d) const { return d < G0 ? 32 * d : g.e + 32 * (d - G0); }
+  __device__ int kb(int d) const { return d < G0 ? min(32, g.e - 32 * d) : 32; }
+  // row rr of block row I >= 1: its chunk 0 (add 4096 ch + the column in the chunk)
+  __device__ const float* chunk_row(int I, int rr) const {
+    return F + g.tile(I, 1) + (int64_t)rr * kTlC;
+  }
+  __device__ float dot_left(int i, int d, const float* y, int lane) const {
+    if (d < G0) return row_dot(F + (int64_t)i * m, y, 0, 32 * d, lane);
+    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
+    const CrRag rag(F, g, I);
+    float v = 0.0f;
 #pragma unroll
-  for (int t = 0; t < kTlB / 32; ++t) {
-    const int c = lane + 32 * t;
-    if (c < f.g.e) v = fmaf(rag(rr, c), y[c], v);
+    for (int t = 0; t < kTlB / 32; ++t) {
+      const int c = lane + 32 * t;
+      if (c < e) v = fmaf(rag(rr, c), y[c], v);
+    }
+    return v + chunk_dot(chunk_row(I, rr) + lane, y + e + lane, 0, d - G0);
   }
-  return v;
-}
-
-// Row i's 32 entries in the columns of group d (i in the group, or i < e).
-__device__ __forceinline__ const float* cr_diag_row(const CrFactor& f, int m, int d, int i) {
-  if (d < f.G0) return f.F + (int64_t)i * m + 32 * d;
-  const int h = d - f.G0, rr = (i - f.g.e) & (kTlB - 1);
-  return f.chunk_row(1 + (h >> 2), rr) + (int64_t)h * kTlChunk;
-}
-
-// y <- L^{-1} y then U^{-1} y (left-looking, a warp per row, as lu_apply_inverse).
-__device__ void lu_apply_inverse_cr(const CrFactor& f, int m, float* y, float* t32) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
-  const int e = f.g.e, G = f.groups();
-  for (int d = 0; d < G; ++d) {
-    const int k0 = f.k0(d), kb = f.kb(d);
-    for (int q = warp; q < kb; q += nw) {
-      const int i = k0 + q;
-      float acc;
-      if (d < f.G0) {
-        acc = row_dot(f.F + (int64_t)i * m, y, 0, k0, lane);
-      } else {
-        const int I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
-        acc = rag_dot(f, I, rr, y, lane) +
-              chunk_dot(f.chunk_row(I, rr) + lane, y + e + lane, 0, d - f.G0);
-        acc = warp_sum_f(acc);
-      }
-      if (lane == 0) t32[q] = y[i] - acc;
-    }
-    __syncthreads();
-    for (int q = warp; q < kb; q += nw) {
-      const int i = k0 + q;
-      float v = (lane < q) ? __ldg(cr_diag_row(f, m, d, i) + lane) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = t32[q] + v;
-    }
-    __syncthreads();
+  __device__ float dot_right(int i, int d, const float* y, int lane) const {
+    if (d < G0) return row_dot(F + (int64_t)i * m, y, k0(d) + kb(d), m, lane);
+    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
+    return chunk_dot(chunk_row(I, rr) + lane, y + e + lane, d - G0 + 1, nch);
   }
-  for (int d = G - 1; d >= 0; --d) {
-    const int k0 = f.k0(d), kb = f.kb(d);
-    for (int q = warp; q < kb; q += nw) {
-      const int i = k0 + q;
-      float acc;
-      if (d < f.G0) {
-        acc = row_dot(f.F + (int64_t)i * m, y, k0 + kb, m, lane);
-      } else {
-        const int I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
-        acc = warp_sum_f(
-            chunk_dot(f.chunk_row(I, rr) + lane, y + e + lane, d - f.G0 + 1, f.nch));
-      }
-      if (lane == 0) t32[q] = y[i] - acc;
-    }
-    __syncthreads();
-    for (int q = warp; q < kb; q += nw) {
-      const int i = k0 + q;
-      float v = (lane >= q && lane < kb) ? __ldg(cr_diag_row(f, m, d, i) + lane) * t32[lane]
-                                         : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = v;
-    }
-    __syncthreads();
+  __device__ const float* diag_row(int d, int i) const {
+    if (d < G0) return F + (int64_t)i * m + 32 * d;
+    const int h = d - G0, rr = (i - g.e) & (kTlB - 1);
+    return chunk_row(1 + (h >> 2), rr) + (int64_t)h * kTlChunk;
   }
-}
-
-// y <- U^{-T} y then L^{-T} y (right-looking, a thread per column, as
-// lu_apply_inverse_transposed); in block row I >= 1 the threads of a warp take
-// the 32 columns of one chunk.
-__device__ void lu_apply_inverse_transposed_cr(const CrFactor& f, int m, float* y, float* t32) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
-  const int nt = (int)blockDim.x, e = f.g.e, G = f.groups();
-  for (int d = 0; d < G; ++d) {
-    const int k0 = f.k0(d), kb = f.kb(d);
-    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
-    __syncthreads();
-    for (int q = warp; q < kb; q += nw) {
-      // z_i = sum_{k<=i} Y[k][i] t_k
-      const int i = k0 + q;
-      float v = (lane <= q) ? __ldg(cr_diag_row(f, m, d, k0 + lane) + q) * t32[lane] : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = v;
-    }
-    __syncthreads();
-    if (d < f.G0) {
-      for (int r = k0 + kb + threadIdx.x; r < m; r += nt) {
-        float acc = y[r];
+  __device__ void update_right(int d, float* z, float* nx, int tid, int nth) const {
+    const int k0 = this->k0(d), kb = this->kb(d), c0 = k0 + kb;
+    const int c1 = c0 + this->kb(d + 1);  // end of group d + 1 (d + 1 < groups())
+    if (d < G0) {
+      for (int r = c0 + tid; r < m; r += nth) {
+        float acc = z[r];
 #pragma unroll 8
         for (int t = 0; t < kb; ++t)
-          acc = fmaf(-__ldg(f.F + (int64_t)(k0 + t) * m + r), y[k0 + t], acc);
-        y[r] = acc;
+          acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
+        if (r < c1)
+          nx[r - c0] = acc;
+        else
+          z[r] = acc;
       }
     } else {
-      const int h = d - f.G0;
-      const float* p = f.chunk_row(1 + (h >> 2), 32 * (h & 3));  // row k0 of the group
-      for (int c = 32 * (h + 1) + threadIdx.x; c < 32 * f.nch; c += nt) {
+      const int h = d - G0, e = g.e;
+      const float* p = chunk_row(1 + (h >> 2), 32 * (h & 3));  // row k0 of the group
+      for (int c = 32 * (h + 1) + tid; c < 32 * nch; c += nth) {
         const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
-        float acc = y[e + c];
+        float acc = z[e + c];
 #pragma unroll 8
-        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), y[k0 + t], acc);
-        y[e + c] = acc;
+        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), z[k0 + t], acc);
+        if (e + c < c1)
+          nx[e + c - c0] = acc;
+        else
+          z[e + c] = acc;
       }
     }
-    __syncthreads();
   }
-  for (int d = G - 1; d >= 0; --d) {
-    const int k0 = f.k0(d), kb = f.kb(d);
-    if (threadIdx.x < 32) t32[lane] = (lane < kb) ? y[k0 + lane] : 0.0f;
-    __syncthreads();
-    for (int q = warp; q < kb; q += nw) {
-      // z_i = t_i + sum_{k>i} X[k][i] t_k
-      const int i = k0 + q;
-      float v = (lane > q && lane < kb) ? __ldg(cr_diag_row(f, m, d, k0 + lane) + q) * t32[lane]
-                                        : 0.0f;
-      v = warp_sum_f(v);
-      if (lane == 0) y[i] = t32[q] + v;
-    }
-    __syncthreads();
-    if (d < f.G0) {
-      for (int r = threadIdx.x; r < k0; r += nt) {
-        float acc = y[r];
+  __device__ void update_left(int d, float* z, float* nx, int tid, int nth) const {
+    const int k0 = this->k0(d), kb = this->kb(d);
+    const int p0 = this->k0(d - 1);  // start of group d - 1 (d >= 1)
+    if (d < G0) {
+      for (int r = tid; r < k0; r += nth) {
+        float acc = z[r];
 #pragma unroll 8
         for (int t = 0; t < kb; ++t)
-          acc = fmaf(-__ldg(f.F + (int64_t)(k0 + t) * m + r), y[k0 + t], acc);
-        y[r] = acc;
+          acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
+        if (r >= p0)
+          nx[r - p0] = acc;
+        else
+          z[r] = acc;
       }
     } else {
-      const int h = d - f.G0, I = 1 + (h >> 2), rr0 = 32 * (h & 3);
+      const int h = d - G0, I = 1 + (h >> 2), rr0 = 32 * (h & 3), e = g.e;
       // columns below e: the ragged tile (I, 0)
-      const CrRag rag(f, I);
-      for (int r = threadIdx.x; r < e; r += nt) {
-        float acc = y[r];
+      const CrRag rag(F, g, I);
+      for (int r = tid; r < e; r += nth) {
+        float acc = z[r];
 #pragma unroll 8
-        for (int t = 0; t < 32; ++t) acc = fmaf(-rag(rr0 + t, r), y[k0 + t], acc);
-        y[r] = acc;
+        for (int t = 0; t < 32; ++t) acc = fmaf(-rag(rr0 + t, r), z[k0 + t], acc);
+        if (r >= p0)
+          nx[r - p0] = acc;
+        else
+          z[r] = acc;
       }
       // columns e .. k0 - 1: the chunks before the group's
-      const float* p = f.chunk_row(I, rr0);
-      for (int c = threadIdx.x; c < 32 * h; c += nt) {
+      const float* p = chunk_row(I, rr0);
+      for (int c = tid; c < 32 * h; c += nth) {
         const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
-        float acc = y[e + c];
+        float acc = z[e + c];
 #pragma unroll 8
-        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), y[k0 + t], acc);
-        y[e + c] = acc;
+        for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), z[k0 + t], acc);
+        if (e + c >= p0)
+          nx[e + c - p0] = acc;
+        else
+          z[e + c] = acc;
+      }
+    }
+  }
+};
+
+// FWD: y <- U^{-1} L^{-1} y (scratch ty); TRN: z <- L^{-T} U^{-T} z (scratch tz).
+template <bool FWD, bool TRN, class Fac>
+__device__ void lu_sweeps(const Fac& f, float* y, float* z, float* ty, float* tz) {
+  static_assert(FWD || TRN, "a system to solve");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
+  const int G = f.groups();
+  for (int d = 0; d < G; ++d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    if (FWD) {
+      for (int q = warp; q < kb; q += nw) {
+        const int i = k0 + q;
+        const float acc = warp_sum_f(f.dot_left(i, d, y, lane));
+        if (lane == 0) ty[q] = y[i] - acc;
+      }
+    }
+    if (TRN) {
+      if (d == 0) {
+        if (tid < 32) tz[tid] = (tid < kb) ? z[k0 + tid] : 0.0f;
+      } else {
+        f.update_right(d - 1, z, tz, tid, nt);
+      }
+    }
+    __syncthreads();
+    if (FWD) {
+      for (int q = warp; q < kb; q += nw) {
+        const int i = k0 + q;
+        // y_i = t_i + sum_{k<i} X[i][k] t_k  (X unit lower, stored below the diagonal)
+        float v = (lane < q) ? __ldg(f.diag_row(d, i) + lane) * ty[lane] : 0.0f;
+        v = warp_sum_f(v);
+        if (lane == 0) y[i] = ty[q] + v;
+      }
+    }
+    if (TRN) {
+      for (int q = warp; q < kb; q += nw) {
+        // z_i = sum_{k<=i} Y[k][i] t_k  (Y upper with diagonal)
+        const int i = k0 + q;
+        float v = (lane <= q) ? __ldg(f.diag_row(d, k0 + lane) + q) * tz[lane] : 0.0f;
+        v = warp_sum_f(v);
+        if (lane == 0) z[i] = v;
       }
     }
     __syncthreads();
   }
+  for (int d = G - 1; d >= 0; --d) {
+    const int k0 = f.k0(d), kb = f.kb(d);
+    if (FWD) {
+      for (int q = warp; q < kb; q += nw) {
+        const int i = k0 + q;
+        const float acc = warp_sum_f(f.dot_right(i, d, y, lane));
+        if (lane == 0) ty[q] = y[i] - acc;
+      }
+    }
+    if (TRN) {
+      if (d == G - 1) {
+        if (tid < 32) tz[tid] = (tid < kb) ? z[k0 + tid] : 0.0f;
+      } else {
+        f.update_left(d + 1, z, tz, tid, nt);
+      }
+    }
+    __syncthreads();
+    if (FWD) {
+      for (int q = warp; q < kb; q += nw) {
+        const int i = k0 + q;
+        // y_i = sum_{k>=i} Y[i][k] t_k  (Y upper with diagonal)
+        float v = (lane >= q && lane < kb) ? __ldg(f.diag_row(d, i) + lane) * ty[lane] : 0.0f;
+        v = warp_sum_f(v);
+        if (lane == 0) y[i] = v;
+      }
+    }
+    if (TRN) {
+      for (int q = warp; q < kb; q += nw) {
+        // z_i = t_i + sum_{k>i} X[k][i] t_k  (X unit lower, stored below the diagonal)
+        const int i = k0 + q;
+        float v = (lane > q && lane < kb) ? __ldg(f.diag_row(d, k0 + lane) + q) * tz[lane] : 0.0f;
+        v = warp_sum_f(v);
+        if (lane == 0) z[i] = tz[q] + v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The forward system (fw), the transposed one (tr) or both; ty, tz: 32 floats
+// each.  Both at once (COMBINE) or one after the other.
+template <bool COMBINE, class Fac>
+__device__ void lu_solve(const Fac& f, bool fw, bool tr, float* y, float* z, float* ty,
+                         float* tz) {
+  if (COMBINE && fw && tr) {
+    lu_sweeps<true, true>(f, y, z, ty, tz);
+    return;
+  }
+  if (fw) lu_sweeps<true, false>(f, y, z, ty, tz);
+  if (tr) lu_sweeps<false, true>(f, y, z, ty, tz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1136,6 +1139,7 @@ __device__ void residual_cols(const float* __restrict__ Ah, const float* __restr
 // accumulators and are merged across the warps through `part` ((int)(blockDim.x >> 5) x m).
 constexpr int kFuseM = 288;
 constexpr int kFuseT = (kFuseM + 31) / 32;
+static_assert(kFuseM <= kLargeM, "KEEP launches never hold a blocked (tiled) factor");
 template <class Acc, int FT = kFuseT, class Rhs, class RT>
 __device__ void residual_both(const float* __restrict__ Ah, const float* __restrict__ Al, int m,
                               const float* xh, const float* xl, const float* yh, const float* yl,
@@ -1296,6 +1300,12 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   // the fused residual pass (ResAcc, launches with n_max + 1 <= kFuseM)
   float* part = reinterpret_cast<float*>(
       (reinterpret_cast<uintptr_t>(t32 + 32) + 15) & ~(uintptr_t)15);
+  // The corrections: the forward one in y, the transposed one in z, which is
+  // the transposed system's float copy of lambda (rewritten from lambda before
+  // it is read again); the transposed sweeps' 32-float group scratch is `red`
+  // (free while the sweeps run).
+  float* z = sys[1].xh;
+  float* t32z = reinterpret_cast<float*>(red);
   // the factor buffer holds an inverse (exchanges stored as -(row + 1)) or an LU
   const bool gj = gpiv_first(a, b) < 0;
 
@@ -1303,10 +1313,13 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   const float* Ah = a.A_hi + moff;
   const float* Al = a.A_lo + moff;
   const float* F = a.LU + moff;
-  // above kLargeM - 1 panels: the blocked factor's tiled layout
-  const bool cr = !gj && m > kLargeM;
+  // above kLargeM - 1 panels: the blocked factor's tiled layout (never in a
+  // KEEP launch: n_max + 1 <= kFuseM there)
+  const bool cr = !KEEP && !gj && m > kLargeM;
   CrFactor crf;
-  if (cr) crf.init(F, m, moff);
+  if constexpr (!KEEP) {
+    if (cr) crf.init(F, m, moff);
+  }
   const int32_t* gpiv = a.piv + vec_off(bt, b);
   const double s = border_scale(Ah, n, m, red);
   const bool act0 = a.u != nullptr, act1 = a.lam != nullptr;
@@ -1368,38 +1381,36 @@ __global__ void __launch_bounds__(NT, MINB) k_ir_mixed(SolveArgs a) {
   double dprev[2] = {0.0, 0.0};  // size of the previous correction
   int it = 0;
   for (;; ++it) {
-    for (int q = 0; q < 2; ++q) {
-      if (!active[q] || conv[q]) continue;
-      IrSystem<RT>& S = sys[q];
-      if (q == 0) {
-        // y = P S_r r;  solve;  dx = S_c y
-        for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
-          const int src = perm[k];
-          y[k] = solve_input(S.r[src], src, n, s);
-        }
-        __syncthreads();
-        if (gj)
-          gj_apply(F, m, y, part);
-        else if (cr)
-          lu_apply_inverse_cr(crf, m, y, t32);
-        else
-          lu_apply_inverse(F, m, y, t32);
-      } else {
-        // z = Mt^{-T} S_c r;  dlambda = S_r P^T z
-        for (int k = threadIdx.x; k < m; k += (int)blockDim.x)
-          y[k] = solve_input(S.r[k], k, n, s);
-        __syncthreads();
-        if (gj)
-          gj_apply_transposed(F, m, y, part);
-        else if (cr)
-          lu_apply_inverse_transposed_cr(crf, m, y, t32);
-        else
-          lu_apply_inverse_transposed(F, m, y, t32);
+    const bool run0 = active[0] && !conv[0], run1 = active[1] && !conv[1];
+    // the corrections' right-hand sides: y = P S_r r (forward system; then
+    // dx = S_c y) and z = S_c r (transposed system; then dlambda = S_r P^T z)
+    for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
+      if (run0) {
+        const int src = perm[k];
+        y[k] = solve_input(sys[0].r[src], src, n, s);
       }
+      if (run1) z[k] = solve_input(sys[1].r[k], k, n, s);
+    }
+    __syncthreads();
+    if (gj) {
+      if (run0) gj_apply(F, m, y, part);
+      if (run1) gj_apply_transposed(F, m, z, part);
+    } else if constexpr (!KEEP) {
+      if (cr)
+        lu_solve<true>(crf, run0, run1, y, z, t32, t32z);
+      else
+        lu_solve<true>(RmFactor{F, m}, run0, run1, y, z, t32, t32z);
+    } else {
+      lu_solve<false>(RmFactor{F, m}, run0, run1, y, z, t32, t32z);
+    }
+    for (int q = 0; q < 2; ++q) {
+      if (!(q == 0 ? run0 : run1)) continue;
+      IrSystem<RT>& S = sys[q];
+      const float* w = (q == 0) ? y : z;
       double dmax = 0.0;
       for (int k = threadIdx.x; k < m; k += (int)blockDim.x) {
         const int dst = (q == 0) ? k : perm[k];
-        const double d = (dst == n) ? (double)y[k] * s : (double)y[k];
+        const double d = (dst == n) ? (double)w[k] * s : (double)w[k];
         S.x[dst] += d;
         dmax = fmax(dmax, fabs(d));
       }
