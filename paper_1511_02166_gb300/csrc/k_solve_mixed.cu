@@ -618,22 +618,53 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// One lane's share of sum_{k in [k0, k1)} row[k] y[k] (k = lane + 32 t), with
-// eight independent partial sums so that eight loads of the row are in flight
-// per lane (a long row is otherwise a chain of dependent round trips to L2).
-__device__ __forceinline__ float row_dot(const float* __restrict__ row, const float* y, int k0,
-                                         int k1, int lane) {
+__device__ __forceinline__ float sum8(const float (&a)[8]) {
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+// One lane's shares of sum_{k in [k0, k1)} row[k] y[k] (k = lane + 32 t) for
+// two rows r0 and r1 (r1 only if `two`) over the same columns, with eight
+// independent partial sums per row, so that up to sixteen loads are in flight
+// per lane (a long row is otherwise a chain of dependent round trips to L2);
+// the last (< 256) columns take one masked pass.
+__device__ __forceinline__ float2 row_dot2(const float* __restrict__ r0,
+                                           const float* __restrict__ r1, bool two,
+                                           const float* y, int k0, int k1, int lane) {
   float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  float b[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   int k = k0 + lane;
   for (; k + 7 * 32 < k1; k += 8 * 32) {
-    float r[8];
+    float u[8], v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) r[u] = __ldg(row + k + 32 * u);
+    for (int t = 0; t < 8; ++t) {
+      u[t] = __ldg(r0 + k + 32 * t);
+      v[t] = two ? __ldg(r1 + k + 32 * t) : 0.0f;
+    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = fmaf(r[u], y[k + 32 * u], a[u]);
+    for (int t = 0; t < 8; ++t) {
+      const float yy = y[k + 32 * t];
+      a[t] = fmaf(u[t], yy, a[t]);
+      b[t] = fmaf(v[t], yy, b[t]);
+    }
   }
-  for (; k < k1; k += 32) a[0] = fmaf(__ldg(row + k), y[k], a[0]);
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  if (k < k1) {
+    float u[8], v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const bool ok = k + 32 * t < k1;
+      u[t] = ok ? __ldg(r0 + k + 32 * t) : 0.0f;
+      v[t] = (ok && two) ? __ldg(r1 + k + 32 * t) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (k + 32 * t < k1) {
+        const float yy = y[k + 32 * t];
+        a[t] = fmaf(u[t], yy, a[t]);
+        b[t] = fmaf(v[t], yy, b[t]);
+      }
+    }
+  }
+  return make_float2(sum8(a), sum8(b));
 }
 
 // The factor of an airfoil of at most kLargeM - 1 panels: row-major, ld m,
@@ -644,12 +675,13 @@ struct RmFactor {
   __device__ int groups() const { return (m + 31) >> 5; }
   __device__ int k0(int d) const { return 32 * d; }
   __device__ int kb(int d) const { return min(32, m - 32 * d); }
-  // lane shares of row i . y over the columns before / after group d
-  __device__ float dot_left(int i, int d, const float* y, int lane) const {
-    return row_dot(F + (int64_t)i * m, y, 0, 32 * d, lane);
+  // lane shares of row i . y (and of row i1 . y if `two`) over the columns
+  // before / after group d
+  __device__ float2 dot_left(int i, int i1, bool two, int d, const float* y, int lane) const {
+    return row_dot2(F + (int64_t)i * m, F + (int64_t)i1 * m, two, y, 0, 32 * d, lane);
   }
-  __device__ float dot_right(int i, int d, const float* y, int lane) const {
-    return row_dot(F + (int64_t)i * m, y, 32 * d + kb(d), m, lane);
+  __device__ float2 dot_right(int i, int i1, bool two, int d, const float* y, int lane) const {
+    return row_dot2(F + (int64_t)i * m, F + (int64_t)i1 * m, two, y, 32 * d + kb(d), m, lane);
   }
   // row i's entries in the columns of group d
   __device__ const float* diag_row(int d, int i) const { return F + (int64_t)i * m + 32 * d; }
@@ -709,20 +741,46 @@ struct CrRag {
 };
 
 // sum_{ch in [c0, c1)} p[4096 ch] yy[32 ch] (one lane's share of a chunked row:
-// p and yy already offset by the lane), eight loads in flight.
-__device__ __forceinline__ float chunk_dot(const float* __restrict__ p, const float* yy, int c0,
-                                           int c1) {
+// p and yy already offset by the lane) for two rows p0 and p1 (p1 only if
+// `two`), as row_dot2.
+__device__ __forceinline__ float2 chunk_dot2(const float* __restrict__ p0,
+                                             const float* __restrict__ p1, bool two,
+                                             const float* yy, int c0, int c1) {
   float a[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  float b[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   int ch = c0;
   for (; ch + 7 < c1; ch += 8) {
-    float r[8];
+    float u[8], v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) r[u] = __ldg(p + (int64_t)(ch + u) * kTlChunk);
+    for (int t = 0; t < 8; ++t) {
+      u[t] = __ldg(p0 + (int64_t)(ch + t) * kTlChunk);
+      v[t] = two ? __ldg(p1 + (int64_t)(ch + t) * kTlChunk) : 0.0f;
+    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = fmaf(r[u], yy[32 * (ch + u)], a[u]);
+    for (int t = 0; t < 8; ++t) {
+      const float y = yy[32 * (ch + t)];
+      a[t] = fmaf(u[t], y, a[t]);
+      b[t] = fmaf(v[t], y, b[t]);
+    }
   }
-  for (; ch < c1; ++ch) a[0] = fmaf(__ldg(p + (int64_t)ch * kTlChunk), yy[32 * ch], a[0]);
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+  if (ch < c1) {
+    float u[8], v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const bool ok = ch + t < c1;
+      u[t] = ok ? __ldg(p0 + (int64_t)(ch + t) * kTlChunk) : 0.0f;
+      v[t] = (ok && two) ? __ldg(p1 + (int64_t)(ch + t) * kTlChunk) : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (ch + t < c1) {
+        const float y = yy[32 * (ch + t)];
+        a[t] = fmaf(u[t], y, a[t]);
+        b[t] = fmaf(v[t], y, b[t]);
+      }
+    }
+  }
+  return make_float2(sum8(a), sum8(b));
 }
 
 struct CrFactor {
@@ -745,22 +803,30 @@ struct CrFactor {
   __device__ const float* chunk_row(int I, int rr) const {
     return F + g.tile(I, 1) + (int64_t)rr * kTlC;
   }
-  __device__ float dot_left(int i, int d, const float* y, int lane) const {
-    if (d < G0) return row_dot(F + (int64_t)i * m, y, 0, 32 * d, lane);
-    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
+  // rows i and i1 (i1 only if `two`) of group d, as RmFactor
+  __device__ float2 dot_left(int i, int i1, bool two, int d, const float* y, int lane) const {
+    if (d < G0) return row_dot2(F + (int64_t)i * m, F + (int64_t)i1 * m, two, y, 0, 32 * d, lane);
+    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1), rr1 = (i1 - e) & (kTlB - 1);
     const CrRag rag(F, g, I);
-    float v = 0.0f;
+    float v = 0.0f, w = 0.0f;
 #pragma unroll
     for (int t = 0; t < kTlB / 32; ++t) {
       const int c = lane + 32 * t;
-      if (c < e) v = fmaf(rag(rr, c), y[c], v);
+      if (c < e) {
+        v = fmaf(rag(rr, c), y[c], v);
+        if (two) w = fmaf(rag(rr1, c), y[c], w);
+      }
     }
-    return v + chunk_dot(chunk_row(I, rr) + lane, y + e + lane, 0, d - G0);
+    const float2 p = chunk_dot2(chunk_row(I, rr) + lane, chunk_row(I, rr1) + lane, two,
+                                y + e + lane, 0, d - G0);
+    return make_float2(v + p.x, w + p.y);
   }
-  __device__ float dot_right(int i, int d, const float* y, int lane) const {
-    if (d < G0) return row_dot(F + (int64_t)i * m, y, k0(d) + kb(d), m, lane);
-    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1);
-    return chunk_dot(chunk_row(I, rr) + lane, y + e + lane, d - G0 + 1, nch);
+  __device__ float2 dot_right(int i, int i1, bool two, int d, const float* y, int lane) const {
+    if (d < G0)
+      return row_dot2(F + (int64_t)i * m, F + (int64_t)i1 * m, two, y, k0(d) + kb(d), m, lane);
+    const int e = g.e, I = 1 + ((i - e) >> 7), rr = (i - e) & (kTlB - 1), rr1 = (i1 - e) & (kTlB - 1);
+    return chunk_dot2(chunk_row(I, rr) + lane, chunk_row(I, rr1) + lane, two, y + e + lane,
+                      d - G0 + 1, nch);
   }
   __device__ const float* diag_row(int d, int i) const {
     if (d < G0) return F + (int64_t)i * m + 32 * d;
@@ -849,10 +915,16 @@ __device__ void lu_sweeps(const Fac& f, float* y, float* z, float* ty, float* tz
   for (int d = 0; d < G; ++d) {
     const int k0 = f.k0(d), kb = f.kb(d);
     if (FWD) {
-      for (int q = warp; q < kb; q += nw) {
-        const int i = k0 + q;
-        const float acc = warp_sum_f(f.dot_left(i, d, y, lane));
-        if (lane == 0) ty[q] = y[i] - acc;
+      // rows q and q + nw of the group together
+      for (int q = warp; q < kb; q += 2 * nw) {
+        const int i = k0 + q, q1 = q + nw;
+        const bool two = q1 < kb;
+        const float2 p = f.dot_left(i, two ? k0 + q1 : i, two, d, y, lane);
+        const float acc = warp_sum_f(p.x), acc1 = warp_sum_f(p.y);
+        if (lane == 0) {
+          ty[q] = y[i] - acc;
+          if (two) ty[q1] = y[k0 + q1] - acc1;
+        }
       }
     }
     if (TRN) {
@@ -886,10 +958,15 @@ __device__ void lu_sweeps(const Fac& f, float* y, float* z, float* ty, float* tz
   for (int d = G - 1; d >= 0; --d) {
     const int k0 = f.k0(d), kb = f.kb(d);
     if (FWD) {
-      for (int q = warp; q < kb; q += nw) {
-        const int i = k0 + q;
-        const float acc = warp_sum_f(f.dot_right(i, d, y, lane));
-        if (lane == 0) ty[q] = y[i] - acc;
+      for (int q = warp; q < kb; q += 2 * nw) {
+        const int i = k0 + q, q1 = q + nw;
+        const bool two = q1 < kb;
+        const float2 p = f.dot_right(i, two ? k0 + q1 : i, two, d, y, lane);
+        const float acc = warp_sum_f(p.x), acc1 = warp_sum_f(p.y);
+        if (lane == 0) {
+          ty[q] = y[i] - acc;
+          if (two) ty[q1] = y[k0 + q1] - acc1;
+        }
       }
     }
     if (TRN) {
@@ -941,8 +1018,9 @@ __device__ void lu_solve(const Fac& f, bool fw, bool tr, float* y, float* z, flo
 // Accumulator for sum_k (h_k + l_k)(xh_k + xl_k) with error ~2^-70 sum|p|:
 // s1 collects the exact leading products h*xh through two_sum (their rounding
 // errors go to s2), s2 (double-float) collects the ~2^-24 terms (the two_prod
-// error of h*xh, h*xl, l*xh) and s3 (float) the ~2^-48 terms (the errors of
-// h*xl and l*xh, and l*xl).  Every product is exact via two_prod.
+// error of h*xh, h*xl, l*xh), summed error-free into one float per entry
+// first, and s3 (float) the ~2^-48 terms (the errors of h*xl, l*xh and of
+// that sum, and l*xl).  Every product is exact via two_prod.
 // Corrections with the Gauss-Jordan inverse X = (P Mt)^{-1}: y <- X y (rows
 // over the warps, 4 rows per pass, lanes along the row) and y <- X^T y (the
 // rows split into 8 ranges, one per warp, a column per lane, partial sums in
@@ -1006,11 +1084,15 @@ __device__ __forceinline__ void resacc_add(ResAcc& a, float h, float l, float xh
   const df2 p3 = two_prod(l, xh);
   const df2 t = two_sum(a.s1, p1.hi);
   a.s1 = t.hi;
-  a.s2 = df_add_f(a.s2, t.lo);
-  a.s2 = df_add_f(a.s2, p1.lo);
-  a.s2 = df_add_f(a.s2, p2.hi);
-  a.s2 = df_add_f(a.s2, p3.hi);
-  a.s3 = __fadd_rn(a.s3, __fadd_rn(__fadd_rn(p2.lo, p3.lo), __fmul_rn(l, xl)));
+  // the four ~2^-24 terms summed error-free (u, v, w) before the one
+  // double-float addition; the three sums' errors are ~2^-48 terms
+  const df2 u = two_sum(t.lo, p1.lo);
+  const df2 v = two_sum(p2.hi, p3.hi);
+  const df2 w = two_sum(u.hi, v.hi);
+  a.s2 = df_add_f(a.s2, w.hi);
+  const float e1 = __fadd_rn(__fadd_rn(u.lo, v.lo), w.lo);
+  const float e2 = __fadd_rn(__fadd_rn(p2.lo, p3.lo), __fmul_rn(l, xl));
+  a.s3 = __fadd_rn(a.s3, __fadd_rn(e1, e2));
 }
 __device__ __forceinline__ void resacc_merge(ResAcc& a, const ResAcc& b) {
   const df2 t = two_sum(a.s1, b.s1);
