@@ -558,14 +558,29 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     float* XD = reinterpret_cast<float*>(gbase + kTsBlo);     // 4 x 32 x 32, X_ii column-major
     const float* Td = F + g.tile(K, K);
     const bool unit = (kind == 0);
-    for (int e = tid; e < kTlTile; e += kThreadsTc) {
-      const int r = e >> 7, c = e & 127;
-      const float v = Td[((c >> 5) << 12) + r * 32 + (c & 31)];  // tile element (r, c)
-      // kind 0: W = L (W[r][c] = tile(r, c)); kind 1: W = U^T (W[c][r] = tile(r, c))
-      if (kind == 0)
-        WT[c * kTsLdW + r] = v;
-      else
-        WT[r * kTsLdW + c] = v;
+    // the tile's 16384 values, 26 loads of a thread in flight at a time
+    constexpr int kPerT = (kTlTile + kThreadsTc - 1) / kThreadsTc;  // 52
+    constexpr int kBatch = kPerT / 2;
+    static_assert(2 * kBatch == kPerT, "two batches");
+#pragma unroll 1
+    for (int e0 = 0; e0 < kPerT; e0 += kBatch) {
+      float v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = tid + (e0 + u) * kThreadsTc, r = e >> 7, c = e & 127;
+        v[u] = (e < kTlTile) ? __ldg(Td + ((c >> 5) << 12) + r * 32 + (c & 31)) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int e = tid + (e0 + u) * kThreadsTc, r = e >> 7, c = e & 127;
+        // kind 0: W = L (W[r][c] = tile(r, c)); kind 1: W = U^T (W[c][r] = tile(r, c))
+        if (e < kTlTile) {
+          if (kind == 0)
+            WT[c * kTsLdW + r] = v[u];
+          else
+            WT[r * kTsLdW + c] = v[u];
+        }
+      }
     }
     __syncthreads();
     if (warp < 4) {
@@ -651,7 +666,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     for (int e = tid; e < kTlTile; e += kThreadsTc) Xc[e] = X[e];
     __syncthreads();
     for (int e = tid; e < kTlTile; e += kThreadsTc) {
-      const int k = e >> 7, t = e & 127;
+      const int t = e >> 7, k = e & 127;  // along rows of X: conflict-free reads and writes
       const float v = Xc[t * 128 + k];
       const float h = tf32_hi(v);
       const uint32_t o = (uint32_t)(k >> 5) * kOpBytes + sw_off(t, k & 31);
