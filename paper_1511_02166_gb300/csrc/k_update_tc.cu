@@ -490,19 +490,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
 //      operands read as broadcast vector loads); it is split into TF32 hi / lo
 //      and kept in shared memory as the B operand of all the block's tiles
 //      (128 KB);
-//   2. the tiles stream through two stages: warp 8 loads a K-chunk by TMA (a
-//      128 x 32 chunk of A21, or four 32 x 32 boxes of A12 that the converters
-//      transpose to A12^T), warps 4-7 split it into hi / lo, warp 9 issues the
-//      3xTF32 MMAs into one of two TMEM accumulators, warps 0-3 store the result
-//      over the tile (the tile's loads have all completed by then).
+//   2. the tiles stream through three stages of 32 KB: warp 8 loads a K-chunk
+//      by TMA (a 128 x 32 chunk of A21, or four 32 x 32 boxes of A12, each of
+//      which a converter warp transposes to rows of A12^T in place: a box and
+//      its swizzled image are the same 4 KB), warps 4-7 split it into hi (in
+//      place) and lo, warp 9 issues the 3xTF32 MMAs into one of two TMEM
+//      accumulators, warps 0-3 store the result over the tile (the tile's loads
+//      have all completed by then).
 // Waits are bounded as in k_update_tc.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint32_t kTsBhi = 0;                        // B hi: 4 chunks [t][32 k], 128-byte swizzle
 constexpr uint32_t kTsBlo = 4 * kOpBytes;             // B lo
-constexpr uint32_t kTsA = 8 * kOpBytes;               // A stages: raw, hi, lo (16 KB each)
-constexpr uint32_t kTsStage = 3 * kOpBytes;
-constexpr int kTsStages = 2;
+constexpr uint32_t kTsA = 8 * kOpBytes;               // A stages: raw -> hi in place, lo
+constexpr uint32_t kTsStage = 2 * kOpBytes;
+constexpr int kTsStages = 3;
 constexpr uint32_t kTsBar = kTsA + kTsStages * kTsStage;
 constexpr uint32_t kTsSmem = kTsBar + 1024 + 1024;    // barriers, then alignment slack
 constexpr int kTsLdW = 132;                           // column stride of the staged triangle
@@ -534,11 +536,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   const uint32_t bar_base = sbase + kTsBar;
   // full[2] conv[2] empty[2] tfull[2] tempty[2] done
   auto full_bar = [&](int st) { return bar_base + 8u * st; };
-  auto conv_bar = [&](int st) { return bar_base + 8u * (2 + st); };
-  auto empty_bar = [&](int st) { return bar_base + 8u * (4 + st); };
-  auto tfull_bar = [&](int ac) { return bar_base + 8u * (6 + ac); };
-  auto tempty_bar = [&](int ac) { return bar_base + 8u * (8 + ac); };
-  const uint32_t done_bar = bar_base + 8u * 10;
+  auto conv_bar = [&](int st) { return bar_base + 8u * (kTsStages + st); };
+  auto empty_bar = [&](int st) { return bar_base + 8u * (2 * kTsStages + st); };
+  auto tfull_bar = [&](int ac) { return bar_base + 8u * (3 * kTsStages + ac); };
+  auto tempty_bar = [&](int ac) { return bar_base + 8u * (3 * kTsStages + 2 + ac); };
+  const uint32_t done_bar = bar_base + 8u * (3 * kTsStages + 4);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + kTsBar + 128);
   volatile int* fail = reinterpret_cast<volatile int*>(gbase + kTsBar + 132);
   float* F = a.LU + bt.mat_off[b];
@@ -742,32 +744,39 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       const int st = q % kTsStages, u = q / kTsStages;
       const bool ok = mbar_wait(full_bar(st), u & 1, fail, spin);
       if (!__all_sync(0xffffffffu, ok)) break;
-      unsigned char* S = gbase + kTsA + st * kTsStage;  // raw, hi, lo
+      unsigned char* S = gbase + kTsA + st * kTsStage;  // raw -> hi, lo
       if (kind == 1) {
         // raw is already in the MMA's swizzled layout: split element by element
-        const float4* R4 = reinterpret_cast<const float4*>(S);
-        float4* H4 = reinterpret_cast<float4*>(S + kOpBytes);
-        float4* L4 = reinterpret_cast<float4*>(S + 2 * kOpBytes);
+        float4* H4 = reinterpret_cast<float4*>(S);
+        float4* L4 = reinterpret_cast<float4*>(S + kOpBytes);
 #pragma unroll 4
         for (int j = 0; j < (int)(kOpBytes / 16) / 128; ++j) {
           const int i = ct + 128 * j;
-          const float4 v = R4[i];
+          const float4 v = H4[i];
           const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
           H4[i] = h;
           L4[i] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
         }
       } else {
-        // raw [c / 32][k][c % 32] -> A^T element (row c, column k), swizzled
-        const float* R = reinterpret_cast<const float*>(S);
-#pragma unroll 4
-        for (int j = 0; j < kTM * kKC / 128; ++j) {
-          const int e = ct + 128 * j;
-          const int k = e >> 7, c = e & 127;
-          const float v = R[(c >> 5) * (kTM * kKC / 4) + k * 32 + (c & 31)];
-          const float h = tf32_hi(v);
-          const uint32_t o = sw_off(c, k);
-          *reinterpret_cast<float*>(S + kOpBytes + o) = h;
-          *reinterpret_cast<float*>(S + 2 * kOpBytes + o) = v - h;
+        // raw [c / 32][k][c % 32]: box w = ct / 32 holds columns c = 32 w .. of
+        // A12, i.e. rows c of A^T, whose swizzled image (rows 32 w .. 32 w + 31,
+        // 128 bytes each) is the same 4 KB: the warp reads its box into
+        // registers (lane = c % 32, conflict-free) and writes it back transposed
+        const int w = ct >> 5, c = 32 * w + lane;
+        const float* R = reinterpret_cast<const float*>(S) + w * (kTM * kKC / 4);
+        float col[kKC];
+#pragma unroll
+        for (int k = 0; k < kKC; ++k) col[k] = R[k * 32 + lane];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kKC / 4; ++j) {
+          const uint32_t o = (uint32_t)(c * 128 + (((j ^ (c & 7)) & 7) << 4));
+          const float4 h = make_float4(tf32_hi(col[4 * j]), tf32_hi(col[4 * j + 1]),
+                                       tf32_hi(col[4 * j + 2]), tf32_hi(col[4 * j + 3]));
+          *reinterpret_cast<float4*>(S + o) = h;
+          *reinterpret_cast<float4*>(S + kOpBytes + o) =
+              make_float4(col[4 * j] - h.x, col[4 * j + 1] - h.y, col[4 * j + 2] - h.z,
+                          col[4 * j + 3] - h.w);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -783,7 +792,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         if (!mbar_wait(conv_bar(st), u & 1, fail, spin)) break;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ac * kTN);
-        const uint32_t ah = sbase + kTsA + st * kTsStage + kOpBytes, al = ah + kOpBytes;
+        const uint32_t ah = sbase + kTsA + st * kTsStage, al = ah + kOpBytes;
         const uint32_t bh = sbase + kTsBhi + kk * kOpBytes, bl = sbase + kTsBlo + kk * kOpBytes;
 #pragma unroll
         for (int s = 0; s < kKC / 8; ++s) {
