@@ -105,19 +105,19 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
       }
       continue;
     }
+    // a warp reads two whole rows of a tile (2 x 512 contiguous bytes of A_hi)
+    // and writes them as 128-byte rows of the tile's four chunks
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(kU == 8 && kInitThreads == 256, "8 warps x 2 rows x 4 chunks");
     for (int J = 1; J < g.T; ++J) {
       float* Tt = F + g.tile(I, J);
       const int c0 = g.start(J);
-      for (int p0 = 0; p0 < kTlTile; p0 += kU * kInitThreads) {
+      for (int rb = 2 * warp; rb < kTlB; rb += 16) {
         float v[kU];
 #pragma unroll
-        for (int i = 0; i < kU; ++i) {
-          const int p = p0 + i * kInitThreads + threadIdx.x;
-          const int kc = p >> 12, r = (p & 4095) >> 5, c = (kc << 5) + (p & 31);
-          v[i] = scaled(r0 + r, c0 + c);
-        }
+        for (int i = 0; i < kU; ++i) v[i] = scaled(r0 + rb + (i >> 2), c0 + 32 * (i & 3) + lane);
 #pragma unroll
-        for (int i = 0; i < kU; ++i) Tt[p0 + i * kInitThreads + threadIdx.x] = v[i];
+        for (int i = 0; i < kU; ++i) Tt[(i & 3) * kTlChunk + (rb + (i >> 2)) * kTlC + lane] = v[i];
       }
     }
     // the ragged tile (I, 0), kU loads in flight per thread

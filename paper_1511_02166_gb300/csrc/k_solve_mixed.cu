@@ -839,7 +839,7 @@ struct CrFactor {
     if (d < G0) {
       for (int r = c0 + tid; r < m; r += nth) {
         float acc = z[r];
-#pragma unroll 8
+#pragma unroll 16
         for (int t = 0; t < kb; ++t)
           acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
         if (r < c1)
@@ -853,7 +853,7 @@ struct CrFactor {
       for (int c = 32 * (h + 1) + tid; c < 32 * nch; c += nth) {
         const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
         float acc = z[e + c];
-#pragma unroll 8
+#pragma unroll 16
         for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), z[k0 + t], acc);
         if (e + c < c1)
           nx[e + c - c0] = acc;
@@ -868,7 +868,7 @@ struct CrFactor {
     if (d < G0) {
       for (int r = tid; r < k0; r += nth) {
         float acc = z[r];
-#pragma unroll 8
+#pragma unroll 16
         for (int t = 0; t < kb; ++t)
           acc = fmaf(-__ldg(F + (int64_t)(k0 + t) * m + r), z[k0 + t], acc);
         if (r >= p0)
@@ -882,7 +882,7 @@ struct CrFactor {
       const CrRag rag(F, g, I);
       for (int r = tid; r < e; r += nth) {
         float acc = z[r];
-#pragma unroll 8
+#pragma unroll 16
         for (int t = 0; t < 32; ++t) acc = fmaf(-rag(rr0 + t, r), z[k0 + t], acc);
         if (r >= p0)
           nx[r - p0] = acc;
@@ -894,7 +894,7 @@ struct CrFactor {
       for (int c = tid; c < 32 * h; c += nth) {
         const float* pc = p + (int64_t)(c >> 5) * kTlChunk + (c & 31);
         float acc = z[e + c];
-#pragma unroll 8
+#pragma unroll 16
         for (int t = 0; t < 32; ++t) acc = fmaf(-__ldg(pc + t * kTlC), z[k0 + t], acc);
         if (e + c >= p0)
           nx[e + c - p0] = acc;
