@@ -424,13 +424,16 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
   __syncthreads();
   if (tid < kBW) dinv[tid] = 1.0f / D[tid * kLdI + tid];
   __syncthreads();
-  if (tid < kBW) {
+  // Only the first kb rows and columns of the inverses are used (the products
+  // below run over k < kb; X is zero beyond); their entries at t >= kb are zero.
+  if (tid < kb) {
     // column j of L11^{-1}: x_j = 1, x_t = -sum_{j <= q < t} L[t][q] x_q
     const int j = tid;
     float* x = Li + j * kLdI;
     for (int t = 0; t < j; ++t) x[t] = 0.0f;
+    for (int t = kb; t < kBW; ++t) x[t] = 0.0f;
     x[j] = 1.0f;
-    for (int t = j + 1; t < kBW; ++t) {
+    for (int t = j + 1; t < kb; ++t) {
       const float* Lt = D + t * kLdI;
       float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
       int q = j;
@@ -443,13 +446,14 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
       for (; q < t; ++q) s0 = fmaf(Lt[q], x[q], s0);
       x[t] = -((s0 + s1) + (s2 + s3));
     }
-  } else {
+  } else if (tid >= kBW && tid - kBW < kb) {
     // row i of U11^{-1}: y_i = 1 / U_ii, y_t = -(sum_{i <= q < t} y_q U[q][t]) / U_tt
     const int i = tid - kBW;
     float* y = Ui + i * kLdI;
     for (int t = 0; t < i; ++t) y[t] = 0.0f;
+    for (int t = kb; t < kBW; ++t) y[t] = 0.0f;
     y[i] = dinv[i];
-    for (int t = i + 1; t < kBW; ++t) {
+    for (int t = i + 1; t < kb; ++t) {
       float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
       int q = i;
       for (; q + 3 < t; q += 4) {
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
     if (cols) {
       // U12[t][c] = sum_k (L11^{-1})[t][k] X[k][c]
 #pragma unroll 2
-      for (int k = 0; k < kBW; ++k) {
+      for (int k = 0; k < kb; ++k) {
         const float* lk = Li + k * kLdI;
         float av[8];
 #pragma unroll
@@ -567,7 +571,7 @@ __global__ void __launch_bounds__(256) k_large_trsm(SolveArgs a, int K) {
     } else {
       // L21[r][t] = sum_k X[k][r] (U11^{-1})[k][t]
 #pragma unroll 2
-      for (int k = 0; k < kBW; ++k) {
+      for (int k = 0; k < kb; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(X + k * kLdX + 4 * ty);
         const float4 a1 = *reinterpret_cast<const float4*>(X + k * kLdX + 64 + 4 * ty);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
