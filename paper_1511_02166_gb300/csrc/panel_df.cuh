@@ -143,23 +143,40 @@ __device__ __forceinline__ PairGeom pair_geom(const point3& p, const float* __re
 // do not depend on the panel's orientation or length (they are the same for
 // the pair seen from either end: P -> -P leaves them unchanged exactly):
 // X + iY = P^2 (X = px^2 - py^2, Y = 2 px py), inv = 1/|P|^2, inv2 = inv^2,
-// lgh = log|P|.  Terms n = 1, 2 in double-float, n >= 3 in float32.
+// lgh = log|P|.  Term n = 1 in double-float, n = 2 in double-float within
+// 32 panel lengths (q > 1/4096), n >= 3 in float32.
 __device__ __forceinline__ df2 panel_G_far(const df2 X, const df2 Y, const df2 inv,
                                            const df2 inv2, const df2 lgh,
                                            const float* __restrict__ s, int ld, int i, float Lh) {
   const df2 Z = df_add(df_mul(pf(s, ld, kC2, i), X), df_mul(pf(s, ld, kS2, i), Y));
   const df2 cc = df_mul(Z, inv);  // cos 2phi
   const df2 t1 = df_mul(df_mul(pf(s, ld, kQ6, i), inv), cc);       // q c / 6
+  const float q = __fmul_rn(__fmul_rn(0.25f * Lh, Lh), inv.hi);
+  const float c = cc.hi;
+  const float c2 = __fmul_rn(2.0f, c);
+  const float T3 = __fmul_rn(c, __fsub_rn(__fmul_rn(__fmul_rn(4.0f, c), c), 3.0f));
+  if (q <= 1.0f / 4096.0f) {
+    // |P| >= 32 L: the n = 2 term (at most 3e-9 of the leading one) joins
+    // the float32 tail, q^2 (T2/20 + q (T3/42 + q (T4/72 + ...)))
+    const float T2 = __fsub_rn(__fmul_rn(c2, c), 1.0f);
+    const float T4 = __fsub_rn(__fmul_rn(c2, T3), T2);
+    const float T5 = __fsub_rn(__fmul_rn(c2, T4), T3);
+    const float T6 = __fsub_rn(__fmul_rn(c2, T5), T4);
+    const float T7 = __fsub_rn(__fmul_rn(c2, T6), T5);
+    float tail = __fadd_rn(__fmul_rn(T6, 1.0f / 156.0f), __fmul_rn(__fmul_rn(q, T7), 1.0f / 210.0f));
+    tail = __fadd_rn(__fmul_rn(T5, 1.0f / 110.0f), __fmul_rn(q, tail));
+    tail = __fadd_rn(__fmul_rn(T4, 1.0f / 72.0f), __fmul_rn(q, tail));
+    tail = __fadd_rn(__fmul_rn(T3, 1.0f / 42.0f), __fmul_rn(q, tail));
+    tail = __fadd_rn(__fmul_rn(T2, 1.0f / 20.0f), __fmul_rn(q, tail));
+    tail = __fmul_rn(tail, __fmul_rn(q, q));
+    return df_mul(pf(s, ld, kLg, i), df_sub(lgh, df_add_f(t1, tail)));
+  }
   df2 T2 = df_sqr(cc);
   T2.hi *= 2.0f;
   T2.lo *= 2.0f;
   T2 = df_add_f(T2, -1.0f);                                        // 2c^2 - 1
   const df2 t2 = df_mul(df_mul(pf(s, ld, kQ20, i), inv2), T2);     // q^2 T2 / 20
   // n >= 3 in float32: q^3 (T3/42 + q (T4/72 + q (T5/110 + q (T6/156 + q T7/210))))
-  const float q = __fmul_rn(__fmul_rn(0.25f * Lh, Lh), inv.hi);
-  const float c = cc.hi;
-  const float c2 = __fmul_rn(2.0f, c);
-  const float T3 = __fmul_rn(c, __fsub_rn(__fmul_rn(__fmul_rn(4.0f, c), c), 3.0f));
   const float T4 = __fsub_rn(__fmul_rn(c2, T3), T2.hi);
   const float T5 = __fsub_rn(__fmul_rn(c2, T4), T3);
   const float T6 = __fsub_rn(__fmul_rn(c2, T5), T4);
