@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // blocks: the four diagonal blocks X_ii = W_ii^{-1} (warps 0-3, lane j the
   // column j of X_ii in registers, right-looking substitution), then the blocks
   // at distance d = 1, 2, 3 below the diagonal, X_ij = -X_ii sum_{j<=k<i} W_ik
-  // X_kj (one warp per block, lane c the column c of the block in registers).
+  // X_kj (all threads, 8 rows of one column of a block each).
   {
     float* WT = reinterpret_cast<float*>(gbase + kTsA);       // 128 x kTsLdW, column-major
     float* X = reinterpret_cast<float*>(gbase);               // 128 x 128, row-major
@@ -620,44 +620,57 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       if ((c >> 5) > (r >> 5)) X[e] = 0.0f;
     }
     __syncthreads();
+    // The blocks at distance d = 1, 2, 3 below the diagonal, all threads: a
+    // task is 8 rows x 1 column of a block (lane = column, so that the W and
+    // X_ii values of the task's rows are broadcast vector loads).  First
+    // T_ij = sum_{j<=k<i} W_ik X_kj into TB, then X_ij = -X_ii T_ij into X.
+    float* TB = XD + 4 * 1024;  // 3 x 32 x 32, row-major per block
     for (int d = 1; d < 4; ++d) {
-      if (warp < 4 - d) {
-        const int j = warp, i = warp + d;
-        // T = sum_{j<=k<i} W_ik X_kj (rows of the block in registers, column c)
-        float acc[32];
+      const int ntask = (4 - d) * 128;
+      for (int task = tid; task < ntask; task += kThreadsTc) {
+        const int j = task >> 7, r0 = 8 * ((task >> 5) & 3), c = task & 31, i = j + d;
+        float acc[8];
 #pragma unroll
-        for (int t = 0; t < 32; ++t) acc[t] = 0.0f;
+        for (int t = 0; t < 8; ++t) acc[t] = 0.0f;
         for (int kk = 32 * j; kk < 32 * i; ++kk) {
-          const float xv = X[kk * 128 + 32 * j + lane];
-          const float* wc = WT + kk * kTsLdW + 32 * i;  // W[32 i + t][kk], t = 0..31
-#pragma unroll
-          for (int t4 = 0; t4 < 32; t4 += 4) {
-            const float4 w = *reinterpret_cast<const float4*>(wc + t4);
-            acc[t4] = fmaf(w.x, xv, acc[t4]);
-            acc[t4 + 1] = fmaf(w.y, xv, acc[t4 + 1]);
-            acc[t4 + 2] = fmaf(w.z, xv, acc[t4 + 2]);
-            acc[t4 + 3] = fmaf(w.w, xv, acc[t4 + 3]);
-          }
+          const float xv = X[kk * 128 + 32 * j + c];
+          const float4 w0 = *reinterpret_cast<const float4*>(WT + kk * kTsLdW + 32 * i + r0);
+          const float4 w1 = *reinterpret_cast<const float4*>(WT + kk * kTsLdW + 32 * i + r0 + 4);
+          acc[0] = fmaf(w0.x, xv, acc[0]);
+          acc[1] = fmaf(w0.y, xv, acc[1]);
+          acc[2] = fmaf(w0.z, xv, acc[2]);
+          acc[3] = fmaf(w0.w, xv, acc[3]);
+          acc[4] = fmaf(w1.x, xv, acc[4]);
+          acc[5] = fmaf(w1.y, xv, acc[5]);
+          acc[6] = fmaf(w1.z, xv, acc[6]);
+          acc[7] = fmaf(w1.w, xv, acc[7]);
         }
-        // X_ij = -X_ii T: column c of the result from the lane's T column
-        float out[32];
 #pragma unroll
-        for (int t = 0; t < 32; ++t) out[t] = 0.0f;
-        const float* xd = XD + i * 1024;
+        for (int t = 0; t < 8; ++t) TB[j * 1024 + (r0 + t) * 32 + c] = acc[t];
+      }
+      __syncthreads();
+      for (int task = tid; task < ntask; task += kThreadsTc) {
+        const int j = task >> 7, r0 = 8 * ((task >> 5) & 3), c = task & 31, i = j + d;
+        const float* xd = XD + i * 1024;  // X_ii column-major: X_ii[t][kk] = xd[32 kk + t]
+        float acc[8];
 #pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = 0.0f;
+#pragma unroll 4
         for (int kk = 0; kk < 32; ++kk) {
-          const float tv = acc[kk];
-#pragma unroll
-          for (int t4 = 0; t4 < 32; t4 += 4) {
-            const float4 w = *reinterpret_cast<const float4*>(xd + kk * 32 + t4);  // X_ii[t][kk]
-            out[t4] = fmaf(-w.x, tv, out[t4]);
-            out[t4 + 1] = fmaf(-w.y, tv, out[t4 + 1]);
-            out[t4 + 2] = fmaf(-w.z, tv, out[t4 + 2]);
-            out[t4 + 3] = fmaf(-w.w, tv, out[t4 + 3]);
-          }
+          const float tv = TB[j * 1024 + kk * 32 + c];
+          const float4 x0 = *reinterpret_cast<const float4*>(xd + kk * 32 + r0);
+          const float4 x1 = *reinterpret_cast<const float4*>(xd + kk * 32 + r0 + 4);
+          acc[0] = fmaf(-x0.x, tv, acc[0]);
+          acc[1] = fmaf(-x0.y, tv, acc[1]);
+          acc[2] = fmaf(-x0.z, tv, acc[2]);
+          acc[3] = fmaf(-x0.w, tv, acc[3]);
+          acc[4] = fmaf(-x1.x, tv, acc[4]);
+          acc[5] = fmaf(-x1.y, tv, acc[5]);
+          acc[6] = fmaf(-x1.z, tv, acc[6]);
+          acc[7] = fmaf(-x1.w, tv, acc[7]);
         }
 #pragma unroll
-        for (int t = 0; t < 32; ++t) X[(32 * i + t) * 128 + 32 * j + lane] = out[t];
+        for (int t = 0; t < 8; ++t) X[(32 * i + r0 + t) * 128 + 32 * j + c] = acc[t];
       }
       __syncthreads();
     }
