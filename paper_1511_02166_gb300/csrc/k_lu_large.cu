@@ -21,7 +21,9 @@
 //                     (k_update_tc.cu);
 //   k_tl_untranspose  the U tiles back from their transposed order to row
 //                     chunks, one block per tile, in place;
-//   k_large_finish    the 32 x 32 diagonal blocks of L and U inverted in place.
+//   k_large_finish    the 32 x 32 diagonal blocks of L and U of the first block
+//                     row inverted in place (k_large_diag inverts those of the
+//                     full diagonal tiles).
 // The per-airfoil kernels take gridDim.y blocks per airfoil striding over
 // slabs / tiles / rows, so a batch of few airfoils still fills the GPU.
 //
@@ -136,6 +138,11 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
     }
   }
 }
+
+// A 32 x 32 diagonal block's triangles inverted (invert_block) in a call of
+// its own, so that its 32-register columns do not weigh on the register
+// allocation of the LU around it.
+__device__ __noinline__ void invert_block32(float* B, int ld) { invert_block(B, ld, 32); }
 
 // LU of the diagonal block K with partial pivoting inside the block.
 __global__ void __launch_bounds__(256, 3) k_large_diag(SolveArgs a, int K) {
@@ -330,6 +337,15 @@ __global__ void __launch_bounds__(256, 3) k_large_diag(SolveArgs a, int K) {
         for (int jj = 0; jj < 4; ++jj)
           if (r0 + i < kb && cc0 + jj < kb) D[(r0 + i) * kLdD + cc0 + jj] -= acc[i][jj];
     }
+    __syncthreads();
+  }
+  if (K >= 1) {
+    // A full diagonal tile leaves with its four 32 x 32 diagonal blocks of L and
+    // U inverted in place, the form the refinement takes; k_trsm_tc reads them
+    // as the diagonal blocks of its triangular inverse.  (Block row 0's, which
+    // the step-0 solve still needs as they are, are inverted by k_large_finish.)
+    const int warp = tid >> 5;
+    if (warp < 4) invert_block32(D + 32 * warp * kLdD + 32 * warp, kLdD);
     __syncthreads();
   }
   for (int e = tid; e < kBW * kBW; e += 256) {
@@ -664,13 +680,12 @@ __global__ void __launch_bounds__(kUtThreads, 3) k_tl_untranspose(SolveArgs a) {
   }
 }
 
-// The 32 x 32 diagonal blocks of L and U inverted in place, the form the
-// refinement's triangular sweeps take.  The blocks follow the tiles:
-// ceil(e / 32) blocks in the first block row (row-major, row stride m; the
-// last one e - 32 floor((e - 1) / 32) wide), then four per full diagonal tile,
-// each the diagonal 32 x 32 block of one of its row chunks (contiguous, row
-// stride 32).  Each warp stages a block in shared memory, inverts both
-// triangles there and writes the block back.
+// The 32 x 32 diagonal blocks of L and U of the first block row inverted in
+// place, the form the refinement's triangular sweeps take: ceil(e / 32) blocks
+// (row-major, row stride m; the last one e - 32 floor((e - 1) / 32) wide).
+// The full diagonal tiles' four blocks each are inverted by k_large_diag.
+// Each warp stages a block in shared memory, inverts both triangles there and
+// writes the block back.
 __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   __shared__ float S[8][32 * 33];
   const Batch& bt = a.bt;
@@ -681,21 +696,11 @@ __global__ void __launch_bounds__(256) k_large_finish(SolveArgs a) {
   TlGeom g;
   g.init(m, bt.mat_off[b]);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int G0 = (g.e + 31) >> 5, G = G0 + 4 * (g.T - 1);
+  const int G0 = (g.e + 31) >> 5;
   float* W = S[warp];
-  for (int d = blockIdx.y * 8 + warp; d < G; d += 8 * (int)gridDim.y) {
-    float* B;
-    int ld, kb;
-    if (d < G0) {
-      B = F + (int64_t)(32 * d) * m + 32 * d;
-      ld = m;
-      kb = min(32, g.e - 32 * d);
-    } else {
-      const int h = d - G0;  // chunk 4 (I - 1) + q of block row I = 1 + h / 4
-      B = F + g.tile(1 + (h >> 2), 1) + (int64_t)h * kTlChunk + (h & 3) * 32 * kTlC;
-      ld = kTlC;
-      kb = 32;
-    }
+  for (int d = blockIdx.y * 8 + warp; d < G0; d += 8 * (int)gridDim.y) {
+    float* B = F + (int64_t)(32 * d) * m + 32 * d;
+    const int ld = m, kb = min(32, g.e - 32 * d);
     float v[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = (r < kb && lane < kb) ? B[(int64_t)r * ld + lane] : 0.0f;
@@ -764,7 +769,7 @@ cudaError_t launch_lu_large(const SolveArgs& a, cudaStream_t s) {
   }
   const int tiles = (T_max - 1) * (T_max - 2) / 2;  // U tiles of the largest airfoil
   if (tiles > 0) k_tl_untranspose<<<dim3(B, tiles), kUtThreads, kUtSmem, s>>>(a);
-  k_large_finish<<<dim3(B, split_for(B, 8, 8)), 256, 0, s>>>(a);
+  k_large_finish<<<dim3(B, 1), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

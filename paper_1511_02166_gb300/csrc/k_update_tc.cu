@@ -550,10 +550,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   // (unit diagonal) for U12, W = U11^T for L21 (then X = (U11^{-1})^T).  W is
   // staged column-major (WT[c][r] = W[r][c], columns 16-byte aligned, so a
   // piece of a column is a broadcast vector load) and inverted by 32 x 32
-  // blocks: the four diagonal blocks X_ii = W_ii^{-1} (warps 0-3, lane j the
-  // column j of X_ii in registers, right-looking substitution), then the blocks
-  // at distance d = 1, 2, 3 below the diagonal, X_ij = -X_ii sum_{j<=k<i} W_ik
-  // X_kj (all threads, 8 rows of one column of a block each).
+  // blocks: the four diagonal blocks X_ii = W_ii^{-1} are stored inverted in
+  // the tile already, then the blocks at distance d = 1, 2, 3 below the
+  // diagonal, X_ij = -X_ii sum_{j<=k<i} W_ik X_kj (all threads, 8 rows of one
+  // column of a block each; W_ik, i > k, are the tile's untouched entries).
   {
     float* WT = reinterpret_cast<float*>(gbase + kTsA);       // 128 x kTsLdW, column-major
     float* X = reinterpret_cast<float*>(gbase);               // 128 x 128, row-major
@@ -586,30 +586,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     }
     __syncthreads();
     if (warp < 4) {
-      // X_ii, i = warp: W_ii x = e_j for the lane's column j
+      // X_ii, i = warp, column `lane`: the diagonal tile's 32 x 32 diagonal
+      // blocks hold L_ii^{-1} below the diagonal (unit diagonal implied) and
+      // U_ii^{-1} on and above it (k_large_diag), so X_ii[t][l] = W_ii^{-1}[t][l]
+      // is the staged WT value at (t, l) for t > l -- L_ii^{-1}[t][l], or for
+      // W = U^T, U_ii^{-1}[l][t] -- and on the diagonal 1 (L) or U_ii^{-1}[l][l].
       const int i0 = 32 * warp;
-      float acc[32];
-#pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] = (t == lane) ? 1.0f : 0.0f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float* wk = WT + (i0 + k) * kTsLdW + i0;  // column k of W_ii
-        const float xk = unit ? acc[k] : acc[k] / wk[k];
-        acc[k] = xk;
-#pragma unroll
-        for (int t4 = 0; t4 < 32; t4 += 4) {
-          if (t4 + 3 > k) {
-            const float4 w = *reinterpret_cast<const float4*>(wk + t4);
-            if (t4 > k) acc[t4] = fmaf(-w.x, xk, acc[t4]);
-            if (t4 + 1 > k) acc[t4 + 1] = fmaf(-w.y, xk, acc[t4 + 1]);
-            if (t4 + 2 > k) acc[t4 + 2] = fmaf(-w.z, xk, acc[t4 + 2]);
-            acc[t4 + 3] = fmaf(-w.w, xk, acc[t4 + 3]);
-          }
-        }
-      }
-#pragma unroll
+#pragma unroll 4
       for (int t = 0; t < 32; ++t) {
-        const float v = (t >= lane) ? acc[t] : 0.0f;
+        float v = 0.0f;
+        if (t > lane || (t == lane && !unit)) v = WT[(i0 + lane) * kTsLdW + i0 + t];
+        if (t == lane && unit) v = 1.0f;
         X[(i0 + t) * 128 + i0 + lane] = v;
         XD[warp * 1024 + lane * 32 + t] = v;  // column lane of X_ii
       }
