@@ -139,10 +139,16 @@ __global__ void __launch_bounds__(kInitThreads) k_large_init(SolveArgs a) {
   }
 }
 
-// A 32 x 32 diagonal block's triangles inverted (invert_block) in a call of
-// its own, so that its 32-register columns do not weigh on the register
-// allocation of the LU around it.
-__device__ __noinline__ void invert_block32(float* B, int ld) { invert_block(B, ld, 32); }
+// One triangle of a 32 x 32 diagonal block inverted (the unit lower one, or
+// the upper one; they touch disjoint entries, so two warps may work on one
+// block at once), in a call of its own, so that its 32-register columns do
+// not weigh on the register allocation of the LU around it.
+__device__ __noinline__ void invert_triangle32(float* B, int ld, bool lower) {
+  if (lower)
+    invert_lower_unit(B, ld, 32);
+  else
+    invert_upper(B, ld, 32);
+}
 
 // LU of the diagonal block K with partial pivoting inside the block.
 __global__ void __launch_bounds__(256, 3) k_large_diag(SolveArgs a, int K) {
@@ -344,8 +350,8 @@ __global__ void __launch_bounds__(256, 3) k_large_diag(SolveArgs a, int K) {
     // U inverted in place, the form the refinement takes; k_trsm_tc reads them
     // as the diagonal blocks of its triangular inverse.  (Block row 0's, which
     // the step-0 solve still needs as they are, are inverted by k_large_finish.)
-    const int warp = tid >> 5;
-    if (warp < 4) invert_block32(D + 32 * warp * kLdD + 32 * warp, kLdD);
+    const int warp = tid >> 5, q = warp & 3;  // warps 0-3: L, warps 4-7: U of block q
+    invert_triangle32(D + 32 * q * kLdD + 32 * q, kLdD, warp < 4);
     __syncthreads();
   }
   for (int e = tid; e < kBW * kBW; e += 256) {
